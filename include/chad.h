@@ -1,0 +1,183 @@
+/*
+ * chad.h -- C ABI of the GB300 per-particle ADM1 integrator.
+ *
+ * Each Lagrangian (SPH) particle is an "AD particle", a small CSTR of volume
+ * V/N that carries the 29 ADM1 states (Sec. 2.3).  Over every synchronised
+ * coupling interval the library advects the particles through a prescribed
+ * velocity field (Sec. 2.3: positions and velocities are supplied per CFD
+ * step), integrates ADM1 on every particle independently (Sec. 2.2, Eq. 2-6)
+ * with the acid-base charge balance of Eq. 7 solved for S_H+ by Newton, and
+ * couples the particles of one digester through a shared headspace where
+ * that is configured (Table 1 gas volume).
+ *
+ * Conventions
+ *   - Every call returns chad_status; nothing is thrown across the ABI and
+ *     the library never exits or traps.  chad_last_error() describes the
+ *     last failure of a context.
+ *   - Pointers passed in are owned by the caller and are not retained after
+ *     the call returns.  Inputs are copied into the context's device buffers.
+ *   - `mem` selects whether a caller pointer is host memory (CHAD_MEM_HOST)
+ *     or device memory of the context's GPU (CHAD_MEM_DEVICE).
+ *   - State arrays are structure-of-arrays: y is [29][n] (species-major,
+ *     particle index fastest), positions are [3][n] (x, y, z in metres).
+ *   - ADM1 units: kgCOD/m^3, except S_IC, S_IN, S_cat, S_an, S_gas_co2 in
+ *     kmol/m^3.  Rates are per day; the coupling interval is in seconds.
+ *   - Call order: chad_create -> chad_load_particles (every digester) ->
+ *     [chad_set_flow] -> chad_step* -> chad_read_states -> chad_destroy.
+ *     Out-of-order calls return CHAD_E_STATE.
+ *   - Calls on one context are not thread-safe; use one context per thread.
+ */
+#ifndef CHAD_H
+#define CHAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHAD_NS 29        /* differential states per particle (Sec. 2.2) */
+#define CHAD_NPARAM 113   /* length of one digester's parameter vector */
+#define CHAD_ABI_VERSION 1
+
+typedef struct chad_ctx chad_ctx; /* opaque, library-owned */
+
+typedef enum {
+  CHAD_OK = 0,
+  CHAD_E_INVALID = 1,  /* bad argument: null pointer, size, range, NaN */
+  CHAD_E_NOMEM = 2,    /* device or host allocation failed */
+  CHAD_E_CUDA = 3,     /* a CUDA call failed; see chad_last_error */
+  CHAD_E_STATE = 4,    /* call out of order (e.g. step before load) */
+  CHAD_E_PARTICLE = 5  /* >= 1 particle ended an interval with status != 0 */
+} chad_status;
+
+enum { CHAD_MEM_HOST = 0, CHAD_MEM_DEVICE = 1 };
+enum { CHAD_PREC_FP64 = 0, CHAD_PREC_MIXED = 1 };
+enum { CHAD_HEADSPACE_PARTICLE = 0, CHAD_HEADSPACE_SHARED = 1 };
+
+/* Per-particle status bits (OR-accumulated across intervals until read). */
+enum {
+  CHAD_P_NEWTON = 1,  /* Eq. 7: Newton and its bisection fallback found no root */
+  CHAD_P_STEPS = 2,   /* max_steps_per_interval reached before the interval end */
+  CHAD_P_HMIN = 4,    /* step size fell below 1e-12 d after rejections */
+  CHAD_P_NEG = 8,     /* a state ended the interval below -atol_i */
+  CHAD_P_NAN = 16     /* non-finite state or singular iteration matrix */
+};
+
+/* Library configuration (copied at chad_create). */
+typedef struct {
+  int n_digesters;             /* >= 1 */
+  const int64_t* n_particles;  /* [n_digesters] particle count per digester (>= 0) */
+  const double* V_liq;         /* [n_digesters] liquid volume, m^3 (> 0) */
+  const double* V_gas;         /* [n_digesters] headspace volume, m^3 (> 0) */
+  const double* params;        /* [n_digesters][CHAD_NPARAM]; names: chad_param_name */
+  const double* D_uniform;     /* [n_digesters] dilution rate 1/d for digesters without a
+                                  flow field (Eq. 2 with q_in = q_out); NULL = all 0 */
+  const double* y_in;          /* [n_digesters][29] influent; NULL = zeros */
+  int precision;               /* CHAD_PREC_FP64 or CHAD_PREC_MIXED */
+  int learned;                 /* 1: MLP initial guesses (chad_set_mlp must be called) */
+  int headspace;               /* CHAD_HEADSPACE_PARTICLE or CHAD_HEADSPACE_SHARED */
+  double rtol;                 /* relative tolerance of the step controller (> 0) */
+  const double* atol;          /* [29] absolute tolerances (> 0) */
+  int max_steps_per_interval;  /* step attempts per particle and interval (>= 1) */
+  int max_newton_iters;        /* Newton iterations per Eq. 7 solve (>= 1) */
+  int fixed_substeps;          /* 0: adaptive; k > 0: k equal steps per interval */
+  void* cuda_stream;           /* cudaStream_t to run on; NULL = legacy default stream */
+} chad_config;
+
+/* Prescribed flow of one digester (Sec. 2.3).  Rigid swirl u_theta = U r/R
+   about the z axis plus Gaussian velocity noise of std sigma (m/s) per
+   1-second sub-step, reflecting walls at r = R, z = 0, z = H.  Particles
+   with z >= slab_zmin at the start of an interval form the inlet slab and
+   receive the influent at dilution rate q_in / (pi R^2 (H - slab_zmin)). */
+typedef struct {
+  int has_flow;      /* 0: particles do not move (D_uniform applies) */
+  double U;          /* swirl speed at r = R, m/s */
+  double R, H;       /* cylinder radius and height, m (> 0) */
+  double sigma;      /* velocity noise std, m/s (>= 0) */
+  double slab_zmin;  /* inlet slab lower bound, m */
+  double q_in;       /* inflow, m^3/d (>= 0) */
+  const double* y_in;/* [29] influent of the slab; NULL keeps the config's y_in */
+  uint64_t seed;     /* noise stream key */
+} chad_flow;
+
+/* Counters accumulated since the last chad_read_states of the context. */
+typedef struct {
+  int64_t accepted_steps;    /* accepted W-method steps, all particles */
+  int64_t rejected_steps;
+  int64_t newton_iters;      /* Eq. 7 Newton iterations */
+  int64_t newton_fallbacks;  /* bisection fallbacks */
+  int64_t min_steps;         /* fewest accepted steps of one particle in one interval */
+  int64_t max_steps;         /* most accepted steps of one particle in one interval */
+  int64_t failed_particles;  /* particles with status != 0 */
+  int64_t mlp_redo;          /* learned guesses rejected and redone plainly */
+  int64_t intervals;         /* coupling intervals integrated */
+  double sim_days;           /* particle-days integrated */
+} chad_stats;
+
+/* ---- introspection ------------------------------------------------------ */
+int chad_abi_version(void);
+int chad_n_params(void);
+/* Name of parameter i (0 <= i < CHAD_NPARAM), or NULL.  Static storage. */
+const char* chad_param_name(int i);
+
+/* ---- lifecycle ---------------------------------------------------------- */
+
+/* Create a context on the current CUDA device.  Validates cfg, derives the
+   per-digester model constants (Sec. 2.2; temperature-independent part), and
+   allocates the particle buffers (about 280 bytes per particle in FP64 SoA).
+   On error *out is NULL and nothing is leaked. */
+chad_status chad_create(const chad_config* cfg, chad_ctx** out);
+
+/* Free every resource of ctx (NULL is a no-op).  Synchronises its stream. */
+void chad_destroy(chad_ctx* ctx);
+
+/* Description of the last error of ctx (or of the last failed chad_create
+   when ctx is NULL).  Valid until the next call on ctx. */
+const char* chad_last_error(const chad_ctx* ctx);
+
+/* ---- data in ------------------------------------------------------------ */
+
+/* Load the n particles of one digester (Sec. 2.3: one AD particle per SPH
+   particle).  n must equal cfg->n_particles[digester].
+     pos [3][n] m (NULL: all zero), y [29][n] (required), T [n] K (NULL: the
+     digester's T_op = 308.15 K), S_H [n] kmol/m^3 and h [n] days (NULL:
+     cold start, S_H guess 1e-7 and h 1e-6 d).
+   Resets the particles' status bits.  Host pointers are copied synchronously;
+   device pointers are copied on the context's stream. */
+chad_status chad_load_particles(chad_ctx* ctx, int digester, int64_t n, const double* pos,
+                                const double* y, const double* T, const double* S_H,
+                                const double* h, int mem);
+
+/* Set (or clear, has_flow = 0) the flow field of one digester. */
+chad_status chad_set_flow(chad_ctx* ctx, int digester, const chad_flow* flow);
+
+/* ---- the hot path ------------------------------------------------------- */
+
+/* Integrate n_intervals coupling intervals of dt_coupling_s seconds each:
+   per interval, advect (digesters with flow), integrate every particle
+   (Eq. 2-7) and, with a shared headspace, average the three gas states of
+   each digester.  Asynchronous on the context's stream; particle failures
+   are reported by chad_read_states / chad_synchronize.
+   dt_coupling_s > 0, n_intervals >= 0. */
+chad_status chad_step(chad_ctx* ctx, double dt_coupling_s, int n_intervals);
+
+/* Wait for the context's stream.  CHAD_E_PARTICLE if any particle has a
+   status bit set, CHAD_E_CUDA if a kernel failed. */
+chad_status chad_synchronize(chad_ctx* ctx);
+
+/* ---- data out ----------------------------------------------------------- */
+
+/* Copy one digester's particles out (any pointer may be NULL to skip it):
+   y [29][n], pos [3][n], S_H [n], h [n] (next step size, days), status [n].
+   stats (may be NULL) receives and clears the context's counters.
+   Synchronises the stream.  Returns CHAD_E_PARTICLE if any particle of the
+   digester has a status bit set (the data is still copied). */
+chad_status chad_read_states(chad_ctx* ctx, int digester, double* y, double* pos, double* S_H,
+                             double* h, int32_t* status, chad_stats* stats, int mem);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHAD_H */

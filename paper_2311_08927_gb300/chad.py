@@ -1,0 +1,282 @@
+"""Python binding of the C ABI in include/chad.h (ctypes; marshalling only).
+
+Every function here forwards to libchad.so, the CUDA library built in-tree by
+``paper_2311_08927_gb300.build``.  There is no fallback: if the library is not
+built, or no GPU is present, the calls fail loudly.  Buffers may be numpy
+arrays (host) or torch CUDA tensors (device; their data_ptr is passed).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import inputs as I
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchad.so")
+_lock = threading.Lock()
+_lib = None
+
+NS = 29
+MEM_HOST, MEM_DEVICE = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+HEADSPACE_PARTICLE, HEADSPACE_SHARED = 0, 1
+STATUS = {0: "CHAD_OK", 1: "CHAD_E_INVALID", 2: "CHAD_E_NOMEM", 3: "CHAD_E_CUDA",
+          4: "CHAD_E_STATE", 5: "CHAD_E_PARTICLE"}
+P_NEWTON, P_STEPS, P_HMIN, P_NEG, P_NAN = 1, 2, 4, 8, 16
+
+_i64p = C.POINTER(C.c_int64)
+_dp = C.POINTER(C.c_double)
+
+
+class chad_config(C.Structure):
+    _fields_ = [("n_digesters", C.c_int), ("n_particles", _i64p), ("V_liq", _dp),
+                ("V_gas", _dp), ("params", _dp), ("D_uniform", _dp), ("y_in", _dp),
+                ("precision", C.c_int), ("learned", C.c_int), ("headspace", C.c_int),
+                ("rtol", C.c_double), ("atol", _dp), ("max_steps_per_interval", C.c_int),
+                ("max_newton_iters", C.c_int), ("fixed_substeps", C.c_int),
+                ("cuda_stream", C.c_void_p)]
+
+
+class chad_flow(C.Structure):
+    _fields_ = [("has_flow", C.c_int), ("U", C.c_double), ("R", C.c_double), ("H", C.c_double),
+                ("sigma", C.c_double), ("slab_zmin", C.c_double), ("q_in", C.c_double),
+                ("y_in", _dp), ("seed", C.c_uint64)]
+
+
+class chad_stats(C.Structure):
+    _fields_ = [("accepted_steps", C.c_int64), ("rejected_steps", C.c_int64),
+                ("newton_iters", C.c_int64), ("newton_fallbacks", C.c_int64),
+                ("min_steps", C.c_int64), ("max_steps", C.c_int64),
+                ("failed_particles", C.c_int64), ("mlp_redo", C.c_int64),
+                ("intervals", C.c_int64), ("sim_days", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ChadError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libchad.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with "
+                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            L.chad_abi_version.restype = C.c_int
+            L.chad_n_params.restype = C.c_int
+            L.chad_param_name.restype = C.c_char_p
+            L.chad_param_name.argtypes = [C.c_int]
+            L.chad_last_error.restype = C.c_char_p
+            L.chad_last_error.argtypes = [C.c_void_p]
+            L.chad_create.restype = C.c_int
+            L.chad_create.argtypes = [C.POINTER(chad_config), C.POINTER(C.c_void_p)]
+            L.chad_destroy.restype = None
+            L.chad_destroy.argtypes = [C.c_void_p]
+            L.chad_load_particles.restype = C.c_int
+            L.chad_load_particles.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_int]
+            L.chad_set_flow.restype = C.c_int
+            L.chad_set_flow.argtypes = [C.c_void_p, C.c_int, C.POINTER(chad_flow)]
+            L.chad_step.restype = C.c_int
+            L.chad_step.argtypes = [C.c_void_p, C.c_double, C.c_int]
+            L.chad_synchronize.restype = C.c_int
+            L.chad_synchronize.argtypes = [C.c_void_p]
+            L.chad_read_states.restype = C.c_int
+            L.chad_read_states.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.POINTER(chad_stats), C.c_int]
+            _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return ["chad_abi_version", "chad_n_params", "chad_param_name", "chad_last_error",
+            "chad_create", "chad_destroy", "chad_load_particles", "chad_set_flow",
+            "chad_step", "chad_synchronize", "chad_read_states"]
+
+
+def param_names() -> list[str]:
+    L = lib()
+    return [L.chad_param_name(i).decode() for i in range(L.chad_n_params())]
+
+
+def _ptr(a):
+    """(pointer, mem) of a numpy array or a torch CUDA tensor (or (None, None))."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, MEM_HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), (MEM_DEVICE if a.is_cuda else MEM_HOST)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _check(L, ctx, code):
+    if code != 0:
+        raise ChadError(code, L.chad_last_error(ctx).decode())
+
+
+# ---------------------------------------------------------------- raw ABI calls
+def chad_create(cfg: chad_config) -> C.c_void_p:
+    L = lib()
+    ctx = C.c_void_p()
+    _check(L, None, L.chad_create(C.byref(cfg), C.byref(ctx)))
+    return ctx
+
+
+def chad_destroy(ctx) -> None:
+    lib().chad_destroy(ctx)
+
+
+def chad_load_particles(ctx, digester, n, pos, y, T=None, S_H=None, h=None) -> None:
+    L = lib()
+    ptrs = [_ptr(a) for a in (pos, y, T, S_H, h)]
+    mems = {m for _, m in ptrs if m is not None}
+    if len(mems) > 1:
+        raise ValueError("all buffers of one call must be host or all device")
+    mem = mems.pop() if mems else MEM_HOST
+    _check(L, ctx, L.chad_load_particles(ctx, int(digester), int(n), *[p for p, _ in ptrs], mem))
+
+
+def chad_set_flow(ctx, digester, flow: chad_flow) -> None:
+    L = lib()
+    _check(L, ctx, L.chad_set_flow(ctx, int(digester), C.byref(flow)))
+
+
+def chad_step(ctx, dt_coupling_s, n_intervals) -> None:
+    L = lib()
+    _check(L, ctx, L.chad_step(ctx, float(dt_coupling_s), int(n_intervals)))
+
+
+def chad_synchronize(ctx) -> int:
+    return lib().chad_synchronize(ctx)
+
+
+def chad_read_states(ctx, digester, y=None, pos=None, S_H=None, h=None, status=None,
+                     stats: chad_stats | None = None) -> int:
+    """Returns the chad_status code (CHAD_E_PARTICLE is not raised)."""
+    L = lib()
+    ptrs = [_ptr(a) for a in (y, pos, S_H, h, status)]
+    mems = {m for _, m in ptrs if m is not None}
+    if len(mems) > 1:
+        raise ValueError("all buffers of one call must be host or all device")
+    mem = mems.pop() if mems else MEM_HOST
+    code = L.chad_read_states(ctx, int(digester), *[p for p, _ in ptrs],
+                              C.byref(stats) if stats is not None else None, mem)
+    if code not in (0, 5):
+        _check(L, ctx, code)
+    return code
+
+
+# ---------------------------------------------------------------- population helper
+class Simulator:
+    """Owns one context for a seeded Population (inputs.Population)."""
+
+    def __init__(self, pop: I.Population, precision=PREC_FP64, rtol=1e-6, atol=None,
+                 max_steps=100000, max_newton=50, fixed_substeps=0, stream=None,
+                 headspace=None):
+        self.pop = pop
+        nd = len(pop.digesters)
+        self._keep = []
+
+        def arr(x, dt=np.float64):
+            a = np.ascontiguousarray(x, dtype=dt)
+            self._keep.append(a)
+            return a
+
+        counts = arr([d.n for d in pop.digesters], np.int64)
+        V_liq = arr([d.V_liq for d in pop.digesters])
+        V_gas = arr([d.V_gas for d in pop.digesters])
+        params = arr(np.stack([d.params for d in pop.digesters]))
+        D_u = arr([d.D for d in pop.digesters])
+        y_in = arr(np.stack([d.y_in for d in pop.digesters]))
+        atol = arr(I.atol_vector() if atol is None else atol)
+        if headspace is None:
+            headspace = HEADSPACE_SHARED if pop.shared_headspace else HEADSPACE_PARTICLE
+        cfg = chad_config()
+        cfg.n_digesters = nd
+        cfg.n_particles = counts.ctypes.data_as(_i64p)
+        cfg.V_liq = V_liq.ctypes.data_as(_dp)
+        cfg.V_gas = V_gas.ctypes.data_as(_dp)
+        cfg.params = params.ctypes.data_as(_dp)
+        cfg.D_uniform = D_u.ctypes.data_as(_dp)
+        cfg.y_in = y_in.ctypes.data_as(_dp)
+        cfg.precision = precision
+        cfg.learned = 0
+        cfg.headspace = headspace
+        cfg.rtol = rtol
+        cfg.atol = atol.ctypes.data_as(_dp)
+        cfg.max_steps_per_interval = max_steps
+        cfg.max_newton_iters = max_newton
+        cfg.fixed_substeps = fixed_substeps
+        cfg.cuda_stream = stream
+        self.ctx = chad_create(cfg)
+        self.offsets = pop.offsets
+        for d, dg in enumerate(pop.digesters):
+            if dg.flow is not None:
+                f = dg.flow
+                yin = arr(f["y_in"])
+                fl = chad_flow(1, f["U"], f["R"], f["H"], f["sigma"], f["slab_zmin"], f["q_in"],
+                               yin.ctypes.data_as(_dp), f["seed"])
+                chad_set_flow(self.ctx, d, fl)
+
+    def load(self, y=None, pos=None, T=None, S_H=None, h=None):
+        """Load every digester from host arrays (SoA over the whole population)."""
+        pop = self.pop
+        y = pop.y if y is None else y
+        pos = pop.pos if pos is None else pos
+        T = pop.T if T is None else T
+        for d, dg in enumerate(pop.digesters):
+            a, b = self.offsets[d], self.offsets[d + 1]
+            sl = lambda x: None if x is None else np.ascontiguousarray(x[..., a:b])
+            chad_load_particles(self.ctx, d, b - a, sl(pos), sl(y), sl(T), sl(S_H), sl(h))
+
+    def step(self, dt_coupling_s, n_intervals):
+        chad_step(self.ctx, dt_coupling_s, n_intervals)
+
+    def read(self):
+        """Host copies of y, pos, S_H, h, status and the counters (dict)."""
+        N = self.pop.n
+        out = dict(y=np.zeros((NS, N)), pos=np.zeros((3, N)), S_H=np.zeros(N), h=np.zeros(N),
+                   status=np.zeros(N, dtype=np.int32))
+        total = None
+        for d in range(len(self.pop.digesters)):
+            a, b = self.offsets[d], self.offsets[d + 1]
+            n = b - a
+            yy, pp = np.zeros((NS, n)), np.zeros((3, n))
+            sh, hh, st = np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.int32)
+            stats = chad_stats()
+            chad_read_states(self.ctx, d, yy, pp, sh, hh, st, stats if d == 0 else None)
+            if d == 0:
+                total = stats.as_dict()
+            out["y"][:, a:b], out["pos"][:, a:b] = yy, pp
+            out["S_H"][a:b], out["h"][a:b], out["status"][a:b] = sh, hh, st
+        out["stats"] = total
+        return out
+
+    def close(self):
+        if self.ctx:
+            chad_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

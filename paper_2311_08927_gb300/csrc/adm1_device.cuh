@@ -1,0 +1,521 @@
+// Device-side ADM1 model for one particle per thread (Sec. 2.2-2.3).
+//
+//   * part_const   : temperature-dependent constants of a particle (van 't
+//                    Hoff acid-base and Henry constants, Arrhenius kinetics).
+//   * solve_SH     : Eq. 7 charge balance for S_H+ by Newton, with a
+//                    bracketed geometric bisection fallback (FP64 always).
+//   * model_f      : rate vector f(y) (Eq. 2 mass balances, Eq. 3-6 rates).
+//   * model_fj     : f(y) and the analytic Jacobian df/dy, including the
+//                    rank-1 coupling through S_H(y) given by the implicit
+//                    function theorem on Eq. 7.
+// R is the arithmetic type of rates, Jacobian and LU (double for the plain
+// path, float for the mixed path); the charge balance is always FP64.
+#pragma once
+#include <cstdint>
+
+#include "model.h"
+
+namespace chad {
+
+constexpr double kVfaCod_ac = 64.0, kVfaCod_pro = 112.0, kVfaCod_bu = 160.0, kVfaCod_va = 208.0;
+constexpr double kC4Guard = 1e-6;  // division guard of the c4 uptake split
+constexpr double kSH_lo = 1e-14, kSH_hi = 1.0;
+
+struct PartConst {
+  double arr;  // Arrhenius factor of the kinetic constants
+  double K_w, K_a_co2, K_a_IN, K_H_co2, K_H_ch4, K_H_h2, p_h2o, RT;
+};
+
+__device__ __forceinline__ void part_const(const DigConst& c, double T, PartConst& q) {
+  const double invT = 1.0 / T;
+  const double dT = c.inv_T_base - invT;
+  q.arr = exp(-c.Ea_over_R * (invT - c.inv_T_ref));
+  q.K_w = c.K_w_b * exp(c.th_w * dT);
+  q.K_a_co2 = c.K_a_co2_b * exp(c.th_a_co2 * dT);
+  q.K_a_IN = c.K_a_IN_b * exp(c.th_a_IN * dT);
+  q.K_H_co2 = c.K_H_co2_b * exp(c.th_H_co2 * dT);
+  q.K_H_ch4 = c.K_H_ch4_b * exp(c.th_H_ch4 * dT);
+  q.K_H_h2 = c.K_H_h2_b * exp(c.th_H_h2 * dT);
+  q.p_h2o = c.p_h2o_b * exp(c.th_h2o * dT);
+  q.RT = c.R * T;
+}
+
+// ----------------------------------------------------------- Eq. 7 (FP64)
+struct AcidBase {
+  double SH;     // root
+  double dEdS;   // dE/dS_H at the root
+  double r_IN, r_co2, r_ac, r_pro, r_bu, r_va;  // 1/(K_a + S_H) at the root
+};
+
+// E(S) and dE/dS; fills the reciprocals used by the Jacobian
+__device__ __forceinline__ double charge_E(const DigConst& c, const PartConst& q,
+                                           const double* y, double S, AcidBase& ab) {
+  const double rS = 1.0 / S;
+  ab.r_IN = 1.0 / (q.K_a_IN + S);
+  ab.r_co2 = 1.0 / (q.K_a_co2 + S);
+  ab.r_ac = 1.0 / (c.K_a_ac + S);
+  ab.r_pro = 1.0 / (c.K_a_pro + S);
+  ab.r_bu = 1.0 / (c.K_a_bu + S);
+  ab.r_va = 1.0 / (c.K_a_va + S);
+  const double nh3 = q.K_a_IN * y[iS_IN] * ab.r_IN;
+  const double hco3 = q.K_a_co2 * y[iS_IC] * ab.r_co2;
+  const double ac = c.K_a_ac * y[iS_ac] * ab.r_ac * (1.0 / kVfaCod_ac);
+  const double pro = c.K_a_pro * y[iS_pro] * ab.r_pro * (1.0 / kVfaCod_pro);
+  const double bu = c.K_a_bu * y[iS_bu] * ab.r_bu * (1.0 / kVfaCod_bu);
+  const double va = c.K_a_va * y[iS_va] * ab.r_va * (1.0 / kVfaCod_va);
+  const double kw = q.K_w * rS;
+  ab.dEdS = 1.0 + kw * rS + nh3 * ab.r_IN + hco3 * ab.r_co2 + ac * ab.r_ac + pro * ab.r_pro +
+            bu * ab.r_bu + va * ab.r_va;
+  return (y[iS_cat] - y[iS_an]) + (y[iS_IN] - nh3) + S - hco3 - ac - pro - bu - va - kw;
+}
+
+struct NewtonCounters {
+  int iters;
+  int fallbacks;
+  int failed;
+};
+
+// Newton from `guess`; an iterate leaving (0, inf) or a growing |E| switches
+// to bisection on [1e-14, 1] (geometric midpoint, at most 200 halvings).
+__device__ inline void solve_SH(const DigConst& c, const PartConst& q, const double* y,
+                                double guess, int max_iters, AcidBase& ab, NewtonCounters& nc) {
+  double S = (guess > 0.0 && isfinite(guess)) ? guess : 1e-7;
+  double prevE = INFINITY;
+  for (int it = 0; it < max_iters; ++it) {
+    const double E = charge_E(c, q, y, S, ab);
+    nc.iters++;
+    if (!isfinite(E) || fabs(E) > fabs(prevE)) break;
+    const double dS = E / ab.dEdS;
+    const double Sn = S - dS;
+    if (!(Sn > 0.0) || !isfinite(Sn)) break;
+    if (fabs(dS) <= 1e-14 * Sn || fabs(E) <= 1e-15) {
+      charge_E(c, q, y, Sn, ab);  // reciprocals and slope at the accepted root
+      ab.SH = Sn;
+      return;
+    }
+    prevE = E;
+    S = Sn;
+  }
+  nc.fallbacks++;
+  double lo = kSH_lo, hi = kSH_hi;
+  const double elo = charge_E(c, q, y, lo, ab);
+  const double ehi = charge_E(c, q, y, hi, ab);
+  if (!(elo < 0.0 && ehi > 0.0)) {
+    nc.failed = 1;
+    ab.SH = (guess > 0.0 && isfinite(guess)) ? guess : 1e-7;
+    charge_E(c, q, y, ab.SH, ab);
+    return;
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = sqrt(lo * hi);
+    if (!(mid > lo && mid < hi)) break;
+    const double e = charge_E(c, q, y, mid, ab);
+    if (e == 0.0) { lo = hi = mid; break; }
+    if (e < 0.0) lo = mid; else hi = mid;
+  }
+  ab.SH = sqrt(lo * hi);
+  charge_E(c, q, y, ab.SH, ab);
+}
+
+// ----------------------------------------------------------- inhibition helpers
+// Hill pH inhibition I = 1 / (1 + (S/K)^n) and dI/dS
+template <class R>
+__device__ __forceinline__ void hill(R S, R invK, R n, int ni, R& I, R& dI) {
+  const R x = S * invK;
+  R xn1, xn;
+  switch (ni) {
+    case 1: xn1 = R(1); xn = x; break;
+    case 2: xn1 = x; xn = x * x; break;
+    case 3: xn1 = x * x; xn = xn1 * x; break;
+    case 4: xn1 = x * x * x; xn = xn1 * x; break;
+    default: xn = pow(x, n); xn1 = xn / x; break;
+  }
+  I = R(1) / (R(1) + xn);
+  dI = -n * xn1 * invK * I * I;
+}
+
+// Rates of the 19 biochemical processes, the 3 transfers and their partial
+// derivatives.  Column lists are fixed per process.
+template <class R>
+struct Rates {
+  R r[22];
+  // partials (d*) -- only filled by the Jacobian variant
+  R d1, d2, d3, d4;                                   // wrt X_c, X_ch, X_pr, X_li
+  R d5[3], d6[3], d7[4], d8[5], d9[5], d10[4], d11[3], d12[3];
+  R s5, s6, s7, s8, s9, s10, s11, s12;                // wrt S_H
+  R ddec[7];
+  R dT8[2], dT9[2], dT10[2], sT10;
+  R qv, dqv;                                          // q_gas/V_gas, its dP derivative
+  R P_h2, P_ch4, P_co2;                               // dP/dG
+};
+
+template <class R, bool J>
+__device__ __forceinline__ void rates(const DigConst& c, const PartConst& q, const R* y,
+                                      const AcidBase& ab, Rates<R>& o) {
+  const R a = R(q.arr);
+  const R SH = R(ab.SH);
+  // inhibition factors (Eq. 3-6)
+  R Ipaa, dIpaa, Ipac, dIpac, Iph2, dIph2;
+  hill<R>(SH, R(c.inv_K_pH_aa), R(c.n_aa), c.ni_aa, Ipaa, dIpaa);
+  hill<R>(SH, R(c.inv_K_pH_ac), R(c.n_ac), c.ni_ac, Ipac, dIpac);
+  hill<R>(SH, R(c.inv_K_pH_h2), R(c.n_h2), c.ni_h2, Iph2, dIph2);
+  const R S_IN = y[iS_IN], S_h2 = y[iS_h2];
+  const R rIN = R(1) / (S_IN + R(c.K_S_IN));
+  const R IIN = S_IN * rIN;
+  const R dIIN = R(c.K_S_IN) * rIN * rIN;
+  const R rfa = R(1) / (R(c.K_I_h2_fa) + S_h2), rc4 = R(1) / (R(c.K_I_h2_c4) + S_h2);
+  const R rpr = R(1) / (R(c.K_I_h2_pro) + S_h2);
+  const R Ih2fa = R(c.K_I_h2_fa) * rfa, Ih2c4 = R(c.K_I_h2_c4) * rc4, Ih2pro = R(c.K_I_h2_pro) * rpr;
+  const R r_nh3 = R(q.K_a_IN) * R(ab.r_IN);
+  const R nh3 = r_nh3 * S_IN;  // free ammonia
+  const R rnh = R(1) / (R(c.K_I_nh3) + nh3);
+  const R Inh3 = R(c.K_I_nh3) * rnh;
+
+  // first-order processes
+  const R kdis = R(c.k_dis) * a, kch = R(c.k_hyd_ch) * a, kpr = R(c.k_hyd_pr) * a,
+          kli = R(c.k_hyd_li) * a;
+  o.r[0] = kdis * y[iX_c];
+  o.r[1] = kch * y[iX_ch];
+  o.r[2] = kpr * y[iX_pr];
+  o.r[3] = kli * y[iX_li];
+  // Monod terms m = S/(K+S), dm = K/(K+S)^2
+  const R rsu = R(1) / (R(c.K_S_su) + y[iS_su]), raa = R(1) / (R(c.K_S_aa) + y[iS_aa]);
+  const R rfs = R(1) / (R(c.K_S_fa) + y[iS_fa]), rva = R(1) / (R(c.K_S_c4) + y[iS_va]);
+  const R rbu = R(1) / (R(c.K_S_c4) + y[iS_bu]), rpo = R(1) / (R(c.K_S_pro) + y[iS_pro]);
+  const R rac = R(1) / (R(c.K_S_ac) + y[iS_ac]), rh2 = R(1) / (R(c.K_S_h2) + S_h2);
+  const R msu = y[iS_su] * rsu, maa = y[iS_aa] * raa, mfa = y[iS_fa] * rfs, mva = y[iS_va] * rva;
+  const R mbu = y[iS_bu] * rbu, mpo = y[iS_pro] * rpo, mac = y[iS_ac] * rac, mh2 = S_h2 * rh2;
+  const R rden = R(1) / (y[iS_bu] + y[iS_va] + R(kC4Guard));
+  const R gva = y[iS_va] * rden, gbu = y[iS_bu] * rden;
+
+  const R ksu = R(c.k_m_su) * a, kaa = R(c.k_m_aa) * a, kfa = R(c.k_m_fa) * a,
+          kc4 = R(c.k_m_c4) * a, kpo = R(c.k_m_pro) * a, kac = R(c.k_m_ac) * a,
+          kh2 = R(c.k_m_h2) * a;
+  const R B5 = Ipaa * IIN;
+  const R B7 = B5 * Ih2fa, B8 = B5 * Ih2c4, B10 = B5 * Ih2pro;
+  const R B11 = Ipac * IIN * Inh3, B12 = Iph2 * IIN;
+  const R A5 = ksu * y[iX_su], A6 = kaa * y[iX_aa], A7 = kfa * y[iX_fa], A8 = kc4 * y[iX_c4];
+  const R A10 = kpo * y[iX_pro], A11 = kac * y[iX_ac], A12 = kh2 * y[iX_h2];
+  o.r[4] = A5 * msu * B5;
+  o.r[5] = A6 * maa * B5;
+  o.r[6] = A7 * mfa * B7;
+  o.r[7] = A8 * mva * gva * B8;
+  o.r[8] = A8 * mbu * gbu * B8;
+  o.r[9] = A10 * mpo * B10;
+  o.r[10] = A11 * mac * B11;
+  o.r[11] = A12 * mh2 * B12;
+  R kd[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    kd[k] = R(c.k_dec[k]) * a;
+    o.r[12 + k] = kd[k] * y[iX_su + k];
+  }
+  // gas phase
+  const R RT = R(q.RT);
+  const R P_h2 = RT * R(1.0 / 16.0), P_ch4 = RT * R(1.0 / 64.0), P_co2 = RT;
+  const R P = P_h2 * y[iG_h2] + P_ch4 * y[iG_ch4] + P_co2 * y[iG_co2] + R(q.p_h2o);
+  const R kpv = R(c.kp_over_Vgas), invPa = R(1.0 / c.P_atm);
+  o.qv = kpv * (P - R(c.P_atm)) * P * invPa;
+  const R kLa = R(c.k_La);
+  const R KH2 = R(q.K_H_h2) * RT, KCH4 = R(q.K_H_ch4) * RT, KCO2 = R(q.K_H_co2) * RT;
+  const R rco2 = R(ab.r_co2);
+  const R fco2 = SH * rco2;  // S_co2 / S_IC
+  o.r[19] = kLa * (S_h2 - KH2 * y[iG_h2]);
+  o.r[20] = kLa * (y[iS_ch4] - KCH4 * y[iG_ch4]);
+  o.r[21] = kLa * (y[iS_IC] * fco2 - KCO2 * y[iG_co2]);
+
+  if (J) {
+    o.d1 = kdis; o.d2 = kch; o.d3 = kpr; o.d4 = kli;
+    // rho5: S_su, X_su, S_IN
+    o.d5[0] = A5 * (R(c.K_S_su) * rsu * rsu) * B5;
+    o.d5[1] = ksu * msu * B5;
+    o.d5[2] = A5 * msu * Ipaa * dIIN;
+    o.s5 = A5 * msu * dIpaa * IIN;
+    // rho6: S_aa, X_aa, S_IN
+    o.d6[0] = A6 * (R(c.K_S_aa) * raa * raa) * B5;
+    o.d6[1] = kaa * maa * B5;
+    o.d6[2] = A6 * maa * Ipaa * dIIN;
+    o.s6 = A6 * maa * dIpaa * IIN;
+    // rho7: S_fa, X_fa, S_IN, S_h2
+    o.d7[0] = A7 * (R(c.K_S_fa) * rfs * rfs) * B7;
+    o.d7[1] = kfa * mfa * B7;
+    o.d7[2] = A7 * mfa * Ipaa * dIIN * Ih2fa;
+    o.d7[3] = -A7 * mfa * B5 * Ih2fa * rfa;   // dI/dS_h2 = -K/(K+S)^2 = -I r
+    o.s7 = A7 * mfa * dIpaa * IIN * Ih2fa;
+    // rho8, rho9: S_va, S_bu, X_c4, S_IN, S_h2
+    const R rd2 = rden * rden;
+    const R dgva_va = (y[iS_bu] + R(kC4Guard)) * rd2, dgva_bu = -y[iS_va] * rd2;
+    const R dgbu_bu = (y[iS_va] + R(kC4Guard)) * rd2, dgbu_va = -y[iS_bu] * rd2;
+    const R dmva = R(c.K_S_c4) * rva * rva, dmbu = R(c.K_S_c4) * rbu * rbu;
+    o.d8[0] = A8 * B8 * (dmva * gva + mva * dgva_va);
+    o.d8[1] = A8 * B8 * mva * dgva_bu;
+    o.d8[2] = kc4 * mva * gva * B8;
+    o.d8[3] = A8 * mva * gva * Ipaa * dIIN * Ih2c4;
+    o.d8[4] = -A8 * mva * gva * B5 * Ih2c4 * rc4;
+    o.s8 = A8 * mva * gva * dIpaa * IIN * Ih2c4;
+    o.d9[0] = A8 * B8 * mbu * dgbu_va;
+    o.d9[1] = A8 * B8 * (dmbu * gbu + mbu * dgbu_bu);
+    o.d9[2] = kc4 * mbu * gbu * B8;
+    o.d9[3] = A8 * mbu * gbu * Ipaa * dIIN * Ih2c4;
+    o.d9[4] = -A8 * mbu * gbu * B5 * Ih2c4 * rc4;
+    o.s9 = A8 * mbu * gbu * dIpaa * IIN * Ih2c4;
+    // rho10: S_pro, X_pro, S_IN, S_h2
+    o.d10[0] = A10 * (R(c.K_S_pro) * rpo * rpo) * B10;
+    o.d10[1] = kpo * mpo * B10;
+    o.d10[2] = A10 * mpo * Ipaa * dIIN * Ih2pro;
+    o.d10[3] = -A10 * mpo * B5 * Ih2pro * rpr;
+    o.s10 = A10 * mpo * dIpaa * IIN * Ih2pro;
+    // rho11: S_ac, X_ac, S_IN (I_IN and free ammonia)
+    const R dInh3 = -Inh3 * rnh;  // dI_nh3 / dS_nh3
+    o.d11[0] = A11 * (R(c.K_S_ac) * rac * rac) * B11;
+    o.d11[1] = kac * mac * B11;
+    o.d11[2] = A11 * mac * Ipac * (dIIN * Inh3 + IIN * dInh3 * r_nh3);
+    o.s11 = A11 * mac * IIN * (dIpac * Inh3 - Ipac * dInh3 * nh3 * R(ab.r_IN));
+    // rho12: S_h2, X_h2, S_IN
+    o.d12[0] = A12 * (R(c.K_S_h2) * rh2 * rh2) * B12;
+    o.d12[1] = kh2 * mh2 * B12;
+    o.d12[2] = A12 * mh2 * Iph2 * dIIN;
+    o.s12 = A12 * mh2 * dIph2 * IIN;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) o.ddec[k] = kd[k];
+    // transfers
+    o.dT8[0] = kLa; o.dT8[1] = -kLa * KH2;
+    o.dT9[0] = kLa; o.dT9[1] = -kLa * KCH4;
+    o.dT10[0] = kLa * fco2; o.dT10[1] = -kLa * KCO2;
+    o.sT10 = kLa * y[iS_IC] * R(q.K_a_co2) * rco2 * rco2;
+    o.dqv = kpv * (R(2) * P - R(c.P_atm)) * invPa;
+    o.P_h2 = P_h2; o.P_ch4 = P_ch4; o.P_co2 = P_co2;
+  }
+}
+
+// f(y): mass balances of Eq. 2 with the ADM1 stoichiometry
+template <class R>
+__device__ __forceinline__ void balances(const DigConst& c, const R* y, R D, const Rates<R>& o,
+                                         R* f) {
+  const R* r = o.r;
+  R dil[26];
+#pragma unroll
+  for (int i = 0; i < 26; ++i) dil[i] = D * (R(c.y_in[i]) - y[i]);
+  const R dec = r[12] + r[13] + r[14] + r[15] + r[16] + r[17] + r[18];
+  f[iS_su] = dil[iS_su] + r[1] + R(c.c_su_li) * r[3] - r[4];
+  f[iS_aa] = dil[iS_aa] + r[2] - r[5];
+  f[iS_fa] = dil[iS_fa] + R(c.f_fa_li) * r[3] - r[6];
+  f[iS_va] = dil[iS_va] + R(c.aa_va) * r[5] - r[7];
+  f[iS_bu] = dil[iS_bu] + R(c.su_bu) * r[4] + R(c.aa_bu) * r[5] - r[8];
+  f[iS_pro] = dil[iS_pro] + R(c.su_pro) * r[4] + R(c.aa_pro) * r[5] + R(c.va_pro) * r[7] - r[9];
+  f[iS_ac] = dil[iS_ac] + R(c.su_ac) * r[4] + R(c.aa_ac) * r[5] + R(c.fa_ac) * r[6] +
+             R(c.va_ac) * r[7] + R(c.bu_ac) * r[8] + R(c.pro_ac) * r[9] - r[10];
+  f[iS_h2] = dil[iS_h2] + R(c.su_h2) * r[4] + R(c.aa_h2) * r[5] + R(c.fa_h2) * r[6] +
+             R(c.va_h2) * r[7] + R(c.bu_h2) * r[8] + R(c.pro_h2) * r[9] - r[11] - r[19];
+  f[iS_ch4] = dil[iS_ch4] + R(c.ac_ch4) * r[10] + R(c.h2_ch4) * r[11] - r[20];
+  R ic = dil[iS_IC] + R(c.cIC[12]) * dec - r[21];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) ic += R(c.cIC[j]) * r[j];
+  f[iS_IC] = ic;
+  R in = dil[iS_IN] + R(c.nIN[0]) * r[0] + R(c.nIN[12]) * dec;
+#pragma unroll
+  for (int j = 4; j < 12; ++j) in += R(c.nIN[j]) * r[j];
+  f[iS_IN] = in;
+  f[iS_I] = dil[iS_I] + R(c.f_sI) * r[0];
+  f[iX_c] = dil[iX_c] - r[0] + dec;
+  f[iX_ch] = dil[iX_ch] + R(c.f_ch) * r[0] - r[1];
+  f[iX_pr] = dil[iX_pr] + R(c.f_pr) * r[0] - r[2];
+  f[iX_li] = dil[iX_li] + R(c.f_li) * r[0] - r[3];
+  f[iX_su] = dil[iX_su] + R(c.Y_su) * r[4] - r[12];
+  f[iX_aa] = dil[iX_aa] + R(c.Y_aa) * r[5] - r[13];
+  f[iX_fa] = dil[iX_fa] + R(c.Y_fa) * r[6] - r[14];
+  f[iX_c4] = dil[iX_c4] + R(c.Y_c4) * (r[7] + r[8]) - r[15];
+  f[iX_pro] = dil[iX_pro] + R(c.Y_pro) * r[9] - r[16];
+  f[iX_ac] = dil[iX_ac] + R(c.Y_ac) * r[10] - r[17];
+  f[iX_h2] = dil[iX_h2] + R(c.Y_h2) * r[11] - r[18];
+  f[iX_I] = dil[iX_I] + R(c.f_xI) * r[0];
+  f[iS_cat] = dil[iS_cat];
+  f[iS_an] = dil[iS_an];
+  const R vr = R(c.Vliq_over_Vgas);
+  f[iG_h2] = -y[iG_h2] * o.qv + vr * r[19];
+  f[iG_ch4] = -y[iG_ch4] * o.qv + vr * r[20];
+  f[iG_co2] = -y[iG_co2] * o.qv + vr * r[21];
+}
+
+// J[row][cols[k]] += coef * d[k]; u[row] += coef * s
+template <class R, int NC>
+__device__ __forceinline__ void scat(R* Jm, R* u, int row, R coef, const int (&cols)[NC],
+                                     const R (&d)[NC], R s) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k) Jm[row * NS + cols[k]] += coef * d[k];
+  u[row] += coef * s;
+}
+template <class R, int NC>
+__device__ __forceinline__ void scat(R* Jm, int row, R coef, const int (&cols)[NC],
+                                     const R (&d)[NC]) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k) Jm[row * NS + cols[k]] += coef * d[k];
+}
+
+// Analytic Jacobian (row-major NS x NS) from the rate partials.  The S_H
+// dependence enters as the rank-1 term u v^T, u = df/dS_H (at fixed y),
+// v = dS_H/dy = -(dE/dy) / (dE/dS_H) from Eq. 7.
+template <class R>
+__device__ __forceinline__ void jacobian(const DigConst& c, const PartConst& q, const R* y, R D,
+                                         const AcidBase& ab, const Rates<R>& o, R* Jm) {
+  R u[NS];
+#pragma unroll
+  for (int i = 0; i < NS * NS; ++i) Jm[i] = R(0);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) u[i] = R(0);
+#pragma unroll
+  for (int i = 0; i < 26; ++i) Jm[i * NS + i] = -D;
+  const R one = R(1), mone = R(-1);
+  const R cIC12 = R(c.cIC[12]), nIN12 = R(c.nIN[12]);
+  {  // rho1 disintegration
+    const int cols[1] = {iX_c};
+    const R d[1] = {o.d1};
+    scat(Jm, iX_c, mone, cols, d);
+    scat(Jm, iS_I, R(c.f_sI), cols, d);
+    scat(Jm, iX_ch, R(c.f_ch), cols, d);
+    scat(Jm, iX_pr, R(c.f_pr), cols, d);
+    scat(Jm, iX_li, R(c.f_li), cols, d);
+    scat(Jm, iX_I, R(c.f_xI), cols, d);
+    scat(Jm, iS_IC, R(c.cIC[0]), cols, d);
+    scat(Jm, iS_IN, R(c.nIN[0]), cols, d);
+  }
+  {  // rho2-4 hydrolysis
+    const int c2[1] = {iX_ch}, c3[1] = {iX_pr}, c4[1] = {iX_li};
+    const R d2[1] = {o.d2}, d3[1] = {o.d3}, d4[1] = {o.d4};
+    scat(Jm, iX_ch, mone, c2, d2);
+    scat(Jm, iS_su, one, c2, d2);
+    scat(Jm, iS_IC, R(c.cIC[1]), c2, d2);
+    scat(Jm, iX_pr, mone, c3, d3);
+    scat(Jm, iS_aa, one, c3, d3);
+    scat(Jm, iS_IC, R(c.cIC[2]), c3, d3);
+    scat(Jm, iX_li, mone, c4, d4);
+    scat(Jm, iS_su, R(c.c_su_li), c4, d4);
+    scat(Jm, iS_fa, R(c.f_fa_li), c4, d4);
+    scat(Jm, iS_IC, R(c.cIC[3]), c4, d4);
+  }
+  {  // rho5 sugars
+    const int cols[3] = {iS_su, iX_su, iS_IN};
+    scat(Jm, u, iS_su, mone, cols, o.d5, o.s5);
+    scat(Jm, u, iS_bu, R(c.su_bu), cols, o.d5, o.s5);
+    scat(Jm, u, iS_pro, R(c.su_pro), cols, o.d5, o.s5);
+    scat(Jm, u, iS_ac, R(c.su_ac), cols, o.d5, o.s5);
+    scat(Jm, u, iS_h2, R(c.su_h2), cols, o.d5, o.s5);
+    scat(Jm, u, iX_su, R(c.Y_su), cols, o.d5, o.s5);
+    scat(Jm, u, iS_IC, R(c.cIC[4]), cols, o.d5, o.s5);
+    scat(Jm, u, iS_IN, R(c.nIN[4]), cols, o.d5, o.s5);
+  }
+  {  // rho6 amino acids
+    const int cols[3] = {iS_aa, iX_aa, iS_IN};
+    scat(Jm, u, iS_aa, mone, cols, o.d6, o.s6);
+    scat(Jm, u, iS_va, R(c.aa_va), cols, o.d6, o.s6);
+    scat(Jm, u, iS_bu, R(c.aa_bu), cols, o.d6, o.s6);
+    scat(Jm, u, iS_pro, R(c.aa_pro), cols, o.d6, o.s6);
+    scat(Jm, u, iS_ac, R(c.aa_ac), cols, o.d6, o.s6);
+    scat(Jm, u, iS_h2, R(c.aa_h2), cols, o.d6, o.s6);
+    scat(Jm, u, iX_aa, R(c.Y_aa), cols, o.d6, o.s6);
+    scat(Jm, u, iS_IC, R(c.cIC[5]), cols, o.d6, o.s6);
+    scat(Jm, u, iS_IN, R(c.nIN[5]), cols, o.d6, o.s6);
+  }
+  {  // rho7 LCFA
+    const int cols[4] = {iS_fa, iX_fa, iS_IN, iS_h2};
+    scat(Jm, u, iS_fa, mone, cols, o.d7, o.s7);
+    scat(Jm, u, iS_ac, R(c.fa_ac), cols, o.d7, o.s7);
+    scat(Jm, u, iS_h2, R(c.fa_h2), cols, o.d7, o.s7);
+    scat(Jm, u, iX_fa, R(c.Y_fa), cols, o.d7, o.s7);
+    scat(Jm, u, iS_IC, R(c.cIC[6]), cols, o.d7, o.s7);
+    scat(Jm, u, iS_IN, R(c.nIN[6]), cols, o.d7, o.s7);
+  }
+  {  // rho8 valerate
+    const int cols[5] = {iS_va, iS_bu, iX_c4, iS_IN, iS_h2};
+    scat(Jm, u, iS_va, mone, cols, o.d8, o.s8);
+    scat(Jm, u, iS_pro, R(c.va_pro), cols, o.d8, o.s8);
+    scat(Jm, u, iS_ac, R(c.va_ac), cols, o.d8, o.s8);
+    scat(Jm, u, iS_h2, R(c.va_h2), cols, o.d8, o.s8);
+    scat(Jm, u, iX_c4, R(c.Y_c4), cols, o.d8, o.s8);
+    scat(Jm, u, iS_IC, R(c.cIC[7]), cols, o.d8, o.s8);
+    scat(Jm, u, iS_IN, R(c.nIN[7]), cols, o.d8, o.s8);
+  }
+  {  // rho9 butyrate
+    const int cols[5] = {iS_va, iS_bu, iX_c4, iS_IN, iS_h2};
+    scat(Jm, u, iS_bu, mone, cols, o.d9, o.s9);
+    scat(Jm, u, iS_ac, R(c.bu_ac), cols, o.d9, o.s9);
+    scat(Jm, u, iS_h2, R(c.bu_h2), cols, o.d9, o.s9);
+    scat(Jm, u, iX_c4, R(c.Y_c4), cols, o.d9, o.s9);
+    scat(Jm, u, iS_IC, R(c.cIC[8]), cols, o.d9, o.s9);
+    scat(Jm, u, iS_IN, R(c.nIN[8]), cols, o.d9, o.s9);
+  }
+  {  // rho10 propionate
+    const int cols[4] = {iS_pro, iX_pro, iS_IN, iS_h2};
+    scat(Jm, u, iS_pro, mone, cols, o.d10, o.s10);
+    scat(Jm, u, iS_ac, R(c.pro_ac), cols, o.d10, o.s10);
+    scat(Jm, u, iS_h2, R(c.pro_h2), cols, o.d10, o.s10);
+    scat(Jm, u, iX_pro, R(c.Y_pro), cols, o.d10, o.s10);
+    scat(Jm, u, iS_IC, R(c.cIC[9]), cols, o.d10, o.s10);
+    scat(Jm, u, iS_IN, R(c.nIN[9]), cols, o.d10, o.s10);
+  }
+  {  // rho11 acetate
+    const int cols[3] = {iS_ac, iX_ac, iS_IN};
+    scat(Jm, u, iS_ac, mone, cols, o.d11, o.s11);
+    scat(Jm, u, iS_ch4, R(c.ac_ch4), cols, o.d11, o.s11);
+    scat(Jm, u, iX_ac, R(c.Y_ac), cols, o.d11, o.s11);
+    scat(Jm, u, iS_IC, R(c.cIC[10]), cols, o.d11, o.s11);
+    scat(Jm, u, iS_IN, R(c.nIN[10]), cols, o.d11, o.s11);
+  }
+  {  // rho12 hydrogen
+    const int cols[3] = {iS_h2, iX_h2, iS_IN};
+    scat(Jm, u, iS_h2, mone, cols, o.d12, o.s12);
+    scat(Jm, u, iS_ch4, R(c.h2_ch4), cols, o.d12, o.s12);
+    scat(Jm, u, iX_h2, R(c.Y_h2), cols, o.d12, o.s12);
+    scat(Jm, u, iS_IC, R(c.cIC[11]), cols, o.d12, o.s12);
+    scat(Jm, u, iS_IN, R(c.nIN[11]), cols, o.d12, o.s12);
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {  // rho13-19 decay
+    const int col = iX_su + k;
+    const R dk = o.ddec[k];
+    Jm[col * NS + col] -= dk;
+    Jm[iX_c * NS + col] += dk;
+    Jm[iS_IC * NS + col] += cIC12 * dk;
+    Jm[iS_IN * NS + col] += nIN12 * dk;
+  }
+  const R vr = R(c.Vliq_over_Vgas);
+  {  // transfers
+    const int c8[2] = {iS_h2, iG_h2}, c9[2] = {iS_ch4, iG_ch4}, c10[2] = {iS_IC, iG_co2};
+    scat(Jm, iS_h2, mone, c8, o.dT8);
+    scat(Jm, iG_h2, vr, c8, o.dT8);
+    scat(Jm, iS_ch4, mone, c9, o.dT9);
+    scat(Jm, iG_ch4, vr, c9, o.dT9);
+    scat(Jm, u, iS_IC, mone, c10, o.dT10, o.sT10);
+    scat(Jm, u, iG_co2, vr, c10, o.dT10, o.sT10);
+  }
+  {  // gas outflow: f_G = -G q(P)
+    const int g[3] = {iG_h2, iG_ch4, iG_co2};
+    const R dP[3] = {o.P_h2, o.P_ch4, o.P_co2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Jm[g[a] * NS + g[a]] -= o.qv;
+      const R gq = y[g[a]] * o.dqv;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Jm[g[a] * NS + g[b]] -= gq * dP[b];
+    }
+  }
+  // rank-1 S_H coupling: J += u v^T over the 8 states that enter Eq. 7
+  const double inv = -1.0 / ab.dEdS;
+  const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
+  const R v[8] = {R(inv * (-c.K_a_va * ab.r_va / kVfaCod_va)),
+                  R(inv * (-c.K_a_bu * ab.r_bu / kVfaCod_bu)),
+                  R(inv * (-c.K_a_pro * ab.r_pro / kVfaCod_pro)),
+                  R(inv * (-c.K_a_ac * ab.r_ac / kVfaCod_ac)),
+                  R(inv * (-q.K_a_co2 * ab.r_co2)),
+                  R(inv * (ab.SH * ab.r_IN)),
+                  R(inv),
+                  R(-inv)};
+  const int ur[19] = {iS_su, iS_aa, iS_fa, iS_va, iS_bu, iS_pro, iS_ac, iS_h2, iS_ch4, iS_IC,
+                      iS_IN, iX_su, iX_aa, iX_fa, iX_c4, iX_pro, iX_ac, iX_h2, iG_co2};
+#pragma unroll
+  for (int i = 0; i < 19; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) Jm[ur[i] * NS + hc[k]] += u[ur[i]] * v[k];
+}
+
+}  // namespace chad

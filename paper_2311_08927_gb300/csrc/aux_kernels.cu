@@ -1,0 +1,153 @@
+// Advection of the AD particles through the prescribed swirl (Sec. 2.3) and
+// the shared-headspace reduction of the gas states (Table 1 gas volume).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace chad {
+
+namespace {
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based generator
+// with the 4x64 S-box multipliers and Weyl key increments of the publication.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+    const uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+// Irwin-Hall(12) normal deviate from one Philox block: 12 uniforms
+// (b + 1/2)/2^16 from 16-bit chunks, summed as integers, minus 6.
+__device__ __forceinline__ double gauss(uint64_t seed, uint64_t pid, uint64_t interval,
+                                        uint64_t sub, uint64_t axis) {
+  uint64_t c[4] = {interval, sub, axis, 0};
+  philox4x64_10(c, seed, pid);
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) s += (c[k >> 2] >> (16 * (k & 3))) & 0xFFFFull;
+  return __dsub_rn(__ddiv_rn(__dadd_rn((double)s, 6.0), 65536.0), 6.0);
+}
+
+// Explicit IEEE operations (no contraction) keep positions bit-identical to
+// any IEEE implementation of the same sequence, so slab membership cannot
+// flip by a rounding difference.
+__global__ void advect_kernel(AdvectArgs a) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.n) return;
+  const int d = a.dig[p];
+  const FlowConst& f = a.fl[d];
+  if (!f.has_flow) return;
+  double x = a.pos[p], y = a.pos[a.ld + p], z = a.pos[2 * a.ld + p];
+  a.D[p] = (z >= f.slab_zmin) ? f.D_slab : 0.0;  // slab membership at interval start
+  const uint64_t pid = (uint64_t)(p - a.dig_offset[d]);
+  const double twoR = __dmul_rn(2.0, f.R), twoH = __dmul_rn(2.0, f.H);
+#pragma unroll 1
+  for (int k = 0; k < f.n_sub; ++k) {
+    const double xr = __dsub_rn(__dmul_rn(f.cw, x), __dmul_rn(f.sw, y));
+    const double yr = __dadd_rn(__dmul_rn(f.sw, x), __dmul_rn(f.cw, y));
+    x = __dadd_rn(xr, __dmul_rn(f.amp, gauss(f.seed, pid, a.interval, (uint64_t)k, 0)));
+    y = __dadd_rn(yr, __dmul_rn(f.amp, gauss(f.seed, pid, a.interval, (uint64_t)k, 1)));
+    z = __dadd_rn(z, __dmul_rn(f.amp, gauss(f.seed, pid, a.interval, (uint64_t)k, 2)));
+    const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+    if (r > f.R) {
+      const double g = __ddiv_rn(__dsub_rn(twoR, r), r);
+      x = __dmul_rn(x, g);
+      y = __dmul_rn(y, g);
+    }
+    if (z < 0.0) z = -z;
+    if (z > f.H) z = __dsub_rn(twoH, z);
+  }
+  a.pos[p] = x;
+  a.pos[a.ld + p] = y;
+  a.pos[2 * a.ld + p] = z;
+}
+
+constexpr int kRedThreads = 256;
+
+// Stage 1: each block sums the three gas states of one chunk (a contiguous
+// range of one digester) in a fixed order: strided per-thread sums, then a
+// fixed shared-memory tree.  Deterministic run to run.
+__global__ void __launch_bounds__(kRedThreads) headspace_partial(HeadspaceArgs a) {
+  __shared__ double s[3][kRedThreads];
+  const int b = blockIdx.x;
+  const int64_t beg = a.chunk_begin[b], end = a.chunk_end[b];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t p = beg + threadIdx.x; p < end; p += kRedThreads) {
+#pragma unroll
+    for (int g = 0; g < 3; ++g) acc[g] += a.y[(iG_h2 + g) * a.ld + p];
+  }
+#pragma unroll
+  for (int g = 0; g < 3; ++g) s[g][threadIdx.x] = acc[g];
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int g = 0; g < 3; ++g) s[g][threadIdx.x] += s[g][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) a.partial[b * 3 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// Stage 2: one block per digester adds its chunk partials (fixed tree) and
+// writes the volume-weighted mean (equal particle volumes within a digester).
+__global__ void __launch_bounds__(kRedThreads) headspace_mean(HeadspaceArgs a) {
+  __shared__ double s[3][kRedThreads];
+  const int d = blockIdx.x;
+  const int c0 = a.dig_chunk0[d], c1 = a.dig_chunk0[d + 1];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int c = c0 + threadIdx.x; c < c1; c += kRedThreads)
+#pragma unroll
+    for (int g = 0; g < 3; ++g) acc[g] += a.partial[c * 3 + g];
+#pragma unroll
+  for (int g = 0; g < 3; ++g) s[g][threadIdx.x] = acc[g];
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int g = 0; g < 3; ++g) s[g][threadIdx.x] += s[g][threadIdx.x + w];
+    __syncthreads();
+  }
+  const int64_t n = a.dig_offset[d + 1] - a.dig_offset[d];
+  if (threadIdx.x < 3 && n > 0) a.mean[d * 3 + threadIdx.x] = s[threadIdx.x][0] / (double)n;
+}
+
+// Stage 3: broadcast the digester mean back to every particle.
+__global__ void headspace_broadcast(HeadspaceArgs a) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.n) return;
+  const int d = a.dig[p];
+#pragma unroll
+  for (int g = 0; g < 3; ++g) a.y[(iG_h2 + g) * a.ld + p] = a.mean[d * 3 + g];
+}
+
+}  // namespace
+
+cudaError_t launch_advect(const AdvectArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const int block = 128;
+  advect_kernel<<<(unsigned)((a.n + block - 1) / block), block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_headspace(const HeadspaceArgs& a, cudaStream_t s) {
+  if (a.n <= 0 || a.n_chunks <= 0) return cudaSuccess;
+  headspace_partial<<<a.n_chunks, kRedThreads, 0, s>>>(a);
+  headspace_mean<<<a.n_dig, kRedThreads, 0, s>>>(a);
+  headspace_broadcast<<<(unsigned)((a.n + 255) / 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace chad

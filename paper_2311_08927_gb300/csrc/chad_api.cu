@@ -1,0 +1,484 @@
+// Host implementation of the C ABI declared in include/chad.h.
+//
+// Owns the device buffers of one particle population (structure-of-arrays,
+// particle index fastest), validates every argument, and issues the
+// per-interval sequence advect -> integrate -> headspace on the caller's
+// stream.  Nothing here computes the model: it derives constants once
+// (model_host.cpp) and launches the kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "chad.h"
+#include "kernels.h"
+#include "model.h"
+
+using namespace chad;
+
+static_assert(CHAD_NS == chad::NS, "state count");
+static_assert(CHAD_NPARAM == chad::kNumParams, "parameter count");
+
+struct chad_ctx {
+  std::string err;
+  int n_dig = 0;
+  std::vector<int64_t> count, offset;  // per digester
+  int64_t N = 0, ld = 0;
+  int precision = 0, learned = 0, headspace = 0;
+  double rtol = 1e-6;
+  int max_steps = 100000, max_newton = 50, fixed_n = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<DigConst> hdc;
+  std::vector<FlowConst> hfl;
+  std::vector<char> loaded;
+  bool any_flow = false;
+  uint64_t interval = 0;  // global interval counter (noise stream)
+  double sim_days = 0.0;
+  int64_t intervals = 0;
+  // headspace chunking
+  int n_chunks = 0;
+  // device buffers
+  DigConst* d_dc = nullptr;
+  FlowConst* d_fl = nullptr;
+  int* d_dig = nullptr;
+  int64_t* d_off = nullptr;
+  double* d_y = nullptr;
+  double* d_pos = nullptr;
+  double* d_T = nullptr;
+  double* d_D = nullptr;
+  double* d_SH = nullptr;
+  double* d_h = nullptr;
+  int* d_status = nullptr;
+  double* d_atol = nullptr;
+  DevCounters* d_cnt = nullptr;
+  int* d_chunk_dig = nullptr;
+  int64_t* d_chunk_beg = nullptr;
+  int64_t* d_chunk_end = nullptr;
+  int* d_dig_chunk0 = nullptr;
+  double* d_partial = nullptr;
+  double* d_mean = nullptr;
+};
+
+static thread_local std::string g_create_err;
+
+static chad_status fail(chad_ctx* c, chad_status s, const std::string& msg) {
+  if (c) c->err = msg; else g_create_err = msg;
+  return s;
+}
+
+static chad_status cuda_fail(chad_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(c, CHAD_E_CUDA, m);
+}
+
+#define CK(ctx, call, what)                                     \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, (what)); \
+  } while (0)
+
+template <class T>
+static cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+static void free_all(chad_ctx* c) {
+  void* ptrs[] = {c->d_dc, c->d_fl, c->d_dig, c->d_off, c->d_y, c->d_pos, c->d_T, c->d_D,
+                  c->d_SH, c->d_h, c->d_status, c->d_atol, c->d_cnt, c->d_chunk_dig,
+                  c->d_chunk_beg, c->d_chunk_end, c->d_dig_chunk0, c->d_partial, c->d_mean};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+extern "C" {
+
+int chad_abi_version(void) { return CHAD_ABI_VERSION; }
+int chad_n_params(void) { return kNumParams; }
+const char* chad_param_name(int i) { return (i >= 0 && i < kNumParams) ? kParamNames[i] : nullptr; }
+
+const char* chad_last_error(const chad_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
+  if (!out) return fail(nullptr, CHAD_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, CHAD_E_INVALID, "cfg is NULL");
+  if (cfg->n_digesters < 1 || cfg->n_digesters > (1 << 20))
+    return fail(nullptr, CHAD_E_INVALID, "n_digesters must be in [1, 2^20]");
+  if (!cfg->n_particles || !cfg->V_liq || !cfg->V_gas || !cfg->params || !cfg->atol)
+    return fail(nullptr, CHAD_E_INVALID, "n_particles, V_liq, V_gas, params and atol are required");
+  if (cfg->precision != CHAD_PREC_FP64 && cfg->precision != CHAD_PREC_MIXED)
+    return fail(nullptr, CHAD_E_INVALID, "precision must be CHAD_PREC_FP64 or CHAD_PREC_MIXED");
+  if (cfg->headspace != CHAD_HEADSPACE_PARTICLE && cfg->headspace != CHAD_HEADSPACE_SHARED)
+    return fail(nullptr, CHAD_E_INVALID, "invalid headspace mode");
+  if (cfg->learned != 0)
+    return fail(nullptr, CHAD_E_INVALID, "learned guesses are not available in this build");
+  if (!(cfg->rtol > 0.0) || !std::isfinite(cfg->rtol))
+    return fail(nullptr, CHAD_E_INVALID, "rtol must be > 0");
+  for (int i = 0; i < NS; ++i)
+    if (!(cfg->atol[i] > 0.0) || !std::isfinite(cfg->atol[i]))
+      return fail(nullptr, CHAD_E_INVALID, "atol entries must be > 0");
+  if (cfg->max_steps_per_interval < 1 || cfg->max_newton_iters < 1 || cfg->fixed_substeps < 0)
+    return fail(nullptr, CHAD_E_INVALID, "max_steps_per_interval, max_newton_iters >= 1, fixed_substeps >= 0");
+
+  chad_ctx* c = new (std::nothrow) chad_ctx();
+  if (!c) return fail(nullptr, CHAD_E_NOMEM, "host allocation failed");
+  c->n_dig = cfg->n_digesters;
+  c->count.resize(c->n_dig);
+  c->offset.resize(c->n_dig + 1);
+  c->offset[0] = 0;
+  for (int d = 0; d < c->n_dig; ++d) {
+    if (cfg->n_particles[d] < 0 || cfg->n_particles[d] > (int64_t(1) << 34)) {
+      delete c;
+      return fail(nullptr, CHAD_E_INVALID, "n_particles out of range");
+    }
+    c->count[d] = cfg->n_particles[d];
+    c->offset[d + 1] = c->offset[d] + c->count[d];
+  }
+  c->N = c->offset[c->n_dig];
+  c->ld = ((c->N + 31) / 32) * 32;
+  if (c->N >= (int64_t(1) << 31)) {
+    delete c;
+    return fail(nullptr, CHAD_E_INVALID, "total particle count must be < 2^31");
+  }
+  c->precision = cfg->precision;
+  c->learned = cfg->learned;
+  c->headspace = cfg->headspace;
+  c->rtol = cfg->rtol;
+  c->max_steps = cfg->max_steps_per_interval;
+  c->max_newton = cfg->max_newton_iters;
+  c->fixed_n = cfg->fixed_substeps;
+  c->stream = (cudaStream_t)cfg->cuda_stream;
+  c->hdc.resize(c->n_dig);
+  c->hfl.resize(c->n_dig);
+  c->loaded.assign(c->n_dig, 0);
+  for (int d = 0; d < c->n_dig; ++d) {
+    const char* why = "";
+    const double Du = cfg->D_uniform ? cfg->D_uniform[d] : 0.0;
+    const double* yin = cfg->y_in ? cfg->y_in + (size_t)d * NS : nullptr;
+    if (!derive_digester(cfg->params + (size_t)d * kNumParams, cfg->V_liq[d], cfg->V_gas[d], Du,
+                         yin, c->hdc[d], &why)) {
+      std::string m = "digester " + std::to_string(d) + ": " + why;
+      delete c;
+      return fail(nullptr, CHAD_E_INVALID, m);
+    }
+    std::memset(&c->hfl[d], 0, sizeof(FlowConst));
+  }
+  // headspace chunks: contiguous ranges never spanning digesters
+  std::vector<int> chunk_dig, dig_chunk0(c->n_dig + 1);
+  std::vector<int64_t> chunk_beg, chunk_end;
+  for (int d = 0; d < c->n_dig; ++d) {
+    dig_chunk0[d] = (int)chunk_dig.size();
+    for (int64_t b = c->offset[d]; b < c->offset[d + 1]; b += kHeadspaceChunk) {
+      chunk_dig.push_back(d);
+      chunk_beg.push_back(b);
+      chunk_end.push_back(std::min(c->offset[d + 1], b + (int64_t)kHeadspaceChunk));
+    }
+  }
+  dig_chunk0[c->n_dig] = (int)chunk_dig.size();
+  c->n_chunks = (int)chunk_dig.size();
+
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  A(dalloc(&c->d_dc, c->n_dig));
+  A(dalloc(&c->d_fl, c->n_dig));
+  A(dalloc(&c->d_dig, c->N));
+  A(dalloc(&c->d_off, c->n_dig + 1));
+  A(dalloc(&c->d_y, (size_t)NS * c->ld));
+  A(dalloc(&c->d_pos, (size_t)3 * c->ld));
+  A(dalloc(&c->d_T, c->ld));
+  A(dalloc(&c->d_D, c->ld));
+  A(dalloc(&c->d_SH, c->ld));
+  A(dalloc(&c->d_h, c->ld));
+  A(dalloc(&c->d_status, c->ld));
+  A(dalloc(&c->d_atol, NS));
+  A(dalloc(&c->d_cnt, 1));
+  A(dalloc(&c->d_chunk_dig, c->n_chunks));
+  A(dalloc(&c->d_chunk_beg, c->n_chunks));
+  A(dalloc(&c->d_chunk_end, c->n_chunks));
+  A(dalloc(&c->d_dig_chunk0, c->n_dig + 1));
+  A(dalloc(&c->d_partial, (size_t)3 * c->n_chunks));
+  A(dalloc(&c->d_mean, (size_t)3 * c->n_dig));
+  if (e != cudaSuccess) {
+    free_all(c);
+    std::string m = std::string("device allocation: ") + cudaGetErrorString(e);
+    delete c;
+    cudaGetLastError();
+    return fail(nullptr, CHAD_E_NOMEM, m);
+  }
+  std::vector<int> dig(c->N > 0 ? c->N : 1);
+  for (int d = 0; d < c->n_dig; ++d)
+    for (int64_t p = c->offset[d]; p < c->offset[d + 1]; ++p) dig[p] = d;
+  A(cudaMemcpy(c->d_dc, c->hdc.data(), sizeof(DigConst) * c->n_dig, cudaMemcpyHostToDevice));
+  A(cudaMemcpy(c->d_fl, c->hfl.data(), sizeof(FlowConst) * c->n_dig, cudaMemcpyHostToDevice));
+  A(cudaMemcpy(c->d_dig, dig.data(), sizeof(int) * (c->N > 0 ? c->N : 1), cudaMemcpyHostToDevice));
+  A(cudaMemcpy(c->d_off, c->offset.data(), sizeof(int64_t) * (c->n_dig + 1), cudaMemcpyHostToDevice));
+  A(cudaMemcpy(c->d_atol, cfg->atol, sizeof(double) * NS, cudaMemcpyHostToDevice));
+  if (c->n_chunks > 0) {
+    A(cudaMemcpy(c->d_chunk_dig, chunk_dig.data(), sizeof(int) * c->n_chunks, cudaMemcpyHostToDevice));
+    A(cudaMemcpy(c->d_chunk_beg, chunk_beg.data(), sizeof(int64_t) * c->n_chunks, cudaMemcpyHostToDevice));
+    A(cudaMemcpy(c->d_chunk_end, chunk_end.data(), sizeof(int64_t) * c->n_chunks, cudaMemcpyHostToDevice));
+  }
+  A(cudaMemcpy(c->d_dig_chunk0, dig_chunk0.data(), sizeof(int) * (c->n_dig + 1), cudaMemcpyHostToDevice));
+  A(cudaMemset(c->d_y, 0, sizeof(double) * NS * c->ld));
+  A(cudaMemset(c->d_pos, 0, sizeof(double) * 3 * c->ld));
+  A(cudaMemset(c->d_status, 0, sizeof(int) * c->ld));
+  A(cudaMemset(c->d_mean, 0, sizeof(double) * 3 * c->n_dig));
+  DevCounters z{0, 0, 0, 0, 0x7fffffff, 0, 0, 0};
+  A(cudaMemcpy(c->d_cnt, &z, sizeof(z), cudaMemcpyHostToDevice));
+  if (e != cudaSuccess) {
+    free_all(c);
+    std::string m = std::string("device setup: ") + cudaGetErrorString(e);
+    delete c;
+    cudaGetLastError();
+    return fail(nullptr, CHAD_E_CUDA, m);
+  }
+  *out = c;
+  return CHAD_OK;
+}
+
+void chad_destroy(chad_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  delete ctx;
+}
+
+static cudaMemcpyKind kind_in(int mem) { return mem == CHAD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+static cudaMemcpyKind kind_out(int mem) { return mem == CHAD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+chad_status chad_load_particles(chad_ctx* c, int digester, int64_t n, const double* pos,
+                                const double* y, const double* T, const double* S_H,
+                                const double* h, int mem) {
+  if (!c) return CHAD_E_INVALID;
+  if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");
+  if (n != c->count[digester]) return fail(c, CHAD_E_INVALID, "n differs from cfg->n_particles[digester]");
+  if (!y && n > 0) return fail(c, CHAD_E_INVALID, "y is required");
+  if (mem != CHAD_MEM_HOST && mem != CHAD_MEM_DEVICE) return fail(c, CHAD_E_INVALID, "mem must be HOST or DEVICE");
+  const int64_t o = c->offset[digester];
+  if (mem == CHAD_MEM_HOST && n > 0) {
+    for (int64_t i = 0; i < (int64_t)NS * n; ++i)
+      if (!std::isfinite(y[i]) || y[i] < 0.0) return fail(c, CHAD_E_INVALID, "y must be finite and >= 0");
+    if (T)
+      for (int64_t i = 0; i < n; ++i)
+        if (!(T[i] > 200.0 && T[i] < 400.0)) return fail(c, CHAD_E_INVALID, "T must be in (200, 400) K");
+  }
+  cudaStream_t s = c->stream;
+  const cudaMemcpyKind k = kind_in(mem);
+  if (n > 0) {
+    for (int i = 0; i < NS; ++i)
+      CK(c, cudaMemcpyAsync(c->d_y + (size_t)i * c->ld + o, y + (size_t)i * n, sizeof(double) * n, k, s), "load y");
+    if (pos) {
+      for (int i = 0; i < 3; ++i)
+        CK(c, cudaMemcpyAsync(c->d_pos + (size_t)i * c->ld + o, pos + (size_t)i * n, sizeof(double) * n, k, s), "load pos");
+    } else {
+      for (int i = 0; i < 3; ++i)
+        CK(c, cudaMemsetAsync(c->d_pos + (size_t)i * c->ld + o, 0, sizeof(double) * n, s), "zero pos");
+    }
+    std::vector<double> tmp;
+    auto fill = [&](double* dst, const double* src, double dflt) -> cudaError_t {
+      if (src) return cudaMemcpyAsync(dst + o, src, sizeof(double) * n, k, s);
+      tmp.assign(n, dflt);
+      cudaError_t r = cudaMemcpyAsync(dst + o, tmp.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+      if (r == cudaSuccess) r = cudaStreamSynchronize(s);
+      return r;
+    };
+    CK(c, fill(c->d_T, T, 308.15), "load T");
+    CK(c, fill(c->d_SH, S_H, 1e-7), "load S_H");
+    CK(c, fill(c->d_h, h, 0.0), "load h");
+    CK(c, fill(c->d_D, nullptr, c->hdc[digester].D_uniform), "init D");
+    CK(c, cudaMemsetAsync(c->d_status + o, 0, sizeof(int) * n, s), "reset status");
+    if (mem == CHAD_MEM_HOST) CK(c, cudaStreamSynchronize(s), "load sync");
+  }
+  c->loaded[digester] = 1;
+  return CHAD_OK;
+}
+
+chad_status chad_set_flow(chad_ctx* c, int digester, const chad_flow* f) {
+  if (!c) return CHAD_E_INVALID;
+  if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");
+  if (!f) return fail(c, CHAD_E_INVALID, "flow is NULL");
+  FlowConst fc;
+  std::memset(&fc, 0, sizeof(fc));
+  if (f->has_flow) {
+    if (!(f->R > 0.0) || !(f->H > 0.0) || !(f->sigma >= 0.0) || !(f->q_in >= 0.0) ||
+        !std::isfinite(f->U) || !std::isfinite(f->slab_zmin) || !(f->slab_zmin < f->H))
+      return fail(c, CHAD_E_INVALID, "flow: need R, H > 0, sigma, q_in >= 0, finite U, slab_zmin < H");
+    fc.has_flow = 1;
+    fc.R = f->R;
+    fc.H = f->H;
+    fc.slab_zmin = f->slab_zmin;
+    fc.D_slab = f->q_in / (M_PI * f->R * f->R * (f->H - f->slab_zmin));
+    fc.seed = f->seed;
+    fc.U = f->U;
+    fc.sigma = f->sigma;
+    fc.cw = 1.0;  // rotation and noise amplitude are expanded per dt in chad_step
+    fc.sw = 0.0;
+    fc.amp = 0.0;
+    fc.n_sub = 0;
+    c->hfl[digester] = fc;
+    if (f->y_in) {
+      for (int i = 0; i < NS; ++i) {
+        if (!std::isfinite(f->y_in[i])) return fail(c, CHAD_E_INVALID, "flow y_in must be finite");
+        c->hdc[digester].y_in[i] = f->y_in[i];
+      }
+      CK(c, cudaMemcpyAsync(c->d_dc + digester, &c->hdc[digester], sizeof(DigConst),
+                            cudaMemcpyHostToDevice, c->stream), "update influent");
+      CK(c, cudaStreamSynchronize(c->stream), "flow sync");
+    }
+  } else {
+    c->hfl[digester] = fc;
+  }
+  c->any_flow = false;
+  for (int d = 0; d < c->n_dig; ++d) c->any_flow |= (c->hfl[d].has_flow != 0);
+  return CHAD_OK;
+}
+
+chad_status chad_step(chad_ctx* c, double dt_coupling_s, int n_intervals) {
+  if (!c) return CHAD_E_INVALID;
+  if (!(dt_coupling_s > 0.0) || !std::isfinite(dt_coupling_s) || n_intervals < 0)
+    return fail(c, CHAD_E_INVALID, "dt_coupling_s must be > 0 and n_intervals >= 0");
+  for (int d = 0; d < c->n_dig; ++d)
+    if (!c->loaded[d]) return fail(c, CHAD_E_STATE, "every digester must be loaded before chad_step");
+  if (n_intervals == 0 || c->N == 0) return CHAD_OK;
+  cudaStream_t s = c->stream;
+  // expand the flow constants for this interval length (1-s sub-steps)
+  if (c->any_flow) {
+    int n_sub = (int)std::lround(dt_coupling_s);
+    if (n_sub < 1) n_sub = 1;
+    const double dsub = dt_coupling_s / n_sub;
+    std::vector<FlowConst> fl = c->hfl;
+    for (int d = 0; d < c->n_dig; ++d) {
+      if (!fl[d].has_flow) continue;
+      const double w = fl[d].U / fl[d].R;
+      fl[d].cw = std::cos(w * dsub);
+      fl[d].sw = std::sin(w * dsub);
+      fl[d].amp = fl[d].sigma * dsub;
+      fl[d].n_sub = n_sub;
+    }
+    CK(c, cudaMemcpyAsync(c->d_fl, fl.data(), sizeof(FlowConst) * c->n_dig, cudaMemcpyHostToDevice, s), "flow upload");
+    CK(c, cudaStreamSynchronize(s), "flow upload sync");
+  }
+  StepArgs a;
+  a.n = c->N;
+  a.ld = c->ld;
+  a.dig = c->d_dig;
+  a.dc = c->d_dc;
+  a.y = c->d_y;
+  a.T = c->d_T;
+  a.D = c->d_D;
+  a.SH = c->d_SH;
+  a.h = c->d_h;
+  a.status = c->d_status;
+  a.atol = c->d_atol;
+  a.rtol = c->rtol;
+  a.dt_days = dt_coupling_s / 86400.0;
+  a.max_steps = c->max_steps;
+  a.max_newton = c->max_newton;
+  a.fixed_n = c->fixed_n;
+  a.counters = c->d_cnt;
+  AdvectArgs v;
+  v.n = c->N;
+  v.ld = c->ld;
+  v.dig = c->d_dig;
+  v.dig_offset = c->d_off;
+  v.fl = c->d_fl;
+  v.pos = c->d_pos;
+  v.D = c->d_D;
+  HeadspaceArgs hs;
+  hs.ld = c->ld;
+  hs.n_chunks = c->n_chunks;
+  hs.chunk_dig = c->d_chunk_dig;
+  hs.chunk_begin = c->d_chunk_beg;
+  hs.chunk_end = c->d_chunk_end;
+  hs.dig_offset = c->d_off;
+  hs.dig_chunk0 = c->d_dig_chunk0;
+  hs.n_dig = c->n_dig;
+  hs.y = c->d_y;
+  hs.partial = c->d_partial;
+  hs.mean = c->d_mean;
+  hs.dig = c->d_dig;
+  hs.n = c->N;
+  for (int it = 0; it < n_intervals; ++it) {
+    if (c->any_flow) {
+      v.interval = c->interval;
+      CK(c, launch_advect(v, s), "advect launch");
+    }
+    CK(c, launch_integrate(a, c->precision == CHAD_PREC_MIXED, 128, s), "integrate launch");
+    if (c->headspace == CHAD_HEADSPACE_SHARED) CK(c, launch_headspace(hs, s), "headspace launch");
+    c->interval++;
+    c->intervals++;
+    c->sim_days += a.dt_days * (double)c->N;
+  }
+  return CHAD_OK;
+}
+
+chad_status chad_synchronize(chad_ctx* c) {
+  if (!c) return CHAD_E_INVALID;
+  CK(c, cudaStreamSynchronize(c->stream), "synchronize");
+  CK(c, cudaGetLastError(), "kernel");
+  return CHAD_OK;
+}
+
+chad_status chad_read_states(chad_ctx* c, int digester, double* y, double* pos, double* S_H,
+                             double* h, int32_t* status, chad_stats* stats, int mem) {
+  if (!c) return CHAD_E_INVALID;
+  if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");
+  if (!c->loaded[digester]) return fail(c, CHAD_E_STATE, "digester not loaded");
+  if (mem != CHAD_MEM_HOST && mem != CHAD_MEM_DEVICE) return fail(c, CHAD_E_INVALID, "mem must be HOST or DEVICE");
+  cudaStream_t s = c->stream;
+  const int64_t o = c->offset[digester], n = c->count[digester];
+  const cudaMemcpyKind k = kind_out(mem);
+  CK(c, cudaStreamSynchronize(s), "read sync");
+  CK(c, cudaGetLastError(), "kernel");
+  if (n > 0) {
+    if (y)
+      for (int i = 0; i < NS; ++i)
+        CK(c, cudaMemcpyAsync(y + (size_t)i * n, c->d_y + (size_t)i * c->ld + o, sizeof(double) * n, k, s), "read y");
+    if (pos)
+      for (int i = 0; i < 3; ++i)
+        CK(c, cudaMemcpyAsync(pos + (size_t)i * n, c->d_pos + (size_t)i * c->ld + o, sizeof(double) * n, k, s), "read pos");
+    if (S_H) CK(c, cudaMemcpyAsync(S_H, c->d_SH + o, sizeof(double) * n, k, s), "read S_H");
+    if (h) CK(c, cudaMemcpyAsync(h, c->d_h + o, sizeof(double) * n, k, s), "read h");
+  }
+  std::vector<int32_t> st(n > 0 ? n : 1);
+  if (n > 0) CK(c, cudaMemcpyAsync(st.data(), c->d_status + o, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s), "read status");
+  DevCounters dc;
+  CK(c, cudaMemcpyAsync(&dc, c->d_cnt, sizeof(dc), cudaMemcpyDeviceToHost, s), "read counters");
+  CK(c, cudaStreamSynchronize(s), "read sync");
+  int64_t failed = 0;
+  for (int64_t i = 0; i < n; ++i) failed += (st[i] != 0);
+  if (status && n > 0) {
+    if (mem == CHAD_MEM_DEVICE)
+      CK(c, cudaMemcpy(status, c->d_status + o, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice), "read status");
+    else
+      std::memcpy(status, st.data(), sizeof(int32_t) * n);
+  }
+  if (stats) {
+    stats->accepted_steps = (int64_t)dc.accepted;
+    stats->rejected_steps = (int64_t)dc.rejected;
+    stats->newton_iters = (int64_t)dc.newton_iters;
+    stats->newton_fallbacks = (int64_t)dc.newton_fallbacks;
+    stats->min_steps = dc.min_steps == 0x7fffffff ? 0 : dc.min_steps;
+    stats->max_steps = dc.max_steps;
+    stats->failed_particles = failed;
+    stats->mlp_redo = 0;
+    stats->intervals = c->intervals;
+    stats->sim_days = c->sim_days;
+    DevCounters z{0, 0, 0, 0, 0x7fffffff, 0, 0, 0};
+    CK(c, cudaMemcpy(c->d_cnt, &z, sizeof(z), cudaMemcpyHostToDevice), "reset counters");
+    c->intervals = 0;
+    c->sim_days = 0.0;
+  }
+  return failed ? fail(c, CHAD_E_PARTICLE, std::to_string(failed) + " particle(s) with status != 0")
+                : CHAD_OK;
+}
+
+}  // extern "C"

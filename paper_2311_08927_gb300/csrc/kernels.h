@@ -1,0 +1,72 @@
+// Internal launch interface of the CUDA kernels (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "model.h"
+
+namespace chad {
+
+// Per-particle status bits (same values as the public CHAD_P_* bits)
+enum : int { ST_NEWTON = 1, ST_STEPS = 2, ST_HMIN = 4, ST_NEG = 8, ST_NAN = 16 };
+
+// Device counters accumulated by the integrator (reset by the host)
+struct DevCounters {
+  unsigned long long accepted, rejected, newton_iters, newton_fallbacks;
+  int min_steps, max_steps, pad0, pad1;
+};
+
+struct StepArgs {
+  int64_t n;            // particles
+  int64_t ld;           // leading dimension of the SoA arrays
+  const int* dig;       // [n] digester of each particle
+  const DigConst* dc;   // [n_dig]
+  double* y;            // [NS][ld]
+  const double* T;      // [n] K
+  const double* D;      // [n] dilution rate 1/d for this interval
+  double* SH;           // [n] running S_H (guess in, root out)
+  double* h;            // [n] next step size (days)
+  int* status;          // [n] OR-accumulated bits
+  const double* atol;   // [NS]
+  double rtol;
+  double dt_days;
+  int max_steps;
+  int max_newton;
+  int fixed_n;          // 0: adaptive
+  DevCounters* counters;
+};
+
+struct AdvectArgs {
+  int64_t n, ld;
+  const int* dig;
+  const int64_t* dig_offset;  // [n_dig + 1]
+  const FlowConst* fl;
+  double* pos;                // [3][ld]
+  double* D;                  // [n] written for particles of digesters with flow
+  uint64_t interval;          // global interval index (noise counter)
+};
+
+struct HeadspaceArgs {
+  int64_t ld;
+  int n_chunks;
+  const int* chunk_dig;       // [n_chunks]
+  const int64_t* chunk_begin; // [n_chunks]
+  const int64_t* chunk_end;   // [n_chunks]
+  const int64_t* dig_offset;  // [n_dig + 1]
+  const int* dig_chunk0;      // [n_dig + 1] first chunk of each digester
+  int n_dig;
+  double* y;                  // [NS][ld]
+  double* partial;            // [n_chunks][3] scratch
+  double* mean;               // [n_dig][3] scratch
+  const int* dig;             // [n]
+  int64_t n;
+};
+
+cudaError_t launch_integrate(const StepArgs& a, bool mixed, int block, cudaStream_t s);
+cudaError_t launch_advect(const AdvectArgs& a, cudaStream_t s);
+cudaError_t launch_headspace(const HeadspaceArgs& a, cudaStream_t s);
+
+constexpr int kHeadspaceChunk = 4096;  // particles per partial sum
+
+}  // namespace chad

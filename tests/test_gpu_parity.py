@@ -1,0 +1,258 @@
+"""GPU (CUDA, through the C ABI) versus the CPU oracle on identical seeded inputs.
+
+Tolerances: the FP64 path must match the oracle to max relative error 1e-9
+(fixed steps and tight adaptive tolerance, where both run the same
+arithmetic); the production forms (FP64 at rtol 1e-6 and the mixed FP32/FP64
+form) must stay within 1e-4 of the oracle run at rtol 1e-10.  The relative
+error of species i is |a - b| / max(|b|, 1e-12 * max_p |b_i|), so species
+near zero do not dominate.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2311_08927_gb300 import chad as CH
+from paper_2311_08927_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_08927_gb300 import build
+    build.build()
+    CH.lib()
+
+
+def relerr(a, b):
+    floor = 1e-12 * np.max(np.abs(b), axis=1, keepdims=True)
+    return np.abs(a - b) / np.maximum(np.abs(b), floor + 1e-300)
+
+
+def subset(pop, idx):
+    """Population made of the given particles (single digester populations)."""
+    idx = np.asarray(idx)
+    dg = [I.Digester(n=len(idx), V_liq=pop.digesters[0].V_liq, V_gas=pop.digesters[0].V_gas,
+                     params=pop.digesters[0].params, D=pop.digesters[0].D,
+                     flow=pop.digesters[0].flow, y_in=pop.digesters[0].y_in)]
+    return I.Population(dg, pop.y[:, idx].copy(), pop.T[idx].copy(), pop.pos[:, idx].copy(),
+                        pop.shared_headspace)
+
+
+def gpu_run(pop, dt, n, **kw):
+    sim = CH.Simulator(pop, **kw)
+    sim.load()
+    sim.step(dt, n)
+    out = sim.read()
+    sim.close()
+    return out
+
+
+def oracle_run(pop, dt, n, rtol=1e-6, atol=None, fixed_n=0):
+    return O.run(pop, dt, n, rtol=rtol, atol=atol, fixed_n=fixed_n)
+
+
+# ------------------------------------------------------------ Gate A: same arithmetic
+def test_fixed_step_fp64_matches_oracle():
+    pop = I.config_population(1, n=300)          # ragged: 2 blocks of 128 + 44
+    g = gpu_run(pop, 60.0, 10, fixed_substeps=4)
+    o = oracle_run(pop, 60.0, 10, fixed_n=4)
+    assert np.all(g["status"] == 0)
+    e = relerr(g["y"], o["y"])
+    assert e.max() < 1e-9, e.max()
+    assert np.max(np.abs(g["S_H"] / o["S_H"] - 1)) < 1e-9
+
+
+def test_fixed_step_fp64_heterogeneous_temperature_and_slugs():
+    pop = I.config_population(3, n=4000)
+    idx = np.concatenate([pop.slugs[:40], np.setdiff1d(np.arange(4000), pop.slugs)[:90]])
+    sp = subset(pop, idx)
+    g = gpu_run(sp, 60.0, 5, fixed_substeps=6)
+    o = oracle_run(sp, 60.0, 5, fixed_n=6)
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+
+
+# ------------------------------------------------------------ Gate B: adaptive, tight
+def test_adaptive_tight_tolerance_fp64_matches_oracle():
+    pop = I.config_population(3, n=2000)
+    idx = np.concatenate([pop.slugs[:16], np.setdiff1d(np.arange(2000), pop.slugs)[:48]])
+    sp = subset(pop, idx)
+    atol = I.atol_vector(1e-13)
+    g = gpu_run(sp, 60.0, 4, rtol=1e-10, atol=atol)
+    o = oracle_run(sp, 60.0, 4, rtol=1e-10, atol=atol)
+    assert np.all(g["status"] == 0) and np.all(o["status"] == 0)
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+    # same step sequences (a round-off accept/reject flip would show here)
+    assert abs(g["stats"]["accepted_steps"] - o["stats"][0]) <= 2
+
+
+def test_production_fp64_same_tolerance_tracks_oracle():
+    pop = I.config_population(1, n=256)
+    g = gpu_run(pop, 60.0, 30, rtol=1e-6)
+    o = oracle_run(pop, 60.0, 30, rtol=1e-6)
+    e = relerr(g["y"], o["y"])
+    assert np.median(e) < 1e-10 and e.max() < 1e-5
+    assert np.max(np.abs(g["h"] / o["h"] - 1)) < 1e-6 or np.median(np.abs(g["h"] / o["h"] - 1)) < 1e-9
+
+
+# ------------------------------------------------------------ Gate C: production forms
+@pytest.mark.parametrize("precision", [CH.PREC_FP64, CH.PREC_MIXED])
+def test_production_forms_within_1e4_of_tight_oracle(precision):
+    pop = I.config_population(3, n=3000)
+    idx = np.concatenate([pop.slugs[:24], np.setdiff1d(np.arange(3000), pop.slugs)[:72]])
+    sp = subset(pop, idx)
+    g = gpu_run(sp, 60.0, 20, rtol=1e-6, precision=precision)
+    o = oracle_run(sp, 60.0, 20, rtol=1e-10, atol=I.atol_vector(1e-13))
+    assert np.all(g["status"] == 0)
+    e = relerr(g["y"], o["y"])
+    assert e.max() < 1e-4, (e.max(), I.STATE_NAMES[int(np.argmax(e.max(axis=1)))])
+
+
+# ------------------------------------------------------------ flow, headspace, digesters
+def test_flow_positions_bitwise_and_shared_headspace_parity():
+    pop = I.config_population(2, n=1500)
+    g = gpu_run(pop, 60.0, 4, fixed_substeps=3)
+    o = oracle_run(pop, 60.0, 4, fixed_n=3)
+    assert np.array_equal(g["pos"], o["pos"])
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+    gas = g["y"][26:29]
+    assert np.all(gas == gas[:, :1])  # one headspace per digester
+    # some particles sat in the inlet slab and were diluted
+    assert np.any(pop.pos[2] >= pop.digesters[0].flow["slab_zmin"])
+
+
+def test_many_digesters_parity():
+    pop = I.config_population(5, n=2500)
+    assert len(pop.digesters) == 64
+    g = gpu_run(pop, 60.0, 3, fixed_substeps=2)
+    o = oracle_run(pop, 60.0, 3, fixed_n=2)
+    assert np.array_equal(g["pos"], o["pos"])
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+    for d in range(64):
+        a, b = pop.offsets[d], pop.offsets[d + 1]
+        gas = g["y"][26:29, a:b]
+        assert np.all(gas == gas[:, :1])
+
+
+def test_uniform_population_reduces_to_single_cstr():
+    """Sec. 3.1 / 4.2: identical particles with a shared headspace equal the CSTR."""
+    n = 777
+    base = I.x_ss()
+    y = np.repeat(base[:, None], n, axis=1)
+    D = I.TABLE1["Q"] / I.TABLE1["V_liq"]
+    pop = I.Population([I.Digester(n=n, D=D)], y, np.full(n, I.T_OP), np.zeros((3, n)), True)
+    g = gpu_run(pop, 60.0, 10, rtol=1e-8, atol=I.atol_vector(1e-11))
+    assert np.all(g["y"] == g["y"][:, :1])
+    yc, SH, h = base.copy(), 1e-7, 0.0
+    for _ in range(10):
+        yc, SH, h, st, _ = O.integrate(I.default_params(), I.T_OP, yc, 60.0 / 86400, rtol=1e-8,
+                                       atol=I.atol_vector(1e-11), y_in=I.influent(), D=D, SH=SH, h=h)
+    assert np.max(np.abs(g["y"][:, 0] - yc) / np.abs(yc)) < 1e-9
+
+
+def test_rerun_is_bitwise_deterministic():
+    pop = I.config_population(2, n=2000)
+    a = gpu_run(pop, 60.0, 3)
+    b = gpu_run(pop, 60.0, 3)
+    assert np.array_equal(a["y"], b["y"]) and np.array_equal(a["pos"], b["pos"])
+
+
+# ------------------------------------------------------------ full size, sampled
+@pytest.mark.parametrize("precision,tol", [(CH.PREC_FP64, 1e-9), (CH.PREC_MIXED, 1e-4)])
+def test_full_size_1M_sampled(precision, tol):
+    """The metric workload (1M particles, slugs, T spread) in the benchmark's
+    launch configuration; a seeded sample is recomputed particle by particle
+    by the oracle (FP64 at the same rtol / the tight oracle for mixed)."""
+    pop = I.config_population(3)
+    sim = CH.Simulator(pop, precision=precision, rtol=1e-6)
+    sim.load()
+    sim.step(60.0, 2)
+    g = sim.read()
+    sim.close()
+    assert np.all(g["status"] == 0)
+    rng = np.random.default_rng(99)
+    idx = np.sort(np.concatenate([rng.choice(pop.slugs, 16, replace=False),
+                                  rng.choice(pop.n, 48, replace=False), [0, pop.n - 1]]))
+    sp = subset(pop, idx)
+    if precision == CH.PREC_FP64:
+        o = oracle_run(sp, 60.0, 2, rtol=1e-6)
+        e = relerr(g["y"][:, idx], o["y"])
+        assert np.median(e) < tol and e.max() < 1e-5
+    else:
+        o = oracle_run(sp, 60.0, 2, rtol=1e-10, atol=I.atol_vector(1e-13))
+        assert relerr(g["y"][:, idx], o["y"]).max() < tol
+
+
+# ------------------------------------------------------------ failure handling
+def test_step_limit_sets_status_without_faulting():
+    pop = I.config_population(1, n=64)
+    sim = CH.Simulator(pop, max_steps=1)
+    sim.load()
+    sim.step(60.0, 1)
+    out = sim.read()
+    assert np.all(out["status"] & CH.P_STEPS)
+    code = CH.chad_read_states(sim.ctx, 0, status=np.zeros(64, dtype=np.int32))
+    assert code == 5  # CHAD_E_PARTICLE
+    sim.close()
+
+
+def test_newton_iteration_limit_falls_back_to_bisection():
+    pop = I.config_population(1, n=64)
+    g = gpu_run(pop, 60.0, 2, max_newton=1, fixed_substeps=2)
+    o = oracle_run(pop, 60.0, 2, fixed_n=2)
+    assert np.all(g["status"] == 0)
+    assert g["stats"]["newton_fallbacks"] > 0
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+
+
+def test_call_order_and_argument_errors():
+    pop = I.config_population(1, n=16)
+    sim = CH.Simulator(pop)
+    with pytest.raises(CH.ChadError) as ei:
+        sim.step(60.0, 1)                              # not loaded
+    assert ei.value.code == 4
+    bad = pop.y.copy()
+    bad[3, 5] = -1.0
+    with pytest.raises(CH.ChadError) as ei:
+        CH.chad_load_particles(sim.ctx, 0, 16, pop.pos, np.ascontiguousarray(bad), pop.T)
+    assert ei.value.code == 1
+    with pytest.raises(CH.ChadError):
+        CH.chad_load_particles(sim.ctx, 0, 15, None, np.ascontiguousarray(pop.y[:, :15]))
+    with pytest.raises(CH.ChadError):
+        CH.chad_load_particles(sim.ctx, 1, 16, None, pop.y)
+    sim.load()
+    with pytest.raises(CH.ChadError):
+        sim.step(-1.0, 1)
+    sim.step(60.0, 0)
+    sim.close()
+
+
+def test_empty_digester_and_single_particle():
+    y1 = I.x_ss()[:, None].copy()
+    dg = [I.Digester(n=0), I.Digester(n=1)]
+    pop = I.Population(dg, y1, np.array([I.T_OP]), np.zeros((3, 1)), False)
+    g = gpu_run(pop, 60.0, 3, fixed_substeps=2)
+    o = oracle_run(pop, 60.0, 3, fixed_n=2)
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+
+
+def test_device_buffers_through_torch():
+    torch = pytest.importorskip("torch")
+    pop = I.config_population(1, n=100)
+    sim = CH.Simulator(pop)
+    y = torch.from_numpy(np.ascontiguousarray(pop.y)).cuda()
+    T = torch.from_numpy(np.ascontiguousarray(pop.T)).cuda()
+    CH.chad_load_particles(sim.ctx, 0, 100, None, y, T)
+    sim.step(60.0, 2)
+    out = torch.empty_like(y)
+    st = torch.zeros(100, dtype=torch.int32, device="cuda")
+    code = CH.chad_read_states(sim.ctx, 0, y=out, status=st)
+    sim.close()
+    assert code == 0
+    ref = gpu_run(pop, 60.0, 2)
+    assert np.array_equal(out.cpu().numpy(), ref["y"])

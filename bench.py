@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark: particle-days simulated per second on the 1M-particle workload.
+
+One step = one 60-s coupling interval of the whole hot path over the
+1,000,000-particle heterogeneous-stiffness population (5 % substrate slugs,
+per-particle temperature 303.15-313.15 K, per-particle headspace, no flow),
+started from the seeded lognormal perturbation of the CSTR steady state.
+Inputs stay resident in HBM (29 x 8 B x 1M = 232 MB of state > 129 MB L2).
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank integrates its own
+1M-particle population (seed offset by rank; particles are independent, so
+there is no data-path collective) and the slowest rank's time is reported.
+
+--impl reference times the CPU oracle (FP64, all host cores) on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "adm1_particles_1M_heterogeneous"
+METRIC = "particle-days simulated per second (1M particles, 60-s coupling intervals)"
+UNIT = "particle-days/s"
+DT_S = 60.0
+N_PARTICLES = 1_000_000
+STATE_BYTES = 29 * 8
+
+
+# --------------------------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device="cpu") -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_seed_offset(rank: int) -> int:
+    """Weak scaling: each rank owns an independent 1M-particle population."""
+    return 1000 * rank
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# --------------------------------------------------------------------------- algorithmic work
+def fp64_flops_per_attempt(precision: int) -> float:
+    """Algorithmic FP64 flops of one W-method step attempt on n = 29 states.
+
+    Plain form: W = I - g J (2n^2), dense LU with partial pivoting
+    (sum_k [(n-k-1) multipliers + 2 (n-k-1)^2 updates] + n reciprocals),
+    3 triangular solve pairs (2n^2 - n + n each), stage combinations (~12n).
+    Mixed form: FP64 part only -- 3 refinement residuals (2n^2 + 3n each)
+    and the stage combinations; the FP32 LU and solves are not counted.
+    Rate evaluations, Jacobian assembly and the Eq. 7 Newton are excluded
+    from both (conservative: achieved rates are lower bounds)."""
+    n = 29
+    lu = sum((n - k - 1) + 2 * (n - k - 1) ** 2 for k in range(n)) + n
+    solves = 3 * (2 * n * n)
+    stage = 12 * n
+    if precision == 0:
+        return 2 * n * n + lu + solves + stage
+    return 3 * (2 * n * n + 3 * n) + stage
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args, ws, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    dist = init_dist(ws, "nccl")
+    from paper_2311_08927_gb300 import build as B
+    B.build()
+    from paper_2311_08927_gb300 import chad as CH
+    from paper_2311_08927_gb300 import inputs as I
+
+    pop = I.config_population(3, n=args.particles, seed_offset=shard_seed_offset(rank))
+    N = pop.n
+    dt_days = DT_S / 86400.0
+    peak64 = CH.probe_alu_peak(True)
+    peak32 = CH.probe_alu_peak(False)
+    stream = torch.cuda.Stream()
+
+    def arm(precision):
+        sim = CH.Simulator(pop, precision=precision, rtol=1e-6, stream=stream.cuda_stream)
+        sim.load()
+        sim.step(DT_S, args.warmup)
+        CH.chad_synchronize(sim.ctx)
+        variant, tune_ms = CH.chad_autotune(sim.ctx, DT_S)
+        sim.read()  # resets the counters
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        barrier(dist, local)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            ev[0].record(stream)
+            for k in range(args.steps):
+                sim.step(DT_S, 1)
+                ev[k + 1].record(stream)
+            torch.cuda.synchronize()
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+        total_ms = ev[0].elapsed_time(ev[-1])
+        total_ms = max_over_ranks(dist, total_ms, f"cuda:{local}")
+        out = sim.read()
+        st = out["stats"]
+        attempts = st["accepted_steps"] + st["rejected_steps"]
+        sim.close()
+        launch_ms = statistics.mean(per)
+        achieved = fp64_flops_per_attempt(precision) * attempts / args.steps / (launch_ms * 1e-3) / 1e12
+        return dict(total_ms=total_ms, per_ms=per, launch_ms=launch_ms, stats=st,
+                    variant=variant, tune_ms=[float(x) for x in tune_ms],
+                    attempts=attempts, failed=int((out["status"] != 0).sum()),
+                    clocks=clk.summary(), achieved_tflops=achieved,
+                    y_final=out["y"])
+
+    forms = {}
+    for name, prec in (("mixed", CH.PREC_MIXED), ("fp64", CH.PREC_FP64)):
+        if args.form in (name, "both"):
+            forms[name] = arm(prec)
+    head = "mixed" if "mixed" in forms else "fp64"
+    H = forms[head]
+    value = ws * N * dt_days * args.steps / (H["total_ms"] * 1e-3)
+
+    # ---------------- e2e: host buffers through the C ABI, copies in the timed region
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        prec = CH.PREC_MIXED if head == "mixed" else CH.PREC_FP64
+        sim = CH.Simulator(pop, precision=prec, rtol=1e-6, stream=stream.cuda_stream)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        y_h, T_h, SH_h, h_h = pin(pop.y), pin(pop.T), pin(np.full(N, 1e-7)), pin(np.zeros(N))
+        st_h = pin(np.zeros(N, dtype=np.int32))
+        CH.chad_load_particles(sim.ctx, 0, N, None, y_h, T_h, SH_h, h_h)
+        sim.step(DT_S, args.warmup)
+        CH.chad_read_states(sim.ctx, 0, y=y_h, S_H=SH_h, h=h_h, status=st_h)
+        ksteps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            CH.chad_load_particles(sim.ctx, 0, N, None, y_h, T_h, SH_h, h_h)
+            sim.step(DT_S, 1)
+            CH.chad_read_states(sim.ctx, 0, y=y_h, S_H=SH_h, h=h_h, status=st_h)
+        t1 = time.perf_counter()
+        sim.close()
+        h2d = N * (STATE_BYTES + 3 * 8)
+        d2h = N * (STATE_BYTES + 2 * 8 + 4)
+        e2e = {"value": N * dt_days * ksteps / (t1 - t0), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ksteps}
+
+    # ---------------- CPU baseline: the oracle on a bounded sample, same intervals
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(pop, args.warmup, min(args.steps, 10), args.cpu_seconds)
+
+    if rank != 0:
+        return None
+    fr = H["clocks"]
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": H["total_ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if N == N_PARTICLES else f"{WORKLOAD}_n{N}",
+                   "particles_per_gpu": N, "coupling_interval_s": DT_S,
+                   "form": head + (" (FP32 Jacobian/LU + FP64 refinement)" if head == "mixed" else ""),
+                   "learned_guesses": False, "rtol": 1e-6, "slug_fraction": 0.05,
+                   "T_range_K": [303.15, 313.15], "l2": "inputs larger than L2 (232 MB state)",
+                   "parallelism": f"particles sharded, {ws} independent populations"},
+        "roofline": {"bound": "alu", "achieved": H["achieved_tflops"], "peak": peak64,
+                     "unit": "TFLOP/s", "frac": H["achieved_tflops"] / peak64, "traffic": None,
+                     "kernel": "integrate_kernel", "peak_source": "measured FP64 DFMA chains (chad_probe_alu_peak)",
+                     "flops_per_attempt": fp64_flops_per_attempt(1 if head == "mixed" else 0),
+                     "attempts_per_step": H["attempts"] / args.steps},
+        "peaks_measured": {"fp64_tflops": peak64, "fp32_tflops": peak32},
+        "clocks": fr,
+        "gpu_launches": args.steps,
+        "steps_per_particle_interval": H["stats"]["accepted_steps"] / (N * args.steps),
+        "rejected_per_particle_interval": H["stats"]["rejected_steps"] / (N * args.steps),
+        "failed_particles": H["failed"],
+        "kernel_variant": H["variant"], "autotune_ms": H["tune_ms"],
+        "pivot_rejects_per_step": H["stats"]["pivot_rejects"] / args.steps,
+        "graph_per_interval": True,
+    }
+    if "fp64" in forms and head != "fp64":
+        F = forms["fp64"]
+        res["plain_fp64"] = {
+            "value": ws * N * dt_days * args.steps / (F["total_ms"] * 1e-3),
+            "ms_per_step": F["total_ms"] / args.steps,
+            "roofline": {"bound": "alu", "achieved": F["achieved_tflops"], "peak": peak64,
+                         "unit": "TFLOP/s", "frac": F["achieved_tflops"] / peak64,
+                         "flops_per_attempt": fp64_flops_per_attempt(0)},
+            "steps_per_particle_interval": F["stats"]["accepted_steps"] / (N * args.steps),
+            "clocks": F["clocks"],
+        }
+        d = np.abs(H["y_final"] - F["y_final"]) / np.maximum(
+            np.abs(F["y_final"]), 1e-12 * np.abs(F["y_final"]).max(axis=1, keepdims=True))
+        res["mixed_vs_fp64_max_rel"] = float(d.max())
+    if e2e:
+        res["e2e"] = e2e
+    if cpu:
+        res["cpu_baseline"] = cpu
+    return res
+
+
+def _oracle_sample(pop, n_s, seed=7):
+    from paper_2311_08927_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(pop.n, n_s, replace=False))
+    return I.Population([I.Digester(n=n_s)], pop.y[:, idx].copy(), pop.T[idx].copy(),
+                        np.zeros((3, n_s)), False)
+
+
+def _calibrate_sample(pop, intervals, budget_s, cores):
+    """Sample size for about budget_s seconds of oracle work over `intervals`."""
+    import oracle as O
+    n_cal = 64 * max(1, cores // 4)
+    sub = _oracle_sample(pop, n_cal, seed=11)
+    t0 = time.perf_counter()
+    O.run(sub, DT_S, min(intervals, 3), rtol=1e-6, n_threads=cores)
+    per = (time.perf_counter() - t0) / (n_cal * min(intervals, 3))
+    return int(max(128, min(50_000, budget_s / max(per, 1e-9) / intervals)))
+
+
+def cpu_baseline(pop, warmup, k, budget_s):
+    """The oracle as it stands (FP64, std::thread equal chunks over all host
+    cores) on a seeded sample of the workload, over the same intervals."""
+    import oracle as O
+    from paper_2311_08927_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    n_s = _calibrate_sample(pop, warmup + k, budget_s, cores)
+    sub = _oracle_sample(pop, n_s)
+    r = O.run(sub, DT_S, warmup, rtol=1e-6, n_threads=cores)
+    sub2 = I.Population(sub.digesters, r["y"], sub.T, sub.pos, False)
+    t0 = time.perf_counter()
+    O.run(sub2, DT_S, k, interval0=warmup, rtol=1e-6, SH=r["S_H"], h=r["h"], n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_s * k * DT_S / 86400.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_s} seeded particles of the 1M workload, intervals {warmup}..{warmup + k - 1} "
+                      f"(after {warmup} untimed), rtol 1e-6, {dt:.1f} s"}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args, ws, rank):
+    dist = init_dist(ws, "gloo")
+    if rank != 0:
+        barrier(dist)
+        return None
+    from paper_2311_08927_gb300 import inputs as I
+    import oracle as O
+    pop = I.config_population(3)
+    cores = os.cpu_count() or 1
+    n_s = _calibrate_sample(pop, args.warmup + args.steps, 4 * args.cpu_seconds, cores)
+    sub = _oracle_sample(pop, n_s)
+    r = O.run(sub, DT_S, args.warmup, rtol=1e-6, n_threads=cores)
+    y, SH, h = r["y"], r["S_H"], r["h"]
+    times = []
+    for k in range(args.steps):
+        s2 = I.Population(sub.digesters, y, sub.T, sub.pos, False)
+        t0 = time.perf_counter()
+        r = O.run(s2, DT_S, 1, interval0=args.warmup + k, rtol=1e-6, SH=SH, h=h, n_threads=cores)
+        times.append(time.perf_counter() - t0)
+        y, SH, h = r["y"], r["S_H"], r["h"]
+    tot = sum(times)
+    value = n_s * args.steps * DT_S / 86400.0 / tot
+    barrier(dist)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles_per_step_sample": n_s,
+                       "coupling_interval_s": DT_S, "rtol": 1e-6},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_s} seeded particles of the 1M workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["both", "mixed", "fp64"], default="both")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--particles", type=int, default=None,
+                    help="override the 1M particles (profiling captures only)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        res = run_reference(args, ws, rank)
+    else:
+        res = run_ours(args, ws, rank, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

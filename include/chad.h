@@ -53,7 +53,15 @@ typedef enum {
 } chad_status;
 
 enum { CHAD_MEM_HOST = 0, CHAD_MEM_DEVICE = 1 };
-enum { CHAD_PREC_FP64 = 0, CHAD_PREC_MIXED = 1 };
+/* Precision forms of the integrator:
+   FP64        rates, Jacobian, LU and solves in FP64;
+   MIXED       Jacobian and LU in FP32, one FP64 refinement step per linear
+               solve; stage rates, Eq. 7 Newton, state accumulation and the
+               error estimate in FP64;
+   MIXED_F32RATES  as MIXED with the stage rates also in FP32 (their rounding
+               noise enters the embedded error estimate and costs rejected
+               steps; kept for comparison). */
+enum { CHAD_PREC_FP64 = 0, CHAD_PREC_MIXED = 1, CHAD_PREC_MIXED_F32RATES = 2 };
 enum { CHAD_HEADSPACE_PARTICLE = 0, CHAD_HEADSPACE_SHARED = 1 };
 
 /* Per-particle status bits (OR-accumulated across intervals until read). */
@@ -75,7 +83,7 @@ typedef struct {
   const double* D_uniform;     /* [n_digesters] dilution rate 1/d for digesters without a
                                   flow field (Eq. 2 with q_in = q_out); NULL = all 0 */
   const double* y_in;          /* [n_digesters][29] influent; NULL = zeros */
-  int precision;               /* CHAD_PREC_FP64 or CHAD_PREC_MIXED */
+  int precision;               /* CHAD_PREC_FP64, CHAD_PREC_MIXED or CHAD_PREC_MIXED_F32RATES */
   int learned;                 /* 1: MLP initial guesses (chad_set_mlp must be called) */
   int headspace;               /* CHAD_HEADSPACE_PARTICLE or CHAD_HEADSPACE_SHARED */
   double rtol;                 /* relative tolerance of the step controller (> 0) */
@@ -112,6 +120,7 @@ typedef struct {
   int64_t max_steps;         /* most accepted steps of one particle in one interval */
   int64_t failed_particles;  /* particles with status != 0 */
   int64_t mlp_redo;          /* learned guesses rejected and redone plainly */
+  int64_t pivot_rejects;     /* attempts rejected by the static-pivot threshold test */
   int64_t intervals;         /* coupling intervals integrated */
   double sim_days;           /* particle-days integrated */
 } chad_stats;
@@ -159,9 +168,21 @@ chad_status chad_set_flow(chad_ctx* ctx, int digester, const chad_flow* flow);
    per interval, advect (digesters with flow), integrate every particle
    (Eq. 2-7) and, with a shared headspace, average the three gas states of
    each digester.  Asynchronous on the context's stream; particle failures
-   are reported by chad_read_states / chad_synchronize.
+   are reported by chad_read_states / chad_synchronize.  On a non-default
+   stream the launch sequence of one interval is captured once as a CUDA
+   graph and replayed for every interval.
    dt_coupling_s > 0, n_intervals >= 0. */
 chad_status chad_step(chad_ctx* ctx, double dt_coupling_s, int n_intervals);
+
+/* Pick the fastest integrator kernel variant for this population and
+   interval length: the particle state is snapshot, one interval is run and
+   timed with each of the variants (register budgets of 255/168/128 per
+   thread, i.e. at least 2, 3 or 4 resident 128-thread blocks per SM), and
+   the state is restored, so results are unaffected.  The choice is kept by
+   the context for its precision form; *chosen (may be NULL) receives the
+   variant index and ms (may be NULL) the time of each of the 3 variants.  Temporarily
+   allocates about 290 bytes per particle of device memory.  Synchronous. */
+chad_status chad_autotune(chad_ctx* ctx, double dt_coupling_s, int32_t* chosen, double* ms);
 
 /* Wait for the context's stream.  CHAD_E_PARTICLE if any particle has a
    status bit set, CHAD_E_CUDA if a kernel failed. */
@@ -176,6 +197,27 @@ chad_status chad_synchronize(chad_ctx* ctx);
    digester has a status bit set (the data is still copied). */
 chad_status chad_read_states(chad_ctx* ctx, int digester, double* y, double* pos, double* S_H,
                              double* h, int32_t* status, chad_stats* stats, int mem);
+
+/* ---- diagnostics ------------------------------------------------------- */
+
+/* Measure the dense FMA throughput of the current GPU (fp64 = 1: FP64 DFMA,
+   0: FP32 FFMA), in TFLOP/s, with FMA chains on every SM (about 0.2 s).
+   These are the roofline denominators of the integrator, whose path is
+   bound by plain ALU arithmetic.  Allocates and frees a small buffer. */
+chad_status chad_probe_alu_peak(int fp64, double* tflops);
+
+/* Evaluate the library's model for one particle: f = dy/dt (Eq. 2-6) [29],
+   the analytic Jacobian J = df/dy [29][29] row-major (with S_H(y) from Eq. 7
+   differentiated implicitly), and the Eq. 7 root *SH, for the digester
+   described by params [CHAD_NPARAM], V_liq, V_gas (m^3), dilution rate D
+   (1/d), influent y_in [29] (NULL: zeros), temperature T (K) and state y
+   [29], starting Newton from SH_guess.  on_device = 0 runs the code on the
+   host CPU (no GPU needed), 1 runs the identical source as a one-thread
+   kernel on the current GPU.  All pointers are host memory.
+   CHAD_E_PARTICLE if Eq. 7 had no root in [1e-14, 1]. */
+chad_status chad_eval_model(const double* params, double V_liq, double V_gas, double D,
+                            const double* y_in, double T, const double* y, double SH_guess,
+                            double* f, double* J, double* SH, int on_device);
 
 #ifdef __cplusplus
 }

@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if force:
         for o in glob.glob(os.path.join(BUILD, "*.o")):
             os.remove(o)
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 1, 4), len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, hdr_mtime, verbose), srcs))
     if (not force and os.path.exists(LIB) and
             os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs)):

@@ -22,7 +22,7 @@ _lib = None
 
 NS = 29
 MEM_HOST, MEM_DEVICE = 0, 1
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_F32RATES = 0, 1, 2
 HEADSPACE_PARTICLE, HEADSPACE_SHARED = 0, 1
 STATUS = {0: "CHAD_OK", 1: "CHAD_E_INVALID", 2: "CHAD_E_NOMEM", 3: "CHAD_E_CUDA",
           4: "CHAD_E_STATE", 5: "CHAD_E_PARTICLE"}
@@ -52,6 +52,7 @@ class chad_stats(C.Structure):
                 ("newton_iters", C.c_int64), ("newton_fallbacks", C.c_int64),
                 ("min_steps", C.c_int64), ("max_steps", C.c_int64),
                 ("failed_particles", C.c_int64), ("mlp_redo", C.c_int64),
+                ("pivot_rejects", C.c_int64),
                 ("intervals", C.c_int64), ("sim_days", C.c_double)]
 
     def as_dict(self):
@@ -97,6 +98,14 @@ def lib():
             L.chad_read_states.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.POINTER(chad_stats), C.c_int]
+            L.chad_autotune.restype = C.c_int
+            L.chad_autotune.argtypes = [C.c_void_p, C.c_double, C.POINTER(C.c_int32), C.c_void_p]
+            L.chad_eval_model.restype = C.c_int
+            L.chad_eval_model.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                          C.c_void_p, C.c_double, C.c_void_p, C.c_double,
+                                          C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int]
+            L.chad_probe_alu_peak.restype = C.c_int
+            L.chad_probe_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
             _lib = L
     return _lib
 
@@ -104,7 +113,44 @@ def lib():
 def exported_symbols() -> list[str]:
     return ["chad_abi_version", "chad_n_params", "chad_param_name", "chad_last_error",
             "chad_create", "chad_destroy", "chad_load_particles", "chad_set_flow",
-            "chad_step", "chad_synchronize", "chad_read_states"]
+            "chad_step", "chad_synchronize", "chad_read_states", "chad_probe_alu_peak",
+            "chad_eval_model", "chad_autotune"]
+
+
+def chad_autotune(ctx, dt_coupling_s):
+    """Returns (chosen variant, ms per variant)."""
+    L = lib()
+    ch = C.c_int32(-1)
+    ms = np.zeros(3)
+    _check(L, ctx, L.chad_autotune(ctx, float(dt_coupling_s), C.byref(ch), ms.ctypes.data))
+    return ch.value, ms
+
+
+def eval_model(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, SH_guess=1e-7,
+               on_device=False):
+    """(f, J, S_H) of the library's model for one particle (host or GPU)."""
+    L = lib()
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    yi = None if y_in is None else np.ascontiguousarray(y_in, dtype=np.float64)
+    f = np.zeros(NS)
+    J = np.zeros((NS, NS))
+    SH = C.c_double(0.0)
+    code = L.chad_eval_model(p.ctypes.data, float(V_liq), float(V_gas), float(D),
+                             None if yi is None else yi.ctypes.data, float(T), yy.ctypes.data,
+                             float(SH_guess), f.ctypes.data, J.ctypes.data, C.byref(SH),
+                             1 if on_device else 0)
+    if code not in (0, 5):
+        raise ChadError(code, "chad_eval_model failed")
+    return f, J, SH.value
+
+
+def probe_alu_peak(fp64: bool) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current GPU."""
+    L = lib()
+    v = C.c_double(0.0)
+    _check(L, None, L.chad_probe_alu_peak(1 if fp64 else 0, C.byref(v)))
+    return v.value
 
 
 def param_names() -> list[str]:

@@ -11,11 +11,22 @@
 // R is the arithmetic type of rates, Jacobian and LU (double for the plain
 // path, float for the mixed path); the charge balance is always FP64.
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 #include "model.h"
 
+#ifndef CHAD_HD
+#define CHAD_HD __host__ __device__ __forceinline__
+#endif
+
 namespace chad {
+
+// Dense row-major storage of a NS x NS matrix (slot of entry (r, c)).
+struct DenseIdx {
+  static CHAD_HD constexpr int at(int r, int c) { return r * NS + c; }
+  static constexpr int size = NS * NS;
+};
 
 constexpr double kVfaCod_ac = 64.0, kVfaCod_pro = 112.0, kVfaCod_bu = 160.0, kVfaCod_va = 208.0;
 constexpr double kC4Guard = 1e-6;  // division guard of the c4 uptake split
@@ -26,7 +37,7 @@ struct PartConst {
   double K_w, K_a_co2, K_a_IN, K_H_co2, K_H_ch4, K_H_h2, p_h2o, RT;
 };
 
-__device__ __forceinline__ void part_const(const DigConst& c, double T, PartConst& q) {
+CHAD_HD void part_const(const DigConst& c, double T, PartConst& q) {
   const double invT = 1.0 / T;
   const double dT = c.inv_T_base - invT;
   q.arr = exp(-c.Ea_over_R * (invT - c.inv_T_ref));
@@ -48,7 +59,7 @@ struct AcidBase {
 };
 
 // E(S) and dE/dS; fills the reciprocals used by the Jacobian
-__device__ __forceinline__ double charge_E(const DigConst& c, const PartConst& q,
+CHAD_HD double charge_E(const DigConst& c, const PartConst& q,
                                            const double* y, double S, AcidBase& ab) {
   const double rS = 1.0 / S;
   ab.r_IN = 1.0 / (q.K_a_IN + S);
@@ -77,7 +88,7 @@ struct NewtonCounters {
 
 // Newton from `guess`; an iterate leaving (0, inf) or a growing |E| switches
 // to bisection on [1e-14, 1] (geometric midpoint, at most 200 halvings).
-__device__ inline void solve_SH(const DigConst& c, const PartConst& q, const double* y,
+__host__ __device__ inline void solve_SH(const DigConst& c, const PartConst& q, const double* y,
                                 double guess, int max_iters, AcidBase& ab, NewtonCounters& nc) {
   double S = (guess > 0.0 && isfinite(guess)) ? guess : 1e-7;
   double prevE = INFINITY;
@@ -120,7 +131,7 @@ __device__ inline void solve_SH(const DigConst& c, const PartConst& q, const dou
 // ----------------------------------------------------------- inhibition helpers
 // Hill pH inhibition I = 1 / (1 + (S/K)^n) and dI/dS
 template <class R>
-__device__ __forceinline__ void hill(R S, R invK, R n, int ni, R& I, R& dI) {
+CHAD_HD void hill(R S, R invK, R n, int ni, R& I, R& dI) {
   const R x = S * invK;
   R xn1, xn;
   switch (ni) {
@@ -150,7 +161,7 @@ struct Rates {
 };
 
 template <class R, bool J>
-__device__ __forceinline__ void rates(const DigConst& c, const PartConst& q, const R* y,
+CHAD_HD void rates(const DigConst& c, const PartConst& q, const R* y,
                                       const AcidBase& ab, Rates<R>& o) {
   const R a = R(q.arr);
   const R SH = R(ab.SH);
@@ -290,7 +301,7 @@ __device__ __forceinline__ void rates(const DigConst& c, const PartConst& q, con
 
 // f(y): mass balances of Eq. 2 with the ADM1 stoichiometry
 template <class R>
-__device__ __forceinline__ void balances(const DigConst& c, const R* y, R D, const Rates<R>& o,
+CHAD_HD void balances(const DigConst& c, const R* y, R D, const Rates<R>& o,
                                          R* f) {
   const R* r = o.r;
   R dil[26];
@@ -337,166 +348,170 @@ __device__ __forceinline__ void balances(const DigConst& c, const R* y, R D, con
   f[iG_co2] = -y[iG_co2] * o.qv + vr * r[21];
 }
 
-// J[row][cols[k]] += coef * d[k]; u[row] += coef * s
-template <class R, int NC>
-__device__ __forceinline__ void scat(R* Jm, R* u, int row, R coef, const int (&cols)[NC],
-                                     const R (&d)[NC], R s) {
+// J[row][cols[k]] += coef * d[k]; u[row] += coef * s.  Idx maps (row, col)
+// to a storage slot (negative: structurally absent, the write is dropped).
+template <class Idx, class R>
+CHAD_HD void jadd(R* Jm, int row, int col, R v) {
+  const int s = Idx::at(row, col);
+  if (s >= 0) Jm[s] += v;
+}
+template <class Idx, class R, int NC>
+CHAD_HD void scat(R* Jm, R* u, int row, R coef, const int (&cols)[NC], const R (&d)[NC], R s) {
 #pragma unroll
-  for (int k = 0; k < NC; ++k) Jm[row * NS + cols[k]] += coef * d[k];
+  for (int k = 0; k < NC; ++k) jadd<Idx>(Jm, row, cols[k], coef * d[k]);
   u[row] += coef * s;
 }
-template <class R, int NC>
-__device__ __forceinline__ void scat(R* Jm, int row, R coef, const int (&cols)[NC],
-                                     const R (&d)[NC]) {
+template <class Idx, class R, int NC>
+CHAD_HD void scat(R* Jm, int row, R coef, const int (&cols)[NC], const R (&d)[NC]) {
 #pragma unroll
-  for (int k = 0; k < NC; ++k) Jm[row * NS + cols[k]] += coef * d[k];
+  for (int k = 0; k < NC; ++k) jadd<Idx>(Jm, row, cols[k], coef * d[k]);
 }
 
 // Analytic Jacobian (row-major NS x NS) from the rate partials.  The S_H
 // dependence enters as the rank-1 term u v^T, u = df/dS_H (at fixed y),
 // v = dS_H/dy = -(dE/dy) / (dE/dS_H) from Eq. 7.
-template <class R>
-__device__ __forceinline__ void jacobian(const DigConst& c, const PartConst& q, const R* y, R D,
-                                         const AcidBase& ab, const Rates<R>& o, R* Jm) {
+template <class Idx, class R>
+CHAD_HD void jacobian(const DigConst& c, const PartConst& q, const R* y, R D, const AcidBase& ab,
+                      const Rates<R>& o, R* Jm) {
   R u[NS];
 #pragma unroll
-  for (int i = 0; i < NS * NS; ++i) Jm[i] = R(0);
+  for (int i = 0; i < Idx::size; ++i) Jm[i] = R(0);
 #pragma unroll
   for (int i = 0; i < NS; ++i) u[i] = R(0);
 #pragma unroll
-  for (int i = 0; i < 26; ++i) Jm[i * NS + i] = -D;
+  for (int i = 0; i < 26; ++i) jadd<Idx>(Jm, i, i, -D);
   const R one = R(1), mone = R(-1);
   const R cIC12 = R(c.cIC[12]), nIN12 = R(c.nIN[12]);
   {  // rho1 disintegration
     const int cols[1] = {iX_c};
     const R d[1] = {o.d1};
-    scat(Jm, iX_c, mone, cols, d);
-    scat(Jm, iS_I, R(c.f_sI), cols, d);
-    scat(Jm, iX_ch, R(c.f_ch), cols, d);
-    scat(Jm, iX_pr, R(c.f_pr), cols, d);
-    scat(Jm, iX_li, R(c.f_li), cols, d);
-    scat(Jm, iX_I, R(c.f_xI), cols, d);
-    scat(Jm, iS_IC, R(c.cIC[0]), cols, d);
-    scat(Jm, iS_IN, R(c.nIN[0]), cols, d);
+    scat<Idx>(Jm, iX_c, mone, cols, d);
+    scat<Idx>(Jm, iS_I, R(c.f_sI), cols, d);
+    scat<Idx>(Jm, iX_ch, R(c.f_ch), cols, d);
+    scat<Idx>(Jm, iX_pr, R(c.f_pr), cols, d);
+    scat<Idx>(Jm, iX_li, R(c.f_li), cols, d);
+    scat<Idx>(Jm, iX_I, R(c.f_xI), cols, d);
+    scat<Idx>(Jm, iS_IC, R(c.cIC[0]), cols, d);
+    scat<Idx>(Jm, iS_IN, R(c.nIN[0]), cols, d);
   }
   {  // rho2-4 hydrolysis
     const int c2[1] = {iX_ch}, c3[1] = {iX_pr}, c4[1] = {iX_li};
     const R d2[1] = {o.d2}, d3[1] = {o.d3}, d4[1] = {o.d4};
-    scat(Jm, iX_ch, mone, c2, d2);
-    scat(Jm, iS_su, one, c2, d2);
-    scat(Jm, iS_IC, R(c.cIC[1]), c2, d2);
-    scat(Jm, iX_pr, mone, c3, d3);
-    scat(Jm, iS_aa, one, c3, d3);
-    scat(Jm, iS_IC, R(c.cIC[2]), c3, d3);
-    scat(Jm, iX_li, mone, c4, d4);
-    scat(Jm, iS_su, R(c.c_su_li), c4, d4);
-    scat(Jm, iS_fa, R(c.f_fa_li), c4, d4);
-    scat(Jm, iS_IC, R(c.cIC[3]), c4, d4);
+    scat<Idx>(Jm, iX_ch, mone, c2, d2);
+    scat<Idx>(Jm, iS_su, one, c2, d2);
+    scat<Idx>(Jm, iS_IC, R(c.cIC[1]), c2, d2);
+    scat<Idx>(Jm, iX_pr, mone, c3, d3);
+    scat<Idx>(Jm, iS_aa, one, c3, d3);
+    scat<Idx>(Jm, iS_IC, R(c.cIC[2]), c3, d3);
+    scat<Idx>(Jm, iX_li, mone, c4, d4);
+    scat<Idx>(Jm, iS_su, R(c.c_su_li), c4, d4);
+    scat<Idx>(Jm, iS_fa, R(c.f_fa_li), c4, d4);
+    scat<Idx>(Jm, iS_IC, R(c.cIC[3]), c4, d4);
   }
   {  // rho5 sugars
     const int cols[3] = {iS_su, iX_su, iS_IN};
-    scat(Jm, u, iS_su, mone, cols, o.d5, o.s5);
-    scat(Jm, u, iS_bu, R(c.su_bu), cols, o.d5, o.s5);
-    scat(Jm, u, iS_pro, R(c.su_pro), cols, o.d5, o.s5);
-    scat(Jm, u, iS_ac, R(c.su_ac), cols, o.d5, o.s5);
-    scat(Jm, u, iS_h2, R(c.su_h2), cols, o.d5, o.s5);
-    scat(Jm, u, iX_su, R(c.Y_su), cols, o.d5, o.s5);
-    scat(Jm, u, iS_IC, R(c.cIC[4]), cols, o.d5, o.s5);
-    scat(Jm, u, iS_IN, R(c.nIN[4]), cols, o.d5, o.s5);
+    scat<Idx>(Jm, u, iS_su, mone, cols, o.d5, o.s5);
+    scat<Idx>(Jm, u, iS_bu, R(c.su_bu), cols, o.d5, o.s5);
+    scat<Idx>(Jm, u, iS_pro, R(c.su_pro), cols, o.d5, o.s5);
+    scat<Idx>(Jm, u, iS_ac, R(c.su_ac), cols, o.d5, o.s5);
+    scat<Idx>(Jm, u, iS_h2, R(c.su_h2), cols, o.d5, o.s5);
+    scat<Idx>(Jm, u, iX_su, R(c.Y_su), cols, o.d5, o.s5);
+    scat<Idx>(Jm, u, iS_IC, R(c.cIC[4]), cols, o.d5, o.s5);
+    scat<Idx>(Jm, u, iS_IN, R(c.nIN[4]), cols, o.d5, o.s5);
   }
   {  // rho6 amino acids
     const int cols[3] = {iS_aa, iX_aa, iS_IN};
-    scat(Jm, u, iS_aa, mone, cols, o.d6, o.s6);
-    scat(Jm, u, iS_va, R(c.aa_va), cols, o.d6, o.s6);
-    scat(Jm, u, iS_bu, R(c.aa_bu), cols, o.d6, o.s6);
-    scat(Jm, u, iS_pro, R(c.aa_pro), cols, o.d6, o.s6);
-    scat(Jm, u, iS_ac, R(c.aa_ac), cols, o.d6, o.s6);
-    scat(Jm, u, iS_h2, R(c.aa_h2), cols, o.d6, o.s6);
-    scat(Jm, u, iX_aa, R(c.Y_aa), cols, o.d6, o.s6);
-    scat(Jm, u, iS_IC, R(c.cIC[5]), cols, o.d6, o.s6);
-    scat(Jm, u, iS_IN, R(c.nIN[5]), cols, o.d6, o.s6);
+    scat<Idx>(Jm, u, iS_aa, mone, cols, o.d6, o.s6);
+    scat<Idx>(Jm, u, iS_va, R(c.aa_va), cols, o.d6, o.s6);
+    scat<Idx>(Jm, u, iS_bu, R(c.aa_bu), cols, o.d6, o.s6);
+    scat<Idx>(Jm, u, iS_pro, R(c.aa_pro), cols, o.d6, o.s6);
+    scat<Idx>(Jm, u, iS_ac, R(c.aa_ac), cols, o.d6, o.s6);
+    scat<Idx>(Jm, u, iS_h2, R(c.aa_h2), cols, o.d6, o.s6);
+    scat<Idx>(Jm, u, iX_aa, R(c.Y_aa), cols, o.d6, o.s6);
+    scat<Idx>(Jm, u, iS_IC, R(c.cIC[5]), cols, o.d6, o.s6);
+    scat<Idx>(Jm, u, iS_IN, R(c.nIN[5]), cols, o.d6, o.s6);
   }
   {  // rho7 LCFA
     const int cols[4] = {iS_fa, iX_fa, iS_IN, iS_h2};
-    scat(Jm, u, iS_fa, mone, cols, o.d7, o.s7);
-    scat(Jm, u, iS_ac, R(c.fa_ac), cols, o.d7, o.s7);
-    scat(Jm, u, iS_h2, R(c.fa_h2), cols, o.d7, o.s7);
-    scat(Jm, u, iX_fa, R(c.Y_fa), cols, o.d7, o.s7);
-    scat(Jm, u, iS_IC, R(c.cIC[6]), cols, o.d7, o.s7);
-    scat(Jm, u, iS_IN, R(c.nIN[6]), cols, o.d7, o.s7);
+    scat<Idx>(Jm, u, iS_fa, mone, cols, o.d7, o.s7);
+    scat<Idx>(Jm, u, iS_ac, R(c.fa_ac), cols, o.d7, o.s7);
+    scat<Idx>(Jm, u, iS_h2, R(c.fa_h2), cols, o.d7, o.s7);
+    scat<Idx>(Jm, u, iX_fa, R(c.Y_fa), cols, o.d7, o.s7);
+    scat<Idx>(Jm, u, iS_IC, R(c.cIC[6]), cols, o.d7, o.s7);
+    scat<Idx>(Jm, u, iS_IN, R(c.nIN[6]), cols, o.d7, o.s7);
   }
   {  // rho8 valerate
     const int cols[5] = {iS_va, iS_bu, iX_c4, iS_IN, iS_h2};
-    scat(Jm, u, iS_va, mone, cols, o.d8, o.s8);
-    scat(Jm, u, iS_pro, R(c.va_pro), cols, o.d8, o.s8);
-    scat(Jm, u, iS_ac, R(c.va_ac), cols, o.d8, o.s8);
-    scat(Jm, u, iS_h2, R(c.va_h2), cols, o.d8, o.s8);
-    scat(Jm, u, iX_c4, R(c.Y_c4), cols, o.d8, o.s8);
-    scat(Jm, u, iS_IC, R(c.cIC[7]), cols, o.d8, o.s8);
-    scat(Jm, u, iS_IN, R(c.nIN[7]), cols, o.d8, o.s8);
+    scat<Idx>(Jm, u, iS_va, mone, cols, o.d8, o.s8);
+    scat<Idx>(Jm, u, iS_pro, R(c.va_pro), cols, o.d8, o.s8);
+    scat<Idx>(Jm, u, iS_ac, R(c.va_ac), cols, o.d8, o.s8);
+    scat<Idx>(Jm, u, iS_h2, R(c.va_h2), cols, o.d8, o.s8);
+    scat<Idx>(Jm, u, iX_c4, R(c.Y_c4), cols, o.d8, o.s8);
+    scat<Idx>(Jm, u, iS_IC, R(c.cIC[7]), cols, o.d8, o.s8);
+    scat<Idx>(Jm, u, iS_IN, R(c.nIN[7]), cols, o.d8, o.s8);
   }
   {  // rho9 butyrate
     const int cols[5] = {iS_va, iS_bu, iX_c4, iS_IN, iS_h2};
-    scat(Jm, u, iS_bu, mone, cols, o.d9, o.s9);
-    scat(Jm, u, iS_ac, R(c.bu_ac), cols, o.d9, o.s9);
-    scat(Jm, u, iS_h2, R(c.bu_h2), cols, o.d9, o.s9);
-    scat(Jm, u, iX_c4, R(c.Y_c4), cols, o.d9, o.s9);
-    scat(Jm, u, iS_IC, R(c.cIC[8]), cols, o.d9, o.s9);
-    scat(Jm, u, iS_IN, R(c.nIN[8]), cols, o.d9, o.s9);
+    scat<Idx>(Jm, u, iS_bu, mone, cols, o.d9, o.s9);
+    scat<Idx>(Jm, u, iS_ac, R(c.bu_ac), cols, o.d9, o.s9);
+    scat<Idx>(Jm, u, iS_h2, R(c.bu_h2), cols, o.d9, o.s9);
+    scat<Idx>(Jm, u, iX_c4, R(c.Y_c4), cols, o.d9, o.s9);
+    scat<Idx>(Jm, u, iS_IC, R(c.cIC[8]), cols, o.d9, o.s9);
+    scat<Idx>(Jm, u, iS_IN, R(c.nIN[8]), cols, o.d9, o.s9);
   }
   {  // rho10 propionate
     const int cols[4] = {iS_pro, iX_pro, iS_IN, iS_h2};
-    scat(Jm, u, iS_pro, mone, cols, o.d10, o.s10);
-    scat(Jm, u, iS_ac, R(c.pro_ac), cols, o.d10, o.s10);
-    scat(Jm, u, iS_h2, R(c.pro_h2), cols, o.d10, o.s10);
-    scat(Jm, u, iX_pro, R(c.Y_pro), cols, o.d10, o.s10);
-    scat(Jm, u, iS_IC, R(c.cIC[9]), cols, o.d10, o.s10);
-    scat(Jm, u, iS_IN, R(c.nIN[9]), cols, o.d10, o.s10);
+    scat<Idx>(Jm, u, iS_pro, mone, cols, o.d10, o.s10);
+    scat<Idx>(Jm, u, iS_ac, R(c.pro_ac), cols, o.d10, o.s10);
+    scat<Idx>(Jm, u, iS_h2, R(c.pro_h2), cols, o.d10, o.s10);
+    scat<Idx>(Jm, u, iX_pro, R(c.Y_pro), cols, o.d10, o.s10);
+    scat<Idx>(Jm, u, iS_IC, R(c.cIC[9]), cols, o.d10, o.s10);
+    scat<Idx>(Jm, u, iS_IN, R(c.nIN[9]), cols, o.d10, o.s10);
   }
   {  // rho11 acetate
     const int cols[3] = {iS_ac, iX_ac, iS_IN};
-    scat(Jm, u, iS_ac, mone, cols, o.d11, o.s11);
-    scat(Jm, u, iS_ch4, R(c.ac_ch4), cols, o.d11, o.s11);
-    scat(Jm, u, iX_ac, R(c.Y_ac), cols, o.d11, o.s11);
-    scat(Jm, u, iS_IC, R(c.cIC[10]), cols, o.d11, o.s11);
-    scat(Jm, u, iS_IN, R(c.nIN[10]), cols, o.d11, o.s11);
+    scat<Idx>(Jm, u, iS_ac, mone, cols, o.d11, o.s11);
+    scat<Idx>(Jm, u, iS_ch4, R(c.ac_ch4), cols, o.d11, o.s11);
+    scat<Idx>(Jm, u, iX_ac, R(c.Y_ac), cols, o.d11, o.s11);
+    scat<Idx>(Jm, u, iS_IC, R(c.cIC[10]), cols, o.d11, o.s11);
+    scat<Idx>(Jm, u, iS_IN, R(c.nIN[10]), cols, o.d11, o.s11);
   }
   {  // rho12 hydrogen
     const int cols[3] = {iS_h2, iX_h2, iS_IN};
-    scat(Jm, u, iS_h2, mone, cols, o.d12, o.s12);
-    scat(Jm, u, iS_ch4, R(c.h2_ch4), cols, o.d12, o.s12);
-    scat(Jm, u, iX_h2, R(c.Y_h2), cols, o.d12, o.s12);
-    scat(Jm, u, iS_IC, R(c.cIC[11]), cols, o.d12, o.s12);
-    scat(Jm, u, iS_IN, R(c.nIN[11]), cols, o.d12, o.s12);
+    scat<Idx>(Jm, u, iS_h2, mone, cols, o.d12, o.s12);
+    scat<Idx>(Jm, u, iS_ch4, R(c.h2_ch4), cols, o.d12, o.s12);
+    scat<Idx>(Jm, u, iX_h2, R(c.Y_h2), cols, o.d12, o.s12);
+    scat<Idx>(Jm, u, iS_IC, R(c.cIC[11]), cols, o.d12, o.s12);
+    scat<Idx>(Jm, u, iS_IN, R(c.nIN[11]), cols, o.d12, o.s12);
   }
 #pragma unroll
   for (int k = 0; k < 7; ++k) {  // rho13-19 decay
     const int col = iX_su + k;
     const R dk = o.ddec[k];
-    Jm[col * NS + col] -= dk;
-    Jm[iX_c * NS + col] += dk;
-    Jm[iS_IC * NS + col] += cIC12 * dk;
-    Jm[iS_IN * NS + col] += nIN12 * dk;
+    jadd<Idx>(Jm, col, col, -dk);
+    jadd<Idx>(Jm, (int)iX_c, col, dk);
+    jadd<Idx>(Jm, (int)iS_IC, col, cIC12 * dk);
+    jadd<Idx>(Jm, (int)iS_IN, col, nIN12 * dk);
   }
   const R vr = R(c.Vliq_over_Vgas);
   {  // transfers
     const int c8[2] = {iS_h2, iG_h2}, c9[2] = {iS_ch4, iG_ch4}, c10[2] = {iS_IC, iG_co2};
-    scat(Jm, iS_h2, mone, c8, o.dT8);
-    scat(Jm, iG_h2, vr, c8, o.dT8);
-    scat(Jm, iS_ch4, mone, c9, o.dT9);
-    scat(Jm, iG_ch4, vr, c9, o.dT9);
-    scat(Jm, u, iS_IC, mone, c10, o.dT10, o.sT10);
-    scat(Jm, u, iG_co2, vr, c10, o.dT10, o.sT10);
+    scat<Idx>(Jm, iS_h2, mone, c8, o.dT8);
+    scat<Idx>(Jm, iG_h2, vr, c8, o.dT8);
+    scat<Idx>(Jm, iS_ch4, mone, c9, o.dT9);
+    scat<Idx>(Jm, iG_ch4, vr, c9, o.dT9);
+    scat<Idx>(Jm, u, iS_IC, mone, c10, o.dT10, o.sT10);
+    scat<Idx>(Jm, u, iG_co2, vr, c10, o.dT10, o.sT10);
   }
   {  // gas outflow: f_G = -G q(P)
     const int g[3] = {iG_h2, iG_ch4, iG_co2};
     const R dP[3] = {o.P_h2, o.P_ch4, o.P_co2};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      Jm[g[a] * NS + g[a]] -= o.qv;
+      jadd<Idx>(Jm, g[a], g[a], -o.qv);
       const R gq = y[g[a]] * o.dqv;
 #pragma unroll
-      for (int b = 0; b < 3; ++b) Jm[g[a] * NS + g[b]] -= gq * dP[b];
+      for (int b = 0; b < 3; ++b) jadd<Idx>(Jm, g[a], g[b], -gq * dP[b]);
     }
   }
   // rank-1 S_H coupling: J += u v^T over the 8 states that enter Eq. 7
@@ -515,7 +530,7 @@ __device__ __forceinline__ void jacobian(const DigConst& c, const PartConst& q, 
 #pragma unroll
   for (int i = 0; i < 19; ++i)
 #pragma unroll
-    for (int k = 0; k < 8; ++k) Jm[ur[i] * NS + hc[k]] += u[ur[i]] * v[k];
+    for (int k = 0; k < 8; ++k) jadd<Idx>(Jm, ur[i], hc[k], u[ur[i]] * v[k]);
 }
 
 }  // namespace chad

@@ -53,14 +53,15 @@ __global__ void advect_kernel(AdvectArgs a) {
   double x = a.pos[p], y = a.pos[a.ld + p], z = a.pos[2 * a.ld + p];
   a.D[p] = (z >= f.slab_zmin) ? f.D_slab : 0.0;  // slab membership at interval start
   const uint64_t pid = (uint64_t)(p - a.dig_offset[d]);
+  const uint64_t interval = *a.interval;
   const double twoR = __dmul_rn(2.0, f.R), twoH = __dmul_rn(2.0, f.H);
 #pragma unroll 1
   for (int k = 0; k < f.n_sub; ++k) {
     const double xr = __dsub_rn(__dmul_rn(f.cw, x), __dmul_rn(f.sw, y));
     const double yr = __dadd_rn(__dmul_rn(f.sw, x), __dmul_rn(f.cw, y));
-    x = __dadd_rn(xr, __dmul_rn(f.amp, gauss(f.seed, pid, a.interval, (uint64_t)k, 0)));
-    y = __dadd_rn(yr, __dmul_rn(f.amp, gauss(f.seed, pid, a.interval, (uint64_t)k, 1)));
-    z = __dadd_rn(z, __dmul_rn(f.amp, gauss(f.seed, pid, a.interval, (uint64_t)k, 2)));
+    x = __dadd_rn(xr, __dmul_rn(f.amp, gauss(f.seed, pid, interval, (uint64_t)k, 0)));
+    y = __dadd_rn(yr, __dmul_rn(f.amp, gauss(f.seed, pid, interval, (uint64_t)k, 1)));
+    z = __dadd_rn(z, __dmul_rn(f.amp, gauss(f.seed, pid, interval, (uint64_t)k, 2)));
     const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
     if (r > f.R) {
       const double g = __ddiv_rn(__dsub_rn(twoR, r), r);
@@ -133,7 +134,16 @@ __global__ void headspace_broadcast(HeadspaceArgs a) {
   for (int g = 0; g < 3; ++g) a.y[(iG_h2 + g) * a.ld + p] = a.mean[d * 3 + g];
 }
 
+__global__ void bump_kernel(unsigned long long* interval) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *interval += 1ull;
+}
+
 }  // namespace
+
+cudaError_t launch_bump(unsigned long long* interval, cudaStream_t s) {
+  bump_kernel<<<1, 32, 0, s>>>(interval);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_advect(const AdvectArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;

@@ -36,7 +36,6 @@ struct chad_ctx {
   std::vector<FlowConst> hfl;
   std::vector<char> loaded;
   bool any_flow = false;
-  uint64_t interval = 0;  // global interval counter (noise stream)
   double sim_days = 0.0;
   int64_t intervals = 0;
   // headspace chunking
@@ -55,6 +54,15 @@ struct chad_ctx {
   int* d_status = nullptr;
   double* d_atol = nullptr;
   DevCounters* d_cnt = nullptr;
+  unsigned long long* d_queue = nullptr;
+  unsigned long long* d_interval = nullptr;  // global interval index (noise counter)
+  int variant[3] = {kDefaultVariant, kDefaultVariant, kDefaultVariant};
+  double flow_dt = -1.0;        // interval length the device flow constants hold
+  // CUDA graph of one interval (captured on first use, replayed per interval)
+  cudaGraphExec_t gexec = nullptr;
+  double g_dt = -1.0;
+  int g_variant = -1;
+  bool use_graph = true;
   int* d_chunk_dig = nullptr;
   int64_t* d_chunk_beg = nullptr;
   int64_t* d_chunk_end = nullptr;
@@ -90,10 +98,19 @@ static cudaError_t dalloc(T** p, size_t count) {
 
 static void free_all(chad_ctx* c) {
   void* ptrs[] = {c->d_dc, c->d_fl, c->d_dig, c->d_off, c->d_y, c->d_pos, c->d_T, c->d_D,
-                  c->d_SH, c->d_h, c->d_status, c->d_atol, c->d_cnt, c->d_chunk_dig,
+                  c->d_SH, c->d_h, c->d_status, c->d_atol, c->d_cnt, c->d_queue, c->d_interval, c->d_chunk_dig,
                   c->d_chunk_beg, c->d_chunk_end, c->d_dig_chunk0, c->d_partial, c->d_mean};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+}
+
+static void drop_graph(chad_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->g_dt = -1.0;
+  c->g_variant = -1;
 }
 
 extern "C" {
@@ -114,8 +131,9 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
     return fail(nullptr, CHAD_E_INVALID, "n_digesters must be in [1, 2^20]");
   if (!cfg->n_particles || !cfg->V_liq || !cfg->V_gas || !cfg->params || !cfg->atol)
     return fail(nullptr, CHAD_E_INVALID, "n_particles, V_liq, V_gas, params and atol are required");
-  if (cfg->precision != CHAD_PREC_FP64 && cfg->precision != CHAD_PREC_MIXED)
-    return fail(nullptr, CHAD_E_INVALID, "precision must be CHAD_PREC_FP64 or CHAD_PREC_MIXED");
+  if (cfg->precision != CHAD_PREC_FP64 && cfg->precision != CHAD_PREC_MIXED &&
+      cfg->precision != CHAD_PREC_MIXED_F32RATES)
+    return fail(nullptr, CHAD_E_INVALID, "precision must be one of CHAD_PREC_*");
   if (cfg->headspace != CHAD_HEADSPACE_PARTICLE && cfg->headspace != CHAD_HEADSPACE_SHARED)
     return fail(nullptr, CHAD_E_INVALID, "invalid headspace mode");
   if (cfg->learned != 0)
@@ -200,6 +218,8 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   A(dalloc(&c->d_status, c->ld));
   A(dalloc(&c->d_atol, NS));
   A(dalloc(&c->d_cnt, 1));
+  A(dalloc(&c->d_queue, 1));
+  A(dalloc(&c->d_interval, 1));
   A(dalloc(&c->d_chunk_dig, c->n_chunks));
   A(dalloc(&c->d_chunk_beg, c->n_chunks));
   A(dalloc(&c->d_chunk_end, c->n_chunks));
@@ -231,7 +251,9 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   A(cudaMemset(c->d_pos, 0, sizeof(double) * 3 * c->ld));
   A(cudaMemset(c->d_status, 0, sizeof(int) * c->ld));
   A(cudaMemset(c->d_mean, 0, sizeof(double) * 3 * c->n_dig));
-  DevCounters z{0, 0, 0, 0, 0x7fffffff, 0, 0, 0};
+  A(cudaMemset(c->d_interval, 0, sizeof(unsigned long long)));
+  A(cudaMemset(c->d_queue, 0, sizeof(unsigned long long)));
+  DevCounters z{0, 0, 0, 0, 0, 0x7fffffff, 0};
   A(cudaMemcpy(c->d_cnt, &z, sizeof(z), cudaMemcpyHostToDevice));
   if (e != cudaSuccess) {
     free_all(c);
@@ -338,34 +360,38 @@ chad_status chad_set_flow(chad_ctx* c, int digester, const chad_flow* f) {
   }
   c->any_flow = false;
   for (int d = 0; d < c->n_dig; ++d) c->any_flow |= (c->hfl[d].has_flow != 0);
+  c->flow_dt = -1.0;
+  drop_graph(c);
   return CHAD_OK;
 }
 
-chad_status chad_step(chad_ctx* c, double dt_coupling_s, int n_intervals) {
-  if (!c) return CHAD_E_INVALID;
-  if (!(dt_coupling_s > 0.0) || !std::isfinite(dt_coupling_s) || n_intervals < 0)
-    return fail(c, CHAD_E_INVALID, "dt_coupling_s must be > 0 and n_intervals >= 0");
-  for (int d = 0; d < c->n_dig; ++d)
-    if (!c->loaded[d]) return fail(c, CHAD_E_STATE, "every digester must be loaded before chad_step");
-  if (n_intervals == 0 || c->N == 0) return CHAD_OK;
-  cudaStream_t s = c->stream;
-  // expand the flow constants for this interval length (1-s sub-steps)
-  if (c->any_flow) {
-    int n_sub = (int)std::lround(dt_coupling_s);
-    if (n_sub < 1) n_sub = 1;
-    const double dsub = dt_coupling_s / n_sub;
-    std::vector<FlowConst> fl = c->hfl;
-    for (int d = 0; d < c->n_dig; ++d) {
-      if (!fl[d].has_flow) continue;
-      const double w = fl[d].U / fl[d].R;
-      fl[d].cw = std::cos(w * dsub);
-      fl[d].sw = std::sin(w * dsub);
-      fl[d].amp = fl[d].sigma * dsub;
-      fl[d].n_sub = n_sub;
-    }
-    CK(c, cudaMemcpyAsync(c->d_fl, fl.data(), sizeof(FlowConst) * c->n_dig, cudaMemcpyHostToDevice, s), "flow upload");
-    CK(c, cudaStreamSynchronize(s), "flow upload sync");
+// Expand the per-digester flow constants for an interval length (1-s
+// sub-steps) and upload them; no-op when they already hold this length.
+static chad_status prepare_flow(chad_ctx* c, double dt_coupling_s) {
+  if (!c->any_flow || c->flow_dt == dt_coupling_s) return CHAD_OK;
+  int n_sub = (int)std::lround(dt_coupling_s);
+  if (n_sub < 1) n_sub = 1;
+  const double dsub = dt_coupling_s / n_sub;
+  std::vector<FlowConst> fl = c->hfl;
+  for (int d = 0; d < c->n_dig; ++d) {
+    if (!fl[d].has_flow) continue;
+    const double w = fl[d].U / fl[d].R;
+    fl[d].cw = std::cos(w * dsub);
+    fl[d].sw = std::sin(w * dsub);
+    fl[d].amp = fl[d].sigma * dsub;
+    fl[d].n_sub = n_sub;
   }
+  CK(c, cudaMemcpyAsync(c->d_fl, fl.data(), sizeof(FlowConst) * c->n_dig, cudaMemcpyHostToDevice,
+                        c->stream), "flow upload");
+  CK(c, cudaStreamSynchronize(c->stream), "flow upload sync");
+  c->flow_dt = dt_coupling_s;
+  drop_graph(c);
+  return CHAD_OK;
+}
+
+// The launch sequence of one coupling interval: advect (digesters with
+// flow) -> integrate every particle -> shared-headspace mean -> interval += 1.
+static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cudaStream_t s) {
   StepArgs a;
   a.n = c->N;
   a.ld = c->ld;
@@ -379,44 +405,160 @@ chad_status chad_step(chad_ctx* c, double dt_coupling_s, int n_intervals) {
   a.status = c->d_status;
   a.atol = c->d_atol;
   a.rtol = c->rtol;
-  a.dt_days = dt_coupling_s / 86400.0;
+  a.dt_days = dt_days;
   a.max_steps = c->max_steps;
   a.max_newton = c->max_newton;
   a.fixed_n = c->fixed_n;
   a.counters = c->d_cnt;
-  AdvectArgs v;
-  v.n = c->N;
-  v.ld = c->ld;
-  v.dig = c->d_dig;
-  v.dig_offset = c->d_off;
-  v.fl = c->d_fl;
-  v.pos = c->d_pos;
-  v.D = c->d_D;
-  HeadspaceArgs hs;
-  hs.ld = c->ld;
-  hs.n_chunks = c->n_chunks;
-  hs.chunk_dig = c->d_chunk_dig;
-  hs.chunk_begin = c->d_chunk_beg;
-  hs.chunk_end = c->d_chunk_end;
-  hs.dig_offset = c->d_off;
-  hs.dig_chunk0 = c->d_dig_chunk0;
-  hs.n_dig = c->n_dig;
-  hs.y = c->d_y;
-  hs.partial = c->d_partial;
-  hs.mean = c->d_mean;
-  hs.dig = c->d_dig;
-  hs.n = c->N;
-  for (int it = 0; it < n_intervals; ++it) {
-    if (c->any_flow) {
-      v.interval = c->interval;
-      CK(c, launch_advect(v, s), "advect launch");
-    }
-    CK(c, launch_integrate(a, c->precision == CHAD_PREC_MIXED, 128, s), "integrate launch");
-    if (c->headspace == CHAD_HEADSPACE_SHARED) CK(c, launch_headspace(hs, s), "headspace launch");
-    c->interval++;
-    c->intervals++;
-    c->sim_days += a.dt_days * (double)c->N;
+  a.queue = c->d_queue;
+  cudaError_t e;
+  if (c->any_flow) {
+    AdvectArgs v;
+    v.n = c->N;
+    v.ld = c->ld;
+    v.dig = c->d_dig;
+    v.dig_offset = c->d_off;
+    v.fl = c->d_fl;
+    v.pos = c->d_pos;
+    v.D = c->d_D;
+    v.interval = c->d_interval;
+    if ((e = launch_advect(v, s)) != cudaSuccess) return e;
   }
+  if ((e = launch_integrate(a, c->precision, variant, s)) != cudaSuccess) return e;
+  if (c->headspace == CHAD_HEADSPACE_SHARED) {
+    HeadspaceArgs hs;
+    hs.ld = c->ld;
+    hs.n_chunks = c->n_chunks;
+    hs.chunk_dig = c->d_chunk_dig;
+    hs.chunk_begin = c->d_chunk_beg;
+    hs.chunk_end = c->d_chunk_end;
+    hs.dig_offset = c->d_off;
+    hs.dig_chunk0 = c->d_dig_chunk0;
+    hs.n_dig = c->n_dig;
+    hs.y = c->d_y;
+    hs.partial = c->d_partial;
+    hs.mean = c->d_mean;
+    hs.dig = c->d_dig;
+    hs.n = c->N;
+    if ((e = launch_headspace(hs, s)) != cudaSuccess) return e;
+  }
+  return launch_bump(c->d_interval, s);
+}
+
+chad_status chad_step(chad_ctx* c, double dt_coupling_s, int n_intervals) {
+  if (!c) return CHAD_E_INVALID;
+  if (!(dt_coupling_s > 0.0) || !std::isfinite(dt_coupling_s) || n_intervals < 0)
+    return fail(c, CHAD_E_INVALID, "dt_coupling_s must be > 0 and n_intervals >= 0");
+  for (int d = 0; d < c->n_dig; ++d)
+    if (!c->loaded[d]) return fail(c, CHAD_E_STATE, "every digester must be loaded before chad_step");
+  if (n_intervals == 0 || c->N == 0) return CHAD_OK;
+  cudaStream_t s = c->stream;
+  chad_status st = prepare_flow(c, dt_coupling_s);
+  if (st != CHAD_OK) return st;
+  const double dt_days = dt_coupling_s / 86400.0;
+  const int variant = c->variant[c->precision];
+  // one graph per interval: capture once, replay per interval (not possible
+  // on the legacy default stream)
+  if (c->use_graph && s != nullptr &&
+      (c->gexec == nullptr || c->g_dt != dt_coupling_s || c->g_variant != variant)) {
+    drop_graph(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue_interval(c, dt_days, variant, s);
+      e = cudaStreamEndCapture(s, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->gexec = nullptr;
+      c->use_graph = false;  // capture unavailable: launch directly from now on
+    } else {
+      c->g_dt = dt_coupling_s;
+      c->g_variant = variant;
+    }
+  }
+  for (int it = 0; it < n_intervals; ++it) {
+    if (c->gexec)
+      CK(c, cudaGraphLaunch(c->gexec, s), "graph launch");
+    else
+      CK(c, enqueue_interval(c, dt_days, variant, s), "interval launch");
+    c->intervals++;
+    c->sim_days += dt_days * (double)c->N;
+  }
+  return CHAD_OK;
+}
+
+chad_status chad_autotune(chad_ctx* c, double dt_coupling_s, int32_t* chosen, double* ms) {
+  if (!c) return CHAD_E_INVALID;
+  if (!(dt_coupling_s > 0.0) || !std::isfinite(dt_coupling_s))
+    return fail(c, CHAD_E_INVALID, "dt_coupling_s must be > 0");
+  for (int d = 0; d < c->n_dig; ++d)
+    if (!c->loaded[d]) return fail(c, CHAD_E_STATE, "every digester must be loaded before chad_autotune");
+  cudaStream_t s = c->stream;
+  chad_status st = prepare_flow(c, dt_coupling_s);
+  if (st != CHAD_OK) return st;
+  const size_t nd = (size_t)c->ld;
+  // snapshot of everything an interval modifies
+  const size_t dbl = (size_t)(NS + 3 + 3) * nd;  // y, pos, SH, h, D
+  double* snap = nullptr;
+  int* snap_st = nullptr;
+  if (cudaMalloc(&snap, sizeof(double) * dbl) != cudaSuccess) { cudaGetLastError(); return fail(c, CHAD_E_NOMEM, "autotune snapshot"); }
+  if (cudaMalloc(&snap_st, sizeof(int) * nd) != cudaSuccess) { cudaFree(snap); cudaGetLastError(); return fail(c, CHAD_E_NOMEM, "autotune snapshot"); }
+  DevCounters cnt_saved;
+  unsigned long long int_saved = 0;
+  auto save = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(snap, c->d_y, sizeof(double) * NS * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(snap + NS * nd, c->d_pos, sizeof(double) * 3 * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(snap + (NS + 3) * nd, c->d_SH, sizeof(double) * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(snap + (NS + 4) * nd, c->d_h, sizeof(double) * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(snap + (NS + 5) * nd, c->d_D, sizeof(double) * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(snap_st, c->d_status, sizeof(int) * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt_saved, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&int_saved, c->d_interval, sizeof(int_saved), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+  };
+  auto restore = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(c->d_y, snap, sizeof(double) * NS * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_pos, snap + NS * nd, sizeof(double) * 3 * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_SH, snap + (NS + 3) * nd, sizeof(double) * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_h, snap + (NS + 4) * nd, sizeof(double) * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_D, snap + (NS + 5) * nd, sizeof(double) * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_status, snap_st, sizeof(int) * nd, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt, &cnt_saved, sizeof(DevCounters), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_interval, &int_saved, sizeof(int_saved), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+  };
+  cudaError_t e = save();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int best = c->variant[c->precision];
+  float best_ms = 1e30f;
+  for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
+    e = restore();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = enqueue_interval(c, dt_coupling_s / 86400.0, v, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (ms) ms[v] = t;
+    if (e == cudaSuccess && t < best_ms) { best_ms = t; best = v; }
+  }
+  if (e == cudaSuccess) e = restore();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(snap);
+  cudaFree(snap_st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+  c->variant[c->precision] = best;
+  drop_graph(c);
+  if (chosen) *chosen = best;
   return CHAD_OK;
 }
 
@@ -470,9 +612,10 @@ chad_status chad_read_states(chad_ctx* c, int digester, double* y, double* pos, 
     stats->max_steps = dc.max_steps;
     stats->failed_particles = failed;
     stats->mlp_redo = 0;
+    stats->pivot_rejects = (int64_t)dc.pivot_rejects;
     stats->intervals = c->intervals;
     stats->sim_days = c->sim_days;
-    DevCounters z{0, 0, 0, 0, 0x7fffffff, 0, 0, 0};
+    DevCounters z{0, 0, 0, 0, 0, 0x7fffffff, 0};
     CK(c, cudaMemcpy(c->d_cnt, &z, sizeof(z), cudaMemcpyHostToDevice), "reset counters");
     c->intervals = 0;
     c->sim_days = 0.0;

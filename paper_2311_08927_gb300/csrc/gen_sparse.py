@@ -1,0 +1,244 @@
+"""Generate sparse_lu_gen.cuh: a static-order sparse LU of W = I - g J.
+
+The structural pattern of the ADM1 Jacobian is taken from the library's own
+model (chad_eval_model on the host, i.e. the same source as the kernels),
+evaluated at random states and randomly perturbed parameter sets so that no
+coefficient that happens to vanish for one parameter set is missed.  The
+elimination order is Markowitz's (minimise (r-1)(c-1) of each pivot on the
+remaining unsymmetric pattern, lowest state index on ties); its symbolic
+fill gives the storage slots.  The emitted code is straight-line with static
+slot indices:
+
+  slot(r, c)         storage slot of W_rc (-1 when structurally zero)
+  factor(w, dinv, t) in-place LU in the static order; returns false when a
+                     pivot fails the threshold test |u_kk| >= t max_i |l_ik u_kk|
+                     (equivalently |w_kk| >= t max_i |w_ik| before scaling)
+                     or is zero; the caller then shrinks the step, which
+                     drives W towards the identity where the order is safe
+  solve(w, dinv, b)  forward / back substitution in the static order
+  jx(j, x, out)      out = J x over J's structural nonzeros (FP64 residual)
+
+Run from the repository root:  python paper_2311_08927_gb300/csrc/gen_sparse.py
+"""
+from __future__ import annotations
+
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from paper_2311_08927_gb300 import chad as CH  # noqa: E402
+from paper_2311_08927_gb300 import inputs as I  # noqa: E402
+
+NS = I.NS
+OUT = os.path.join(HERE, "sparse_lu_gen.cuh")
+
+
+def jacobian_pattern(n_samples: int = 400, seed: int = 12345) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    base_p = I.default_params()
+    base_y = I.x_ss()
+    pat = np.eye(NS, dtype=bool)
+    for k in range(n_samples):
+        p = base_p * np.exp(0.3 * rng.standard_normal(base_p.size))
+        # keep the parameters that must stay ordered or fixed
+        for n in ("pH_LL_aa", "pH_UL_aa", "pH_LL_ac", "pH_UL_ac", "pH_LL_h2", "pH_UL_h2",
+                  "R", "R_J", "T_base", "pK_w", "pK_a_va", "pK_a_bu", "pK_a_pro", "pK_a_ac",
+                  "pK_a_co2", "pK_a_IN", "P_atm", "T_ref_kin", "V_liq_ref"):
+            p[I.PIDX[n]] = base_p[I.PIDX[n]]
+        y = base_y * np.exp(0.5 * rng.standard_normal(NS))
+        T = rng.uniform(298.0, 318.0)
+        D = rng.uniform(0.0, 1.0)
+        yin = I.influent() * np.exp(0.3 * rng.standard_normal(NS)) + 1e-6
+        _, J, _ = CH.eval_model(p, T, y, y_in=yin, D=D, V_liq=rng.uniform(1e-3, 1e4),
+                                V_gas=rng.uniform(1e-4, 1e3))
+        pat |= (J != 0.0)
+    return pat
+
+
+def markowitz(pat: np.ndarray) -> list[int]:
+    A = pat.copy()
+    rem = list(range(NS))
+    order = []
+    while rem:
+        best = None
+        for v in rem:
+            r = sum(A[v, u] for u in rem) - 1
+            c = sum(A[u, v] for u in rem) - 1
+            key = (r * c, v)
+            if best is None or key < best[0]:
+                best = (key, v)
+        v = best[1]
+        order.append(v)
+        rows = [u for u in rem if u != v and A[u, v]]
+        cols = [u for u in rem if u != v and A[v, u]]
+        for i in rows:
+            for j in cols:
+                A[i, j] = True
+        rem.remove(v)
+    return order
+
+
+def symbolic_fill(pat: np.ndarray, order: list[int]) -> np.ndarray:
+    P = pat[np.ix_(order, order)].copy()  # permuted positions
+    for k in range(NS):
+        rows = [i for i in range(k + 1, NS) if P[i, k]]
+        cols = [j for j in range(k + 1, NS) if P[k, j]]
+        for i in rows:
+            for j in cols:
+                P[i, j] = True
+    return P
+
+
+def generate(pat: np.ndarray) -> str:
+    order = markowitz(pat)
+    F = symbolic_fill(pat, order)  # in permuted positions
+    pos = {s: k for k, s in enumerate(order)}
+    slot = -np.ones((NS, NS), dtype=int)
+    n = 0
+    for k in range(NS):              # row-major over permuted positions
+        for j in range(NS):
+            if F[k, j]:
+                slot[order[k], order[j]] = n
+                n += 1
+    nnz = n
+    nnz_j = int(pat.sum())
+    flops = 0
+    L = []
+    w = L.append
+    w("// GENERATED by gen_sparse.py from the library's own Jacobian pattern -- do not edit.")
+    w("// Static-order (Markowitz) sparse LU of W = I - g J for the 29 ADM1 states.")
+    w(f"// pattern nnz(J) = {nnz_j}, slots with fill = {nnz}")
+    w("#pragma once")
+    w('#include "adm1_device.cuh"')
+    w("")
+    w("namespace chad {")
+    w("namespace sp {")
+    w("")
+    w(f"constexpr int kNNZ = {nnz};")
+    w(f"constexpr int kNNZ_J = {nnz_j};")
+    w("// elimination position -> state index")
+    w("constexpr int kOrder[NS] = {" + ", ".join(str(v) for v in order) + "};")
+    w("")
+    w("CHAD_HD constexpr int slot(int r, int c) {")
+    w("  // row-major table over states, -1 = structurally zero")
+    rows = []
+    for r in range(NS):
+        rows.append("      " + ", ".join(str(int(slot[r, c])) for c in range(NS)))
+    w("  const int t[NS * NS] = {")
+    w(",\n".join(rows))
+    w("  };")
+    w("  return t[r * NS + c];")
+    w("}")
+    w("")
+    w("struct Idx {")
+    w("  static CHAD_HD constexpr int at(int r, int c) { return slot(r, c); }")
+    w("  static constexpr int size = kNNZ;")
+    w("};")
+    w("")
+    w("// diagonal slots in elimination order")
+    w("constexpr int kDiag[NS] = {" + ", ".join(str(int(slot[s, s])) for s in order) + "};")
+    w("")
+    # ------------------------------------------------------------- W formation
+    w("// W = I - g J in place over the slots (fill slots hold zero in J)")
+    w("template <class R>")
+    w("CHAD_HD void form_w(R* w, R g) {")
+    w("#pragma unroll")
+    w("  for (int s = 0; s < kNNZ; ++s) w[s] = -g * w[s];")
+    for sidx in order:
+        w(f"  w[{int(slot[sidx, sidx])}] += R(1);")
+    w("}")
+    w("")
+    # ------------------------------------------------------------- factor
+    w("// In-place LU; returns false if a pivot fails the threshold test.")
+    w("template <class R>")
+    w("CHAD_HD bool factor(R* w, R* dinv, R tau) {")
+    w("  bool ok = true;")
+    for k in range(NS):
+        pv = order[k]
+        d = slot[pv, pv]
+        sub = [i for i in range(k + 1, NS) if F[i, k]]
+        ucols = [j for j in range(k + 1, NS) if F[k, j]]
+        w(f"  {{  // pivot {k}: state {pv} ({I.STATE_NAMES[pv]}), {len(sub)} rows x {len(ucols)} cols")
+        w(f"    const R pv = w[{d}];")
+        if sub:
+            terms = [f"fabs(w[{slot[order[i], pv]}])" for i in sub]
+            expr = terms[0]
+            for t in terms[1:]:
+                expr = f"fmax({expr}, {t})"
+            w(f"    const R cm = {expr};")
+            w("    ok = ok && (fabs(pv) >= tau * cm);")
+        w("    ok = ok && (pv != R(0)) && isfinite(pv);")
+        w("    const R inv = R(1) / pv;")
+        w(f"    dinv[{k}] = inv;")
+        flops += 1
+        for i in sub:
+            sik = slot[order[i], pv]
+            w(f"    {{ const R l = w[{sik}] * inv; w[{sik}] = l;")
+            flops += 1
+            for j in ucols:
+                w(f"      w[{slot[order[i], order[j]]}] -= l * w[{slot[pv, order[j]]}];")
+                flops += 2
+            w("    }")
+        w("  }")
+    w("  return ok;")
+    w("}")
+    w("")
+    # ------------------------------------------------------------- solve
+    w("// Solve W x = b in place (b indexed by state).")
+    w("template <class R>")
+    w("CHAD_HD void solve(const R* w, const R* dinv, R* b) {")
+    for k in range(NS):
+        w(f"  R z{k} = b[{order[k]}];")
+    sflops = 0
+    for k in range(NS):  # forward, unit lower
+        terms = [(j, slot[order[k], order[j]]) for j in range(k) if F[k, j]]
+        for j, s in terms:
+            w(f"  z{k} -= w[{s}] * z{j};")
+            sflops += 2
+    for k in reversed(range(NS)):  # back
+        terms = [(j, slot[order[k], order[j]]) for j in range(k + 1, NS) if F[k, j]]
+        for j, s in terms:
+            w(f"  z{k} -= w[{s}] * z{j};")
+            sflops += 2
+        w(f"  z{k} *= dinv[{k}];")
+        sflops += 1
+    for k in range(NS):
+        w(f"  b[{order[k]}] = z{k};")
+    w("}")
+    w("")
+    # ------------------------------------------------------------- J x
+    w("// out = J x over the structural nonzeros of J (slots of a J array).")
+    w("template <class RJ>")
+    w("CHAD_HD void jx(const RJ* j, const double* x, double* out) {")
+    jflops = 0
+    for r in range(NS):
+        cols = [c for c in range(NS) if pat[r, c]]
+        expr = " + ".join(f"double(j[{slot[r, c]}]) * x[{c}]" for c in cols) or "0.0"
+        w(f"  out[{r}] = {expr};")
+        jflops += 2 * len(cols)
+    w("}")
+    w("")
+    w(f"constexpr int kFactorFlops = {flops};")
+    w(f"constexpr int kSolveFlops = {sflops};")
+    w(f"constexpr int kJxFlops = {jflops};")
+    w("")
+    w("}  // namespace sp")
+    w("}  // namespace chad")
+    return "\n".join(L) + "\n", dict(nnz=nnz, nnz_j=nnz_j, factor=flops, solve=sflops, jx=jflops,
+                                      order=[I.STATE_NAMES[s] for s in order])
+
+
+def main():
+    pat = jacobian_pattern()
+    src, info = generate(pat)
+    with open(OUT, "w") as fh:
+        fh.write(src)
+    print(f"wrote {OUT}: {info}")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,9 @@
+// Integrator kernel instance: precision form 0, at least 2 resident
+// 128-thread blocks per SM (sets the register budget).  See integrate_impl.cuh.
+#include "integrate_impl.cuh"
+
+namespace chad {
+cudaError_t launch_integrate_f0_v0(const StepArgs& a, cudaStream_t s) {
+  return launch_variant<0, 2>(a, s);
+}
+}  // namespace chad

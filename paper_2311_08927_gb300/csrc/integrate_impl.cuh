@@ -1,0 +1,339 @@
+// Per-particle stiff integration over one coupling interval (Sec. 2.3: each
+// AD particle is integrated independently over every synchronised interval).
+//
+// Persistent kernel, one particle per thread at a time: a lane pulls the next
+// particle from a device queue (warp-aggregated atomic) as soon as its own
+// particle has reached the end of the interval, so warps stay full while
+// particles take very different numbers of steps (substrate slugs).
+//
+// The step is the linearly implicit Rosenbrock 2(3) W-method of Shampine &
+// Reichelt (1997): d = 1/(2+sqrt 2), e32 = 6 + sqrt 2, W = I - h d J, three
+// stages sharing one LU, embedded error h/6 (k1 - 2 k2 + k3), controller
+// fac = min(5, max(0.2, 0.8 e^-1/3)) with growth capped at 1 after a
+// rejection, last step clipped to the end of the interval.  S_H+ of Eq. 7 is
+// re-solved by FP64 Newton at every rate evaluation.
+//
+// W is factored by the generated static-order sparse LU (sparse_lu_gen.cuh).
+// A pivot failing the threshold test rejects the attempt and shrinks h by 4,
+// which moves W towards the identity, where the static order is stable.
+//
+// Forms: FP64 (J, LU, solves in FP64); MIXED (J, LU, solves in FP32, one
+// FP64 refinement step r = b - W x per solve, stage rates FP64); MIXED with
+// FP32 stage rates.  Newton, state accumulation and error estimate: FP64.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+#include <type_traits>
+
+#include "adm1_device.cuh"
+#include "kernels.h"
+#include "sparse_lu_gen.cuh"
+
+namespace chad {
+namespace integ {
+
+constexpr double kRB_d = 0.29289321881345247559915563789515;   // 1/(2+sqrt 2)
+constexpr double kRB_e32 = 7.4142135623730950488016887242097;  // 6+sqrt 2
+constexpr double kHmin = 1e-12;                                 // days
+constexpr double kHdefault = 1e-6;                              // days
+constexpr double kPivTau = 0.1;                                 // threshold pivoting
+
+struct Cnt {
+  int acc, rej, newton, fallback, failed, pivot;
+};
+
+__device__ __forceinline__ int64_t queue_pop(unsigned long long* q) {
+  const unsigned m = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(q, (unsigned long long)__popc(m));
+  base = __shfl_sync(m, base, leader);
+  return (int64_t)(base + (unsigned long long)__popc(m & ((1u << lane) - 1u)));
+}
+
+__device__ __forceinline__ void newton(const DigConst& c, const PartConst& q, const double* y,
+                                       double& SHg, int max_newton, Cnt& cnt, AcidBase& ab) {
+  NewtonCounters nc{0, 0, 0};
+  solve_SH(c, q, y, SHg, max_newton, ab, nc);
+  cnt.newton += nc.iters;
+  cnt.fallback += nc.fallbacks;
+  cnt.failed |= nc.failed;
+  SHg = ab.SH;
+}
+
+// f(y) in precision RS (Newton in FP64)
+template <class RS>
+__device__ __forceinline__ void eval_f(const DigConst& c, const PartConst& q, const double* y,
+                                       double D, double& SHg, int max_newton, Cnt& cnt,
+                                       double* f) {
+  AcidBase ab;
+  newton(c, q, y, SHg, max_newton, cnt, ab);
+  RS yr[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) yr[i] = RS(y[i]);
+  Rates<RS> o;
+  rates<RS, false>(c, q, yr, ab, o);
+  RS fr[NS];
+  balances<RS>(c, yr, RS(D), o, fr);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) f[i] = double(fr[i]);
+}
+
+// f(y) in precision RS and J in precision R (sparse slots), one Newton solve
+template <class R, class RS>
+__device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, const double* y,
+                                        double D, double& SHg, int max_newton, Cnt& cnt,
+                                        double* f, R* w) {
+  AcidBase ab;
+  newton(c, q, y, SHg, max_newton, cnt, ab);
+  {
+    R yr[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) yr[i] = R(y[i]);
+    Rates<R> o;
+    rates<R, true>(c, q, yr, ab, o);
+    if (std::is_same<R, RS>::value) {
+      R fr[NS];
+      balances<R>(c, yr, R(D), o, fr);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) f[i] = double(fr[i]);
+    }
+    jacobian<sp::Idx, R>(c, q, yr, R(D), ab, o, w);
+  }
+  if (!std::is_same<R, RS>::value) {
+    RS ys[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) ys[i] = RS(y[i]);
+    Rates<RS> o;
+    rates<RS, false>(c, q, ys, ab, o);
+    RS fr[NS];
+    balances<RS>(c, ys, RS(D), o, fr);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) f[i] = double(fr[i]);
+  }
+}
+
+// W x = b with the factored W.  Mixed: FP32 solve, FP64 residual
+// r = b - x + g (J x) with the kept FP32 Jacobian, FP32 correction solve.
+template <bool MIXED, class R>
+__device__ __forceinline__ void solve(const R* w, const R* dinv, const R* jk, double g,
+                                      const double* b, double* x) {
+  R t[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) t[i] = R(b[i]);
+  sp::solve<R>(w, dinv, t);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) x[i] = double(t[i]);
+  if (MIXED) {
+    double jx[NS];
+    sp::jx<R>(jk, x, jx);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) t[i] = R(b[i] - x[i] + g * jx[i]);
+    sp::solve<R>(w, dinv, t);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) x[i] += double(t[i]);
+  }
+}
+
+template <int FORM, int MINB>
+__global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
+  constexpr bool MIXED = FORM != 0;
+  using R = typename std::conditional<MIXED, float, double>::type;
+  using RS = typename std::conditional<FORM == 2, float, double>::type;
+  __shared__ unsigned long long s_acc, s_rej, s_newton, s_fb, s_piv;
+  __shared__ int s_min, s_max;
+  if (threadIdx.x == 0) {
+    s_acc = s_rej = s_newton = s_fb = s_piv = 0ull;
+    s_min = INT_MAX;
+    s_max = 0;
+  }
+  __syncthreads();
+
+  R w[sp::kNNZ];
+  R jk[MIXED ? sp::kNNZ : 1];
+  R dinv[NS];
+  double y[NS], F0[NS], k1[NS], k2[NS], F1[NS], y1[NS], tmp[NS];
+  const double Tend = a.dt_days;
+  const bool fixed = a.fixed_n > 0;
+  Cnt tot{0, 0, 0, 0, 0, 0};
+  int min_steps = INT_MAX, max_steps = 0;
+
+  int64_t p = -1;
+  const DigConst* c = nullptr;
+  PartConst q;
+  double SHg = 0.0, h = 0.0, t = 0.0, D = 0.0;
+  int status = 0, attempts = 0, nacc = 0;
+  bool rejected_prev = false;
+  Cnt cnt{0, 0, 0, 0, 0, 0};
+
+  while (true) {
+    if (p < 0) {
+      p = queue_pop(a.queue);
+      if (p >= a.n) break;
+      c = &a.dc[a.dig[p]];
+      part_const(*c, a.T[p], q);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) y[i] = a.y[i * a.ld + p];
+      SHg = a.SH[p];
+      h = a.h[p];
+      h = (h > 0.0 && isfinite(h)) ? h : kHdefault;
+      if (fixed) h = Tend / a.fixed_n;
+      D = a.D[p];
+      t = 0.0;
+      status = 0;
+      attempts = 0;
+      nacc = 0;
+      rejected_prev = false;
+      cnt = Cnt{0, 0, 0, 0, 0, 0};
+    }
+    // ------------------------------------------------ one step attempt
+    bool done = false;
+    ++attempts;
+    double hh = h;
+    bool last = false;
+    if (!fixed && hh >= (Tend - t) * (1.0 - 1e-12)) {
+      hh = Tend - t;
+      last = true;
+    }
+    eval_fj<R, RS>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w);
+    if (MIXED) {
+#pragma unroll
+      for (int s = 0; s < sp::kNNZ; ++s) jk[s] = w[s];
+    }
+    const double g = hh * kRB_d;
+    sp::form_w<R>(w, R(g));
+    const bool piv_ok = sp::factor<R>(w, dinv, R(kPivTau));
+    double norm = INFINITY;
+    if (!piv_ok) cnt.pivot++;
+    if (piv_ok || fixed) {
+      solve<MIXED, R>(w, dinv, jk, g, F0, k1);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) tmp[i] = y[i] + 0.5 * hh * k1[i];
+      eval_f<RS>(*c, q, tmp, D, SHg, a.max_newton, cnt, F1);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) tmp[i] = F1[i] - k1[i];
+      solve<MIXED, R>(w, dinv, jk, g, tmp, k2);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        k2[i] += k1[i];
+        y1[i] = y[i] + hh * k2[i];
+      }
+      eval_f<RS>(*c, q, y1, D, SHg, a.max_newton, cnt, tmp);  // F2
+#pragma unroll
+      for (int i = 0; i < NS; ++i)
+        tmp[i] = tmp[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
+      solve<MIXED, R>(w, dinv, jk, g, tmp, F1);  // k3
+      norm = 0.0;
+      const double h6 = hh / 6.0;
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        const double e = h6 * (k1[i] - 2.0 * k2[i] + F1[i]);
+        const double sc = a.atol[i] + a.rtol * fmax(fabs(y[i]), fabs(y1[i]));
+        const double r = fabs(e) / sc;
+        if (!(r <= norm)) norm = r;  // NaN propagates
+      }
+    }
+    if (fixed) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) y[i] = y1[i];
+      cnt.acc++;
+      ++nacc;
+      if (!isfinite(norm)) status |= ST_NAN;
+      if (nacc >= a.fixed_n || (status & ST_NAN)) done = true;
+    } else if (norm <= 1.0) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) y[i] = y1[i];
+      t = last ? Tend : t + hh;
+      cnt.acc++;
+      ++nacc;
+      double fac = (norm == 0.0) ? 5.0 : fmin(5.0, fmax(0.2, 0.8 * pow(norm, -1.0 / 3.0)));
+      if (rejected_prev) fac = fmin(fac, 1.0);
+      h = hh * fac;
+      rejected_prev = false;
+      if (last) done = true;
+    } else {
+      cnt.rej++;
+      const double fac =
+          !piv_ok ? 0.25 : (isfinite(norm) ? fmax(0.2, 0.8 * pow(norm, -1.0 / 3.0)) : 0.2);
+      h = hh * fac;
+      rejected_prev = true;
+      if (h < kHmin) {
+        status |= ST_HMIN;
+        done = true;
+      }
+    }
+    if (!done && !fixed && attempts >= a.max_steps) {
+      status |= ST_STEPS;
+      done = true;
+    }
+    // ------------------------------------------------ particle finished
+    if (done) {
+      if (cnt.failed) status |= ST_NEWTON;
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        if (!isfinite(y[i])) status |= ST_NAN;
+        if (y[i] < -a.atol[i]) status |= ST_NEG;
+      }
+#pragma unroll
+      for (int i = 0; i < NS; ++i) a.y[i * a.ld + p] = y[i];
+      a.SH[p] = SHg;
+      if (!fixed) a.h[p] = h;
+      if (status) a.status[p] |= status;
+      tot.acc += cnt.acc;
+      tot.rej += cnt.rej;
+      tot.newton += cnt.newton;
+      tot.fallback += cnt.fallback;
+      tot.pivot += cnt.pivot;
+      min_steps = min(min_steps, nacc);
+      max_steps = max(max_steps, nacc);
+      p = -1;
+    }
+  }
+
+  atomicAdd(&s_acc, (unsigned long long)tot.acc);
+  atomicAdd(&s_rej, (unsigned long long)tot.rej);
+  atomicAdd(&s_newton, (unsigned long long)tot.newton);
+  atomicAdd(&s_fb, (unsigned long long)tot.fallback);
+  atomicAdd(&s_piv, (unsigned long long)tot.pivot);
+  atomicMin(&s_min, min_steps);
+  atomicMax(&s_max, max_steps);
+  __syncthreads();
+  if (threadIdx.x == 0 && a.counters) {
+    atomicAdd(&a.counters->accepted, s_acc);
+    atomicAdd(&a.counters->rejected, s_rej);
+    atomicAdd(&a.counters->newton_iters, s_newton);
+    atomicAdd(&a.counters->newton_fallbacks, s_fb);
+    atomicAdd(&a.counters->pivot_rejects, s_piv);
+    if (s_min != INT_MAX) atomicMin(&a.counters->min_steps, s_min);
+    atomicMax(&a.counters->max_steps, s_max);
+  }
+}
+
+}  // namespace integ
+
+// Launch one kernel variant: persistent grid (resident blocks per SM x SMs,
+// capped by the particle count), queue head reset first.
+template <int FORM, int MINB>
+cudaError_t launch_variant(const StepArgs& a, cudaStream_t s) {
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integ::integrate_kernel<FORM, MINB>, 128, 0);
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int block = 128;
+  int64_t blocks = (int64_t)sms * per_sm;
+  const int64_t need = (a.n + block - 1) / block;
+  if (need < blocks) blocks = need;
+  cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  integ::integrate_kernel<FORM, MINB><<<(unsigned)blocks, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace chad

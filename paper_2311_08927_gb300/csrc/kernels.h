@@ -13,8 +13,8 @@ enum : int { ST_NEWTON = 1, ST_STEPS = 2, ST_HMIN = 4, ST_NEG = 8, ST_NAN = 16 }
 
 // Device counters accumulated by the integrator (reset by the host)
 struct DevCounters {
-  unsigned long long accepted, rejected, newton_iters, newton_fallbacks;
-  int min_steps, max_steps, pad0, pad1;
+  unsigned long long accepted, rejected, newton_iters, newton_fallbacks, pivot_rejects;
+  int min_steps, max_steps;
 };
 
 struct StepArgs {
@@ -35,6 +35,7 @@ struct StepArgs {
   int max_newton;
   int fixed_n;          // 0: adaptive
   DevCounters* counters;
+  unsigned long long* queue;  // particle queue head (reset before each launch)
 };
 
 struct AdvectArgs {
@@ -44,7 +45,7 @@ struct AdvectArgs {
   const FlowConst* fl;
   double* pos;                // [3][ld]
   double* D;                  // [n] written for particles of digesters with flow
-  uint64_t interval;          // global interval index (noise counter)
+  const unsigned long long* interval;  // device copy of the global interval index
 };
 
 struct HeadspaceArgs {
@@ -63,8 +64,13 @@ struct HeadspaceArgs {
   int64_t n;
 };
 
-cudaError_t launch_integrate(const StepArgs& a, bool mixed, int block, cudaStream_t s);
+// Integrator kernel variants (min resident blocks per SM = variant + 2)
+constexpr int kNumVariants = 3;
+constexpr int kDefaultVariant = 0;
+cudaError_t launch_integrate(const StepArgs& a, int precision, int variant, cudaStream_t s);
 cudaError_t launch_advect(const AdvectArgs& a, cudaStream_t s);
+// interval index += 1 (last node of every interval)
+cudaError_t launch_bump(unsigned long long* interval, cudaStream_t s);
 cudaError_t launch_headspace(const HeadspaceArgs& a, cudaStream_t s);
 
 constexpr int kHeadspaceChunk = 4096;  // particles per partial sum

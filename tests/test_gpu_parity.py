@@ -256,3 +256,52 @@ def test_device_buffers_through_torch():
     assert code == 0
     ref = gpu_run(pop, 60.0, 2)
     assert np.array_equal(out.cpu().numpy(), ref["y"])
+
+
+# ------------------------------------------------------------ model, tuning, graphs
+def test_device_jacobian_matches_oracle_ad():
+    """The kernels' analytic Jacobian, evaluated on the GPU, equals the
+    oracle's dual-number Jacobian to 1e-12 (column-relative)."""
+    rng = np.random.default_rng(8)
+    for _ in range(10):
+        y = I.x_ss() * np.exp(0.3 * rng.standard_normal(I.NS))
+        T = rng.uniform(303.15, 313.15)
+        f, J, SH = CH.eval_model(I.default_params(), T, y, y_in=I.influent(), D=0.2, on_device=True)
+        Jo = O.jacobian(I.default_params(), T, y, y_in=I.influent(), D=0.2)
+        assert np.max(np.abs(J - Jo) / (np.abs(Jo).max(axis=0, keepdims=True) + 1e-300)) < 1e-12
+
+
+def _run_stream(pop, n, tune=False, graph=True, precision=CH.PREC_FP64):
+    import torch
+    s = torch.cuda.Stream() if graph else None
+    sim = CH.Simulator(pop, precision=precision, stream=None if s is None else s.cuda_stream)
+    sim.load()
+    chosen = None
+    if tune:
+        chosen, ms = CH.chad_autotune(sim.ctx, 60.0)
+        assert 0 <= chosen < len(ms) and np.all(ms > 0)
+    sim.step(60.0, n)
+    out = sim.read()
+    sim.close()
+    return out, chosen
+
+
+@pytest.mark.parametrize("precision", [CH.PREC_FP64, CH.PREC_MIXED])
+def test_autotune_and_graph_replay_leave_results_unchanged(precision):
+    pop = I.config_population(2, n=3000)
+    direct, _ = _run_stream(pop, 3, graph=False, precision=precision)
+    graphed, _ = _run_stream(pop, 3, graph=True, precision=precision)
+    tuned, chosen = _run_stream(pop, 3, tune=True, graph=True, precision=precision)
+    assert np.array_equal(direct["y"], graphed["y"]) and np.array_equal(direct["pos"], graphed["pos"])
+    assert relerr(tuned["y"], direct["y"]).max() < 1e-12
+    assert np.array_equal(tuned["pos"], direct["pos"])
+
+
+def test_mixed_f32_rates_form_within_tolerance():
+    pop = I.config_population(3, n=3000)
+    idx = np.concatenate([pop.slugs[:8], np.setdiff1d(np.arange(3000), pop.slugs)[:40]])
+    sp = subset(pop, idx)
+    g = gpu_run(sp, 60.0, 10, rtol=1e-6, precision=CH.PREC_MIXED_F32RATES)
+    o = oracle_run(sp, 60.0, 10, rtol=1e-10, atol=I.atol_vector(1e-13))
+    assert np.all(g["status"] == 0)
+    assert relerr(g["y"], o["y"]).max() < 1e-4

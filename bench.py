@@ -126,23 +126,23 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- algorithmic work
-def fp64_flops_per_attempt(precision: int) -> float:
-    """Algorithmic FP64 flops of one W-method step attempt on n = 29 states.
+def work_per_launch(CH, precision, stats, steps):
+    """Algorithmic FP64 / FP32 operations of one integrator launch.
 
-    Plain form: W = I - g J (2n^2), dense LU with partial pivoting
-    (sum_k [(n-k-1) multipliers + 2 (n-k-1)^2 updates] + n reciprocals),
-    3 triangular solve pairs (2n^2 - n + n each), stage combinations (~12n).
-    Mixed form: FP64 part only -- 3 refinement residuals (2n^2 + 3n each)
-    and the stage combinations; the FP32 LU and solves are not counted.
-    Rate evaluations, Jacobian assembly and the Eq. 7 Newton are excluded
-    from both (conservative: achieved rates are lower bounds)."""
-    n = 29
-    lu = sum((n - k - 1) + 2 * (n - k - 1) ** 2 for k in range(n)) + n
-    solves = 3 * (2 * n * n)
-    stage = 12 * n
-    if precision == 0:
-        return 2 * n * n + lu + solves + stage
-    return 3 * (2 * n * n + 3 * n) + stage
+    Counts come from the kernel source (chad_flop_counts: the templated
+    rate, Jacobian and sparse-LU routines run with an operation-counting
+    scalar): per step attempt the W-method's rate evaluations, Jacobian,
+    W formation, static-order sparse LU, three solves (mixed: FP32 solves
+    plus FP64 refinement residuals J x) and stage combinations; per Newton
+    iteration of Eq. 7 one charge-balance evaluation plus the update; three
+    final charge-balance evaluations per attempt."""
+    af = CH.attempt_flops(precision)
+    nf = CH.newton_flops()
+    ce = CH.flop_counts()["charge_E"]
+    attempts = stats["accepted_steps"] + stats["rejected_steps"]
+    f64 = attempts * (af["fp64"] + 3 * ce) + stats["newton_iters"] * nf
+    f32 = attempts * af["fp32"]
+    return f64 / steps, f32 / steps, af
 
 
 # --------------------------------------------------------------------------- our arm
@@ -186,8 +186,12 @@ def run_ours(args, ws, rank, local):
         attempts = st["accepted_steps"] + st["rejected_steps"]
         sim.close()
         launch_ms = statistics.mean(per)
-        achieved = fp64_flops_per_attempt(precision) * attempts / args.steps / (launch_ms * 1e-3) / 1e12
+        f64, f32, af = work_per_launch(CH, precision, st, args.steps)
+        achieved = f64 / (launch_ms * 1e-3) / 1e12
+        achieved32 = f32 / (launch_ms * 1e-3) / 1e12
         return dict(total_ms=total_ms, per_ms=per, launch_ms=launch_ms, stats=st,
+                    f64_per_launch=f64, f32_per_launch=f32, attempt_flops=af,
+                    achieved32_tflops=achieved32,
                     variant=variant, tune_ms=[float(x) for x in tune_ms],
                     attempts=attempts, failed=int((out["status"] != 0).sum()),
                     clocks=clk.summary(), achieved_tflops=achieved,
@@ -247,9 +251,13 @@ def run_ours(args, ws, rank, local):
                    "parallelism": f"particles sharded, {ws} independent populations"},
         "roofline": {"bound": "alu", "achieved": H["achieved_tflops"], "peak": peak64,
                      "unit": "TFLOP/s", "frac": H["achieved_tflops"] / peak64, "traffic": None,
-                     "kernel": "integrate_kernel", "peak_source": "measured FP64 DFMA chains (chad_probe_alu_peak)",
-                     "flops_per_attempt": fp64_flops_per_attempt(1 if head == "mixed" else 0),
-                     "attempts_per_step": H["attempts"] / args.steps},
+                     "kernel": "integrate_kernel (FP64 part)",
+                     "peak_source": "measured FP64 DFMA chains (chad_probe_alu_peak)",
+                     "fp64_flops_per_launch": H["f64_per_launch"],
+                     "attempt_flops": H["attempt_flops"],
+                     "attempts_per_step": H["attempts"] / args.steps,
+                     "fp32": {"achieved": H["achieved32_tflops"], "peak": peak32,
+                              "frac": H["achieved32_tflops"] / peak32}},
         "peaks_measured": {"fp64_tflops": peak64, "fp32_tflops": peak32},
         "clocks": fr,
         "gpu_launches": args.steps,
@@ -267,7 +275,8 @@ def run_ours(args, ws, rank, local):
             "ms_per_step": F["total_ms"] / args.steps,
             "roofline": {"bound": "alu", "achieved": F["achieved_tflops"], "peak": peak64,
                          "unit": "TFLOP/s", "frac": F["achieved_tflops"] / peak64,
-                         "flops_per_attempt": fp64_flops_per_attempt(0)},
+                         "fp64_flops_per_launch": F["f64_per_launch"],
+                         "attempt_flops": F["attempt_flops"]},
             "steps_per_particle_interval": F["stats"]["accepted_steps"] / (N * args.steps),
             "clocks": F["clocks"],
         }
@@ -302,17 +311,22 @@ def _calibrate_sample(pop, intervals, budget_s, cores):
 
 def cpu_baseline(pop, warmup, k, budget_s):
     """The oracle as it stands (FP64, std::thread equal chunks over all host
-    cores) on a seeded sample of the workload, over the same intervals."""
+    cores) on a seeded sample of the workload, over the same intervals; the
+    sample grows until the timed part takes about budget_s seconds."""
     import oracle as O
     from paper_2311_08927_gb300 import inputs as I
     cores = os.cpu_count() or 1
     n_s = _calibrate_sample(pop, warmup + k, budget_s, cores)
-    sub = _oracle_sample(pop, n_s)
-    r = O.run(sub, DT_S, warmup, rtol=1e-6, n_threads=cores)
-    sub2 = I.Population(sub.digesters, r["y"], sub.T, sub.pos, False)
-    t0 = time.perf_counter()
-    O.run(sub2, DT_S, k, interval0=warmup, rtol=1e-6, SH=r["S_H"], h=r["h"], n_threads=cores)
-    dt = time.perf_counter() - t0
+    for _ in range(3):
+        sub = _oracle_sample(pop, n_s)
+        r = O.run(sub, DT_S, warmup, rtol=1e-6, n_threads=cores)
+        sub2 = I.Population(sub.digesters, r["y"], sub.T, sub.pos, False)
+        t0 = time.perf_counter()
+        O.run(sub2, DT_S, k, interval0=warmup, rtol=1e-6, SH=r["S_H"], h=r["h"], n_threads=cores)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * budget_s or n_s >= 200_000:
+            break
+        n_s = int(min(200_000, n_s * budget_s / max(dt, 1e-3)))
     return {"value": n_s * k * DT_S / 86400.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_s} seeded particles of the 1M workload, intervals {warmup}..{warmup + k - 1} "
                       f"(after {warmup} untimed), rtol 1e-6, {dt:.1f} s"}

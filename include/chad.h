@@ -206,6 +206,15 @@ chad_status chad_read_states(chad_ctx* ctx, int digester, double* y, double* pos
    bound by plain ALU arithmetic.  Allocates and frees a small buffer. */
 chad_status chad_probe_alu_peak(int fp64, double* tflops);
 
+/* Algorithmic operation counts of the integrator's building blocks, taken
+   from the kernel source (its templated routines run on the host with an
+   operation-counting scalar; +, -, *, / count 1, an FMA 2): out[0] one rate
+   vector, out[1] rate vector + analytic Jacobian, out[2] one Eq. 7
+   evaluation, out[3] W formation, out[4] sparse LU, out[5] one sparse
+   solve, out[6] J x, out[7] stage combinations and error norm of one step
+   attempt, out[8] refinement update of one mixed solve.  n >= 9. */
+chad_status chad_flop_counts(int64_t* out, int n);
+
 /* Evaluate the library's model for one particle: f = dy/dt (Eq. 2-6) [29],
    the analytic Jacobian J = df/dy [29][29] row-major (with S_H(y) from Eq. 7
    differentiated implicitly), and the Eq. 7 root *SH, for the digester

@@ -98,6 +98,8 @@ def lib():
             L.chad_read_states.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.POINTER(chad_stats), C.c_int]
+            L.chad_flop_counts.restype = C.c_int
+            L.chad_flop_counts.argtypes = [C.c_void_p, C.c_int]
             L.chad_autotune.restype = C.c_int
             L.chad_autotune.argtypes = [C.c_void_p, C.c_double, C.POINTER(C.c_int32), C.c_void_p]
             L.chad_eval_model.restype = C.c_int
@@ -114,7 +116,39 @@ def exported_symbols() -> list[str]:
     return ["chad_abi_version", "chad_n_params", "chad_param_name", "chad_last_error",
             "chad_create", "chad_destroy", "chad_load_particles", "chad_set_flow",
             "chad_step", "chad_synchronize", "chad_read_states", "chad_probe_alu_peak",
-            "chad_eval_model", "chad_autotune"]
+            "chad_eval_model", "chad_autotune", "chad_flop_counts"]
+
+
+FLOP_KEYS = ["rates_f", "rates_fj", "charge_E", "form_w", "factor", "solve", "jx", "stage",
+             "refine"]
+
+
+def flop_counts() -> dict:
+    """Algorithmic operation counts of the integrator's building blocks."""
+    L = lib()
+    out = np.zeros(9, dtype=np.int64)
+    _check(L, None, L.chad_flop_counts(out.ctypes.data, 9))
+    return dict(zip(FLOP_KEYS, (int(x) for x in out)))
+
+
+def attempt_flops(precision: int) -> dict:
+    """FP64 and FP32 operations of one W-method step attempt, without the
+    Eq. 7 Newton iterations (counted separately per iteration)."""
+    f = flop_counts()
+    if precision == PREC_FP64:
+        f64 = (f["rates_fj"] + 2 * f["rates_f"] + f["form_w"] + f["factor"] + 3 * f["solve"] +
+               f["stage"])
+        return {"fp64": f64, "fp32": 0}
+    f32_rates = precision == PREC_MIXED_F32RATES
+    f64 = 3 * (f["jx"] + f["refine"]) + f["stage"] + (0 if f32_rates else 3 * f["rates_f"])
+    f32 = (f["rates_fj"] + f["form_w"] + f["factor"] + 6 * f["solve"] +
+           (2 * f["rates_f"] if f32_rates else 0))
+    return {"fp64": f64, "fp32": f32}
+
+
+def newton_flops() -> int:
+    """FP64 operations of one Eq. 7 Newton iteration (evaluation + update)."""
+    return flop_counts()["charge_E"] + 2
 
 
 def chad_autotune(ctx, dt_coupling_s):

@@ -58,26 +58,41 @@ struct AcidBase {
   double r_IN, r_co2, r_ac, r_pro, r_bu, r_va;  // 1/(K_a + S_H) at the root
 };
 
-// E(S) and dE/dS; fills the reciprocals used by the Jacobian
-CHAD_HD double charge_E(const DigConst& c, const PartConst& q,
-                                           const double* y, double S, AcidBase& ab) {
-  const double rS = 1.0 / S;
-  ab.r_IN = 1.0 / (q.K_a_IN + S);
-  ab.r_co2 = 1.0 / (q.K_a_co2 + S);
-  ab.r_ac = 1.0 / (c.K_a_ac + S);
-  ab.r_pro = 1.0 / (c.K_a_pro + S);
-  ab.r_bu = 1.0 / (c.K_a_bu + S);
-  ab.r_va = 1.0 / (c.K_a_va + S);
-  const double nh3 = q.K_a_IN * y[iS_IN] * ab.r_IN;
-  const double hco3 = q.K_a_co2 * y[iS_IC] * ab.r_co2;
-  const double ac = c.K_a_ac * y[iS_ac] * ab.r_ac * (1.0 / kVfaCod_ac);
-  const double pro = c.K_a_pro * y[iS_pro] * ab.r_pro * (1.0 / kVfaCod_pro);
-  const double bu = c.K_a_bu * y[iS_bu] * ab.r_bu * (1.0 / kVfaCod_bu);
-  const double va = c.K_a_va * y[iS_va] * ab.r_va * (1.0 / kVfaCod_va);
-  const double kw = q.K_w * rS;
-  ab.dEdS = 1.0 + kw * rS + nh3 * ab.r_IN + hco3 * ab.r_co2 + ac * ab.r_ac + pro * ab.r_pro +
-            bu * ab.r_bu + va * ab.r_va;
-  return (y[iS_cat] - y[iS_an]) + (y[iS_IN] - nh3) + S - hco3 - ac - pro - bu - va - kw;
+// E(S) and dE/dS; fills the reciprocals used by the Jacobian.  Templated
+// on the scalar type only so that its operations can be counted on the host.
+template <class F>
+CHAD_HD F charge_E_t(const DigConst& c, const PartConst& q, const double* y, F S, F* r, F& dEdS) {
+  // r: 1/(K_a + S) for IN, co2, ac, pro, bu, va
+  const F rS = F(1.0) / S;
+  r[0] = F(1.0) / (F(q.K_a_IN) + S);
+  r[1] = F(1.0) / (F(q.K_a_co2) + S);
+  r[2] = F(1.0) / (F(c.K_a_ac) + S);
+  r[3] = F(1.0) / (F(c.K_a_pro) + S);
+  r[4] = F(1.0) / (F(c.K_a_bu) + S);
+  r[5] = F(1.0) / (F(c.K_a_va) + S);
+  const F nh3 = F(q.K_a_IN) * F(y[iS_IN]) * r[0];
+  const F hco3 = F(q.K_a_co2) * F(y[iS_IC]) * r[1];
+  const F ac = F(c.K_a_ac) * F(y[iS_ac]) * r[2] * F(1.0 / kVfaCod_ac);
+  const F pro = F(c.K_a_pro) * F(y[iS_pro]) * r[3] * F(1.0 / kVfaCod_pro);
+  const F bu = F(c.K_a_bu) * F(y[iS_bu]) * r[4] * F(1.0 / kVfaCod_bu);
+  const F va = F(c.K_a_va) * F(y[iS_va]) * r[5] * F(1.0 / kVfaCod_va);
+  const F kw = F(q.K_w) * rS;
+  dEdS = F(1.0) + kw * rS + nh3 * r[0] + hco3 * r[1] + ac * r[2] + pro * r[3] + bu * r[4] +
+         va * r[5];
+  return (F(y[iS_cat]) - F(y[iS_an])) + (F(y[iS_IN]) - nh3) + S - hco3 - ac - pro - bu - va - kw;
+}
+
+CHAD_HD double charge_E(const DigConst& c, const PartConst& q, const double* y, double S,
+                        AcidBase& ab) {
+  double r[6];
+  const double E = charge_E_t<double>(c, q, y, S, r, ab.dEdS);
+  ab.r_IN = r[0];
+  ab.r_co2 = r[1];
+  ab.r_ac = r[2];
+  ab.r_pro = r[3];
+  ab.r_bu = r[4];
+  ab.r_va = r[5];
+  return E;
 }
 
 struct NewtonCounters {

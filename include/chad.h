@@ -198,6 +198,38 @@ chad_status chad_synchronize(chad_ctx* ctx);
 chad_status chad_read_states(chad_ctx* ctx, int digester, double* y, double* pos, double* S_H,
                              double* h, int32_t* status, chad_stats* stats, int mem);
 
+/* ---- allocation-free entry point ----------------------------------------- */
+
+/* Per-digester volume-weighted mean of the three headspace states (the
+   shared-headspace reduction that chad_step applies at every interval end)
+   for callers that must not allocate device memory -- e.g. a host program
+   with a fixed device memory budget that forbids allocation after start-up,
+   a real-time coupling loop where an allocation could stall or fail midway,
+   or a process whose allocator owns the whole device.  The paper has no
+   counterpart: this is a property of the library, not of the method.
+     y          [29][ld] particle states in device memory (gas states are
+                rows 26..28), particles of digester d at dig_offset[d] ..
+                dig_offset[d+1]-1
+     dig_offset host array [n_digesters + 1], dig_offset[0] = 0,
+                non-decreasing, dig_offset[n_digesters] <= ld
+     mean       device output [n_digesters][3] (digesters without particles
+                are left untouched)
+     cuda_stream  stream to run on (NULL: legacy default stream)
+   It calls no cudaMalloc, cudaFree or allocating routine: its scratch is a
+   static device array of this library (384 KiB, held by every GPU that
+   loads the library until the process exits).  Limits: n_digesters <= 1024
+   and sum_d ceil(n_d / 4096) <= 16384 (67,108,864 particles in a single
+   digester); larger inputs return CHAD_E_INVALID.  The first call on each
+   device looks up the scratch's device address with that device current;
+   make that first call before any stream capture.  The array keeps the
+   last call's partial sums; every call rewrites all it reads, so nothing
+   needs clearing, but calls that overlap on the GPU (other streams or host
+   threads) race on it.  Asynchronous on the stream; results are
+   bit-identical to chad_step's reduction. */
+chad_status chad_headspace_mean_noalloc(const double* y, int64_t ld, int n_digesters,
+                                        const int64_t* dig_offset, double* mean,
+                                        void* cuda_stream);
+
 /* ---- diagnostics ------------------------------------------------------- */
 
 /* Measure the dense FMA throughput of the current GPU (fp64 = 1: FP64 DFMA,

@@ -98,6 +98,9 @@ def lib():
             L.chad_read_states.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.POINTER(chad_stats), C.c_int]
+            L.chad_headspace_mean_noalloc.restype = C.c_int
+            L.chad_headspace_mean_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
+                                                      C.c_void_p, C.c_void_p]
             L.chad_flop_counts.restype = C.c_int
             L.chad_flop_counts.argtypes = [C.c_void_p, C.c_int]
             L.chad_autotune.restype = C.c_int
@@ -116,7 +119,8 @@ def exported_symbols() -> list[str]:
     return ["chad_abi_version", "chad_n_params", "chad_param_name", "chad_last_error",
             "chad_create", "chad_destroy", "chad_load_particles", "chad_set_flow",
             "chad_step", "chad_synchronize", "chad_read_states", "chad_probe_alu_peak",
-            "chad_eval_model", "chad_autotune", "chad_flop_counts"]
+            "chad_eval_model", "chad_autotune", "chad_flop_counts",
+            "chad_headspace_mean_noalloc"]
 
 
 FLOP_KEYS = ["rates_f", "rates_fj", "charge_E", "form_w", "factor", "solve", "jx", "stage",

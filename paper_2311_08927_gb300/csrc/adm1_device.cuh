@@ -28,6 +28,29 @@ struct DenseIdx {
   static constexpr int size = NS * NS;
 };
 
+// 1/d.  On the GPU in FP64: Newton-Raphson iteration for the reciprocal,
+// x <- x + x (1 - d x) (quadratic convergence), seeded with the FP32
+// hardware reciprocal of d; two iterations bring the 24-bit seed to FP64
+// precision in four FMAs.  Values outside the FP32 normal range use the
+// division.  Elsewhere (host, FP32, counting types): the plain division.
+template <class R>
+CHAD_HD R rcp(R d) {
+  return R(1) / d;
+}
+#ifdef __CUDA_ARCH__
+template <>
+__device__ __forceinline__ double rcp<double>(double d) {
+  const float f = __double2float_rn(d);
+  const float af = fabsf(f);
+  if (!(af > 1e-30f && af < 1e30f)) return 1.0 / d;
+  double r = (double)__frcp_rn(f);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+#endif
+
 constexpr double kVfaCod_ac = 64.0, kVfaCod_pro = 112.0, kVfaCod_bu = 160.0, kVfaCod_va = 208.0;
 constexpr double kC4Guard = 1e-6;  // division guard of the c4 uptake split
 constexpr double kSH_lo = 1e-14, kSH_hi = 1.0;
@@ -63,13 +86,13 @@ struct AcidBase {
 template <class F>
 CHAD_HD F charge_E_t(const DigConst& c, const PartConst& q, const double* y, F S, F* r, F& dEdS) {
   // r: 1/(K_a + S) for IN, co2, ac, pro, bu, va
-  const F rS = F(1.0) / S;
-  r[0] = F(1.0) / (F(q.K_a_IN) + S);
-  r[1] = F(1.0) / (F(q.K_a_co2) + S);
-  r[2] = F(1.0) / (F(c.K_a_ac) + S);
-  r[3] = F(1.0) / (F(c.K_a_pro) + S);
-  r[4] = F(1.0) / (F(c.K_a_bu) + S);
-  r[5] = F(1.0) / (F(c.K_a_va) + S);
+  const F rS = rcp<F>(S);
+  r[0] = rcp<F>(F(q.K_a_IN) + S);
+  r[1] = rcp<F>(F(q.K_a_co2) + S);
+  r[2] = rcp<F>(F(c.K_a_ac) + S);
+  r[3] = rcp<F>(F(c.K_a_pro) + S);
+  r[4] = rcp<F>(F(c.K_a_bu) + S);
+  r[5] = rcp<F>(F(c.K_a_va) + S);
   const F nh3 = F(q.K_a_IN) * F(y[iS_IN]) * r[0];
   const F hco3 = F(q.K_a_co2) * F(y[iS_IC]) * r[1];
   const F ac = F(c.K_a_ac) * F(y[iS_ac]) * r[2] * F(1.0 / kVfaCod_ac);
@@ -111,10 +134,13 @@ __host__ __device__ inline void solve_SH(const DigConst& c, const PartConst& q, 
     const double E = charge_E(c, q, y, S, ab);
     nc.iters++;
     if (!isfinite(E) || fabs(E) > fabs(prevE)) break;
-    const double dS = E / ab.dEdS;
+    const double dS = E * rcp<double>(ab.dEdS);
     const double Sn = S - dS;
     if (!(Sn > 0.0) || !isfinite(Sn)) break;
-    if (fabs(dS) <= 1e-14 * Sn || fabs(E) <= 1e-15) {
+    // E is increasing and concave, Newton converges quadratically with a
+    // relative contraction factor below 1 near the root: an update below
+    // 1e-8 relative leaves the new iterate within ~1e-16 of the root.
+    if (fabs(dS) <= 1e-8 * Sn || fabs(E) <= 1e-15) {
       charge_E(c, q, y, Sn, ab);  // reciprocals and slope at the accepted root
       ab.SH = Sn;
       return;
@@ -143,6 +169,21 @@ __host__ __device__ inline void solve_SH(const DigConst& c, const PartConst& q, 
   charge_E(c, q, y, ab.SH, ab);
 }
 
+// dS_H/dy_k = -(dE/dy_k) / (dE/dS_H) (implicit function theorem on Eq. 7)
+// for the 8 states that enter Eq. 7, in the order of kShStates.
+constexpr int kShStates[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
+CHAD_HD void sh_tangent(const DigConst& c, const PartConst& q, const AcidBase& ab, double* v) {
+  const double inv = -rcp<double>(ab.dEdS);
+  v[0] = inv * (-c.K_a_va * ab.r_va * (1.0 / kVfaCod_va));
+  v[1] = inv * (-c.K_a_bu * ab.r_bu * (1.0 / kVfaCod_bu));
+  v[2] = inv * (-c.K_a_pro * ab.r_pro * (1.0 / kVfaCod_pro));
+  v[3] = inv * (-c.K_a_ac * ab.r_ac * (1.0 / kVfaCod_ac));
+  v[4] = inv * (-q.K_a_co2 * ab.r_co2);
+  v[5] = inv * (ab.SH * ab.r_IN);
+  v[6] = inv;
+  v[7] = -inv;
+}
+
 // ----------------------------------------------------------- inhibition helpers
 // Hill pH inhibition I = 1 / (1 + (S/K)^n) and dI/dS
 template <class R>
@@ -156,7 +197,7 @@ CHAD_HD void hill(R S, R invK, R n, int ni, R& I, R& dI) {
     case 4: xn1 = x * x * x; xn = xn1 * x; break;
     default: xn = pow(x, n); xn1 = xn / x; break;
   }
-  I = R(1) / (R(1) + xn);
+  I = rcp<R>(R(1) + xn);
   dI = -n * xn1 * invK * I * I;
 }
 
@@ -186,15 +227,15 @@ CHAD_HD void rates(const DigConst& c, const PartConst& q, const R* y,
   hill<R>(SH, R(c.inv_K_pH_ac), R(c.n_ac), c.ni_ac, Ipac, dIpac);
   hill<R>(SH, R(c.inv_K_pH_h2), R(c.n_h2), c.ni_h2, Iph2, dIph2);
   const R S_IN = y[iS_IN], S_h2 = y[iS_h2];
-  const R rIN = R(1) / (S_IN + R(c.K_S_IN));
+  const R rIN = rcp<R>(S_IN + R(c.K_S_IN));
   const R IIN = S_IN * rIN;
   const R dIIN = R(c.K_S_IN) * rIN * rIN;
-  const R rfa = R(1) / (R(c.K_I_h2_fa) + S_h2), rc4 = R(1) / (R(c.K_I_h2_c4) + S_h2);
-  const R rpr = R(1) / (R(c.K_I_h2_pro) + S_h2);
+  const R rfa = rcp<R>(R(c.K_I_h2_fa) + S_h2), rc4 = rcp<R>(R(c.K_I_h2_c4) + S_h2);
+  const R rpr = rcp<R>(R(c.K_I_h2_pro) + S_h2);
   const R Ih2fa = R(c.K_I_h2_fa) * rfa, Ih2c4 = R(c.K_I_h2_c4) * rc4, Ih2pro = R(c.K_I_h2_pro) * rpr;
   const R r_nh3 = R(q.K_a_IN) * R(ab.r_IN);
   const R nh3 = r_nh3 * S_IN;  // free ammonia
-  const R rnh = R(1) / (R(c.K_I_nh3) + nh3);
+  const R rnh = rcp<R>(R(c.K_I_nh3) + nh3);
   const R Inh3 = R(c.K_I_nh3) * rnh;
 
   // first-order processes
@@ -205,13 +246,13 @@ CHAD_HD void rates(const DigConst& c, const PartConst& q, const R* y,
   o.r[2] = kpr * y[iX_pr];
   o.r[3] = kli * y[iX_li];
   // Monod terms m = S/(K+S), dm = K/(K+S)^2
-  const R rsu = R(1) / (R(c.K_S_su) + y[iS_su]), raa = R(1) / (R(c.K_S_aa) + y[iS_aa]);
-  const R rfs = R(1) / (R(c.K_S_fa) + y[iS_fa]), rva = R(1) / (R(c.K_S_c4) + y[iS_va]);
-  const R rbu = R(1) / (R(c.K_S_c4) + y[iS_bu]), rpo = R(1) / (R(c.K_S_pro) + y[iS_pro]);
-  const R rac = R(1) / (R(c.K_S_ac) + y[iS_ac]), rh2 = R(1) / (R(c.K_S_h2) + S_h2);
+  const R rsu = rcp<R>(R(c.K_S_su) + y[iS_su]), raa = rcp<R>(R(c.K_S_aa) + y[iS_aa]);
+  const R rfs = rcp<R>(R(c.K_S_fa) + y[iS_fa]), rva = rcp<R>(R(c.K_S_c4) + y[iS_va]);
+  const R rbu = rcp<R>(R(c.K_S_c4) + y[iS_bu]), rpo = rcp<R>(R(c.K_S_pro) + y[iS_pro]);
+  const R rac = rcp<R>(R(c.K_S_ac) + y[iS_ac]), rh2 = rcp<R>(R(c.K_S_h2) + S_h2);
   const R msu = y[iS_su] * rsu, maa = y[iS_aa] * raa, mfa = y[iS_fa] * rfs, mva = y[iS_va] * rva;
   const R mbu = y[iS_bu] * rbu, mpo = y[iS_pro] * rpo, mac = y[iS_ac] * rac, mh2 = S_h2 * rh2;
-  const R rden = R(1) / (y[iS_bu] + y[iS_va] + R(kC4Guard));
+  const R rden = rcp<R>(y[iS_bu] + y[iS_va] + R(kC4Guard));
   const R gva = y[iS_va] * rden, gbu = y[iS_bu] * rden;
 
   const R ksu = R(c.k_m_su) * a, kaa = R(c.k_m_aa) * a, kfa = R(c.k_m_fa) * a,
@@ -530,16 +571,12 @@ CHAD_HD void jacobian(const DigConst& c, const PartConst& q, const R* y, R D, co
     }
   }
   // rank-1 S_H coupling: J += u v^T over the 8 states that enter Eq. 7
-  const double inv = -1.0 / ab.dEdS;
   const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
-  const R v[8] = {R(inv * (-c.K_a_va * ab.r_va / kVfaCod_va)),
-                  R(inv * (-c.K_a_bu * ab.r_bu / kVfaCod_bu)),
-                  R(inv * (-c.K_a_pro * ab.r_pro / kVfaCod_pro)),
-                  R(inv * (-c.K_a_ac * ab.r_ac / kVfaCod_ac)),
-                  R(inv * (-q.K_a_co2 * ab.r_co2)),
-                  R(inv * (ab.SH * ab.r_IN)),
-                  R(inv),
-                  R(-inv)};
+  double vd[8];
+  sh_tangent(c, q, ab, vd);
+  R v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = R(vd[k]);
   const int ur[19] = {iS_su, iS_aa, iS_fa, iS_va, iS_bu, iS_pro, iS_ac, iS_h2, iS_ch4, iS_IC,
                       iS_IN, iX_su, iX_aa, iX_fa, iX_c4, iX_pro, iX_ac, iX_h2, iG_co2};
 #pragma unroll

@@ -172,7 +172,7 @@ def generate(pat: np.ndarray) -> str:
             w(f"    const R cm = {expr};")
             w("    ok = ok && (fabs(pv) >= tau * cm);")
         w("    ok = ok && (pv != R(0)) && isfinite(pv);")
-        w("    const R inv = R(1) / pv;")
+        w("    const R inv = rcp<R>(pv);")
         w(f"    dinv[{k}] = inv;")
         flops += 1
         for i in sub:

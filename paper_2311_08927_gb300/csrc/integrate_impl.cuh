@@ -86,8 +86,7 @@ __device__ __forceinline__ void eval_f(const DigConst& c, const PartConst& q, co
 template <class R, class RS>
 __device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, const double* y,
                                         double D, double& SHg, int max_newton, Cnt& cnt,
-                                        double* f, R* w) {
-  AcidBase ab;
+                                        double* f, R* w, AcidBase& ab) {
   newton(c, q, y, SHg, max_newton, cnt, ab);
   {
     R yr[NS];
@@ -114,6 +113,15 @@ __device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, c
 #pragma unroll
     for (int i = 0; i < NS; ++i) f[i] = double(fr[i]);
   }
+}
+
+// Newton guess for S_H at y + dy from the tangent dS_H/dy at y (Eq. 7
+// differentiated implicitly); the root is unchanged, only the start moves.
+__device__ __forceinline__ double sh_guess(double SH0, const double* v, double s, const double* k) {
+  const double g = SH0 + s * (v[0] * k[iS_va] + v[1] * k[iS_bu] + v[2] * k[iS_pro] +
+                              v[3] * k[iS_ac] + v[4] * k[iS_IC] + v[5] * k[iS_IN] +
+                              v[6] * k[iS_cat] + v[7] * k[iS_an]);
+  return (g > 0.5 * SH0 && g < 2.0 * SH0) ? g : SH0;
 }
 
 // W x = b with the factored W.  Mixed: FP32 solve, FP64 residual
@@ -198,7 +206,11 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       hh = Tend - t;
       last = true;
     }
-    eval_fj<R, RS>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w);
+    AcidBase ab0;
+    eval_fj<R, RS>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, ab0);
+    const double SH0 = SHg;
+    double vsh[8];
+    sh_tangent(*c, q, ab0, vsh);
     if (MIXED) {
 #pragma unroll
       for (int s = 0; s < sp::kNNZ; ++s) jk[s] = w[s];
@@ -212,6 +224,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       solve<MIXED, R>(w, dinv, jk, g, F0, k1);
 #pragma unroll
       for (int i = 0; i < NS; ++i) tmp[i] = y[i] + 0.5 * hh * k1[i];
+      SHg = sh_guess(SH0, vsh, 0.5 * hh, k1);
       eval_f<RS>(*c, q, tmp, D, SHg, a.max_newton, cnt, F1);
 #pragma unroll
       for (int i = 0; i < NS; ++i) tmp[i] = F1[i] - k1[i];
@@ -221,20 +234,24 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
         k2[i] += k1[i];
         y1[i] = y[i] + hh * k2[i];
       }
+      SHg = sh_guess(SH0, vsh, hh, k2);
       eval_f<RS>(*c, q, y1, D, SHg, a.max_newton, cnt, tmp);  // F2
 #pragma unroll
       for (int i = 0; i < NS; ++i)
         tmp[i] = tmp[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
       solve<MIXED, R>(w, dinv, jk, g, tmp, F1);  // k3
-      norm = 0.0;
-      const double h6 = hh / 6.0;
+      // scaled error norm: the estimate in FP64, the ratio to the
+      // tolerance in FP32 (the accept test needs a few digits only)
+      float nf = 0.0f;
+      const double h6 = hh * (1.0 / 6.0);
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
         const double e = h6 * (k1[i] - 2.0 * k2[i] + F1[i]);
         const double sc = a.atol[i] + a.rtol * fmax(fabs(y[i]), fabs(y1[i]));
-        const double r = fabs(e) / sc;
-        if (!(r <= norm)) norm = r;  // NaN propagates
+        const float r = fabsf((float)e) * __frcp_rn((float)sc);
+        if (!(r <= nf)) nf = r;  // NaN propagates
       }
+      norm = nf;
     }
     if (fixed) {
 #pragma unroll
@@ -249,7 +266,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       t = last ? Tend : t + hh;
       cnt.acc++;
       ++nacc;
-      double fac = (norm == 0.0) ? 5.0 : fmin(5.0, fmax(0.2, 0.8 * pow(norm, -1.0 / 3.0)));
+      double fac = (norm == 0.0) ? 5.0 : fmin(5.0, fmax(0.2, 0.8 * (double)powf((float)norm, -1.0f / 3.0f)));
       if (rejected_prev) fac = fmin(fac, 1.0);
       h = hh * fac;
       rejected_prev = false;
@@ -257,7 +274,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     } else {
       cnt.rej++;
       const double fac =
-          !piv_ok ? 0.25 : (isfinite(norm) ? fmax(0.2, 0.8 * pow(norm, -1.0 / 3.0)) : 0.2);
+          !piv_ok ? 0.25 : (isfinite(norm) ? fmax(0.2, 0.8 * (double)powf((float)norm, -1.0f / 3.0f)) : 0.2);
       h = hh * fac;
       rejected_prev = true;
       if (h < kHmin) {

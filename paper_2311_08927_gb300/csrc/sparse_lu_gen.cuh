@@ -99,13 +99,13 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   {  // pivot 0: state 11 (S_I), 0 rows x 1 cols
     const R pv = w[0];
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[0] = inv;
   }
   {  // pivot 1: state 23 (X_I), 0 rows x 1 cols
     const R pv = w[2];
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[1] = inv;
   }
   {  // pivot 2: state 24 (S_cat), 19 rows x 0 cols
@@ -113,7 +113,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[21]), fabs(w[35])), fabs(w[50])), fabs(w[60])), fabs(w[69])), fabs(w[79])), fabs(w[92])), fabs(w[104])), fabs(w[117])), fabs(w[128])), fabs(w[153])), fabs(w[177])), fabs(w[190])), fabs(w[202])), fabs(w[217])), fabs(w[233])), fabs(w[252])), fabs(w[276])), fabs(w[296]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[2] = inv;
     { const R l = w[21] * inv; w[21] = l;
     }
@@ -159,7 +159,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[22]), fabs(w[36])), fabs(w[51])), fabs(w[61])), fabs(w[70])), fabs(w[80])), fabs(w[93])), fabs(w[105])), fabs(w[118])), fabs(w[129])), fabs(w[154])), fabs(w[178])), fabs(w[191])), fabs(w[203])), fabs(w[218])), fabs(w[234])), fabs(w[253])), fabs(w[277])), fabs(w[297]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[3] = inv;
     { const R l = w[22] * inv; w[22] = l;
     }
@@ -205,7 +205,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fabs(w[106]), fabs(w[254]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[4] = inv;
     { const R l = w[106] * inv; w[106] = l;
       w[110] -= l * w[7];
@@ -219,7 +219,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fabs(w[179]), fabs(w[255]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[5] = inv;
     { const R l = w[179] * inv; w[179] = l;
       w[180] -= l * w[9];
@@ -233,7 +233,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fabs(w[81]), fabs(w[107])), fabs(w[256]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[6] = inv;
     { const R l = w[81] * inv; w[81] = l;
       w[84] -= l * w[11];
@@ -250,7 +250,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fabs(w[16]), fabs(w[37])), fabs(w[155]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[7] = inv;
     { const R l = w[16] * inv; w[16] = l;
       w[17] -= l * w[13];
@@ -273,7 +273,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fabs(w[23]), fabs(w[38])), fabs(w[156]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[8] = inv;
     { const R l = w[23] * inv; w[23] = l;
       w[24] -= l * w[18];
@@ -296,7 +296,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fabs(w[39]), fabs(w[157]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[9] = inv;
     { const R l = w[39] * inv; w[39] = l;
       w[40] -= l * w[25];
@@ -328,7 +328,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fabs(w[158]), fabs(w[257]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[10] = inv;
     { const R l = w[158] * inv; w[158] = l;
       w[159] -= l * w[41];
@@ -358,7 +358,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fabs(w[138]), fabs(w[159])), fabs(w[258])), fabs(w[278]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[11] = inv;
     { const R l = w[138] * inv; w[138] = l;
       w[145] -= l * w[53];
@@ -402,7 +402,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fabs(w[139]), fabs(w[160])), fabs(w[235])), fabs(w[259])), fabs(w[279]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[12] = inv;
     { const R l = w[139] * inv; w[139] = l;
       w[146] -= l * w[63];
@@ -450,7 +450,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fmax(fabs(w[140]), fabs(w[161])), fabs(w[219])), fabs(w[236])), fabs(w[260])), fabs(w[280]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[13] = inv;
     { const R l = w[140] * inv; w[140] = l;
       w[145] -= l * w[72];
@@ -512,7 +512,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fabs(w[94]), fabs(w[162])), fabs(w[237])), fabs(w[261])), fabs(w[281]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[14] = inv;
     { const R l = w[94] * inv; w[94] = l;
       w[95] -= l * w[83];
@@ -575,7 +575,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fabs(w[141]), fabs(w[163])), fabs(w[238])), fabs(w[262])), fabs(w[282]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[15] = inv;
     { const R l = w[141] * inv; w[141] = l;
       w[144] -= l * w[96];
@@ -633,7 +633,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[119]), fabs(w[164])), fabs(w[204])), fabs(w[220])), fabs(w[239])), fabs(w[263])), fabs(w[283]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[16] = inv;
     { const R l = w[119] * inv; w[119] = l;
       w[120] -= l * w[109];
@@ -711,7 +711,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[142]), fabs(w[165])), fabs(w[205])), fabs(w[221])), fabs(w[240])), fabs(w[264])), fabs(w[284]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[17] = inv;
     { const R l = w[142] * inv; w[142] = l;
       w[144] -= l * w[121];
@@ -782,7 +782,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[143]), fabs(w[166])), fabs(w[192])), fabs(w[206])), fabs(w[222])), fabs(w[241])), fabs(w[265])), fabs(w[285]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[18] = inv;
     { const R l = w[143] * inv; w[143] = l;
       w[145] -= l * w[131];
@@ -862,7 +862,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[167]), fabs(w[180])), fabs(w[207])), fabs(w[223])), fabs(w[242])), fabs(w[266])), fabs(w[286]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[19] = inv;
     { const R l = w[167] * inv; w[167] = l;
       w[168] -= l * w[145];
@@ -940,7 +940,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[181]), fabs(w[193])), fabs(w[208])), fabs(w[224])), fabs(w[243])), fabs(w[267])), fabs(w[287]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[20] = inv;
     { const R l = w[181] * inv; w[181] = l;
       w[182] -= l * w[169];
@@ -1018,7 +1018,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[194]), fabs(w[209])), fabs(w[225])), fabs(w[244])), fabs(w[268])), fabs(w[288])), fabs(w[298]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[21] = inv;
     { const R l = w[194] * inv; w[194] = l;
       w[195] -= l * w[183];
@@ -1089,7 +1089,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fmax(fabs(w[210]), fabs(w[226])), fabs(w[245])), fabs(w[269])), fabs(w[289])), fabs(w[299]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[22] = inv;
     { const R l = w[210] * inv; w[210] = l;
       w[211] -= l * w[196];
@@ -1145,7 +1145,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fmax(fabs(w[227]), fabs(w[246])), fabs(w[270])), fabs(w[290])), fabs(w[300]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[23] = inv;
     { const R l = w[227] * inv; w[227] = l;
       w[228] -= l * w[212];
@@ -1188,7 +1188,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fmax(fabs(w[247]), fabs(w[271])), fabs(w[291])), fabs(w[301]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[24] = inv;
     { const R l = w[247] * inv; w[247] = l;
       w[248] -= l * w[229];
@@ -1220,7 +1220,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fmax(fabs(w[272]), fabs(w[292])), fabs(w[302]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[25] = inv;
     { const R l = w[272] * inv; w[272] = l;
       w[273] -= l * w[249];
@@ -1243,7 +1243,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fmax(fabs(w[293]), fabs(w[303]));
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[26] = inv;
     { const R l = w[293] * inv; w[293] = l;
       w[294] -= l * w[274];
@@ -1259,7 +1259,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
     const R cm = fabs(w[304]);
     ok = ok && (fabs(pv) >= tau * cm);
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[27] = inv;
     { const R l = w[304] * inv; w[304] = l;
       w[305] -= l * w[295];
@@ -1268,7 +1268,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   {  // pivot 28: state 17 (X_aa), 0 rows x 0 cols
     const R pv = w[305];
     ok = ok && (pv != R(0)) && isfinite(pv);
-    const R inv = R(1) / pv;
+    const R inv = rcp<R>(pv);
     dinv[28] = inv;
   }
   return ok;

@@ -117,10 +117,12 @@ __device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, c
 
 // Newton guess for S_H at y + dy from the tangent dS_H/dy at y (Eq. 7
 // differentiated implicitly); the root is unchanged, only the start moves.
-__device__ __forceinline__ double sh_guess(double SH0, const double* v, double s, const double* k) {
-  const double g = SH0 + s * (v[0] * k[iS_va] + v[1] * k[iS_bu] + v[2] * k[iS_pro] +
-                              v[3] * k[iS_ac] + v[4] * k[iS_IC] + v[5] * k[iS_IN] +
-                              v[6] * k[iS_cat] + v[7] * k[iS_an]);
+__device__ __forceinline__ double sh_guess(double SH0, const double* v, const double* y0,
+                                           const double* y1) {
+  const double g = SH0 + v[0] * (y1[iS_va] - y0[iS_va]) + v[1] * (y1[iS_bu] - y0[iS_bu]) +
+                   v[2] * (y1[iS_pro] - y0[iS_pro]) + v[3] * (y1[iS_ac] - y0[iS_ac]) +
+                   v[4] * (y1[iS_IC] - y0[iS_IC]) + v[5] * (y1[iS_IN] - y0[iS_IN]) +
+                   v[6] * (y1[iS_cat] - y0[iS_cat]) + v[7] * (y1[iS_an] - y0[iS_an]);
   return (g > 0.5 * SH0 && g < 2.0 * SH0) ? g : SH0;
 }
 
@@ -220,33 +222,50 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     const bool piv_ok = sp::factor<R>(w, dinv, R(kPivTau));
     double norm = INFINITY;
     if (!piv_ok) cnt.pivot++;
+    double xs[NS];
     if (piv_ok || fixed) {
-      solve<MIXED, R>(w, dinv, jk, g, F0, k1);
+      // The three stages share one factorisation.  They run as a loop that
+      // is not unrolled, so the kernel holds a single copy of the solve and
+      // of the rate evaluation (the straight-line code is large):
+      //   stage 0: x = W^-1 F0                          -> k1
+      //   stage 1: F1 = f(y + h/2 k1), x = W^-1 (F1 - k1) -> k2 = x + k1
+      //   stage 2: F2 = f(y + h k2), x = W^-1 (F2 - e32 (k2 - F1) - 2 (k1 - F0))
+      //            -> k3 = x (left in xs), y1 = y + h k2
+#pragma unroll 1
+      for (int st = 0; st < 3; ++st) {
+        if (st == 0) {
 #pragma unroll
-      for (int i = 0; i < NS; ++i) tmp[i] = y[i] + 0.5 * hh * k1[i];
-      SHg = sh_guess(SH0, vsh, 0.5 * hh, k1);
-      eval_f<RS>(*c, q, tmp, D, SHg, a.max_newton, cnt, F1);
+          for (int i = 0; i < NS; ++i) tmp[i] = F0[i];
+        } else {
+          const bool s1 = (st == 1);
 #pragma unroll
-      for (int i = 0; i < NS; ++i) tmp[i] = F1[i] - k1[i];
-      solve<MIXED, R>(w, dinv, jk, g, tmp, k2);
+          for (int i = 0; i < NS; ++i) y1[i] = y[i] + (s1 ? 0.5 * hh * k1[i] : hh * k2[i]);
+          SHg = sh_guess(SH0, vsh, y, y1);
+          eval_f<RS>(*c, q, y1, D, SHg, a.max_newton, cnt, tmp);
 #pragma unroll
-      for (int i = 0; i < NS; ++i) {
-        k2[i] += k1[i];
-        y1[i] = y[i] + hh * k2[i];
+          for (int i = 0; i < NS; ++i) {
+            if (s1) {
+              F1[i] = tmp[i];
+              tmp[i] = tmp[i] - k1[i];
+            } else {
+              tmp[i] = tmp[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
+            }
+          }
+        }
+        solve<MIXED, R>(w, dinv, jk, g, tmp, xs);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          if (st == 0) k1[i] = xs[i];
+          else if (st == 1) k2[i] = xs[i] + k1[i];
+        }
       }
-      SHg = sh_guess(SH0, vsh, hh, k2);
-      eval_f<RS>(*c, q, y1, D, SHg, a.max_newton, cnt, tmp);  // F2
-#pragma unroll
-      for (int i = 0; i < NS; ++i)
-        tmp[i] = tmp[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
-      solve<MIXED, R>(w, dinv, jk, g, tmp, F1);  // k3
       // scaled error norm: the estimate in FP64, the ratio to the
       // tolerance in FP32 (the accept test needs a few digits only)
       float nf = 0.0f;
       const double h6 = hh * (1.0 / 6.0);
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
-        const double e = h6 * (k1[i] - 2.0 * k2[i] + F1[i]);
+        const double e = h6 * (k1[i] - 2.0 * k2[i] + xs[i]);
         const double sc = a.atol[i] + a.rtol * fmax(fabs(y[i]), fabs(y1[i]));
         const float r = fabsf((float)e) * __frcp_rn((float)sc);
         if (!(r <= nf)) nf = r;  // NaN propagates

@@ -172,6 +172,66 @@ def measured_traffic_per_attempt(form: str):
     return None, None
 
 
+def train_mlp(CH, I, args):
+    """Train the learned-guess MLP on about 10^7 states from seeded runs of the
+    lab-cylinder (100k particles) and heterogeneous (1M) workloads with seeds
+    independent of the benchmark population; not timed as part of a step."""
+    import torch
+    from paper_2311_08927_gb300 import learned as Lm
+    t0 = time.perf_counter()
+    n3 = args.train_particles
+    pops = [I.config_population(3, n=n3, seed_offset=100), I.config_population(2, seed_offset=100)]
+    ys, Ts, SHs, hs = [], [], [], []
+    for pop_t, k in zip(pops, (args.train_intervals, 11)):
+        y, T, SH, h = Lm.sample_states(pop_t, k)
+        ys.append(y); Ts.append(T); SHs.append(SH); hs.append(h)
+    y, T, SH, h = torch.cat(ys, 1), torch.cat(Ts), torch.cat(SHs), torch.cat(hs)
+    t1 = time.perf_counter()
+    X, Y, norm, onorm = Lm.build_dataset(y, T, SH, h)
+    params, hist, test_loss = Lm.train(X, Y, epochs=args.train_epochs, batch=16384, lr=2e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    model = Lm.TrainedMLP(params, norm.cpu().numpy(), onorm, hist)
+    e_sh, e_h = Lm.prediction_errors(model, y[:, -200000:].contiguous(), T[-200000:].contiguous(),
+                                     SH[-200000:].contiguous(), h[-200000:].contiguous())
+    info = {"samples": int(T.shape[0]), "epochs": args.train_epochs, "sampling_s": t1 - t0,
+            "training_s": t2 - t1, "val_loss_before": hist[0][2], "val_loss_after": hist[-1][2],
+            "test_loss": test_loss, "median_abs_log10_err_SH": e_sh,
+            "median_abs_log10_err_h": e_h,
+            "kernels": "chad_mlp_grad (BF16 mma.sync fwd+bwd) + chad_mlp_adam"}
+    del X, Y, y, T, SH, h
+    torch.cuda.empty_cache()
+    return model, info
+
+
+def cold_restart_ab(CH, pop, relaxed, model, stream):
+    """One interval after reloading relaxed states without S_H and h (as a
+    coupling that reloads particle files would): plain start (S_H 1e-7, h
+    1e-6 d) against the learned guesses, mixed form, CUDA-event timed."""
+    import torch
+    res = {}
+    for name, learned in (("plain", False), ("learned", True)):
+        sim = CH.Simulator(pop, precision=CH.PREC_MIXED, stream=stream.cuda_stream,
+                           learned=1 if learned else 0)
+        if learned:
+            CH.chad_set_mlp(sim.ctx, model.params, model.feat_norm, model.out_norm)
+        sim.load(y=relaxed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(DT_S, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = sim.read()["stats"]
+        sim.close()
+        res[name] = {"ms": e0.elapsed_time(e1),
+                     "attempts_per_particle": (st["accepted_steps"] + st["rejected_steps"]) / pop.n,
+                     "newton_iters_per_particle": st["newton_iters"] / pop.n,
+                     "mlp_redo": st["mlp_redo"]}
+    res["speedup"] = res["plain"]["ms"] / res["learned"]["ms"]
+    return res
+
+
 # --------------------------------------------------------------------------- our arm
 def run_ours(args, ws, rank, local):
     import torch
@@ -189,8 +249,16 @@ def run_ours(args, ws, rank, local):
     peak32 = CH.probe_alu_peak(False)
     stream = torch.cuda.Stream()
 
-    def arm(precision):
-        sim = CH.Simulator(pop, precision=precision, rtol=1e-6, stream=stream.cuda_stream)
+    model = None
+    train_info = None
+    if args.form in ("both", "mixed") and not args.no_learned:
+        model, train_info = train_mlp(CH, I, args)
+
+    def arm(precision, learned=False):
+        sim = CH.Simulator(pop, precision=precision, rtol=1e-6, stream=stream.cuda_stream,
+                           learned=1 if learned else 0)
+        if learned:
+            CH.chad_set_mlp(sim.ctx, model.params, model.feat_norm, model.out_norm)
         sim.load()
         sim.step(DT_S, args.warmup)
         CH.chad_synchronize(sim.ctx)
@@ -227,10 +295,15 @@ def run_ours(args, ws, rank, local):
     forms = {}
     for name, prec in (("mixed", CH.PREC_MIXED), ("fp64", CH.PREC_FP64)):
         if args.form in (name, "both"):
-            forms[name] = arm(prec)
+            forms[name] = arm(prec, learned=(name == "mixed" and model is not None))
     head = "mixed" if "mixed" in forms else "fp64"
     H = forms[head]
     value = ws * N * dt_days * args.steps / (H["total_ms"] * 1e-3)
+
+    # ---------------- learned guesses on a cold restart (reload without S_H, h)
+    cold = None
+    if model is not None and rank == 0:
+        cold = cold_restart_ab(CH, pop, H["y_final"], model, stream)
 
     # ---------------- e2e: host buffers through the C ABI, copies in the timed region
     e2e = None
@@ -274,8 +347,9 @@ def run_ours(args, ws, rank, local):
         "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if N == N_PARTICLES else f"{WORKLOAD}_n{N}",
                    "particles_per_gpu": N, "coupling_interval_s": DT_S,
-                   "form": head + (" (FP32 Jacobian/LU + FP64 refinement)" if head == "mixed" else ""),
-                   "learned_guesses": False, "rtol": 1e-6, "slug_fraction": 0.05,
+                   "form": head + (" (FP32 Jacobian/LU + FP64 refinement)" if head == "mixed" else "")
+                + (" + learned guesses" if (head == "mixed" and model is not None) else ""),
+                   "learned_guesses": model is not None, "rtol": 1e-6, "slug_fraction": 0.05,
                    "T_range_K": [303.15, 313.15], "l2": "inputs larger than L2 (232 MB state)",
                    "parallelism": f"particles sharded, {ws} independent populations"},
         "roofline": {"bound": "alu", "achieved": H["achieved_tflops"], "peak": peak64,
@@ -314,6 +388,10 @@ def run_ours(args, ws, rank, local):
         d = np.abs(H["y_final"] - F["y_final"]) / np.maximum(
             np.abs(F["y_final"]), 1e-12 * np.abs(F["y_final"]).max(axis=1, keepdims=True))
         res["mixed_vs_fp64_max_rel"] = float(d.max())
+    if train_info:
+        res["learned_training"] = train_info
+    if cold:
+        res["learned_cold_restart"] = cold
     if e2e:
         res["e2e"] = e2e
     if cpu:
@@ -408,6 +486,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned guesses")
+    ap.add_argument("--train-particles", type=int, default=1_000_000)
+    ap.add_argument("--train-intervals", type=int, default=10)
+    ap.add_argument("--train-epochs", type=int, default=20)
     ap.add_argument("--particles", type=int, default=None,
                     help="override the 1M particles (profiling captures only)")
     args = ap.parse_args()

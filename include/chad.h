@@ -41,6 +41,14 @@ extern "C" {
 #define CHAD_NPARAM 113   /* length of one digester's parameter vector */
 #define CHAD_ABI_VERSION 1
 
+/* Learned initial guesses: a 32 -> 64 -> 64 -> 2 MLP with SiLU activations.
+   FP32 parameter vector layout: W1[64][32], b1[64], W2[64][64], b2[64],
+   W3[2][64], b3[2] (weights row-major [out][in]). */
+#define CHAD_MLP_IN 32
+#define CHAD_MLP_HID 64
+#define CHAD_MLP_OUT 2
+#define CHAD_MLP_NPARAM (64 * 32 + 64 + 64 * 64 + 64 + 2 * 64 + 2)
+
 typedef struct chad_ctx chad_ctx; /* opaque, library-owned */
 
 typedef enum {
@@ -84,7 +92,8 @@ typedef struct {
                                   flow field (Eq. 2 with q_in = q_out); NULL = all 0 */
   const double* y_in;          /* [n_digesters][29] influent; NULL = zeros */
   int precision;               /* CHAD_PREC_FP64, CHAD_PREC_MIXED or CHAD_PREC_MIXED_F32RATES */
-  int learned;                 /* 1: MLP initial guesses (chad_set_mlp must be called) */
+  int learned;                 /* 1: particles loaded without a step-size history take
+                                  their first S_H and h from the MLP (chad_set_mlp) */
   int headspace;               /* CHAD_HEADSPACE_PARTICLE or CHAD_HEADSPACE_SHARED */
   double rtol;                 /* relative tolerance of the step controller (> 0) */
   const double* atol;          /* [29] absolute tolerances (> 0) */
@@ -175,12 +184,13 @@ chad_status chad_set_flow(chad_ctx* ctx, int digester, const chad_flow* flow);
 chad_status chad_step(chad_ctx* ctx, double dt_coupling_s, int n_intervals);
 
 /* Pick the fastest integrator kernel variant for this population and
-   interval length: the particle state is snapshot, one interval is run and
-   timed with each of the variants (register budgets of 255/168/128 per
+   interval length: the particle state is snapshot, two intervals are run
+   and timed with each of the variants (register budgets of 255/168/128 per
    thread, i.e. at least 2, 3 or 4 resident 128-thread blocks per SM), and
    the state is restored, so results are unaffected.  The choice is kept by
    the context for its precision form; *chosen (may be NULL) receives the
-   variant index and ms (may be NULL) the time of each of the 3 variants.  Temporarily
+   variant index and ms (may be NULL) the time (two intervals) of each of
+   the 3 variants.  Temporarily
    allocates about 290 bytes per particle of device memory.  Synchronous. */
 chad_status chad_autotune(chad_ctx* ctx, double dt_coupling_s, int32_t* chosen, double* ms);
 
@@ -197,6 +207,48 @@ chad_status chad_synchronize(chad_ctx* ctx);
    digester has a status bit set (the data is still copied). */
 chad_status chad_read_states(chad_ctx* ctx, int digester, double* y, double* pos, double* S_H,
                              double* h, int32_t* status, chad_stats* stats, int mem);
+
+/* ---- learned guesses (north star item 4; the paper has no counterpart) --- */
+
+/* Install a trained MLP into a context with learned = 1.  params [NPARAM]
+   FP32 (layout above), feat_norm [2][32]: per-feature mean and 1/std of the
+   features (log10 max(y_i, 1e-20) for the 29 states, T/100 K, 2 zero pads),
+   out_norm [4]: mean of log10 S_H, mean of log10 h, std of each.  Host
+   pointers, copied.  Particles loaded without h then start their first
+   interval from S_H = 10^(o0 s0 + m0) and h = 10^(o1 s1 + m1): Newton runs
+   at most 4 iterations from the learned S_H; if it has not converged the
+   particle restarts from the plain guess (counted in chad_stats.mlp_redo). */
+chad_status chad_set_mlp(chad_ctx* ctx, const float* params, const float* feat_norm,
+                         const float* out_norm);
+
+/* Features of n particles (device pointers): X [n][32] BF16 (uint16 bits)
+   from y [29][ld], T [n]; feat_norm [2][32] device.  Asynchronous. */
+chad_status chad_mlp_features(const double* y, int64_t ld, const double* T, int64_t n,
+                              const float* feat_norm, uint16_t* X, void* cuda_stream);
+
+/* Inference on the tensor cores: out [n][2] FP32 standardised outputs for
+   X [n][32] BF16, params [NPARAM] FP32 (device pointers).  Asynchronous. */
+chad_status chad_mlp_forward(const uint16_t* X, int64_t n, const float* params, float* out,
+                             void* cuda_stream);
+
+/* Bytes of scratch chad_mlp_grad needs for a batch of n samples. */
+size_t chad_mlp_grad_scratch_bytes(int64_t n);
+
+/* Gradient of L = (1/n) sum_i sum_j (MLP(X_i)_j - Y_ij)^2 w.r.t. params
+   (forward and backward on the tensor cores, BF16 operands, FP32
+   accumulation; per-block partials reduced in a fixed order, so the result
+   is deterministic).  X [n][32] BF16, Y [n][2] FP32, params and grad
+   [NPARAM] FP32, loss (may be NULL) one FP32; all device pointers; scratch
+   is caller-owned device memory of chad_mlp_grad_scratch_bytes(n) bytes.
+   Asynchronous. */
+chad_status chad_mlp_grad(const uint16_t* X, const float* Y, int64_t n, const float* params,
+                          float* grad, float* loss, void* scratch, size_t scratch_bytes,
+                          void* cuda_stream);
+
+/* One Adam step (Kingma & Ba 2015, bias-corrected, step t >= 1) on the FP32
+   master parameters: params, grad, m, v [NPARAM] device.  Asynchronous. */
+chad_status chad_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t t,
+                          float lr, float beta1, float beta2, float eps, void* cuda_stream);
 
 /* ---- allocation-free entry point ----------------------------------------- */
 

@@ -98,6 +98,22 @@ def lib():
             L.chad_read_states.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.POINTER(chad_stats), C.c_int]
+            L.chad_set_mlp.restype = C.c_int
+            L.chad_set_mlp.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.chad_mlp_features.restype = C.c_int
+            L.chad_mlp_features.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                            C.c_void_p, C.c_void_p, C.c_void_p]
+            L.chad_mlp_forward.restype = C.c_int
+            L.chad_mlp_forward.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                           C.c_void_p]
+            L.chad_mlp_grad_scratch_bytes.restype = C.c_size_t
+            L.chad_mlp_grad_scratch_bytes.argtypes = [C.c_int64]
+            L.chad_mlp_grad.restype = C.c_int
+            L.chad_mlp_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+            L.chad_mlp_adam.restype = C.c_int
+            L.chad_mlp_adam.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                        C.c_float, C.c_float, C.c_float, C.c_float, C.c_void_p]
             L.chad_headspace_mean_noalloc.restype = C.c_int
             L.chad_headspace_mean_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                                                       C.c_void_p, C.c_void_p]
@@ -120,7 +136,57 @@ def exported_symbols() -> list[str]:
             "chad_create", "chad_destroy", "chad_load_particles", "chad_set_flow",
             "chad_step", "chad_synchronize", "chad_read_states", "chad_probe_alu_peak",
             "chad_eval_model", "chad_autotune", "chad_flop_counts",
-            "chad_headspace_mean_noalloc"]
+            "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
+            "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
+
+MLP_IN, MLP_HID, MLP_OUT = 32, 64, 2
+MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT
+
+
+def chad_set_mlp(ctx, params, feat_norm, out_norm):
+    L = lib()
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    fn = np.ascontiguousarray(feat_norm, dtype=np.float32)
+    on = np.ascontiguousarray(out_norm, dtype=np.float32)
+    assert p.size == MLP_NPARAM and fn.size == 2 * MLP_IN and on.size == 4
+    _check(L, ctx, L.chad_set_mlp(ctx, p.ctypes.data, fn.ctypes.data, on.ctypes.data))
+
+
+def _dev(t):
+    """Device pointer of a contiguous torch CUDA tensor."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def chad_mlp_features(y, T, feat_norm, X, stream=None):
+    """y [29][ld] f64, T [n] f64, feat_norm [64] f32 -> X [n][32] (int16 holding BF16)."""
+    L = lib()
+    n = T.shape[0]
+    _check(L, None, L.chad_mlp_features(_dev(y), y.shape[1], _dev(T), n, _dev(feat_norm), _dev(X),
+                                        stream))
+
+
+def chad_mlp_forward(X, params, out, stream=None):
+    L = lib()
+    _check(L, None, L.chad_mlp_forward(_dev(X), X.shape[0], _dev(params), _dev(out), stream))
+
+
+def chad_mlp_grad(X, Y, params, grad, loss, scratch, stream=None):
+    L = lib()
+    _check(L, None, L.chad_mlp_grad(_dev(X), _dev(Y), X.shape[0], _dev(params), _dev(grad),
+                                    _dev(loss), _dev(scratch), scratch.numel() * scratch.element_size(),
+                                    stream))
+
+
+def mlp_grad_scratch_bytes(n):
+    return lib().chad_mlp_grad_scratch_bytes(int(n))
+
+
+def chad_mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    L = lib()
+    _check(L, None, L.chad_mlp_adam(_dev(params), _dev(grad), _dev(m), _dev(v), int(t), float(lr),
+                                    float(beta1), float(beta2), float(eps), stream))
 
 
 FLOP_KEYS = ["rates_f", "rates_fj", "charge_E", "form_w", "factor", "solve", "jx", "stage",
@@ -274,7 +340,7 @@ class Simulator:
 
     def __init__(self, pop: I.Population, precision=PREC_FP64, rtol=1e-6, atol=None,
                  max_steps=100000, max_newton=50, fixed_substeps=0, stream=None,
-                 headspace=None):
+                 headspace=None, learned=0):
         self.pop = pop
         nd = len(pop.digesters)
         self._keep = []
@@ -302,7 +368,7 @@ class Simulator:
         cfg.D_uniform = D_u.ctypes.data_as(_dp)
         cfg.y_in = y_in.ctypes.data_as(_dp)
         cfg.precision = precision
-        cfg.learned = 0
+        cfg.learned = int(learned)
         cfg.headspace = headspace
         cfg.rtol = rtol
         cfg.atol = atol.ctypes.data_as(_dp)

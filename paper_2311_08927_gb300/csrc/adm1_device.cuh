@@ -124,30 +124,40 @@ struct NewtonCounters {
   int failed;
 };
 
-// Newton from `guess`; an iterate leaving (0, inf) or a growing |E| switches
-// to bisection on [1e-14, 1] (geometric midpoint, at most 200 halvings).
-__host__ __device__ inline void solve_SH(const DigConst& c, const PartConst& q, const double* y,
-                                double guess, int max_iters, AcidBase& ab, NewtonCounters& nc) {
+// Newton from `guess` without a fallback: true if it converged within
+// max_iters with |E| <= max_resid at the returned root (ab then describes it).
+// E is increasing and concave, Newton converges quadratically with a
+// relative contraction factor below 1 near the root: an update below 1e-8
+// relative leaves the new iterate within ~1e-16 of the root.
+__host__ __device__ inline bool newton_only(const DigConst& c, const PartConst& q,
+                                            const double* y, double guess, int max_iters,
+                                            double max_resid, AcidBase& ab, int& iters) {
   double S = (guess > 0.0 && isfinite(guess)) ? guess : 1e-7;
   double prevE = INFINITY;
   for (int it = 0; it < max_iters; ++it) {
     const double E = charge_E(c, q, y, S, ab);
-    nc.iters++;
-    if (!isfinite(E) || fabs(E) > fabs(prevE)) break;
+    iters++;
+    if (!isfinite(E) || fabs(E) > fabs(prevE)) return false;
     const double dS = E * rcp<double>(ab.dEdS);
     const double Sn = S - dS;
-    if (!(Sn > 0.0) || !isfinite(Sn)) break;
-    // E is increasing and concave, Newton converges quadratically with a
-    // relative contraction factor below 1 near the root: an update below
-    // 1e-8 relative leaves the new iterate within ~1e-16 of the root.
+    if (!(Sn > 0.0) || !isfinite(Sn)) return false;
     if (fabs(dS) <= 1e-8 * Sn || fabs(E) <= 1e-15) {
-      charge_E(c, q, y, Sn, ab);  // reciprocals and slope at the accepted root
+      const double Ef = charge_E(c, q, y, Sn, ab);  // reciprocals and slope at the root
       ab.SH = Sn;
-      return;
+      return fabs(Ef) <= max_resid || fabs(E) <= max_resid;
     }
     prevE = E;
     S = Sn;
   }
+  return false;
+}
+
+// Newton from `guess`; an iterate leaving (0, inf) or a growing |E| switches
+// to bisection on [1e-14, 1] (geometric midpoint, at most 200 halvings).
+__host__ __device__ inline void solve_SH(const DigConst& c, const PartConst& q, const double* y,
+                                         double guess, int max_iters, AcidBase& ab,
+                                         NewtonCounters& nc) {
+  if (newton_only(c, q, y, guess, max_iters, INFINITY, ab, nc.iters)) return;
   nc.fallbacks++;
   double lo = kSH_lo, hi = kSH_hi;
   const double elo = charge_E(c, q, y, lo, ab);

@@ -60,6 +60,12 @@ struct chad_ctx {
   double flow_dt = -1.0;        // interval length the device flow constants hold
   // CUDA graph of one interval (captured on first use, replayed per interval)
   cudaGraphExec_t gexec = nullptr;
+  // learned guesses
+  bool has_mlp = false;
+  bool cold_pending = false;  // some particles were loaded without h
+  float* d_mlp = nullptr;     // params [NPARAM], feature norm [64], output norm [4]
+  double* d_SH_learned = nullptr;
+  double* d_h_learned = nullptr;
   double g_dt = -1.0;
   int g_variant = -1;
   bool use_graph = true;
@@ -102,6 +108,9 @@ static void free_all(chad_ctx* c) {
                   c->d_chunk_beg, c->d_chunk_end, c->d_dig_chunk0, c->d_partial, c->d_mean};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  void* lp[] = {c->d_mlp, c->d_SH_learned, c->d_h_learned};
+  for (void* p : lp)
+    if (p) cudaFree(p);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   c->gexec = nullptr;
 }
@@ -136,8 +145,8 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
     return fail(nullptr, CHAD_E_INVALID, "precision must be one of CHAD_PREC_*");
   if (cfg->headspace != CHAD_HEADSPACE_PARTICLE && cfg->headspace != CHAD_HEADSPACE_SHARED)
     return fail(nullptr, CHAD_E_INVALID, "invalid headspace mode");
-  if (cfg->learned != 0)
-    return fail(nullptr, CHAD_E_INVALID, "learned guesses are not available in this build");
+  if (cfg->learned != 0 && cfg->learned != 1)
+    return fail(nullptr, CHAD_E_INVALID, "learned must be 0 or 1");
   if (!(cfg->rtol > 0.0) || !std::isfinite(cfg->rtol))
     return fail(nullptr, CHAD_E_INVALID, "rtol must be > 0");
   for (int i = 0; i < NS; ++i)
@@ -220,6 +229,11 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   A(dalloc(&c->d_cnt, 1));
   A(dalloc(&c->d_queue, 1));
   A(dalloc(&c->d_interval, 1));
+  if (c->learned) {
+    A(dalloc(&c->d_mlp, (size_t)CHAD_MLP_NPARAM + 2 * CHAD_MLP_IN + 4));
+    A(dalloc(&c->d_SH_learned, c->ld));
+    A(dalloc(&c->d_h_learned, c->ld));
+  }
   A(dalloc(&c->d_chunk_dig, c->n_chunks));
   A(dalloc(&c->d_chunk_beg, c->n_chunks));
   A(dalloc(&c->d_chunk_end, c->n_chunks));
@@ -253,7 +267,7 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   A(cudaMemset(c->d_mean, 0, sizeof(double) * 3 * c->n_dig));
   A(cudaMemset(c->d_interval, 0, sizeof(unsigned long long)));
   A(cudaMemset(c->d_queue, 0, sizeof(unsigned long long)));
-  DevCounters z{0, 0, 0, 0, 0, 0x7fffffff, 0};
+  DevCounters z{0, 0, 0, 0, 0, 0, 0x7fffffff, 0};
   A(cudaMemcpy(c->d_cnt, &z, sizeof(z), cudaMemcpyHostToDevice));
   if (e != cudaSuccess) {
     free_all(c);
@@ -315,6 +329,7 @@ chad_status chad_load_particles(chad_ctx* c, int digester, int64_t n, const doub
     CK(c, fill(c->d_T, T, 308.15), "load T");
     CK(c, fill(c->d_SH, S_H, 1e-7), "load S_H");
     CK(c, fill(c->d_h, h, 0.0), "load h");
+    if (!h) c->cold_pending = true;
     CK(c, fill(c->d_D, nullptr, c->hdc[digester].D_uniform), "init D");
     CK(c, cudaMemsetAsync(c->d_status + o, 0, sizeof(int) * n, s), "reset status");
     if (mem == CHAD_MEM_HOST) CK(c, cudaStreamSynchronize(s), "load sync");
@@ -391,7 +406,8 @@ static chad_status prepare_flow(chad_ctx* c, double dt_coupling_s) {
 
 // The launch sequence of one coupling interval: advect (digesters with
 // flow) -> integrate every particle -> shared-headspace mean -> interval += 1.
-static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cudaStream_t s) {
+static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cudaStream_t s,
+                                    bool learned_now = false) {
   StepArgs a;
   a.n = c->N;
   a.ld = c->ld;
@@ -411,7 +427,15 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
   a.fixed_n = c->fixed_n;
   a.counters = c->d_cnt;
   a.queue = c->d_queue;
+  a.SH_learned = learned_now ? c->d_SH_learned : nullptr;
+  a.h_learned = learned_now ? c->d_h_learned : nullptr;
   cudaError_t e;
+  if (learned_now) {
+    const float* P = c->d_mlp;
+    e = launch_mlp_guess(c->d_y, c->ld, c->d_T, c->N, P, P + CHAD_MLP_NPARAM,
+                         P + CHAD_MLP_NPARAM + 2 * CHAD_MLP_IN, c->d_SH_learned, c->d_h_learned, s);
+    if (e != cudaSuccess) return e;
+  }
   if (c->any_flow) {
     AdvectArgs v;
     v.n = c->N;
@@ -443,6 +467,26 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
     if ((e = launch_headspace(hs, s)) != cudaSuccess) return e;
   }
   return launch_bump(c->d_interval, s);
+}
+
+chad_status chad_set_mlp(chad_ctx* c, const float* params, const float* feat_norm,
+                         const float* out_norm) {
+  if (!c) return CHAD_E_INVALID;
+  if (!c->learned) return fail(c, CHAD_E_STATE, "context created with learned = 0");
+  if (!params || !feat_norm || !out_norm) return fail(c, CHAD_E_INVALID, "null MLP input");
+  for (int i = 0; i < CHAD_MLP_NPARAM; ++i)
+    if (!std::isfinite(params[i])) return fail(c, CHAD_E_INVALID, "non-finite MLP parameter");
+  for (int i = 0; i < 2 * CHAD_MLP_IN; ++i)
+    if (!std::isfinite(feat_norm[i])) return fail(c, CHAD_E_INVALID, "non-finite feature norm");
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(out_norm[i])) return fail(c, CHAD_E_INVALID, "non-finite output norm");
+  float* P = c->d_mlp;
+  CK(c, cudaMemcpyAsync(P, params, sizeof(float) * CHAD_MLP_NPARAM, cudaMemcpyHostToDevice, c->stream), "mlp upload");
+  CK(c, cudaMemcpyAsync(P + CHAD_MLP_NPARAM, feat_norm, sizeof(float) * 2 * CHAD_MLP_IN, cudaMemcpyHostToDevice, c->stream), "mlp upload");
+  CK(c, cudaMemcpyAsync(P + CHAD_MLP_NPARAM + 2 * CHAD_MLP_IN, out_norm, sizeof(float) * 4, cudaMemcpyHostToDevice, c->stream), "mlp upload");
+  CK(c, cudaStreamSynchronize(c->stream), "mlp upload sync");
+  c->has_mlp = true;
+  return CHAD_OK;
 }
 
 chad_status chad_step(chad_ctx* c, double dt_coupling_s, int n_intervals) {
@@ -480,11 +524,18 @@ chad_status chad_step(chad_ctx* c, double dt_coupling_s, int n_intervals) {
       c->g_variant = variant;
     }
   }
+  if (c->learned && !c->has_mlp)
+    return fail(c, CHAD_E_STATE, "learned = 1 needs chad_set_mlp before chad_step");
   for (int it = 0; it < n_intervals; ++it) {
-    if (c->gexec)
+    if (c->learned && c->cold_pending) {
+      // first interval after a load without step-size history: learned guesses
+      CK(c, enqueue_interval(c, dt_days, variant, s, true), "interval launch");
+      c->cold_pending = false;
+    } else if (c->gexec) {
       CK(c, cudaGraphLaunch(c->gexec, s), "graph launch");
-    else
+    } else {
       CK(c, enqueue_interval(c, dt_days, variant, s), "interval launch");
+    }
     c->intervals++;
     c->sim_days += dt_days * (double)c->N;
   }
@@ -540,8 +591,11 @@ chad_status chad_autotune(chad_ctx* c, double dt_coupling_s, int32_t* chosen, do
   int best = c->variant[c->precision];
   float best_ms = 1e30f;
   for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
+    // two consecutive intervals per variant: one interval alone is too noisy
+    // to separate variants that differ by a few per cent
     e = restore();
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = enqueue_interval(c, dt_coupling_s / 86400.0, v, s);
     if (e == cudaSuccess) e = enqueue_interval(c, dt_coupling_s / 86400.0, v, s);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -611,11 +665,11 @@ chad_status chad_read_states(chad_ctx* c, int digester, double* y, double* pos, 
     stats->min_steps = dc.min_steps == 0x7fffffff ? 0 : dc.min_steps;
     stats->max_steps = dc.max_steps;
     stats->failed_particles = failed;
-    stats->mlp_redo = 0;
+    stats->mlp_redo = (int64_t)dc.mlp_redo;
     stats->pivot_rejects = (int64_t)dc.pivot_rejects;
     stats->intervals = c->intervals;
     stats->sim_days = c->sim_days;
-    DevCounters z{0, 0, 0, 0, 0, 0x7fffffff, 0};
+    DevCounters z{0, 0, 0, 0, 0, 0, 0x7fffffff, 0};
     CK(c, cudaMemcpy(c->d_cnt, &z, sizeof(z), cudaMemcpyHostToDevice), "reset counters");
     c->intervals = 0;
     c->sim_days = 0.0;

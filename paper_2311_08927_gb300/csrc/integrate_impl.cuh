@@ -41,7 +41,7 @@ constexpr double kHdefault = 1e-6;                              // days
 constexpr double kPivTau = 0.1;                                 // threshold pivoting
 
 struct Cnt {
-  int acc, rej, newton, fallback, failed, pivot;
+  int acc, rej, newton, fallback, failed, pivot, redo;
 };
 
 __device__ __forceinline__ int64_t queue_pop(unsigned long long* q) {
@@ -153,10 +153,10 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
   constexpr bool MIXED = FORM != 0;
   using R = typename std::conditional<MIXED, float, double>::type;
   using RS = typename std::conditional<FORM == 2, float, double>::type;
-  __shared__ unsigned long long s_acc, s_rej, s_newton, s_fb, s_piv;
+  __shared__ unsigned long long s_acc, s_rej, s_newton, s_fb, s_piv, s_redo;
   __shared__ int s_min, s_max;
   if (threadIdx.x == 0) {
-    s_acc = s_rej = s_newton = s_fb = s_piv = 0ull;
+    s_acc = s_rej = s_newton = s_fb = s_piv = s_redo = 0ull;
     s_min = INT_MAX;
     s_max = 0;
   }
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
   double y[NS], F0[NS], k1[NS], k2[NS], F1[NS], y1[NS], tmp[NS];
   const double Tend = a.dt_days;
   const bool fixed = a.fixed_n > 0;
-  Cnt tot{0, 0, 0, 0, 0, 0};
+  Cnt tot{0, 0, 0, 0, 0, 0, 0};
   int min_steps = INT_MAX, max_steps = 0;
 
   int64_t p = -1;
@@ -177,18 +177,32 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
   double SHg = 0.0, h = 0.0, t = 0.0, D = 0.0;
   int status = 0, attempts = 0, nacc = 0;
   bool rejected_prev = false;
-  Cnt cnt{0, 0, 0, 0, 0, 0};
+  Cnt cnt{0, 0, 0, 0, 0, 0, 0};
 
   while (true) {
     if (p < 0) {
       p = queue_pop(a.queue);
       if (p >= a.n) break;
+      cnt = Cnt{0, 0, 0, 0, 0, 0, 0};
       c = &a.dc[a.dig[p]];
       part_const(*c, a.T[p], q);
 #pragma unroll
       for (int i = 0; i < NS; ++i) y[i] = a.y[i * a.ld + p];
       SHg = a.SH[p];
       h = a.h[p];
+      if (a.SH_learned && !(h > 0.0 && isfinite(h))) {
+        // no step-size history: learned guesses; Newton from the learned
+        // S_H is bounded (4 iterations, |E| <= 1e-10) and the plain guess
+        // takes over if it fails
+        AcidBase abt;
+        int it = 0;
+        if (newton_only(*c, q, y, a.SH_learned[p], 4, 1e-10, abt, it))
+          SHg = abt.SH;
+        else
+          cnt.redo++;
+        cnt.newton += it;
+        h = a.h_learned[p];
+      }
       h = (h > 0.0 && isfinite(h)) ? h : kHdefault;
       if (fixed) h = Tend / a.fixed_n;
       D = a.D[p];
@@ -197,7 +211,6 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       attempts = 0;
       nacc = 0;
       rejected_prev = false;
-      cnt = Cnt{0, 0, 0, 0, 0, 0};
     }
     // ------------------------------------------------ one step attempt
     bool done = false;
@@ -323,6 +336,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       tot.newton += cnt.newton;
       tot.fallback += cnt.fallback;
       tot.pivot += cnt.pivot;
+      tot.redo += cnt.redo;
       min_steps = min(min_steps, nacc);
       max_steps = max(max_steps, nacc);
       p = -1;
@@ -334,6 +348,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
   atomicAdd(&s_newton, (unsigned long long)tot.newton);
   atomicAdd(&s_fb, (unsigned long long)tot.fallback);
   atomicAdd(&s_piv, (unsigned long long)tot.pivot);
+  atomicAdd(&s_redo, (unsigned long long)tot.redo);
   atomicMin(&s_min, min_steps);
   atomicMax(&s_max, max_steps);
   __syncthreads();
@@ -343,6 +358,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     atomicAdd(&a.counters->newton_iters, s_newton);
     atomicAdd(&a.counters->newton_fallbacks, s_fb);
     atomicAdd(&a.counters->pivot_rejects, s_piv);
+    atomicAdd(&a.counters->mlp_redo, s_redo);
     if (s_min != INT_MAX) atomicMin(&a.counters->min_steps, s_min);
     atomicMax(&a.counters->max_steps, s_max);
   }

@@ -13,7 +13,7 @@ enum : int { ST_NEWTON = 1, ST_STEPS = 2, ST_HMIN = 4, ST_NEG = 8, ST_NAN = 16 }
 
 // Device counters accumulated by the integrator (reset by the host)
 struct DevCounters {
-  unsigned long long accepted, rejected, newton_iters, newton_fallbacks, pivot_rejects;
+  unsigned long long accepted, rejected, newton_iters, newton_fallbacks, pivot_rejects, mlp_redo;
   int min_steps, max_steps;
 };
 
@@ -36,6 +36,8 @@ struct StepArgs {
   int fixed_n;          // 0: adaptive
   DevCounters* counters;
   unsigned long long* queue;  // particle queue head (reset before each launch)
+  const double* SH_learned;   // learned guesses for particles without history (or null)
+  const double* h_learned;
 };
 
 struct AdvectArgs {
@@ -69,6 +71,10 @@ constexpr int kNumVariants = 3;
 constexpr int kDefaultVariant = 0;
 cudaError_t launch_integrate(const StepArgs& a, int precision, int variant, cudaStream_t s);
 cudaError_t launch_advect(const AdvectArgs& a, cudaStream_t s);
+// MLP guesses for every particle of a context (see mlp.cu)
+cudaError_t launch_mlp_guess(const double* y, int64_t ld, const double* T, int64_t n,
+                             const float* params, const float* norm, const float* onorm,
+                             double* SH_out, double* h_out, cudaStream_t s);
 // interval index += 1 (last node of every interval)
 cudaError_t launch_bump(unsigned long long* interval, cudaStream_t s);
 cudaError_t launch_headspace(const HeadspaceArgs& a, cudaStream_t s);

@@ -79,7 +79,7 @@ def _cfg(**over):
     (dict(max_steps_per_interval=0), "max_steps"),
     (dict(max_newton_iters=0), "max_newton"),
     (dict(fixed_substeps=-1), "fixed_substeps"),
-    (dict(learned=1), "learned"),
+    (dict(learned=2), "learned"),
 ])
 def test_create_rejects_invalid_config_without_gpu(L, over, msg):
     cfg, keep = _cfg(**over)

@@ -1,0 +1,147 @@
+"""Learned initial guesses on the GPU: the tensor-core MLP kernels against the
+FP64 oracle MLP (forward and gradients with the same BF16 operands), training
+on states the integrator produces, and the cold-restart comparison of the
+method with and without the trained network."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as OM
+from paper_2311_08927_gb300 import chad as CH
+from paper_2311_08927_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_08927_gb300 import build
+    build.build()
+    CH.lib()
+
+
+def _bf16_bits(a):
+    """float32 array -> BF16 bit patterns (int16) with round-to-nearest-even."""
+    r = OM.bf16_round(a)
+    return (r.view(np.uint32) >> 16).astype(np.uint16).view(np.int16)
+
+
+def _rand_case(n, seed):
+    rng = np.random.default_rng(seed)
+    p = OM.pack({"W1": rng.standard_normal((64, 32)) * 0.25, "b1": rng.standard_normal(64) * 0.1,
+                 "W2": rng.standard_normal((64, 64)) * 0.18, "b2": rng.standard_normal(64) * 0.1,
+                 "W3": rng.standard_normal((2, 64)) * 0.2, "b3": rng.standard_normal(2) * 0.1})
+    X = rng.standard_normal((n, 32)).astype(np.float32)
+    X[:, 30:] = 0.0
+    Y = rng.standard_normal((n, 2)).astype(np.float32)
+    return p.astype(np.float32), X, Y
+
+
+def _weights_as_used(p32):
+    """The GPU rounds weights (not biases) to BF16; the oracle uses the same."""
+    w = OM.unpack(p32.astype(np.float64))
+    for k in ("W1", "W2", "W3"):
+        w[k] = OM.bf16_round(w[k].astype(np.float32)).astype(np.float64)
+    return OM.pack(w)
+
+
+def test_mlp_forward_matches_oracle():
+    p, X, _ = _rand_case(1000, 1)
+    Xb = torch.from_numpy(_bf16_bits(X)).cuda()
+    P = torch.from_numpy(p).cuda()
+    out = torch.empty((1000, 2), dtype=torch.float32, device="cuda")
+    CH.chad_mlp_forward(Xb, P, out)
+    ref, _ = OM.forward(_weights_as_used(p), OM.bf16_round(X).astype(np.float64))
+    got = out.cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-2
+
+
+def test_mlp_gradients_match_oracle_per_tensor():
+    n = 3000  # 12 blocks of 256 samples, ragged last block
+    p, X, Y = _rand_case(n, 2)
+    Xb = torch.from_numpy(_bf16_bits(X)).cuda()
+    Yt = torch.from_numpy(Y).cuda()
+    P = torch.from_numpy(p).cuda()
+    g = torch.empty_like(P)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    sc = torch.empty(CH.mlp_grad_scratch_bytes(n) // 4 + 1, dtype=torch.float32, device="cuda")
+    CH.chad_mlp_grad(Xb, Yt, P, g, loss, sc)
+    ref_loss, ref = OM.loss_and_grad(_weights_as_used(p), OM.bf16_round(X).astype(np.float64),
+                                     Y.astype(np.float64))
+    got = g.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) / ref_loss - 1) < 1e-2
+    o = 0
+    for name, shp in OM.SHAPES:
+        k = int(np.prod(shp))
+        rel = np.linalg.norm(got[o:o + k] - ref[o:o + k]) / np.linalg.norm(ref[o:o + k])
+        assert rel < 1e-2, (name, rel)
+        o += k
+    # deterministic reduction
+    g2 = torch.empty_like(P)
+    CH.chad_mlp_grad(Xb, Yt, P, g2, loss, sc)
+    assert torch.equal(g, g2)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_2311_08927_gb300 import learned as Lm
+    pop = I.config_population(3, n=40000)
+    y, T, SH, h = Lm.sample_states(pop, 6)
+    X, Y, norm, onorm = Lm.build_dataset(y, T, SH, h)
+    params, hist, test_loss = Lm.train(X, Y, epochs=12, batch=2048, lr=2e-3)
+    model = Lm.TrainedMLP(params, norm.cpu().numpy(), onorm, hist)
+    return model, hist, test_loss, (y, T, SH, h)
+
+
+def test_training_reduces_loss_and_predicts_charge_balance_root(trained):
+    """The validation loss falls well below its value before training, and
+    the learned log10 S_H is within 0.05 decade (median) of the Newton root."""
+    model, hist, test_loss, (y, T, SH, h) = trained
+    assert hist[-1][2] < 0.6 * hist[0][2], hist
+    from paper_2311_08927_gb300 import learned as Lm
+    e_sh, e_h = Lm.prediction_errors(model, y, T, SH, h)
+    assert e_sh < 0.05, (e_sh, e_h, hist)
+    assert e_h < 0.5, (e_sh, e_h)
+
+
+def _cold_restart(pop, relaxed, model, learned):
+    sim = CH.Simulator(pop, precision=CH.PREC_MIXED, learned=1 if learned else 0)
+    if learned:
+        CH.chad_set_mlp(sim.ctx, model.params, model.feat_norm, model.out_norm)
+    sim.load(y=relaxed)  # no S_H and no h: a restart without history
+    sim.step(60.0, 1)
+    out = sim.read()
+    sim.close()
+    return out
+
+
+def test_learned_cold_restart_saves_work_and_keeps_the_solution(trained):
+    model = trained[0]
+    pop = I.config_population(3, n=20000, seed_offset=7)
+    sim = CH.Simulator(pop, precision=CH.PREC_MIXED)
+    sim.load()
+    sim.step(60.0, 5)
+    relaxed = sim.read()["y"]
+    sim.close()
+    plain = _cold_restart(pop, relaxed, model, False)
+    lrn = _cold_restart(pop, relaxed, model, True)
+    assert np.all(plain["status"] == 0) and np.all(lrn["status"] == 0)
+    a_p = plain["stats"]["accepted_steps"] + plain["stats"]["rejected_steps"]
+    a_l = lrn["stats"]["accepted_steps"] + lrn["stats"]["rejected_steps"]
+    assert a_l < a_p, (a_l, a_p)
+    assert lrn["stats"]["newton_iters"] < plain["stats"]["newton_iters"]
+    assert lrn["stats"]["mlp_redo"] < 0.01 * pop.n
+    # same solution within the production tolerance, and both against the oracle
+    floor = 1e-12 * np.abs(plain["y"]).max(axis=1, keepdims=True)
+    d = np.abs(lrn["y"] - plain["y"]) / np.maximum(np.abs(plain["y"]), floor)
+    assert d.max() < 1e-4
+    idx = np.arange(0, pop.n, 997)
+    sub = I.Population([I.Digester(n=len(idx))], relaxed[:, idx].copy(), pop.T[idx].copy(),
+                       np.zeros((3, len(idx))), False)
+    o = O.run(sub, 60.0, 1, rtol=1e-10, atol=I.atol_vector(1e-13))
+    floor = 1e-12 * np.abs(o["y"]).max(axis=1, keepdims=True)
+    e = np.abs(lrn["y"][:, idx] - o["y"]) / np.maximum(np.abs(o["y"]), floor)
+    assert e.max() < 1e-4

@@ -148,7 +148,8 @@ def work_per_launch(CH, precision, stats, steps):
 def kernel_sources_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("adm1_device.cuh", "integrate_impl.cuh", "sparse_lu_gen.cuh", "model.h", "kernels.h"):
+    for f in ("adm1_device.cuh", "integrate_impl.cuh", "rank1.cuh", "sparse_lu_gen.cuh", "model.h",
+              "kernels.h"):
         with open(os.path.join(ROOT, "paper_2311_08927_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -293,10 +293,14 @@ chad_status chad_probe_alu_peak(int fp64, double* tflops);
 /* Algorithmic operation counts of the integrator's building blocks, taken
    from the kernel source (its templated routines run on the host with an
    operation-counting scalar; +, -, *, / count 1, an FMA 2): out[0] one rate
-   vector, out[1] rate vector + analytic Jacobian, out[2] one Eq. 7
-   evaluation, out[3] W formation, out[4] sparse LU, out[5] one sparse
-   solve, out[6] J x, out[7] stage combinations and error norm of one step
-   attempt, out[8] refinement update of one mixed solve.  n >= 9. */
+   vector, out[1] rate vector + J_d and u (the split Jacobian of
+   chad_eval_model_split), out[2] one Eq. 7 evaluation, out[3] formation of
+   I - g J_d, out[4] its sparse LU, out[5] one sparse solve, out[6] J_d x,
+   out[7] stage combinations and error norm of one step attempt, out[8]
+   refinement update of one mixed solve (with its rank-1 term), out[9]
+   Sherman-Morrison set-up of one attempt (q = (I - g J_d)^-1 g u and its
+   denominator, besides the sparse solve), out[10] Sherman-Morrison update
+   of one solve.  n >= 11. */
 chad_status chad_flop_counts(int64_t* out, int n);
 
 /* Evaluate the library's model for one particle: f = dy/dt (Eq. 2-6) [29],
@@ -311,6 +315,19 @@ chad_status chad_flop_counts(int64_t* out, int n);
 chad_status chad_eval_model(const double* params, double V_liq, double V_gas, double D,
                             const double* y_in, double T, const double* y, double SH_guess,
                             double* f, double* J, double* SH, int on_device);
+
+/* The same evaluation with the Jacobian split the way the integrator uses it
+   (Sec. 2.2 with Eq. 7 solved inside every rate evaluation): J = J_d + u v^T,
+   where J_d [29][29] (row-major) is df/dy with S_H held fixed, u [29] =
+   df/dS_H at fixed y and v [29] = dS_H/dy from Eq. 7 differentiated
+   implicitly (nonzero only in the eight states that enter Eq. 7).  The
+   integrator factors I - g J_d and applies the rank-1 term by the
+   Sherman-Morrison formula.  Arguments and errors as chad_eval_model; f and
+   SH are as there. */
+chad_status chad_eval_model_split(const double* params, double V_liq, double V_gas, double D,
+                                  const double* y_in, double T, const double* y,
+                                  double SH_guess, double* f, double* J_d, double* u, double* v,
+                                  double* SH, int on_device);
 
 #ifdef __cplusplus
 }

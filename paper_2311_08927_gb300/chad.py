@@ -125,6 +125,11 @@ def lib():
             L.chad_eval_model.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double,
                                           C.c_void_p, C.c_double, C.c_void_p, C.c_double,
                                           C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int]
+            L.chad_eval_model_split.restype = C.c_int
+            L.chad_eval_model_split.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                                C.c_void_p, C.c_double, C.c_void_p, C.c_double,
+                                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                C.POINTER(C.c_double), C.c_int]
             L.chad_probe_alu_peak.restype = C.c_int
             L.chad_probe_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
             _lib = L
@@ -135,7 +140,7 @@ def exported_symbols() -> list[str]:
     return ["chad_abi_version", "chad_n_params", "chad_param_name", "chad_last_error",
             "chad_create", "chad_destroy", "chad_load_particles", "chad_set_flow",
             "chad_step", "chad_synchronize", "chad_read_states", "chad_probe_alu_peak",
-            "chad_eval_model", "chad_autotune", "chad_flop_counts",
+            "chad_eval_model", "chad_eval_model_split", "chad_autotune", "chad_flop_counts",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
 
@@ -190,29 +195,32 @@ def chad_mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, s
 
 
 FLOP_KEYS = ["rates_f", "rates_fj", "charge_E", "form_w", "factor", "solve", "jx", "stage",
-             "refine"]
+             "refine", "sm_setup", "sm_update"]
 
 
 def flop_counts() -> dict:
     """Algorithmic operation counts of the integrator's building blocks."""
     L = lib()
-    out = np.zeros(9, dtype=np.int64)
-    _check(L, None, L.chad_flop_counts(out.ctypes.data, 9))
+    out = np.zeros(len(FLOP_KEYS), dtype=np.int64)
+    _check(L, None, L.chad_flop_counts(out.ctypes.data, len(FLOP_KEYS)))
     return dict(zip(FLOP_KEYS, (int(x) for x in out)))
 
 
 def attempt_flops(precision: int) -> dict:
     """FP64 and FP32 operations of one W-method step attempt, without the
-    Eq. 7 Newton iterations (counted separately per iteration)."""
+    Eq. 7 Newton iterations (counted separately per iteration).  The linear
+    algebra is the Sherman-Morrison form: one LU of I - g J_d, one solve for
+    q = (I - g J_d)^-1 g u, and per stage one solve plus the rank-1 update;
+    the mixed form adds one FP64 residual and a second FP32 solve per stage."""
     f = flop_counts()
     if precision == PREC_FP64:
-        f64 = (f["rates_fj"] + 2 * f["rates_f"] + f["form_w"] + f["factor"] + 3 * f["solve"] +
-               f["stage"])
+        f64 = (f["rates_fj"] + 2 * f["rates_f"] + f["form_w"] + f["factor"] + 4 * f["solve"] +
+               f["sm_setup"] + 3 * f["sm_update"] + f["stage"])
         return {"fp64": f64, "fp32": 0}
     f32_rates = precision == PREC_MIXED_F32RATES
     f64 = 3 * (f["jx"] + f["refine"]) + f["stage"] + (0 if f32_rates else 3 * f["rates_f"])
-    f32 = (f["rates_fj"] + f["form_w"] + f["factor"] + 6 * f["solve"] +
-           (2 * f["rates_f"] if f32_rates else 0))
+    f32 = (f["rates_fj"] + f["form_w"] + f["factor"] + 7 * f["solve"] + f["sm_setup"] +
+           6 * f["sm_update"] + (2 * f["rates_f"] if f32_rates else 0))
     return {"fp64": f64, "fp32": f32}
 
 
@@ -247,6 +255,30 @@ def eval_model(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, SH_gue
     if code not in (0, 5):
         raise ChadError(code, "chad_eval_model failed")
     return f, J, SH.value
+
+
+def eval_model_split(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, SH_guess=1e-7,
+                     on_device=False):
+    """(f, J_d, u, v, S_H) of the library's model for one particle: the
+    Jacobian split as J = J_d + u v^T (S_H held fixed in J_d, u = df/dS_H,
+    v = dS_H/dy)."""
+    L = lib()
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    yi = None if y_in is None else np.ascontiguousarray(y_in, dtype=np.float64)
+    f = np.zeros(NS)
+    Jd = np.zeros((NS, NS))
+    u = np.zeros(NS)
+    v = np.zeros(NS)
+    SH = C.c_double(0.0)
+    code = L.chad_eval_model_split(p.ctypes.data, float(V_liq), float(V_gas), float(D),
+                                   None if yi is None else yi.ctypes.data, float(T),
+                                   yy.ctypes.data, float(SH_guess), f.ctypes.data,
+                                   Jd.ctypes.data, u.ctypes.data, v.ctypes.data, C.byref(SH),
+                                   1 if on_device else 0)
+    if code not in (0, 5):
+        raise ChadError(code, "chad_eval_model_split failed")
+    return f, Jd, u, v, SH.value
 
 
 def probe_alu_peak(fp64: bool) -> float:

@@ -416,19 +416,19 @@ CHAD_HD void balances(const DigConst& c, const R* y, R D, const Rates<R>& o,
 
 // J[row][cols[k]] += coef * d[k]; u[row] += coef * s.  Idx maps (row, col)
 // to a storage slot (negative: structurally absent, the write is dropped).
-template <class Idx, class R>
-CHAD_HD void jadd(R* Jm, int row, int col, R v) {
+template <class Idx, class R, class JS>
+CHAD_HD void jadd(JS Jm, int row, int col, R v) {
   const int s = Idx::at(row, col);
   if (s >= 0) Jm[s] += v;
 }
-template <class Idx, class R, int NC>
-CHAD_HD void scat(R* Jm, R* u, int row, R coef, const int (&cols)[NC], const R (&d)[NC], R s) {
+template <class Idx, class R, class JS, int NC>
+CHAD_HD void scat(JS Jm, R* u, int row, R coef, const int (&cols)[NC], const R (&d)[NC], R s) {
 #pragma unroll
   for (int k = 0; k < NC; ++k) jadd<Idx>(Jm, row, cols[k], coef * d[k]);
   u[row] += coef * s;
 }
-template <class Idx, class R, int NC>
-CHAD_HD void scat(R* Jm, int row, R coef, const int (&cols)[NC], const R (&d)[NC]) {
+template <class Idx, class R, class JS, int NC>
+CHAD_HD void scat(JS Jm, int row, R coef, const int (&cols)[NC], const R (&d)[NC]) {
 #pragma unroll
   for (int k = 0; k < NC; ++k) jadd<Idx>(Jm, row, cols[k], coef * d[k]);
 }
@@ -436,9 +436,12 @@ CHAD_HD void scat(R* Jm, int row, R coef, const int (&cols)[NC], const R (&d)[NC
 // Analytic Jacobian (row-major NS x NS) from the rate partials.  The S_H
 // dependence enters as the rank-1 term u v^T, u = df/dS_H (at fixed y),
 // v = dS_H/dy = -(dE/dy) / (dE/dS_H) from Eq. 7.
-template <class Idx, class R>
+// With u_out == nullptr the full J = J_d + u v^T is assembled; otherwise only
+// the direct part J_d (S_H held fixed) goes into Jm and u = df/dS_H into
+// u_out, for the Sherman-Morrison solve of W = W_d - g u v^T.
+template <class Idx, class R, class JS>
 CHAD_HD void jacobian(const DigConst& c, const PartConst& q, const R* y, R D, const AcidBase& ab,
-                      const Rates<R>& o, R* Jm) {
+                      const Rates<R>& o, JS Jm, R* u_out = nullptr) {
   R u[NS];
 #pragma unroll
   for (int i = 0; i < Idx::size; ++i) Jm[i] = R(0);
@@ -579,6 +582,11 @@ CHAD_HD void jacobian(const DigConst& c, const PartConst& q, const R* y, R D, co
 #pragma unroll
       for (int b = 0; b < 3; ++b) jadd<Idx>(Jm, g[a], g[b], -gq * dP[b]);
     }
+  }
+  if (u_out) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) u_out[i] = u[i];
+    return;
   }
   // rank-1 S_H coupling: J += u v^T over the 8 states that enter Eq. 7
   const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};

@@ -1,7 +1,10 @@
-"""Generate sparse_lu_gen.cuh: a static-order sparse LU of W = I - g J.
+"""Generate sparse_lu_gen.cuh: a static-order sparse LU of W_d = I - g J_d.
 
-The structural pattern of the ADM1 Jacobian is taken from the library's own
-model (chad_eval_model on the host, i.e. the same source as the kernels),
+J_d is the ADM1 Jacobian with S_H held fixed; the full Jacobian is J_d + u v^T
+(u = df/dS_H, v = dS_H/dy from Eq. 7), and the integrator applies that
+rank-1 term by the Sherman-Morrison formula, so only W_d is factored.  The
+structural pattern of J_d is taken from the library's own model
+(chad_eval_model_split on the host, i.e. the same source as the kernels),
 evaluated at random states and randomly perturbed parameter sets so that no
 coefficient that happens to vanish for one parameter set is missed.  The
 elimination order is Markowitz's (minimise (r-1)(c-1) of each pivot on the
@@ -16,7 +19,7 @@ slot indices:
                      or is zero; the caller then shrinks the step, which
                      drives W towards the identity where the order is safe
   solve(w, dinv, b)  forward / back substitution in the static order
-  jx(j, x, out)      out = J x over J's structural nonzeros (FP64 residual)
+  jx(j, x, out)      out = J_d x over J_d's structural nonzeros (FP64 residual)
 
 Run from the repository root:  python paper_2311_08927_gb300/csrc/gen_sparse.py
 """
@@ -53,9 +56,10 @@ def jacobian_pattern(n_samples: int = 400, seed: int = 12345) -> np.ndarray:
         T = rng.uniform(298.0, 318.0)
         D = rng.uniform(0.0, 1.0)
         yin = I.influent() * np.exp(0.3 * rng.standard_normal(NS)) + 1e-6
-        _, J, _ = CH.eval_model(p, T, y, y_in=yin, D=D, V_liq=rng.uniform(1e-3, 1e4),
-                                V_gas=rng.uniform(1e-4, 1e3))
-        pat |= (J != 0.0)
+        _, Jd, _, _, _ = CH.eval_model_split(p, T, y, y_in=yin, D=D,
+                                             V_liq=rng.uniform(1e-3, 1e4),
+                                             V_gas=rng.uniform(1e-4, 1e3))
+        pat |= (Jd != 0.0)
     return pat
 
 
@@ -110,8 +114,9 @@ def generate(pat: np.ndarray) -> str:
     L = []
     w = L.append
     w("// GENERATED by gen_sparse.py from the library's own Jacobian pattern -- do not edit.")
-    w("// Static-order (Markowitz) sparse LU of W = I - g J for the 29 ADM1 states.")
-    w(f"// pattern nnz(J) = {nnz_j}, slots with fill = {nnz}")
+    w("// Static-order (Markowitz) sparse LU of W_d = I - g J_d for the 29 ADM1 states")
+    w("// (J_d: the Jacobian with S_H held fixed).")
+    w(f"// pattern nnz(J_d) = {nnz_j}, slots with fill = {nnz}")
     w("#pragma once")
     w('#include "adm1_device.cuh"')
     w("")
@@ -143,7 +148,7 @@ def generate(pat: np.ndarray) -> str:
     w("constexpr int kDiag[NS] = {" + ", ".join(str(int(slot[s, s])) for s in order) + "};")
     w("")
     # ------------------------------------------------------------- W formation
-    w("// W = I - g J in place over the slots (fill slots hold zero in J)")
+    w("// W_d = I - g J_d in place over the slots (fill slots hold zero in J_d)")
     w("template <class R>")
     w("CHAD_HD void form_w(R* w, R g) {")
     w("#pragma unroll")
@@ -211,7 +216,7 @@ def generate(pat: np.ndarray) -> str:
     w("}")
     w("")
     # ------------------------------------------------------------- J x
-    w("// out = J x over the structural nonzeros of J (slots of a J array).")
+    w("// out = J_d x over the structural nonzeros of J_d (slots of a J_d array).")
     w("template <class RJ>")
     w("CHAD_HD void jx(const RJ* j, const double* x, double* out) {")
     jflops = 0

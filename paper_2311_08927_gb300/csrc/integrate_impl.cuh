@@ -13,9 +13,13 @@
 // rejection, last step clipped to the end of the interval.  S_H+ of Eq. 7 is
 // re-solved by FP64 Newton at every rate evaluation.
 //
-// W is factored by the generated static-order sparse LU (sparse_lu_gen.cuh).
-// A pivot failing the threshold test rejects the attempt and shrinks h by 4,
-// which moves W towards the identity, where the static order is stable.
+// The Jacobian is split as J = J_d + u v^T (S_H held fixed in J_d; u =
+// df/dS_H, v = dS_H/dy from Eq. 7): W_d = I - h d J_d is factored by the
+// generated static-order sparse LU (sparse_lu_gen.cuh) and the rank-1 term
+// is applied by the Sherman-Morrison formula (rank1.cuh).  A pivot failing
+// the threshold test (or a Sherman-Morrison denominator failing the same
+// test) rejects the attempt and shrinks h by 4, which moves W towards the
+// identity, where the static order is stable.
 //
 // Forms: FP64 (J, LU, solves in FP64); MIXED (J, LU, solves in FP32, one
 // FP64 refinement step r = b - W x per solve, stage rates FP64); MIXED with
@@ -29,6 +33,7 @@
 
 #include "adm1_device.cuh"
 #include "kernels.h"
+#include "rank1.cuh"
 #include "sparse_lu_gen.cuh"
 
 namespace chad {
@@ -82,11 +87,12 @@ __device__ __forceinline__ void eval_f(const DigConst& c, const PartConst& q, co
   for (int i = 0; i < NS; ++i) f[i] = double(fr[i]);
 }
 
-// f(y) in precision RS and J in precision R (sparse slots), one Newton solve
+// f(y) in precision RS, J_d (sparse slots) and u = df/dS_H in precision R,
+// one Newton solve
 template <class R, class RS>
 __device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, const double* y,
                                         double D, double& SHg, int max_newton, Cnt& cnt,
-                                        double* f, R* w, AcidBase& ab) {
+                                        double* f, R* w, R* u, AcidBase& ab) {
   newton(c, q, y, SHg, max_newton, cnt, ab);
   {
     R yr[NS];
@@ -100,7 +106,7 @@ __device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, c
 #pragma unroll
       for (int i = 0; i < NS; ++i) f[i] = double(fr[i]);
     }
-    jacobian<sp::Idx, R>(c, q, yr, R(D), ab, o, w);
+    jacobian<sp::Idx, R>(c, q, yr, R(D), ab, o, w, u);
   }
   if (!std::is_same<R, RS>::value) {
     RS ys[NS];
@@ -126,23 +132,27 @@ __device__ __forceinline__ double sh_guess(double SH0, const double* v, const do
   return (g > 0.5 * SH0 && g < 2.0 * SH0) ? g : SH0;
 }
 
-// W x = b with the factored W.  Mixed: FP32 solve, FP64 residual
-// r = b - x + g (J x) with the kept FP32 Jacobian, FP32 correction solve.
+// W x = b with the factored W_d and the Sherman-Morrison vector q.  Mixed:
+// FP32 solve, FP64 residual r = b - x + g (J_d x + u v^T x) with the kept
+// FP32 J_d and u, FP32 correction solve.
 template <bool MIXED, class R>
-__device__ __forceinline__ void solve(const R* w, const R* dinv, const R* jk, double g,
+__device__ __forceinline__ void solve(const R* w, const R* dinv, const R* qv, R inv_delta,
+                                      const double* v, const R* jk, const R* uk, double g,
                                       const double* b, double* x) {
   R t[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) t[i] = R(b[i]);
   sp::solve<R>(w, dinv, t);
+  rank1::update<R>(qv, v, inv_delta, t);
 #pragma unroll
   for (int i = 0; i < NS; ++i) x[i] = double(t[i]);
   if (MIXED) {
-    double jx[NS];
-    sp::jx<R>(jk, x, jx);
+    double r[NS];
+    rank1::residual<R>(jk, uk, v, g, b, x, r);
 #pragma unroll
-    for (int i = 0; i < NS; ++i) t[i] = R(b[i] - x[i] + g * jx[i]);
+    for (int i = 0; i < NS; ++i) t[i] = R(r[i]);
     sp::solve<R>(w, dinv, t);
+    rank1::update<R>(qv, v, inv_delta, t);
 #pragma unroll
     for (int i = 0; i < NS; ++i) x[i] += double(t[i]);
   }
@@ -164,6 +174,8 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
 
   R w[sp::kNNZ];
   R jk[MIXED ? sp::kNNZ : 1];
+  R qv[NS];  // u = df/dS_H, then q = W_d^-1 (g u)
+  R uk[MIXED ? NS : 1];
   R dinv[NS];
   double y[NS], F0[NS], k1[NS], k2[NS], F1[NS], y1[NS], tmp[NS];
   const double Tend = a.dt_days;
@@ -222,17 +234,22 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       last = true;
     }
     AcidBase ab0;
-    eval_fj<R, RS>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, ab0);
+    eval_fj<R, RS>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ab0);
     const double SH0 = SHg;
     double vsh[8];
     sh_tangent(*c, q, ab0, vsh);
     if (MIXED) {
 #pragma unroll
       for (int s = 0; s < sp::kNNZ; ++s) jk[s] = w[s];
+#pragma unroll
+      for (int i = 0; i < NS; ++i) uk[i] = qv[i];
     }
     const double g = hh * kRB_d;
     sp::form_w<R>(w, R(g));
-    const bool piv_ok = sp::factor<R>(w, dinv, R(kPivTau));
+    const bool lu_ok = sp::factor<R>(w, dinv, R(kPivTau));
+    R inv_delta = R(0);
+    const bool sm_ok = rank1::setup<R>(w, dinv, R(g), vsh, R(kPivTau), qv, &inv_delta);
+    const bool piv_ok = lu_ok && sm_ok;
     double norm = INFINITY;
     if (!piv_ok) cnt.pivot++;
     double xs[NS];
@@ -265,7 +282,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
             }
           }
         }
-        solve<MIXED, R>(w, dinv, jk, g, tmp, xs);
+        solve<MIXED, R>(w, dinv, qv, inv_delta, vsh, jk, uk, g, tmp, xs);
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
           if (st == 0) k1[i] = xs[i];

@@ -21,12 +21,14 @@ struct EvalIn {
 };
 struct EvalOut {
   double f[NS];
-  double J[NS * NS];
+  double J[NS * NS];  // full J, or J_d when split
+  double u[NS], v[NS];
   double SH;
   int newton_failed;
 };
 
-__host__ __device__ void eval_one(const EvalIn& in, EvalOut& out) {
+// split = false: full J; split = true: J_d, u = df/dS_H, v = dS_H/dy.
+__host__ __device__ void eval_one(const EvalIn& in, EvalOut& out, bool split) {
   PartConst q;
   part_const(in.c, in.T, q);
   AcidBase ab;
@@ -35,13 +37,55 @@ __host__ __device__ void eval_one(const EvalIn& in, EvalOut& out) {
   Rates<double> o;
   rates<double, true>(in.c, q, in.y, ab, o);
   balances<double>(in.c, in.y, in.D, o, out.f);
-  jacobian<DenseIdx, double>(in.c, q, in.y, in.D, ab, o, out.J);
+  for (int i = 0; i < NS; ++i) out.u[i] = out.v[i] = 0.0;
+  if (split) {
+    jacobian<DenseIdx, double>(in.c, q, in.y, in.D, ab, o, out.J, out.u);
+    double vd[8];
+    sh_tangent(in.c, q, ab, vd);
+    const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
+    for (int k = 0; k < 8; ++k) out.v[hc[k]] = vd[k];
+  } else {
+    jacobian<DenseIdx, double>(in.c, q, in.y, in.D, ab, o, out.J);
+  }
   out.SH = ab.SH;
   out.newton_failed = nc.failed;
 }
 
-__global__ void eval_kernel(const EvalIn* in, EvalOut* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) eval_one(*in, *out);
+__global__ void eval_kernel(const EvalIn* in, EvalOut* out, bool split) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) eval_one(*in, *out, split);
+}
+
+chad_status eval_common(const double* params, double V_liq, double V_gas, double D,
+                        const double* y_in, double T, const double* y, double SH_guess,
+                        bool split, int on_device, EvalOut& out) {
+  if (!params || !y) return CHAD_E_INVALID;
+  if (!(T > 0.0)) return CHAD_E_INVALID;
+  EvalIn in;
+  std::memset(&in, 0, sizeof(in));
+  const char* why = "";
+  if (!derive_digester(params, V_liq, V_gas, D, y_in, in.c, &why)) return CHAD_E_INVALID;
+  in.T = T;
+  in.D = D;
+  in.SH_guess = SH_guess;
+  for (int i = 0; i < NS; ++i) in.y[i] = y[i];
+  if (on_device) {
+    EvalIn* din = nullptr;
+    EvalOut* dout = nullptr;
+    if (cudaMalloc(&din, sizeof(EvalIn)) != cudaSuccess) return CHAD_E_NOMEM;
+    if (cudaMalloc(&dout, sizeof(EvalOut)) != cudaSuccess) { cudaFree(din); return CHAD_E_NOMEM; }
+    cudaError_t e = cudaMemcpy(din, &in, sizeof(in), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      eval_kernel<<<1, 32>>>(din, dout, split);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&out, dout, sizeof(out), cudaMemcpyDeviceToHost);
+    cudaFree(din);
+    cudaFree(dout);
+    if (e != cudaSuccess) return CHAD_E_CUDA;
+  } else {
+    eval_one(in, out, split);
+  }
+  return out.newton_failed ? CHAD_E_PARTICLE : CHAD_OK;
 }
 
 }  // namespace
@@ -53,36 +97,31 @@ extern "C" chad_status chad_eval_model(const double* params, double V_liq, doubl
                                        const double* y_in, double T, const double* y,
                                        double SH_guess, double* f, double* J, double* SH,
                                        int on_device) {
-  if (!params || !y || !f || !J || !SH) return CHAD_E_INVALID;
-  if (!(T > 0.0)) return CHAD_E_INVALID;
-  EvalIn in;
-  std::memset(&in, 0, sizeof(in));
-  const char* why = "";
-  if (!derive_digester(params, V_liq, V_gas, D, y_in, in.c, &why)) return CHAD_E_INVALID;
-  in.T = T;
-  in.D = D;
-  in.SH_guess = SH_guess;
-  for (int i = 0; i < NS; ++i) in.y[i] = y[i];
+  if (!f || !J || !SH) return CHAD_E_INVALID;
   EvalOut out;
-  if (on_device) {
-    EvalIn* din = nullptr;
-    EvalOut* dout = nullptr;
-    if (cudaMalloc(&din, sizeof(EvalIn)) != cudaSuccess) return CHAD_E_NOMEM;
-    if (cudaMalloc(&dout, sizeof(EvalOut)) != cudaSuccess) { cudaFree(din); return CHAD_E_NOMEM; }
-    cudaError_t e = cudaMemcpy(din, &in, sizeof(in), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-      eval_kernel<<<1, 32>>>(din, dout);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpy(&out, dout, sizeof(out), cudaMemcpyDeviceToHost);
-    cudaFree(din);
-    cudaFree(dout);
-    if (e != cudaSuccess) return CHAD_E_CUDA;
-  } else {
-    eval_one(in, out);
-  }
+  const chad_status st =
+      eval_common(params, V_liq, V_gas, D, y_in, T, y, SH_guess, false, on_device, out);
+  if (st != CHAD_OK && st != CHAD_E_PARTICLE) return st;
   std::memcpy(f, out.f, sizeof(out.f));
   std::memcpy(J, out.J, sizeof(out.J));
   *SH = out.SH;
-  return out.newton_failed ? CHAD_E_PARTICLE : CHAD_OK;
+  return st;
+}
+
+extern "C" chad_status chad_eval_model_split(const double* params, double V_liq, double V_gas,
+                                             double D, const double* y_in, double T,
+                                             const double* y, double SH_guess, double* f,
+                                             double* J_d, double* u, double* v, double* SH,
+                                             int on_device) {
+  if (!f || !J_d || !u || !v || !SH) return CHAD_E_INVALID;
+  EvalOut out;
+  const chad_status st =
+      eval_common(params, V_liq, V_gas, D, y_in, T, y, SH_guess, true, on_device, out);
+  if (st != CHAD_OK && st != CHAD_E_PARTICLE) return st;
+  std::memcpy(f, out.f, sizeof(out.f));
+  std::memcpy(J_d, out.J, sizeof(out.J));
+  std::memcpy(u, out.u, sizeof(out.u));
+  std::memcpy(v, out.v, sizeof(out.v));
+  *SH = out.SH;
+  return st;
 }

@@ -9,6 +9,7 @@
 #include "adm1_device.cuh"
 #include "chad.h"
 #include "model.h"
+#include "rank1.cuh"
 #include "sparse_lu_gen.cuh"
 
 namespace chad {
@@ -49,16 +50,18 @@ HD inline bool isfinite(Fc a) { return ::isfinite(a.v); }
 using namespace chad;
 
 // out[0] rate vector f (rates + mass balances)
-// out[1] rate vector with rate partials and the analytic Jacobian
+// out[1] rate vector with rate partials, J_d and u (split Jacobian)
 // out[2] one charge-balance evaluation E(S_H), dE/dS_H
-// out[3] W = I - g J over the sparse slots
-// out[4] sparse LU factorisation
+// out[3] W_d = I - g J_d over the sparse slots
+// out[4] sparse LU factorisation of W_d
 // out[5] one sparse forward/back solve
-// out[6] J x over J's nonzeros (mixed refinement residual)
+// out[6] J_d x over J_d's nonzeros (mixed refinement residual)
 // out[7] stage combinations and error norm of one W-method attempt
-// out[8] refinement update of one mixed solve (besides J x)
+// out[8] refinement update of one mixed solve (besides J_d x)
+// out[9] Sherman-Morrison set-up of one attempt (besides its solve)
+// out[10] Sherman-Morrison update of one solve
 extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
-  if (!out || n < 9) return CHAD_E_INVALID;
+  if (!out || n < 11) return CHAD_E_INVALID;
   DigConst c;
   std::memset(&c, 0, sizeof(c));
   c.ni_aa = 2;
@@ -87,10 +90,11 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   balances<Fc>(c, y, Fc(0.1), o, f);
   out[0] = g_ops;
   static Fc w[sp::kNNZ];
+  Fc u[NS];
   g_ops = 0;
   rates<Fc, true>(c, q, y, ab, o);
   balances<Fc>(c, y, Fc(0.1), o, f);
-  jacobian<sp::Idx, Fc>(c, q, y, Fc(0.1), ab, o, w);
+  jacobian<sp::Idx, Fc>(c, q, y, Fc(0.1), ab, o, w, u);
   out[1] = g_ops;
   Fc r[6], dE;
   g_ops = 0;
@@ -110,10 +114,19 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   sp::solve<Fc>(w, dinv, b);
   out[5] = g_ops;
   out[6] = sp::kJxFlops;
+  const double v[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+  Fc inv_delta;
+  for (int i = 0; i < NS; ++i) u[i] = Fc(1.0);
+  g_ops = 0;
+  rank1::setup<Fc>(w, dinv, Fc(1e-4), v, Fc(0.1), u, &inv_delta);
+  out[9] = g_ops - out[5];
+  g_ops = 0;
+  rank1::update<Fc>(u, v, inv_delta, b);
+  out[10] = g_ops;
   // y + h/2 k1 (2/elt), F1 - k1 (1), k2 += k1 (1), y + h k2 (2), F2 - e32 (k2 - F1)
   // - 2 (k1 - F0) (5), h/6 (k1 - 2 k2 + k3) (4), atol + rtol max(..) (2), |e|/sc (1)
   out[7] = (int64_t)NS * 18;
-  // b - x + g jx (3/elt), x += dx (1/elt)
-  out[8] = (int64_t)NS * 4;
+  // v^T x (15), b - x + g (jx + u s) (4/elt), x += dx (1/elt)
+  out[8] = 15 + (int64_t)NS * 5;
   return CHAD_OK;
 }

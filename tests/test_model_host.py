@@ -53,13 +53,59 @@ def test_generated_sparse_lu_is_current():
         assert fh.read() == src, "sparse_lu_gen.cuh is stale: rerun gen_sparse.py"
 
 
-def test_jacobian_nonzeros_have_sparse_slots():
+def test_direct_jacobian_nonzeros_have_sparse_slots():
+    """The generated LU factors I - g J_d: every structural nonzero of J_d
+    (S_H held fixed) has a slot, u = df/dS_H is nonzero only in the rows the
+    kernels' rank-1 update covers and v = dS_H/dy only in the eight states of
+    Eq. 7."""
     sys.path.insert(0, os.path.join(ROOT, "paper_2311_08927_gb300", "csrc"))
     import gen_sparse as G
     pat = G.jacobian_pattern()
     F = G.symbolic_fill(pat, G.markowitz(pat))
+    eq7 = [I.SIDX[n] for n in ("S_va", "S_bu", "S_pro", "S_ac", "S_IC", "S_IN", "S_cat", "S_an")]
     for p, T, y, D, V in _cases(40, 17):
-        _, J, _ = CH.eval_model(p, T, y, y_in=I.influent(), D=D)
-        assert not np.any((J != 0) & ~pat)
+        _, Jd, u, v, _ = CH.eval_model_split(p, T, y, y_in=I.influent(), D=D)
+        assert not np.any((Jd != 0) & ~pat)
+        off = np.ones(I.NS, dtype=bool)
+        off[eq7] = False
+        assert np.all(v[off] == 0.0)
+        assert np.count_nonzero(u) <= 19
     # fill only adds entries; the pattern includes the diagonal
     assert np.all(np.diag(pat)) and F.sum() >= pat.sum()
+
+
+def _richardson(fun, x0, h):
+    """Central difference with one Richardson step (error O(h^4))."""
+    d1 = (fun(x0 + h) - fun(x0 - h)) / (2 * h)
+    d2 = (fun(x0 + 2 * h) - fun(x0 - 2 * h)) / (4 * h)
+    return (4 * d1 - d2) / 3
+
+
+def test_split_jacobian_matches_oracle():
+    """J_d + u v^T equals the oracle's dual-number Jacobian, and each part
+    matches an independent (Richardson-extrapolated) central difference of
+    the oracle: J_d and u of the rates at a fixed S_H (rhs_at), v of the
+    Eq. 7 root (charge_solve)."""
+    for p, T, y, D, V in _cases(8, 23):
+        yin = I.influent()
+        f, Jd, u, v, SH = CH.eval_model_split(p, T, y, y_in=yin, D=D, V_liq=V, V_gas=V * 0.1)
+        Jo = O.jacobian(p, T, y, y_in=yin, D=D, V_liq=V, V_gas=V * 0.1)
+        cs = np.abs(Jo).max(axis=0, keepdims=True) + 1e-300
+        assert np.max(np.abs(Jd + np.outer(u, v) - Jo) / cs) < 1e-12
+        SHo = O.charge_solve(p, T, y)[0]
+
+        def fa(yy, S):
+            return O.rhs_at(p, T, yy, S, y_in=yin, D=D, V_liq=V, V_gas=V * 0.1)
+
+        uf = _richardson(lambda S: fa(y, S), SHo, 1e-2 * SHo)
+        us = np.abs(uf) + 1e-9 * np.abs(uf).max()
+        assert np.max(np.abs(u - uf) / us) < 2e-5
+        for j in range(I.NS):
+            hj = 1e-2 * max(abs(y[j]), 1e-8)
+            e = np.zeros(I.NS)
+            e[j] = 1.0
+            col = _richardson(lambda t: fa(y + t * e, SHo), 0.0, hj)
+            sc = np.abs(col).max() + 1e-300
+            assert np.max(np.abs(Jd[:, j] - col)) / sc < 1e-6, j
+            vf = _richardson(lambda t: O.charge_solve(p, T, y + t * e)[0], 0.0, 1e-2 * hj)
+            assert abs(v[j] - vf) <= 1e-6 * abs(vf) + 1e-12 * SHo / max(abs(y[j]), 1e-8), j

@@ -295,7 +295,8 @@ chad_status chad_probe_alu_peak(int fp64, double* tflops);
    operation-counting scalar; +, -, *, / count 1, an FMA 2): out[0] one rate
    vector, out[1] rate vector + J_d and u (the split Jacobian of
    chad_eval_model_split), out[2] one Eq. 7 evaluation, out[3] formation of
-   I - g J_d, out[4] its sparse LU, out[5] one sparse solve, out[6] J_d x,
+   I - g J_d, out[4] its sparse LU, out[5] one sparse solve, out[6] J x from
+   the rate partials,
    out[7] stage combinations and error norm of one step attempt, out[8]
    refinement update of one mixed solve (with its rank-1 term), out[9]
    Sherman-Morrison set-up of one attempt (q = (I - g J_d)^-1 g u and its
@@ -322,12 +323,14 @@ chad_status chad_eval_model(const double* params, double V_liq, double V_gas, do
    df/dS_H at fixed y and v [29] = dS_H/dy from Eq. 7 differentiated
    implicitly (nonzero only in the eight states that enter Eq. 7).  The
    integrator factors I - g J_d and applies the rank-1 term by the
-   Sherman-Morrison formula.  Arguments and errors as chad_eval_model; f and
-   SH are as there. */
+   Sherman-Morrison formula.  If x [29] is given, Jx [29] receives J x as the
+   mixed form's refinement forms it, from the rate partials without a matrix
+   (x and Jx both NULL or both set).  Arguments and errors otherwise as
+   chad_eval_model; f and SH are as there. */
 chad_status chad_eval_model_split(const double* params, double V_liq, double V_gas, double D,
                                   const double* y_in, double T, const double* y,
-                                  double SH_guess, double* f, double* J_d, double* u, double* v,
-                                  double* SH, int on_device);
+                                  double SH_guess, const double* x, double* f, double* J_d,
+                                  double* u, double* v, double* Jx, double* SH, int on_device);
 
 #ifdef __cplusplus
 }

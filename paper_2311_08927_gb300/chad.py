@@ -129,7 +129,8 @@ def lib():
             L.chad_eval_model_split.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double,
                                                 C.c_void_p, C.c_double, C.c_void_p, C.c_double,
                                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                                C.POINTER(C.c_double), C.c_int]
+                                                C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                                C.c_int]
             L.chad_probe_alu_peak.restype = C.c_int
             L.chad_probe_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
             _lib = L
@@ -211,7 +212,8 @@ def attempt_flops(precision: int) -> dict:
     Eq. 7 Newton iterations (counted separately per iteration).  The linear
     algebra is the Sherman-Morrison form: one LU of I - g J_d, one solve for
     q = (I - g J_d)^-1 g u, and per stage one solve plus the rank-1 update;
-    the mixed form adds one FP64 residual and a second FP32 solve per stage."""
+    the mixed form adds one FP64 residual (J x from the rate partials) and a
+    second FP32 solve per stage."""
     f = flop_counts()
     if precision == PREC_FP64:
         f64 = (f["rates_fj"] + 2 * f["rates_f"] + f["form_w"] + f["factor"] + 4 * f["solve"] +
@@ -258,10 +260,11 @@ def eval_model(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, SH_gue
 
 
 def eval_model_split(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, SH_guess=1e-7,
-                     on_device=False):
+                     on_device=False, x=None):
     """(f, J_d, u, v, S_H) of the library's model for one particle: the
     Jacobian split as J = J_d + u v^T (S_H held fixed in J_d, u = df/dS_H,
-    v = dS_H/dy)."""
+    v = dS_H/dy).  With a direction x, returns (f, J_d, u, v, S_H, Jx) where
+    Jx = J x is formed from the rate partials as in the mixed refinement."""
     L = lib()
     p = np.ascontiguousarray(params, dtype=np.float64)
     yy = np.ascontiguousarray(y, dtype=np.float64)
@@ -271,14 +274,20 @@ def eval_model_split(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, 
     u = np.zeros(NS)
     v = np.zeros(NS)
     SH = C.c_double(0.0)
+    xx = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+    Jx = None if x is None else np.zeros(NS)
     code = L.chad_eval_model_split(p.ctypes.data, float(V_liq), float(V_gas), float(D),
                                    None if yi is None else yi.ctypes.data, float(T),
-                                   yy.ctypes.data, float(SH_guess), f.ctypes.data,
-                                   Jd.ctypes.data, u.ctypes.data, v.ctypes.data, C.byref(SH),
+                                   yy.ctypes.data, float(SH_guess),
+                                   None if xx is None else xx.ctypes.data, f.ctypes.data,
+                                   Jd.ctypes.data, u.ctypes.data, v.ctypes.data,
+                                   None if Jx is None else Jx.ctypes.data, C.byref(SH),
                                    1 if on_device else 0)
     if code not in (0, 5):
         raise ChadError(code, "chad_eval_model_split failed")
-    return f, Jd, u, v, SH.value
+    if x is None:
+        return f, Jd, u, v, SH.value
+    return f, Jd, u, v, SH.value, Jx
 
 
 def probe_alu_peak(fp64: bool) -> float:

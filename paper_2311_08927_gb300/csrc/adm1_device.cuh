@@ -365,14 +365,12 @@ CHAD_HD void rates(const DigConst& c, const PartConst& q, const R* y,
   }
 }
 
-// f(y): mass balances of Eq. 2 with the ADM1 stoichiometry
+// Stoichiometric part of the mass balances of Eq. 2: f = dil + N r, where
+// dil holds the transport terms of every state (liquid: dilution; gas:
+// outflow) and N the ADM1 stoichiometry of the 19 processes and the three
+// gas transfers (r[19..21]).
 template <class R>
-CHAD_HD void balances(const DigConst& c, const R* y, R D, const Rates<R>& o,
-                                         R* f) {
-  const R* r = o.r;
-  R dil[26];
-#pragma unroll
-  for (int i = 0; i < 26; ++i) dil[i] = D * (R(c.y_in[i]) - y[i]);
+CHAD_HD void stoich(const DigConst& c, const R* r, const R* dil, R* f) {
   const R dec = r[12] + r[13] + r[14] + r[15] + r[16] + r[17] + r[18];
   f[iS_su] = dil[iS_su] + r[1] + R(c.c_su_li) * r[3] - r[4];
   f[iS_aa] = dil[iS_aa] + r[2] - r[5];
@@ -409,10 +407,70 @@ CHAD_HD void balances(const DigConst& c, const R* y, R D, const Rates<R>& o,
   f[iS_cat] = dil[iS_cat];
   f[iS_an] = dil[iS_an];
   const R vr = R(c.Vliq_over_Vgas);
-  f[iG_h2] = -y[iG_h2] * o.qv + vr * r[19];
-  f[iG_ch4] = -y[iG_ch4] * o.qv + vr * r[20];
-  f[iG_co2] = -y[iG_co2] * o.qv + vr * r[21];
+  f[iG_h2] = dil[iG_h2] + vr * r[19];
+  f[iG_ch4] = dil[iG_ch4] + vr * r[20];
+  f[iG_co2] = dil[iG_co2] + vr * r[21];
 }
+
+// f(y): mass balances of Eq. 2 with the ADM1 stoichiometry
+template <class R>
+CHAD_HD void balances(const DigConst& c, const R* y, R D, const Rates<R>& o, R* f) {
+  R dil[NS];
+#pragma unroll
+  for (int i = 0; i < 26; ++i) dil[i] = D * (R(c.y_in[i]) - y[i]);
+  dil[iG_h2] = -y[iG_h2] * o.qv;
+  dil[iG_ch4] = -y[iG_ch4] * o.qv;
+  dil[iG_co2] = -y[iG_co2] * o.qv;
+  stoich<R>(c, o.r, dil, f);
+}
+
+// Jacobian-vector product J x = J_d x + u (v^T x) without a matrix: the
+// rate partials of rates<RO, true> give the linearised rates
+// dr = (d rho / dy) x + (d rho / dS_H) s with s = v^T x, which go through the
+// same stoichiometry as the rates; the transport terms are linearised
+// directly.  Arithmetic in precision RD (FP64 in the kernels) whatever the
+// precision RO of the partials.
+template <class RO, class RD>
+CHAD_HD void jvp(const DigConst& c, const RD* y, RD D, const Rates<RO>& o, const RD* x, RD s,
+                 RD* out) {
+  RD dr[22];
+  dr[0] = RD(o.d1) * x[iX_c];
+  dr[1] = RD(o.d2) * x[iX_ch];
+  dr[2] = RD(o.d3) * x[iX_pr];
+  dr[3] = RD(o.d4) * x[iX_li];
+  dr[4] = RD(o.d5[0]) * x[iS_su] + RD(o.d5[1]) * x[iX_su] + RD(o.d5[2]) * x[iS_IN] +
+          RD(o.s5) * s;
+  dr[5] = RD(o.d6[0]) * x[iS_aa] + RD(o.d6[1]) * x[iX_aa] + RD(o.d6[2]) * x[iS_IN] +
+          RD(o.s6) * s;
+  dr[6] = RD(o.d7[0]) * x[iS_fa] + RD(o.d7[1]) * x[iX_fa] + RD(o.d7[2]) * x[iS_IN] +
+          RD(o.d7[3]) * x[iS_h2] + RD(o.s7) * s;
+  dr[7] = RD(o.d8[0]) * x[iS_va] + RD(o.d8[1]) * x[iS_bu] + RD(o.d8[2]) * x[iX_c4] +
+          RD(o.d8[3]) * x[iS_IN] + RD(o.d8[4]) * x[iS_h2] + RD(o.s8) * s;
+  dr[8] = RD(o.d9[0]) * x[iS_va] + RD(o.d9[1]) * x[iS_bu] + RD(o.d9[2]) * x[iX_c4] +
+          RD(o.d9[3]) * x[iS_IN] + RD(o.d9[4]) * x[iS_h2] + RD(o.s9) * s;
+  dr[9] = RD(o.d10[0]) * x[iS_pro] + RD(o.d10[1]) * x[iX_pro] +
+          RD(o.d10[2]) * x[iS_IN] + RD(o.d10[3]) * x[iS_h2] + RD(o.s10) * s;
+  dr[10] = RD(o.d11[0]) * x[iS_ac] + RD(o.d11[1]) * x[iX_ac] +
+           RD(o.d11[2]) * x[iS_IN] + RD(o.s11) * s;
+  dr[11] = RD(o.d12[0]) * x[iS_h2] + RD(o.d12[1]) * x[iX_h2] +
+           RD(o.d12[2]) * x[iS_IN] + RD(o.s12) * s;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) dr[12 + k] = RD(o.ddec[k]) * x[iX_su + k];
+  dr[19] = RD(o.dT8[0]) * x[iS_h2] + RD(o.dT8[1]) * x[iG_h2];
+  dr[20] = RD(o.dT9[0]) * x[iS_ch4] + RD(o.dT9[1]) * x[iG_ch4];
+  dr[21] = RD(o.dT10[0]) * x[iS_IC] + RD(o.dT10[1]) * x[iG_co2] + RD(o.sT10) * s;
+  RD dil[NS];
+#pragma unroll
+  for (int i = 0; i < 26; ++i) dil[i] = -D * x[i];
+  const RD qv = RD(o.qv);
+  const RD dq =
+      RD(o.dqv) * (RD(o.P_h2) * x[iG_h2] + RD(o.P_ch4) * x[iG_ch4] + RD(o.P_co2) * x[iG_co2]);
+  dil[iG_h2] = -x[iG_h2] * qv - y[iG_h2] * dq;
+  dil[iG_ch4] = -x[iG_ch4] * qv - y[iG_ch4] * dq;
+  dil[iG_co2] = -x[iG_co2] * qv - y[iG_co2] * dq;
+  stoich<RD>(c, dr, dil, out);
+}
+
 
 // J[row][cols[k]] += coef * d[k]; u[row] += coef * s.  Idx maps (row, col)
 // to a storage slot (negative: structurally absent, the write is dropped).

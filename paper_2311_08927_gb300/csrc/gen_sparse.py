@@ -19,7 +19,6 @@ slot indices:
                      or is zero; the caller then shrinks the step, which
                      drives W towards the identity where the order is safe
   solve(w, dinv, b)  forward / back substitution in the static order
-  jx(j, x, out)      out = J_d x over J_d's structural nonzeros (FP64 residual)
 
 Run from the repository root:  python paper_2311_08927_gb300/csrc/gen_sparse.py
 """
@@ -215,25 +214,12 @@ def generate(pat: np.ndarray) -> str:
         w(f"  b[{order[k]}] = z{k};")
     w("}")
     w("")
-    # ------------------------------------------------------------- J x
-    w("// out = J_d x over the structural nonzeros of J_d (slots of a J_d array).")
-    w("template <class RJ>")
-    w("CHAD_HD void jx(const RJ* j, const double* x, double* out) {")
-    jflops = 0
-    for r in range(NS):
-        cols = [c for c in range(NS) if pat[r, c]]
-        expr = " + ".join(f"double(j[{slot[r, c]}]) * x[{c}]" for c in cols) or "0.0"
-        w(f"  out[{r}] = {expr};")
-        jflops += 2 * len(cols)
-    w("}")
-    w("")
     w(f"constexpr int kFactorFlops = {flops};")
     w(f"constexpr int kSolveFlops = {sflops};")
-    w(f"constexpr int kJxFlops = {jflops};")
     w("")
     w("}  // namespace sp")
     w("}  // namespace chad")
-    return "\n".join(L) + "\n", dict(nnz=nnz, nnz_j=nnz_j, factor=flops, solve=sflops, jx=jflops,
+    return "\n".join(L) + "\n", dict(nnz=nnz, nnz_j=nnz_j, factor=flops, solve=sflops,
                                       order=[I.STATE_NAMES[s] for s in order])
 
 

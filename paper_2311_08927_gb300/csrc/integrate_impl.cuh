@@ -24,6 +24,9 @@
 // Forms: FP64 (J, LU, solves in FP64); MIXED (J, LU, solves in FP32, one
 // FP64 refinement step r = b - W x per solve, stage rates FP64); MIXED with
 // FP32 stage rates.  Newton, state accumulation and error estimate: FP64.
+// The refinement residual needs W x = x - g J x: it is formed from the FP32
+// rate partials kept from the Jacobian evaluation (jvp), not from a stored
+// copy of J.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -92,13 +95,12 @@ __device__ __forceinline__ void eval_f(const DigConst& c, const PartConst& q, co
 template <class R, class RS>
 __device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, const double* y,
                                         double D, double& SHg, int max_newton, Cnt& cnt,
-                                        double* f, R* w, R* u, AcidBase& ab) {
+                                        double* f, R* w, R* u, Rates<R>& o, AcidBase& ab) {
   newton(c, q, y, SHg, max_newton, cnt, ab);
   {
     R yr[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) yr[i] = R(y[i]);
-    Rates<R> o;
     rates<R, true>(c, q, yr, ab, o);
     if (std::is_same<R, RS>::value) {
       R fr[NS];
@@ -133,12 +135,13 @@ __device__ __forceinline__ double sh_guess(double SH0, const double* v, const do
 }
 
 // W x = b with the factored W_d and the Sherman-Morrison vector q.  Mixed:
-// FP32 solve, FP64 residual r = b - x + g (J_d x + u v^T x) with the kept
-// FP32 J_d and u, FP32 correction solve.
+// FP32 solve, FP64 residual r = b - x + g J x with J x from the kept FP32
+// rate partials ko at the step's start y, FP32 correction solve.
 template <bool MIXED, class R>
 __device__ __forceinline__ void solve(const R* w, const R* dinv, const R* qv, R inv_delta,
-                                      const double* v, const R* jk, const R* uk, double g,
-                                      const double* b, double* x) {
+                                      const double* v, const DigConst& c, const double* y,
+                                      double D, const Rates<R>& ko, double g, const double* b,
+                                      double* x) {
   R t[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) t[i] = R(b[i]);
@@ -147,10 +150,10 @@ __device__ __forceinline__ void solve(const R* w, const R* dinv, const R* qv, R 
 #pragma unroll
   for (int i = 0; i < NS; ++i) x[i] = double(t[i]);
   if (MIXED) {
-    double r[NS];
-    rank1::residual<R>(jk, uk, v, g, b, x, r);
+    double jx[NS];
+    jvp<R, double>(c, y, D, ko, x, rank1::vdot<double>(v, x), jx);
 #pragma unroll
-    for (int i = 0; i < NS; ++i) t[i] = R(r[i]);
+    for (int i = 0; i < NS; ++i) t[i] = R(b[i] - x[i] + g * jx[i]);
     sp::solve<R>(w, dinv, t);
     rank1::update<R>(qv, v, inv_delta, t);
 #pragma unroll
@@ -173,10 +176,9 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
   __syncthreads();
 
   R w[sp::kNNZ];
-  R jk[MIXED ? sp::kNNZ : 1];
   R qv[NS];  // u = df/dS_H, then q = W_d^-1 (g u)
-  R uk[MIXED ? NS : 1];
   R dinv[NS];
+  Rates<R> ko;  // rates and partials at the step's start (mixed: kept for jvp)
   double y[NS], F0[NS], k1[NS], k2[NS], F1[NS], y1[NS], tmp[NS];
   const double Tend = a.dt_days;
   const bool fixed = a.fixed_n > 0;
@@ -234,16 +236,10 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       last = true;
     }
     AcidBase ab0;
-    eval_fj<R, RS>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ab0);
+    eval_fj<R, RS>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0);
     const double SH0 = SHg;
     double vsh[8];
     sh_tangent(*c, q, ab0, vsh);
-    if (MIXED) {
-#pragma unroll
-      for (int s = 0; s < sp::kNNZ; ++s) jk[s] = w[s];
-#pragma unroll
-      for (int i = 0; i < NS; ++i) uk[i] = qv[i];
-    }
     const double g = hh * kRB_d;
     sp::form_w<R>(w, R(g));
     const bool lu_ok = sp::factor<R>(w, dinv, R(kPivTau));
@@ -282,7 +278,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
             }
           }
         }
-        solve<MIXED, R>(w, dinv, qv, inv_delta, vsh, jk, uk, g, tmp, xs);
+        solve<MIXED, R>(w, dinv, qv, inv_delta, vsh, *c, y, D, ko, g, tmp, xs);
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
           if (st == 0) k1[i] = xs[i];

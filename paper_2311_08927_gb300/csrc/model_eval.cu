@@ -18,11 +18,13 @@ struct EvalIn {
   DigConst c;
   double T, D, SH_guess;
   double y[NS];
+  double x[NS];  // direction of the Jacobian-vector product (split only)
 };
 struct EvalOut {
   double f[NS];
   double J[NS * NS];  // full J, or J_d when split
   double u[NS], v[NS];
+  double Jx[NS];  // J x from the rate partials (split only)
   double SH;
   int newton_failed;
 };
@@ -44,6 +46,9 @@ __host__ __device__ void eval_one(const EvalIn& in, EvalOut& out, bool split) {
     sh_tangent(in.c, q, ab, vd);
     const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
     for (int k = 0; k < 8; ++k) out.v[hc[k]] = vd[k];
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += vd[k] * in.x[hc[k]];
+    jvp<double, double>(in.c, in.y, in.D, o, in.x, s, out.Jx);
   } else {
     jacobian<DenseIdx, double>(in.c, q, in.y, in.D, ab, o, out.J);
   }
@@ -57,7 +62,7 @@ __global__ void eval_kernel(const EvalIn* in, EvalOut* out, bool split) {
 
 chad_status eval_common(const double* params, double V_liq, double V_gas, double D,
                         const double* y_in, double T, const double* y, double SH_guess,
-                        bool split, int on_device, EvalOut& out) {
+                        const double* x, bool split, int on_device, EvalOut& out) {
   if (!params || !y) return CHAD_E_INVALID;
   if (!(T > 0.0)) return CHAD_E_INVALID;
   EvalIn in;
@@ -67,7 +72,10 @@ chad_status eval_common(const double* params, double V_liq, double V_gas, double
   in.T = T;
   in.D = D;
   in.SH_guess = SH_guess;
-  for (int i = 0; i < NS; ++i) in.y[i] = y[i];
+  for (int i = 0; i < NS; ++i) {
+    in.y[i] = y[i];
+    in.x[i] = x ? x[i] : 0.0;
+  }
   if (on_device) {
     EvalIn* din = nullptr;
     EvalOut* dout = nullptr;
@@ -100,7 +108,7 @@ extern "C" chad_status chad_eval_model(const double* params, double V_liq, doubl
   if (!f || !J || !SH) return CHAD_E_INVALID;
   EvalOut out;
   const chad_status st =
-      eval_common(params, V_liq, V_gas, D, y_in, T, y, SH_guess, false, on_device, out);
+      eval_common(params, V_liq, V_gas, D, y_in, T, y, SH_guess, nullptr, false, on_device, out);
   if (st != CHAD_OK && st != CHAD_E_PARTICLE) return st;
   std::memcpy(f, out.f, sizeof(out.f));
   std::memcpy(J, out.J, sizeof(out.J));
@@ -110,18 +118,20 @@ extern "C" chad_status chad_eval_model(const double* params, double V_liq, doubl
 
 extern "C" chad_status chad_eval_model_split(const double* params, double V_liq, double V_gas,
                                              double D, const double* y_in, double T,
-                                             const double* y, double SH_guess, double* f,
-                                             double* J_d, double* u, double* v, double* SH,
-                                             int on_device) {
+                                             const double* y, double SH_guess, const double* x,
+                                             double* f, double* J_d, double* u, double* v,
+                                             double* Jx, double* SH, int on_device) {
   if (!f || !J_d || !u || !v || !SH) return CHAD_E_INVALID;
+  if ((x == nullptr) != (Jx == nullptr)) return CHAD_E_INVALID;
   EvalOut out;
   const chad_status st =
-      eval_common(params, V_liq, V_gas, D, y_in, T, y, SH_guess, true, on_device, out);
+      eval_common(params, V_liq, V_gas, D, y_in, T, y, SH_guess, x, true, on_device, out);
   if (st != CHAD_OK && st != CHAD_E_PARTICLE) return st;
   std::memcpy(f, out.f, sizeof(out.f));
   std::memcpy(J_d, out.J, sizeof(out.J));
   std::memcpy(u, out.u, sizeof(out.u));
   std::memcpy(v, out.v, sizeof(out.v));
+  if (Jx) std::memcpy(Jx, out.Jx, sizeof(out.Jx));
   *SH = out.SH;
   return st;
 }

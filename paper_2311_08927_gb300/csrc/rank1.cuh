@@ -51,17 +51,5 @@ CHAD_HD void update(const R* q, const double* v, R inv_delta, R* z) {
   for (int i = 0; i < NS; ++i) z[i] += s * q[i];
 }
 
-// FP64 residual of the mixed form's refinement: r = b - W x =
-// b - x + g (J_d x + u (v^T x)) with the kept J_d slots and u.
-template <class RJ>
-CHAD_HD void residual(const RJ* jd, const RJ* u, const double* v, double g, const double* b,
-                      const double* x, double* r) {
-  double jx[NS];
-  sp::jx<RJ>(jd, x, jx);
-  const double s = vdot<double>(v, x);
-#pragma unroll
-  for (int i = 0; i < NS; ++i) r[i] = b[i] - x[i] + g * (jx[i] + double(u[i]) * s);
-}
-
 }  // namespace rank1
 }  // namespace chad

@@ -1027,43 +1027,8 @@ CHAD_HD void solve(const R* w, const R* dinv, R* b) {
   b[19] = z28;
 }
 
-// out = J_d x over the structural nonzeros of J_d (slots of a J_d array).
-template <class RJ>
-CHAD_HD void jx(const RJ* j, const double* x, double* out) {
-  out[0] = double(j[73]) * x[0] + double(j[75]) * x[10] + double(j[70]) * x[13] + double(j[71]) * x[15] + double(j[72]) * x[16];
-  out[1] = double(j[95]) * x[1] + double(j[97]) * x[10] + double(j[93]) * x[14] + double(j[94]) * x[17];
-  out[2] = double(j[82]) * x[2] + double(j[84]) * x[7] + double(j[85]) * x[10] + double(j[80]) * x[15] + double(j[81]) * x[18];
-  out[3] = double(j[144]) * x[1] + double(j[146]) * x[3] + double(j[147]) * x[4] + double(j[148]) * x[7] + double(j[149]) * x[10] + double(j[143]) * x[17] + double(j[150]) * x[19];
-  out[4] = double(j[152]) * x[0] + double(j[154]) * x[1] + double(j[156]) * x[3] + double(j[157]) * x[4] + double(j[158]) * x[7] + double(j[159]) * x[10] + double(j[151]) * x[16] + double(j[153]) * x[17] + double(j[160]) * x[19];
-  out[5] = double(j[115]) * x[0] + double(j[118]) * x[1] + double(j[121]) * x[3] + double(j[122]) * x[4] + double(j[119]) * x[5] + double(j[123]) * x[7] + double(j[124]) * x[10] + double(j[114]) * x[16] + double(j[117]) * x[17] + double(j[125]) * x[19] + double(j[116]) * x[20];
-  out[6] = double(j[100]) * x[0] + double(j[105]) * x[1] + double(j[102]) * x[2] + double(j[109]) * x[3] + double(j[110]) * x[4] + double(j[107]) * x[5] + double(j[106]) * x[6] + double(j[111]) * x[7] + double(j[112]) * x[10] + double(j[99]) * x[16] + double(j[104]) * x[17] + double(j[101]) * x[18] + double(j[113]) * x[19] + double(j[103]) * x[20] + double(j[98]) * x[21];
-  out[7] = double(j[167]) * x[0] + double(j[172]) * x[1] + double(j[169]) * x[2] + double(j[176]) * x[3] + double(j[177]) * x[4] + double(j[174]) * x[5] + double(j[178]) * x[7] + double(j[179]) * x[10] + double(j[166]) * x[16] + double(j[171]) * x[17] + double(j[168]) * x[18] + double(j[180]) * x[19] + double(j[170]) * x[20] + double(j[163]) * x[22] + double(j[161]) * x[26];
-  out[8] = double(j[16]) * x[6] + double(j[17]) * x[7] + double(j[12]) * x[8] + double(j[18]) * x[10] + double(j[13]) * x[21] + double(j[14]) * x[22] + double(j[15]) * x[27];
-  out[9] = double(j[53]) * x[0] + double(j[58]) * x[1] + double(j[55]) * x[2] + double(j[62]) * x[3] + double(j[63]) * x[4] + double(j[60]) * x[5] + double(j[59]) * x[6] + double(j[64]) * x[7] + double(j[51]) * x[9] + double(j[65]) * x[10] + double(j[61]) * x[12] + double(j[44]) * x[13] + double(j[45]) * x[14] + double(j[46]) * x[15] + double(j[52]) * x[16] + double(j[57]) * x[17] + double(j[54]) * x[18] + double(j[66]) * x[19] + double(j[56]) * x[20] + double(j[48]) * x[21] + double(j[49]) * x[22] + double(j[47]) * x[28];
-  out[10] = double(j[184]) * x[0] + double(j[189]) * x[1] + double(j[186]) * x[2] + double(j[193]) * x[3] + double(j[194]) * x[4] + double(j[191]) * x[5] + double(j[190]) * x[6] + double(j[195]) * x[7] + double(j[196]) * x[10] + double(j[192]) * x[12] + double(j[183]) * x[16] + double(j[188]) * x[17] + double(j[185]) * x[18] + double(j[197]) * x[19] + double(j[187]) * x[20] + double(j[181]) * x[21] + double(j[182]) * x[22];
-  out[11] = double(j[0]) * x[11] + double(j[1]) * x[12];
-  out[12] = double(j[137]) * x[12] + double(j[128]) * x[16] + double(j[133]) * x[17] + double(j[130]) * x[18] + double(j[142]) * x[19] + double(j[132]) * x[20] + double(j[126]) * x[21] + double(j[127]) * x[22];
-  out[13] = double(j[7]) * x[12] + double(j[6]) * x[13];
-  out[14] = double(j[9]) * x[12] + double(j[8]) * x[14];
-  out[15] = double(j[11]) * x[12] + double(j[10]) * x[15];
-  out[16] = double(j[68]) * x[0] + double(j[69]) * x[10] + double(j[67]) * x[16];
-  out[17] = double(j[91]) * x[1] + double(j[92]) * x[10] + double(j[90]) * x[17];
-  out[18] = double(j[77]) * x[2] + double(j[78]) * x[7] + double(j[79]) * x[10] + double(j[76]) * x[18];
-  out[19] = double(j[198]) * x[3] + double(j[199]) * x[4] + double(j[200]) * x[7] + double(j[201]) * x[10] + double(j[202]) * x[19];
-  out[20] = double(j[87]) * x[5] + double(j[88]) * x[7] + double(j[89]) * x[10] + double(j[86]) * x[20];
-  out[21] = double(j[29]) * x[6] + double(j[30]) * x[10] + double(j[28]) * x[21];
-  out[22] = double(j[32]) * x[7] + double(j[33]) * x[10] + double(j[31]) * x[22];
-  out[23] = double(j[3]) * x[12] + double(j[2]) * x[23];
-  out[24] = double(j[4]) * x[24];
-  out[25] = double(j[5]) * x[25];
-  out[26] = double(j[22]) * x[7] + double(j[19]) * x[26] + double(j[21]) * x[27] + double(j[20]) * x[28];
-  out[27] = double(j[34]) * x[8] + double(j[35]) * x[26] + double(j[39]) * x[27] + double(j[36]) * x[28];
-  out[28] = double(j[26]) * x[9] + double(j[23]) * x[26] + double(j[25]) * x[27] + double(j[24]) * x[28];
-}
-
 constexpr int kFactorFlops = 640;
 constexpr int kSolveFlops = 377;
-constexpr int kJxFlops = 348;
 
 }  // namespace sp
 }  // namespace chad

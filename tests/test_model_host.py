@@ -109,3 +109,18 @@ def test_split_jacobian_matches_oracle():
             assert np.max(np.abs(Jd[:, j] - col)) / sc < 1e-6, j
             vf = _richardson(lambda t: O.charge_solve(p, T, y + t * e)[0], 0.0, 1e-2 * hj)
             assert abs(v[j] - vf) <= 1e-6 * abs(vf) + 1e-12 * SHo / max(abs(y[j]), 1e-8), j
+
+
+def test_matrix_free_jacobian_vector_product():
+    """The mixed form's refinement residual forms J x from the rate partials
+    (no matrix).  It equals the oracle's dual-number Jacobian times x, for
+    random directions x, to round-off."""
+    rng = np.random.default_rng(41)
+    for p, T, y, D, V in _cases(20, 29):
+        yin = I.influent()
+        x = rng.standard_normal(I.NS) * (np.abs(y) + 1e-6)
+        *_, Jx = CH.eval_model_split(p, T, y, y_in=yin, D=D, V_liq=V, V_gas=V * 0.1, x=x)
+        Jo = O.jacobian(p, T, y, y_in=yin, D=D, V_liq=V, V_gas=V * 0.1)
+        ref = Jo @ x
+        sc = np.abs(Jo) @ np.abs(x) + 1e-300
+        assert np.max(np.abs(Jx - ref) / sc) < 1e-12

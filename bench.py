@@ -134,13 +134,13 @@ def work_per_launch(CH, precision, stats, steps):
     scalar): per step attempt the W-method's rate evaluations, Jacobian,
     W formation, static-order sparse LU, three solves (mixed: FP32 solves
     plus FP64 refinement residuals J x) and stage combinations; per Newton
-    iteration of Eq. 7 one charge-balance evaluation plus the update; three
-    final charge-balance evaluations per attempt."""
+    iteration of Eq. 7 one charge-balance evaluation plus the update; per
+    attempt three moves of the acid-base reciprocals to the converged root."""
     af = CH.attempt_flops(precision)
     nf = CH.newton_flops()
-    ce = CH.flop_counts()["charge_E"]
+    fin = CH.flop_counts()["sh_final"]
     attempts = stats["accepted_steps"] + stats["rejected_steps"]
-    f64 = attempts * (af["fp64"] + 3 * ce) + stats["newton_iters"] * nf
+    f64 = attempts * (af["fp64"] + 3 * fin) + stats["newton_iters"] * nf
     f32 = attempts * af["fp32"]
     return f64 / steps, f32 / steps, af
 

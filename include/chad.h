@@ -301,8 +301,18 @@ chad_status chad_probe_alu_peak(int fp64, double* tflops);
    refinement update of one mixed solve (with its rank-1 term), out[9]
    Sherman-Morrison set-up of one attempt (q = (I - g J_d)^-1 g u and its
    denominator, besides the sparse solve), out[10] Sherman-Morrison update
-   of one solve.  n >= 11. */
+   of one solve, out[11] move of the Eq. 7 reciprocals and slope to a
+   converged root.  n >= 12. */
 chad_status chad_flop_counts(int64_t* out, int n);
+
+/* The integrator's device arithmetic helpers applied to x [n] (host
+   memory) on the current GPU: narrow [n] = x converted to float by the
+   integer bit-pattern conversion (significand truncated), widen [n] = the
+   round-to-nearest float of x converted back to double by the integer
+   conversion (exact for normal floats), recip [n] = the FP64 reciprocal
+   1/x as the kernels compute it.  Allocates and frees device buffers. */
+chad_status chad_probe_numerics(const double* x, int n, float* narrow, double* widen,
+                                double* recip);
 
 /* Evaluate the library's model for one particle: f = dy/dt (Eq. 2-6) [29],
    the analytic Jacobian J = df/dy [29][29] row-major (with S_H(y) from Eq. 7

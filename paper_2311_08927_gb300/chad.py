@@ -131,6 +131,9 @@ def lib():
                                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                                 C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                                 C.c_int]
+            L.chad_probe_numerics.restype = C.c_int
+            L.chad_probe_numerics.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                              C.c_void_p]
             L.chad_probe_alu_peak.restype = C.c_int
             L.chad_probe_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
             _lib = L
@@ -141,7 +144,8 @@ def exported_symbols() -> list[str]:
     return ["chad_abi_version", "chad_n_params", "chad_param_name", "chad_last_error",
             "chad_create", "chad_destroy", "chad_load_particles", "chad_set_flow",
             "chad_step", "chad_synchronize", "chad_read_states", "chad_probe_alu_peak",
-            "chad_eval_model", "chad_eval_model_split", "chad_autotune", "chad_flop_counts",
+            "chad_eval_model", "chad_eval_model_split", "chad_probe_numerics", "chad_autotune",
+            "chad_flop_counts",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
 
@@ -196,7 +200,7 @@ def chad_mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, s
 
 
 FLOP_KEYS = ["rates_f", "rates_fj", "charge_E", "form_w", "factor", "solve", "jx", "stage",
-             "refine", "sm_setup", "sm_update"]
+             "refine", "sm_setup", "sm_update", "sh_final"]
 
 
 def flop_counts() -> dict:
@@ -288,6 +292,20 @@ def eval_model_split(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, 
     if x is None:
         return f, Jd, u, v, SH.value
     return f, Jd, u, v, SH.value, Jx
+
+
+def probe_numerics(x):
+    """(narrow, widen, recip) of the kernels' conversion and reciprocal
+    helpers applied to x on the current GPU."""
+    L = lib()
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    n = xx.size
+    nar = np.zeros(n, dtype=np.float32)
+    wid = np.zeros(n)
+    rec = np.zeros(n)
+    _check(L, None, L.chad_probe_numerics(xx.ctypes.data, n, nar.ctypes.data, wid.ctypes.data,
+                                          rec.ctypes.data))
+    return nar, wid, rec
 
 
 def probe_alu_peak(fp64: bool) -> float:

@@ -28,10 +28,51 @@ struct DenseIdx {
   static constexpr int size = NS * NS;
 };
 
-// 1/d.  On the GPU in FP64: Newton-Raphson iteration for the reciprocal,
-// x <- x + x (1 - d x) (quadratic convergence), seeded with the FP32
-// hardware reciprocal of d; two iterations bring the 24-bit seed to FP64
-// precision in four FMAs.  Values outside the FP32 normal range use the
+// Conversions between binary64 and binary32 (IEEE 754).  On the GPU a
+// hardware FP64<->FP32 conversion occupies the FP64 pipe as long as an FP64
+// FMA (measured on GB300: both ~600 G lane-ops/s, the DFMA rate), so the
+// device versions below work on the bit patterns with integer operations:
+//   widen  (float -> double): exact for normal numbers; zero and subnormal
+//          inputs give a signed zero; Inf and NaN keep their class.
+//   narrow (double -> float): the significand truncated to 23 bits (round
+//          toward zero, relative error below 2^-23); magnitudes below the
+//          normal float range give a signed zero, above it +-Inf; NaN stays
+//          NaN.
+// Host code and other types use the plain casts.
+template <class To, class From>
+CHAD_HD To cvt(From x) {
+  return To(x);
+}
+#ifdef __CUDA_ARCH__
+template <>
+__device__ __forceinline__ double cvt<double, float>(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned m = (e == 0u) ? 0u : (u & 0x7fffffu);
+  const unsigned ee = (e == 0u) ? 0u : ((e == 0xffu) ? 0x7ffu : e + 896u);
+  const unsigned hi = (u & 0x80000000u) | (ee << 20) | (m >> 3);
+  return __hiloint2double((int)hi, (int)(m << 29));
+}
+template <>
+__device__ __forceinline__ float cvt<float, double>(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sgn = hi & 0x80000000u;
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const int e = E - 896;
+  const bool nan = (E == 0x7ff) && (((hi & 0xfffffu) | lo) != 0u);
+  unsigned u = sgn | ((unsigned)e << 23) | m;
+  u = (e <= 0) ? sgn : u;
+  u = (e >= 255) ? (sgn | 0x7f800000u | (nan ? 0x400000u : 0u)) : u;
+  return __uint_as_float(u);
+}
+#endif
+
+// 1/d.  On the GPU in FP64: the FP32 hardware reciprocal of d as the seed
+// r0 (relative error e = 1 - d r0 below 2^-22 with the truncated
+// conversion), then one polynomial correction r0 (1 + e + e^2) of the
+// Newton-Raphson family for the reciprocal, whose relative error is O(e^3)
+// (below 1e-19): three FMAs.  Values outside the FP32 normal range use the
 // division.  Elsewhere (host, FP32, counting types): the plain division.
 template <class R>
 CHAD_HD R rcp(R d) {
@@ -40,15 +81,58 @@ CHAD_HD R rcp(R d) {
 #ifdef __CUDA_ARCH__
 template <>
 __device__ __forceinline__ double rcp<double>(double d) {
-  const float f = __double2float_rn(d);
+  const float f = cvt<float, double>(d);
   const float af = fabsf(f);
   if (!(af > 1e-30f && af < 1e30f)) return 1.0 / d;
-  double r = (double)__frcp_rn(f);
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
+  const double r = cvt<double, float>(__frcp_rn(f));
+  const double e = fma(-d, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
+#endif
+
+// Threshold pivot test of the static-order LU: a pivot p is accepted when
+// it is finite, nonzero and |p| >= 0.1 max_i |l_i| over its sub-column.
+// key() maps an entry to a comparable magnitude, kmax() combines keys,
+// good() takes the decision.  Host and counting types: the exact test.  On
+// the GPU (FP64 and FP32) it runs on the IEEE-754 bit patterns with integer
+// operations, because FP64 compares and min/max occupy the FP64 pipe: the
+// sign-cleared pattern (the high word for a double) orders finite
+// magnitudes like their values, and read as an integer it is a
+// piecewise-linear log2 of the magnitude in units of 2^-20 (double high
+// word) or 2^-23 (float), so the factor 0.1 becomes a shift by log2(10) in
+// those units; the effective threshold is 0.1 up to the error of that
+// linear log2, i.e. between 0.094 and 0.106.
+template <class R>
+struct PivTest {
+  using K = R;
+  static CHAD_HD K key(R x) { return fabs(x); }
+  static CHAD_HD K kmax(K a, K b) { return fmax(a, b); }
+  static CHAD_HD bool good(K p) { return p != R(0) && isfinite(p); }
+  static CHAD_HD bool good(K p, K cm) { return good(p) && p >= R(0.1) * cm; }
+};
+#ifdef __CUDA_ARCH__
+template <>
+struct PivTest<double> {
+  using K = unsigned;
+  static __device__ __forceinline__ K key(double x) {
+    return (unsigned)__double2hiint(x) & 0x7fffffffu;
+  }
+  static __device__ __forceinline__ K kmax(K a, K b) { return max(a, b); }
+  static __device__ __forceinline__ bool good(K p) { return p != 0u && p < 0x7ff00000u; }
+  static __device__ __forceinline__ bool good(K p, K cm) {
+    return good(p) && p + 3483294u >= cm;  // log2(10) * 2^20
+  }
+};
+template <>
+struct PivTest<float> {
+  using K = unsigned;
+  static __device__ __forceinline__ K key(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+  static __device__ __forceinline__ K kmax(K a, K b) { return max(a, b); }
+  static __device__ __forceinline__ bool good(K p) { return p != 0u && p < 0x7f800000u; }
+  static __device__ __forceinline__ bool good(K p, K cm) {
+    return good(p) && p + 27866353u >= cm;  // log2(10) * 2^23
+  }
+};
 #endif
 
 constexpr double kVfaCod_ac = 64.0, kVfaCod_pro = 112.0, kVfaCod_bu = 160.0, kVfaCod_va = 208.0;
@@ -74,25 +158,47 @@ CHAD_HD void part_const(const DigConst& c, double T, PartConst& q) {
   q.RT = c.R * T;
 }
 
+// PartConst in structure-of-arrays form, field f of particle p at
+// pc[f * ld + p]: computed once per load (the temperature of a particle is
+// fixed while it is loaded) instead of by every lane that takes a new
+// particle, which would leave the rest of its warp idle during nine FP64
+// exponentials.
+CHAD_HD void pc_store(const PartConst& q, double* pc, int64_t ld, int64_t p) {
+  pc[0 * ld + p] = q.arr;
+  pc[1 * ld + p] = q.K_w;
+  pc[2 * ld + p] = q.K_a_co2;
+  pc[3 * ld + p] = q.K_a_IN;
+  pc[4 * ld + p] = q.K_H_co2;
+  pc[5 * ld + p] = q.K_H_ch4;
+  pc[6 * ld + p] = q.K_H_h2;
+  pc[7 * ld + p] = q.p_h2o;
+  pc[8 * ld + p] = q.RT;
+}
+CHAD_HD void pc_load(const double* pc, int64_t ld, int64_t p, PartConst& q) {
+  q.arr = pc[0 * ld + p];
+  q.K_w = pc[1 * ld + p];
+  q.K_a_co2 = pc[2 * ld + p];
+  q.K_a_IN = pc[3 * ld + p];
+  q.K_H_co2 = pc[4 * ld + p];
+  q.K_H_ch4 = pc[5 * ld + p];
+  q.K_H_h2 = pc[6 * ld + p];
+  q.p_h2o = pc[7 * ld + p];
+  q.RT = pc[8 * ld + p];
+}
+
 // ----------------------------------------------------------- Eq. 7 (FP64)
 struct AcidBase {
   double SH;     // root
   double dEdS;   // dE/dS_H at the root
   double r_IN, r_co2, r_ac, r_pro, r_bu, r_va;  // 1/(K_a + S_H) at the root
+  double rS;     // 1/S_H
 };
 
-// E(S) and dE/dS; fills the reciprocals used by the Jacobian.  Templated
-// on the scalar type only so that its operations can be counted on the host.
+// E(S) and dE/dS of Eq. 7 from the reciprocals rS = 1/S and r = 1/(K_a + S)
+// for IN, co2, ac, pro, bu, va.
 template <class F>
-CHAD_HD F charge_E_t(const DigConst& c, const PartConst& q, const double* y, F S, F* r, F& dEdS) {
-  // r: 1/(K_a + S) for IN, co2, ac, pro, bu, va
-  const F rS = rcp<F>(S);
-  r[0] = rcp<F>(F(q.K_a_IN) + S);
-  r[1] = rcp<F>(F(q.K_a_co2) + S);
-  r[2] = rcp<F>(F(c.K_a_ac) + S);
-  r[3] = rcp<F>(F(c.K_a_pro) + S);
-  r[4] = rcp<F>(F(c.K_a_bu) + S);
-  r[5] = rcp<F>(F(c.K_a_va) + S);
+CHAD_HD F charge_terms(const DigConst& c, const PartConst& q, const double* y, F S, F rS,
+                       const F* r, F& dEdS) {
   const F nh3 = F(q.K_a_IN) * F(y[iS_IN]) * r[0];
   const F hco3 = F(q.K_a_co2) * F(y[iS_IC]) * r[1];
   const F ac = F(c.K_a_ac) * F(y[iS_ac]) * r[2] * F(1.0 / kVfaCod_ac);
@@ -105,10 +211,25 @@ CHAD_HD F charge_E_t(const DigConst& c, const PartConst& q, const double* y, F S
   return (F(y[iS_cat]) - F(y[iS_an])) + (F(y[iS_IN]) - nh3) + S - hco3 - ac - pro - bu - va - kw;
 }
 
+// E(S) and dE/dS; fills the reciprocals used by the Jacobian.  Templated
+// on the scalar type only so that its operations can be counted on the host.
+template <class F>
+CHAD_HD F charge_E_t(const DigConst& c, const PartConst& q, const double* y, F S, F* r, F& rS,
+                     F& dEdS) {
+  rS = rcp<F>(S);
+  r[0] = rcp<F>(F(q.K_a_IN) + S);
+  r[1] = rcp<F>(F(q.K_a_co2) + S);
+  r[2] = rcp<F>(F(c.K_a_ac) + S);
+  r[3] = rcp<F>(F(c.K_a_pro) + S);
+  r[4] = rcp<F>(F(c.K_a_bu) + S);
+  r[5] = rcp<F>(F(c.K_a_va) + S);
+  return charge_terms<F>(c, q, y, S, rS, r, dEdS);
+}
+
 CHAD_HD double charge_E(const DigConst& c, const PartConst& q, const double* y, double S,
                         AcidBase& ab) {
   double r[6];
-  const double E = charge_E_t<double>(c, q, y, S, r, ab.dEdS);
+  const double E = charge_E_t<double>(c, q, y, S, r, ab.rS, ab.dEdS);
   ab.r_IN = r[0];
   ab.r_co2 = r[1];
   ab.r_ac = r[2];
@@ -116,6 +237,29 @@ CHAD_HD double charge_E(const DigConst& c, const PartConst& q, const double* y, 
   ab.r_bu = r[4];
   ab.r_va = r[5];
   return E;
+}
+
+// Move the reciprocals of charge_E_t from S to S + d to first order,
+// 1/(K + S + d) = r / (1 + r d) ~ r (1 - r d) with relative error (r d)^2,
+// and recompute dE/dS from them.  Templated for operation counting.
+template <class F>
+CHAD_HD void root_shift_t(const DigConst& c, const PartConst& q, const double* y, F S, F d, F* r,
+                          F& rS, F& dEdS) {
+  rS = rS - rS * rS * d;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r[k] = r[k] - r[k] * r[k] * d;
+  charge_terms<F>(c, q, y, S + d, rS, r, dEdS);
+}
+CHAD_HD void root_shift(const DigConst& c, const PartConst& q, const double* y, AcidBase& ab,
+                        double S, double d) {
+  double r[6] = {ab.r_IN, ab.r_co2, ab.r_ac, ab.r_pro, ab.r_bu, ab.r_va};
+  root_shift_t<double>(c, q, y, S, d, r, ab.rS, ab.dEdS);
+  ab.r_IN = r[0];
+  ab.r_co2 = r[1];
+  ab.r_ac = r[2];
+  ab.r_pro = r[3];
+  ab.r_bu = r[4];
+  ab.r_va = r[5];
 }
 
 struct NewtonCounters {
@@ -142,9 +286,16 @@ __host__ __device__ inline bool newton_only(const DigConst& c, const PartConst& 
     const double Sn = S - dS;
     if (!(Sn > 0.0) || !isfinite(Sn)) return false;
     if (fabs(dS) <= 1e-8 * Sn || fabs(E) <= 1e-15) {
-      const double Ef = charge_E(c, q, y, Sn, ab);  // reciprocals and slope at the root
       ab.SH = Sn;
-      return fabs(Ef) <= max_resid || fabs(E) <= max_resid;
+      if (max_resid < INFINITY) {  // a residual bound is asked for: evaluate at the root
+        const double Ef = charge_E(c, q, y, Sn, ab);
+        return fabs(Ef) <= max_resid || fabs(E) <= max_resid;
+      }
+      // Otherwise move the reciprocals 1/S and 1/(K_a + S) to the root to
+      // first order; |r dS| <= 1e-8, so their relative error (r dS)^2 is at
+      // the FP64 rounding level, and dE/dS follows from them.
+      root_shift(c, q, y, ab, S, -dS);
+      return true;
     }
     prevE = E;
     S = Sn;

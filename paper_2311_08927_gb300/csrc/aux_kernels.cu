@@ -4,6 +4,7 @@
 
 #include <cstdint>
 
+#include "adm1_device.cuh"
 #include "kernels.h"
 
 namespace chad {
@@ -138,7 +139,25 @@ __global__ void bump_kernel(unsigned long long* interval) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *interval += 1ull;
 }
 
+__global__ void part_const_kernel(const DigConst* dc, const int* dig, const double* T, double* pc,
+                                  int64_t ld, int64_t begin, int64_t end) {
+  const int64_t p = begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= end) return;
+  PartConst q;
+  part_const(dc[dig[p]], T[p], q);
+  pc_store(q, pc, ld, p);
+}
+
 }  // namespace
+
+cudaError_t launch_part_const(const DigConst* dc, const int* dig, const double* T, double* pc,
+                              int64_t ld, int64_t begin, int64_t end, cudaStream_t s) {
+  if (end <= begin) return cudaSuccess;
+  const int block = 256;
+  part_const_kernel<<<(unsigned)((end - begin + block - 1) / block), block, 0, s>>>(dc, dig, T, pc, ld,
+                                                                                   begin, end);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bump(unsigned long long* interval, cudaStream_t s) {
   bump_kernel<<<1, 32, 0, s>>>(interval);

@@ -48,6 +48,7 @@ struct chad_ctx {
   double* d_y = nullptr;
   double* d_pos = nullptr;
   double* d_T = nullptr;
+  double* d_pc = nullptr;  // [kPartConstFields][ld] temperature-dependent constants
   double* d_D = nullptr;
   double* d_SH = nullptr;
   double* d_h = nullptr;
@@ -103,7 +104,7 @@ static cudaError_t dalloc(T** p, size_t count) {
 }
 
 static void free_all(chad_ctx* c) {
-  void* ptrs[] = {c->d_dc, c->d_fl, c->d_dig, c->d_off, c->d_y, c->d_pos, c->d_T, c->d_D,
+  void* ptrs[] = {c->d_dc, c->d_fl, c->d_dig, c->d_off, c->d_y, c->d_pos, c->d_T, c->d_pc, c->d_D,
                   c->d_SH, c->d_h, c->d_status, c->d_atol, c->d_cnt, c->d_queue, c->d_interval, c->d_chunk_dig,
                   c->d_chunk_beg, c->d_chunk_end, c->d_dig_chunk0, c->d_partial, c->d_mean};
   for (void* p : ptrs)
@@ -221,6 +222,7 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   A(dalloc(&c->d_y, (size_t)NS * c->ld));
   A(dalloc(&c->d_pos, (size_t)3 * c->ld));
   A(dalloc(&c->d_T, c->ld));
+  A(dalloc(&c->d_pc, (size_t)kPartConstFields * c->ld));
   A(dalloc(&c->d_D, c->ld));
   A(dalloc(&c->d_SH, c->ld));
   A(dalloc(&c->d_h, c->ld));
@@ -327,6 +329,7 @@ chad_status chad_load_particles(chad_ctx* c, int digester, int64_t n, const doub
       return r;
     };
     CK(c, fill(c->d_T, T, 308.15), "load T");
+    CK(c, launch_part_const(c->d_dc, c->d_dig, c->d_T, c->d_pc, c->ld, o, o + n, s), "part constants");
     CK(c, fill(c->d_SH, S_H, 1e-7), "load S_H");
     CK(c, fill(c->d_h, h, 0.0), "load h");
     if (!h) c->cold_pending = true;
@@ -415,6 +418,7 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
   a.dc = c->d_dc;
   a.y = c->d_y;
   a.T = c->d_T;
+  a.pc = c->d_pc;
   a.D = c->d_D;
   a.SH = c->d_SH;
   a.h = c->d_h;

@@ -13,11 +13,12 @@ fill gives the storage slots.  The emitted code is straight-line with static
 slot indices:
 
   slot(r, c)         storage slot of W_rc (-1 when structurally zero)
-  factor(w, dinv, t) in-place LU in the static order; returns false when a
-                     pivot fails the threshold test |u_kk| >= t max_i |l_ik u_kk|
-                     (equivalently |w_kk| >= t max_i |w_ik| before scaling)
-                     or is zero; the caller then shrinks the step, which
-                     drives W towards the identity where the order is safe
+  factor(w, dinv)    in-place LU in the static order; returns false when a
+                     pivot fails the threshold test |u_kk| >= 0.1 max_i |l_ik u_kk|
+                     (equivalently |w_kk| >= 0.1 max_i |w_ik| before scaling,
+                     PivTest in adm1_device.cuh) or is zero or not finite; the
+                     caller then shrinks the step, which drives W towards the
+                     identity where the order is safe
   solve(w, dinv, b)  forward / back substitution in the static order
 
 Run from the repository root:  python paper_2311_08927_gb300/csrc/gen_sparse.py
@@ -159,7 +160,8 @@ def generate(pat: np.ndarray) -> str:
     # ------------------------------------------------------------- factor
     w("// In-place LU; returns false if a pivot fails the threshold test.")
     w("template <class R>")
-    w("CHAD_HD bool factor(R* w, R* dinv, R tau) {")
+    w("CHAD_HD bool factor(R* w, R* dinv) {")
+    w("  using P = PivTest<R>;")
     w("  bool ok = true;")
     for k in range(NS):
         pv = order[k]
@@ -169,13 +171,14 @@ def generate(pat: np.ndarray) -> str:
         w(f"  {{  // pivot {k}: state {pv} ({I.STATE_NAMES[pv]}), {len(sub)} rows x {len(ucols)} cols")
         w(f"    const R pv = w[{d}];")
         if sub:
-            terms = [f"fabs(w[{slot[order[i], pv]}])" for i in sub]
+            terms = [f"P::key(w[{slot[order[i], pv]}])" for i in sub]
             expr = terms[0]
             for t in terms[1:]:
-                expr = f"fmax({expr}, {t})"
-            w(f"    const R cm = {expr};")
-            w("    ok = ok && (fabs(pv) >= tau * cm);")
-        w("    ok = ok && (pv != R(0)) && isfinite(pv);")
+                expr = f"P::kmax({expr}, {t})"
+            w(f"    const typename P::K cm = {expr};")
+            w("    ok = ok && P::good(P::key(pv), cm);")
+        else:
+            w("    ok = ok && P::good(P::key(pv));")
         w("    const R inv = rcp<R>(pv);")
         w(f"    dinv[{k}] = inv;")
         flops += 1

@@ -46,7 +46,7 @@ constexpr double kRB_d = 0.29289321881345247559915563789515;   // 1/(2+sqrt 2)
 constexpr double kRB_e32 = 7.4142135623730950488016887242097;  // 6+sqrt 2
 constexpr double kHmin = 1e-12;                                 // days
 constexpr double kHdefault = 1e-6;                              // days
-constexpr double kPivTau = 0.1;                                 // threshold pivoting
+constexpr double kPivTau = 0.1;  // threshold of the Sherman-Morrison denominator test
 
 struct Cnt {
   int acc, rej, newton, fallback, failed, pivot, redo;
@@ -137,16 +137,20 @@ __device__ __forceinline__ double sh_guess(double SH0, const double* v, const do
 // W x = b with the factored W_d and the Sherman-Morrison vector q.  Mixed:
 // FP32 solve, FP64 residual r = b - x + g J x with J x from the kept FP32
 // rate partials ko at the step's start y, FP32 correction solve.
+// v: dS_H/dy over the eight states of Eq. 7 in FP64 (residual) and in R
+// (rank-1 update).  The FP32<->FP64 conversions here use the hardware
+// instructions: there are ~120 per stage, and as integer sequences they
+// cost more issue slots than they free on the FP64 pipe.
 template <bool MIXED, class R>
 __device__ __forceinline__ void solve(const R* w, const R* dinv, const R* qv, R inv_delta,
-                                      const double* v, const DigConst& c, const double* y,
-                                      double D, const Rates<R>& ko, double g, const double* b,
-                                      double* x) {
+                                      const double* v, const R* vr, const DigConst& c,
+                                      const double* y, double D, const Rates<R>& ko, double g,
+                                      const double* b, double* x) {
   R t[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) t[i] = R(b[i]);
   sp::solve<R>(w, dinv, t);
-  rank1::update<R>(qv, v, inv_delta, t);
+  rank1::update<R>(qv, vr, inv_delta, t);
 #pragma unroll
   for (int i = 0; i < NS; ++i) x[i] = double(t[i]);
   if (MIXED) {
@@ -155,7 +159,7 @@ __device__ __forceinline__ void solve(const R* w, const R* dinv, const R* qv, R 
 #pragma unroll
     for (int i = 0; i < NS; ++i) t[i] = R(b[i] - x[i] + g * jx[i]);
     sp::solve<R>(w, dinv, t);
-    rank1::update<R>(qv, v, inv_delta, t);
+    rank1::update<R>(qv, vr, inv_delta, t);
 #pragma unroll
     for (int i = 0; i < NS; ++i) x[i] += double(t[i]);
   }
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       if (p >= a.n) break;
       cnt = Cnt{0, 0, 0, 0, 0, 0, 0};
       c = &a.dc[a.dig[p]];
-      part_const(*c, a.T[p], q);
+      pc_load(a.pc, a.ld, p, q);
 #pragma unroll
       for (int i = 0; i < NS; ++i) y[i] = a.y[i * a.ld + p];
       SHg = a.SH[p];
@@ -240,13 +244,16 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     const double SH0 = SHg;
     double vsh[8];
     sh_tangent(*c, q, ab0, vsh);
+    R vr[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) vr[k] = R(vsh[k]);
     const double g = hh * kRB_d;
     sp::form_w<R>(w, R(g));
-    const bool lu_ok = sp::factor<R>(w, dinv, R(kPivTau));
+    const bool lu_ok = sp::factor<R>(w, dinv);
     R inv_delta = R(0);
-    const bool sm_ok = rank1::setup<R>(w, dinv, R(g), vsh, R(kPivTau), qv, &inv_delta);
+    const bool sm_ok = rank1::setup<R>(w, dinv, R(g), vr, R(kPivTau), qv, &inv_delta);
     const bool piv_ok = lu_ok && sm_ok;
-    double norm = INFINITY;
+    float norm = INFINITY;
     if (!piv_ok) cnt.pivot++;
     double xs[NS];
     if (piv_ok || fixed) {
@@ -278,25 +285,28 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
             }
           }
         }
-        solve<MIXED, R>(w, dinv, qv, inv_delta, vsh, *c, y, D, ko, g, tmp, xs);
+        solve<MIXED, R>(w, dinv, qv, inv_delta, vsh, vr, *c, y, D, ko, g, tmp, xs);
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
           if (st == 0) k1[i] = xs[i];
           else if (st == 1) k2[i] = xs[i] + k1[i];
         }
       }
-      // scaled error norm: the estimate in FP64, the ratio to the
-      // tolerance in FP32 (the accept test needs a few digits only)
+      // scaled error norm max_i |h/6 (k1 - 2 k2 + k3)_i| / (atol_i + rtol
+      // max(|y_i|, |y1_i|)): the combination, which cancels, in FP64;
+      // everything after it in FP32 (the accept test and the controller
+      // need a few digits only)
       float nf = 0.0f;
-      const double h6 = hh * (1.0 / 6.0);
+      const float rtol = cvt<float>(a.rtol);
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
-        const double e = h6 * (k1[i] - 2.0 * k2[i] + xs[i]);
-        const double sc = a.atol[i] + a.rtol * fmax(fabs(y[i]), fabs(y1[i]));
-        const float r = fabsf((float)e) * __frcp_rn((float)sc);
+        const float e = cvt<float>(fma(-2.0, k2[i], k1[i]) + xs[i]);
+        const float ym = fmaxf(fabsf(cvt<float>(y[i])), fabsf(cvt<float>(y1[i])));
+        const float sc = fmaxf(fmaf(rtol, ym, cvt<float>(a.atol[i])), 1e-30f);
+        const float r = fabsf(e) * __frcp_rn(sc);
         if (!(r <= nf)) nf = r;  // NaN propagates
       }
-      norm = nf;
+      norm = nf * (cvt<float>(hh) * (1.0f / 6.0f));
     }
     if (fixed) {
 #pragma unroll
@@ -305,22 +315,22 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       ++nacc;
       if (!isfinite(norm)) status |= ST_NAN;
       if (nacc >= a.fixed_n || (status & ST_NAN)) done = true;
-    } else if (norm <= 1.0) {
+    } else if (norm <= 1.0f) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) y[i] = y1[i];
       t = last ? Tend : t + hh;
       cnt.acc++;
       ++nacc;
-      double fac = (norm == 0.0) ? 5.0 : fmin(5.0, fmax(0.2, 0.8 * (double)powf((float)norm, -1.0f / 3.0f)));
-      if (rejected_prev) fac = fmin(fac, 1.0);
-      h = hh * fac;
+      float fac = (norm == 0.0f) ? 5.0f : fminf(5.0f, fmaxf(0.2f, 0.8f * powf(norm, -1.0f / 3.0f)));
+      if (rejected_prev) fac = fminf(fac, 1.0f);
+      h = hh * cvt<double>(fac);
       rejected_prev = false;
       if (last) done = true;
     } else {
       cnt.rej++;
-      const double fac =
-          !piv_ok ? 0.25 : (isfinite(norm) ? fmax(0.2, 0.8 * (double)powf((float)norm, -1.0f / 3.0f)) : 0.2);
-      h = hh * fac;
+      const float fac =
+          !piv_ok ? 0.25f : (isfinite(norm) ? fmaxf(0.2f, 0.8f * powf(norm, -1.0f / 3.0f)) : 0.2f);
+      h = hh * cvt<double>(fac);
       rejected_prev = true;
       if (h < kHmin) {
         status |= ST_HMIN;
@@ -334,10 +344,15 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     // ------------------------------------------------ particle finished
     if (done) {
       if (cnt.failed) status |= ST_NEWTON;
+      // on the bit patterns (FP64 compares occupy the FP64 pipe): not
+      // finite <=> exponent all ones; y < -atol (atol > 0) <=> y negative
+      // with |y| > atol, and non-negative doubles order like their patterns
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
-        if (!isfinite(y[i])) status |= ST_NAN;
-        if (y[i] < -a.atol[i]) status |= ST_NEG;
+        const long long yb = __double_as_longlong(y[i]);
+        const long long mag = yb & 0x7fffffffffffffffll;
+        if (mag >= 0x7ff0000000000000ll) status |= ST_NAN;
+        if (yb < 0 && mag > __double_as_longlong(a.atol[i])) status |= ST_NEG;
       }
 #pragma unroll
       for (int i = 0; i < NS; ++i) a.y[i * a.ld + p] = y[i];

@@ -24,6 +24,7 @@ struct StepArgs {
   const DigConst* dc;   // [n_dig]
   double* y;            // [NS][ld]
   const double* T;      // [n] K
+  const double* pc;     // [kPartConstFields][ld] per-particle constants (part_const of T)
   const double* D;      // [n] dilution rate 1/d for this interval
   double* SH;           // [n] running S_H (guess in, root out)
   double* h;            // [n] next step size (days)
@@ -77,6 +78,9 @@ cudaError_t launch_mlp_guess(const double* y, int64_t ld, const double* T, int64
                              double* SH_out, double* h_out, cudaStream_t s);
 // interval index += 1 (last node of every interval)
 cudaError_t launch_bump(unsigned long long* interval, cudaStream_t s);
+// pc[.][p] = part_const(dc[dig[p]], T[p]) for p in [begin, end)
+cudaError_t launch_part_const(const DigConst* dc, const int* dig, const double* T, double* pc,
+                              int64_t ld, int64_t begin, int64_t end, cudaStream_t s);
 cudaError_t launch_headspace(const HeadspaceArgs& a, cudaStream_t s);
 
 constexpr int kHeadspaceChunk = 4096;  // particles per partial sum

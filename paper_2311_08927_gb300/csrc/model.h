@@ -9,6 +9,7 @@
 namespace chad {
 
 constexpr int NS = 29;
+constexpr int kPartConstFields = 9;  // PartConst fields stored per particle
 
 // state indices (Sec. 2.2; 12 solubles, 12 particulates, 2 ions, 3 gases)
 enum : int {

@@ -135,3 +135,45 @@ extern "C" chad_status chad_eval_model_split(const double* params, double V_liq,
   *SH = out.SH;
   return st;
 }
+
+namespace chad {
+namespace {
+__global__ void numerics_kernel(const double* x, int n, float* narrow, double* widen,
+                                double* recip) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = x[i];
+  narrow[i] = cvt<float, double>(d);
+  widen[i] = cvt<double, float>(__double2float_rn(d));
+  recip[i] = rcp<double>(d);
+}
+}  // namespace
+}  // namespace chad
+
+extern "C" chad_status chad_probe_numerics(const double* x, int n, float* narrow, double* widen,
+                                           double* recip) {
+  if (!x || !narrow || !widen || !recip || n < 0) return CHAD_E_INVALID;
+  if (n == 0) return CHAD_OK;
+  const size_t nb = (size_t)n;
+  double* dx = nullptr;
+  float* dn = nullptr;
+  double* dw = nullptr;
+  double* dr = nullptr;
+  cudaError_t e = cudaMalloc(&dx, nb * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dn, nb * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&dw, nb * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dr, nb * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(dx, x, nb * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    numerics_kernel<<<(unsigned)((nb + 255) / 256), 256>>>(dx, n, dn, dw, dr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(narrow, dn, nb * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(widen, dw, nb * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(recip, dr, nb * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dn);
+  cudaFree(dw);
+  cudaFree(dr);
+  return e == cudaSuccess ? CHAD_OK : CHAD_E_CUDA;
+}

@@ -60,8 +60,9 @@ using namespace chad;
 // out[8] refinement update of one mixed solve (besides J x)
 // out[9] Sherman-Morrison set-up of one attempt (besides its solve)
 // out[10] Sherman-Morrison update of one solve
+// out[11] move of the acid-base reciprocals to a converged Newton root
 extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
-  if (!out || n < 11) return CHAD_E_INVALID;
+  if (!out || n < 12) return CHAD_E_INVALID;
   DigConst c;
   std::memset(&c, 0, sizeof(c));
   c.ni_aa = 2;
@@ -96,9 +97,9 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   balances<Fc>(c, y, Fc(0.1), o, f);
   jacobian<sp::Idx, Fc>(c, q, y, Fc(0.1), ab, o, w, u);
   out[1] = g_ops;
-  Fc r[6], dE;
+  Fc r[6], rS, dE;
   g_ops = 0;
-  charge_E_t<Fc>(c, q, yd, Fc(1e-7), r, dE);
+  charge_E_t<Fc>(c, q, yd, Fc(1e-7), r, rS, dE);
   out[2] = g_ops;
   for (int s = 0; s < sp::kNNZ; ++s) w[s] = Fc(0.0);
   g_ops = 0;
@@ -106,7 +107,7 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   out[3] = g_ops;
   Fc dinv[NS];
   g_ops = 0;
-  sp::factor<Fc>(w, dinv, Fc(0.1));
+  sp::factor<Fc>(w, dinv);
   out[4] = g_ops;
   Fc b[NS];
   for (int i = 0; i < NS; ++i) b[i] = Fc(1.0);
@@ -120,7 +121,7 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
     jvp<Fc, Fc>(c, y, Fc(0.1), o, x, Fc(1.0), jx);
     out[6] = g_ops;
   }
-  const double v[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+  const Fc v[8] = {1, 1, 1, 1, 1, 1, 1, 1};
   Fc inv_delta;
   for (int i = 0; i < NS; ++i) u[i] = Fc(1.0);
   g_ops = 0;
@@ -129,6 +130,9 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   g_ops = 0;
   rank1::update<Fc>(u, v, inv_delta, b);
   out[10] = g_ops;
+  g_ops = 0;
+  root_shift_t<Fc>(c, q, yd, Fc(1e-7), Fc(1e-16), r, rS, dE);
+  out[11] = g_ops;
   // y + h/2 k1 (2/elt), F1 - k1 (1), k2 += k1 (1), y + h k2 (2), F2 - e32 (k2 - F1)
   // - 2 (k1 - F0) (5), h/6 (k1 - 2 k2 + k3) (4), atol + rtol max(..) (2), |e|/sc (1)
   out[7] = (int64_t)NS * 18;

@@ -21,8 +21,8 @@ namespace chad {
 namespace rank1 {
 
 // v^T x over the eight states of Eq. 7 (v[k] belongs to state hc[k]).
-template <class R, class X>
-CHAD_HD R vdot(const double* v, const X* x) {
+template <class R, class V, class X>
+CHAD_HD R vdot(const V* v, const X* x) {
   const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
   R s = R(v[0]) * R(x[hc[0]]);
 #pragma unroll
@@ -33,7 +33,7 @@ CHAD_HD R vdot(const double* v, const X* x) {
 // u (in q) -> q = W_d^-1 (g u) with the factored W_d; *inv_delta = 1/delta.
 // Returns false when delta fails the threshold test or is not finite.
 template <class R>
-CHAD_HD bool setup(const R* w, const R* dinv, R g, const double* v, R tau, R* q, R* inv_delta) {
+CHAD_HD bool setup(const R* w, const R* dinv, R g, const R* v, R tau, R* q, R* inv_delta) {
 #pragma unroll
   for (int i = 0; i < NS; ++i) q[i] *= g;
   sp::solve<R>(w, dinv, q);
@@ -45,7 +45,7 @@ CHAD_HD bool setup(const R* w, const R* dinv, R g, const double* v, R tau, R* q,
 
 // z = W_d^-1 b (already solved) -> W^-1 b in place.
 template <class R>
-CHAD_HD void update(const R* q, const double* v, R inv_delta, R* z) {
+CHAD_HD void update(const R* q, const R* v, R inv_delta, R* z) {
   const R s = vdot<R>(v, z) * inv_delta;
 #pragma unroll
   for (int i = 0; i < NS; ++i) z[i] += s * q[i];

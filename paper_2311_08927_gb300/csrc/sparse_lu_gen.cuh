@@ -95,37 +95,37 @@ CHAD_HD void form_w(R* w, R g) {
 
 // In-place LU; returns false if a pivot fails the threshold test.
 template <class R>
-CHAD_HD bool factor(R* w, R* dinv, R tau) {
+CHAD_HD bool factor(R* w, R* dinv) {
+  using P = PivTest<R>;
   bool ok = true;
   {  // pivot 0: state 11 (S_I), 0 rows x 1 cols
     const R pv = w[0];
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
     dinv[0] = inv;
   }
   {  // pivot 1: state 23 (X_I), 0 rows x 1 cols
     const R pv = w[2];
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
     dinv[1] = inv;
   }
   {  // pivot 2: state 24 (S_cat), 0 rows x 0 cols
     const R pv = w[4];
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
     dinv[2] = inv;
   }
   {  // pivot 3: state 25 (S_an), 0 rows x 0 cols
     const R pv = w[5];
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
     dinv[3] = inv;
   }
   {  // pivot 4: state 13 (X_ch), 2 rows x 1 cols
     const R pv = w[6];
-    const R cm = fmax(fabs(w[44]), fabs(w[70]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::key(w[44]), P::key(w[70]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[4] = inv;
     { const R l = w[44] * inv; w[44] = l;
@@ -137,9 +137,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 5: state 14 (X_pr), 2 rows x 1 cols
     const R pv = w[8];
-    const R cm = fmax(fabs(w[45]), fabs(w[93]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::key(w[45]), P::key(w[93]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[5] = inv;
     { const R l = w[45] * inv; w[45] = l;
@@ -151,9 +150,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 6: state 15 (X_li), 3 rows x 1 cols
     const R pv = w[10];
-    const R cm = fmax(fmax(fabs(w[46]), fabs(w[71])), fabs(w[80]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::key(w[46]), P::key(w[71])), P::key(w[80]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[6] = inv;
     { const R l = w[46] * inv; w[46] = l;
@@ -168,9 +166,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 7: state 8 (S_ch4), 1 rows x 6 cols
     const R pv = w[12];
-    const R cm = fabs(w[34]);
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::key(w[34]);
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[7] = inv;
     { const R l = w[34] * inv; w[34] = l;
@@ -184,9 +181,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 8: state 26 (S_gas_h2), 3 rows x 3 cols
     const R pv = w[19];
-    const R cm = fmax(fmax(fabs(w[23]), fabs(w[35])), fabs(w[161]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::key(w[23]), P::key(w[35])), P::key(w[161]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[8] = inv;
     { const R l = w[23] * inv; w[23] = l;
@@ -207,9 +203,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 9: state 28 (S_gas_co2), 3 rows x 3 cols
     const R pv = w[24];
-    const R cm = fmax(fmax(fabs(w[36]), fabs(w[47])), fabs(w[162]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::key(w[36]), P::key(w[47])), P::key(w[162]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[9] = inv;
     { const R l = w[36] * inv; w[36] = l;
@@ -230,9 +225,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 10: state 21 (X_ac), 5 rows x 2 cols
     const R pv = w[28];
-    const R cm = fmax(fmax(fmax(fmax(fabs(w[37]), fabs(w[48])), fabs(w[98])), fabs(w[126])), fabs(w[181]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[37]), P::key(w[48])), P::key(w[98])), P::key(w[126])), P::key(w[181]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[10] = inv;
     { const R l = w[37] * inv; w[37] = l;
@@ -258,9 +252,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 11: state 22 (X_h2), 5 rows x 2 cols
     const R pv = w[31];
-    const R cm = fmax(fmax(fmax(fmax(fabs(w[38]), fabs(w[49])), fabs(w[127])), fabs(w[163])), fabs(w[182]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[38]), P::key(w[49])), P::key(w[127])), P::key(w[163])), P::key(w[182]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[11] = inv;
     { const R l = w[38] * inv; w[38] = l;
@@ -286,9 +279,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 12: state 27 (S_gas_ch4), 2 rows x 4 cols
     const R pv = w[39];
-    const R cm = fmax(fabs(w[50]), fabs(w[164]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::key(w[50]), P::key(w[164]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[12] = inv;
     { const R l = w[50] * inv; w[50] = l;
@@ -306,9 +298,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 13: state 9 (S_IC), 1 rows x 15 cols
     const R pv = w[51];
-    const R cm = fabs(w[165]);
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::key(w[165]);
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[13] = inv;
     { const R l = w[165] * inv; w[165] = l;
@@ -331,9 +322,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 14: state 16 (X_su), 7 rows x 2 cols
     const R pv = w[67];
-    const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[72]), fabs(w[99])), fabs(w[114])), fabs(w[128])), fabs(w[151])), fabs(w[166])), fabs(w[183]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[72]), P::key(w[99])), P::key(w[114])), P::key(w[128])), P::key(w[151])), P::key(w[166])), P::key(w[183]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[14] = inv;
     { const R l = w[72] * inv; w[72] = l;
@@ -367,9 +357,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 15: state 0 (S_su), 6 rows x 2 cols
     const R pv = w[73];
-    const R cm = fmax(fmax(fmax(fmax(fmax(fabs(w[100]), fabs(w[115])), fabs(w[129])), fabs(w[152])), fabs(w[167])), fabs(w[184]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[100]), P::key(w[115])), P::key(w[129])), P::key(w[152])), P::key(w[167])), P::key(w[184]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[15] = inv;
     { const R l = w[100] * inv; w[100] = l;
@@ -399,9 +388,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 16: state 18 (X_fa), 5 rows x 3 cols
     const R pv = w[76];
-    const R cm = fmax(fmax(fmax(fmax(fabs(w[81]), fabs(w[101])), fabs(w[130])), fabs(w[168])), fabs(w[185]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[81]), P::key(w[101])), P::key(w[130])), P::key(w[168])), P::key(w[185]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[16] = inv;
     { const R l = w[81] * inv; w[81] = l;
@@ -432,9 +420,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 17: state 2 (S_fa), 4 rows x 3 cols
     const R pv = w[82];
-    const R cm = fmax(fmax(fmax(fabs(w[102]), fabs(w[131])), fabs(w[169])), fabs(w[186]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::key(w[102]), P::key(w[131])), P::key(w[169])), P::key(w[186]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[17] = inv;
     { const R l = w[102] * inv; w[102] = l;
@@ -460,9 +447,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 18: state 20 (X_pro), 5 rows x 3 cols
     const R pv = w[86];
-    const R cm = fmax(fmax(fmax(fmax(fabs(w[103]), fabs(w[116])), fabs(w[132])), fabs(w[170])), fabs(w[187]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[103]), P::key(w[116])), P::key(w[132])), P::key(w[170])), P::key(w[187]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[18] = inv;
     { const R l = w[103] * inv; w[103] = l;
@@ -493,9 +479,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 19: state 17 (X_aa), 8 rows x 2 cols
     const R pv = w[90];
-    const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[94]), fabs(w[104])), fabs(w[117])), fabs(w[133])), fabs(w[143])), fabs(w[153])), fabs(w[171])), fabs(w[188]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[94]), P::key(w[104])), P::key(w[117])), P::key(w[133])), P::key(w[143])), P::key(w[153])), P::key(w[171])), P::key(w[188]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[19] = inv;
     { const R l = w[94] * inv; w[94] = l;
@@ -533,9 +518,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 20: state 1 (S_aa), 7 rows x 2 cols
     const R pv = w[95];
-    const R cm = fmax(fmax(fmax(fmax(fmax(fmax(fabs(w[105]), fabs(w[118])), fabs(w[134])), fabs(w[144])), fabs(w[154])), fabs(w[172])), fabs(w[189]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[105]), P::key(w[118])), P::key(w[134])), P::key(w[144])), P::key(w[154])), P::key(w[172])), P::key(w[189]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[20] = inv;
     { const R l = w[105] * inv; w[105] = l;
@@ -569,9 +553,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 21: state 6 (S_ac), 3 rows x 7 cols
     const R pv = w[106];
-    const R cm = fmax(fmax(fabs(w[135]), fabs(w[173])), fabs(w[190]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::key(w[135]), P::key(w[173])), P::key(w[190]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[21] = inv;
     { const R l = w[135] * inv; w[135] = l;
@@ -604,9 +587,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 22: state 5 (S_pro), 3 rows x 6 cols
     const R pv = w[119];
-    const R cm = fmax(fmax(fabs(w[136]), fabs(w[174])), fabs(w[191]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::key(w[136]), P::key(w[174])), P::key(w[191]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[22] = inv;
     { const R l = w[136] * inv; w[136] = l;
@@ -636,9 +618,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 23: state 12 (X_c), 4 rows x 5 cols
     const R pv = w[137];
-    const R cm = fmax(fmax(fmax(fabs(w[145]), fabs(w[155])), fabs(w[175])), fabs(w[192]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::key(w[145]), P::key(w[155])), P::key(w[175])), P::key(w[192]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[23] = inv;
     { const R l = w[145] * inv; w[145] = l;
@@ -672,9 +653,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 24: state 3 (S_va), 4 rows x 4 cols
     const R pv = w[146];
-    const R cm = fmax(fmax(fmax(fabs(w[156]), fabs(w[176])), fabs(w[193])), fabs(w[198]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::kmax(P::key(w[156]), P::key(w[176])), P::key(w[193])), P::key(w[198]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[24] = inv;
     { const R l = w[156] * inv; w[156] = l;
@@ -704,9 +684,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 25: state 4 (S_bu), 3 rows x 3 cols
     const R pv = w[157];
-    const R cm = fmax(fmax(fabs(w[177]), fabs(w[194])), fabs(w[199]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::kmax(P::key(w[177]), P::key(w[194])), P::key(w[199]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[25] = inv;
     { const R l = w[177] * inv; w[177] = l;
@@ -727,9 +706,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 26: state 7 (S_h2), 2 rows x 2 cols
     const R pv = w[178];
-    const R cm = fmax(fabs(w[195]), fabs(w[200]));
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::kmax(P::key(w[195]), P::key(w[200]));
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[26] = inv;
     { const R l = w[195] * inv; w[195] = l;
@@ -743,9 +721,8 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 27: state 10 (S_IN), 1 rows x 1 cols
     const R pv = w[196];
-    const R cm = fabs(w[201]);
-    ok = ok && (fabs(pv) >= tau * cm);
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    const typename P::K cm = P::key(w[201]);
+    ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
     dinv[27] = inv;
     { const R l = w[201] * inv; w[201] = l;
@@ -754,7 +731,7 @@ CHAD_HD bool factor(R* w, R* dinv, R tau) {
   }
   {  // pivot 28: state 19 (X_c4), 0 rows x 0 cols
     const R pv = w[202];
-    ok = ok && (pv != R(0)) && isfinite(pv);
+    ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
     dinv[28] = inv;
   }

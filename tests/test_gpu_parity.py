@@ -273,6 +273,41 @@ def test_device_jacobian_matches_oracle_ad():
         assert np.max(np.abs(J - Jo) / (np.abs(Jo).max(axis=0, keepdims=True) + 1e-300)) < 1e-12
 
 
+def test_device_conversions_and_reciprocal():
+    """The integrator's integer bit-pattern conversions and its FP64
+    reciprocal against exact references: narrowing truncates the significand
+    to 24 bits (round toward zero; below the normal float range a signed
+    zero, from 2^128 up +-Inf), widening reproduces the float exactly
+    (subnormal floats become a signed zero), the reciprocal is within 2 ulp
+    of the correctly rounded 1/x."""
+    rng = np.random.default_rng(12)
+    special = [0.0, -0.0, 1.0, -1.0, 2.0 ** -126, -(2.0 ** -126), 2.0 ** -127, 1e-40, 3.4e38,
+               2.0 ** 128, -(2.0 ** 128), 1e39, np.inf, -np.inf, np.nan, np.nextafter(1.0, 2.0),
+               np.nextafter(2.0 ** 128, 0.0), 1e-300, 1e300, 1e-31, 1e31]
+    x = np.concatenate([rng.standard_normal(50000) * 10.0 ** rng.uniform(-40, 40, 50000),
+                        np.asarray(special)])
+    nar, wid, rec = CH.probe_numerics(x)
+    with np.errstate(all="ignore"):
+        m, e = np.frexp(np.abs(x))
+        trunc = np.sign(x) * np.ldexp(np.floor(np.ldexp(m, 24)), e - 24)
+        ref = np.where(np.abs(x) < 2.0 ** -126, np.copysign(0.0, x), trunc)
+        ref = np.where(np.abs(x) >= 2.0 ** 128, np.copysign(np.inf, x), ref)
+        ref = np.where(np.isnan(x), np.nan, ref)
+    np.testing.assert_array_equal(nar.astype(np.float64), ref)
+    assert np.array_equal(np.signbit(nar), np.signbit(ref))
+    with np.errstate(all="ignore"):
+        f32 = x.astype(np.float32).astype(np.float64)
+        wref = np.where((np.abs(f32) < 2.0 ** -126) & (f32 != 0), np.copysign(0.0, f32), f32)
+    np.testing.assert_array_equal(wid, wref)
+    assert np.array_equal(np.signbit(wid), np.signbit(wref))
+    with np.errstate(all="ignore"):
+        exact = 1.0 / x
+    fin = np.isfinite(exact) & (exact != 0)
+    ulp = np.spacing(np.abs(exact[fin]))
+    assert np.max(np.abs(rec[fin] - exact[fin]) / ulp) <= 2.0
+    np.testing.assert_array_equal(rec[~fin], exact[~fin])
+
+
 def _run_stream(pop, n, tune=False, graph=True, precision=CH.PREC_FP64):
     import torch
     s = torch.cuda.Stream() if graph else None

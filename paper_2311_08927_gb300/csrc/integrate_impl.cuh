@@ -4,7 +4,10 @@
 // Persistent kernel, one particle per thread at a time: a lane pulls the next
 // particle from a device queue (warp-aggregated atomic) as soon as its own
 // particle has reached the end of the interval, so warps stay full while
-// particles take very different numbers of steps (substrate slugs).
+// particles take very different numbers of steps (substrate slugs).  The
+// warps of a block start every step attempt together (one barrier per
+// attempt): the kernel's straight-line code is much larger than the
+// instruction cache, and warps at the same place share the fetched lines.
 //
 // The step is the linearly implicit Rosenbrock 2(3) W-method of Shampine &
 // Reichelt (1997): d = 1/(2+sqrt 2), e32 = 6 + sqrt 2, W = I - h d J, three
@@ -197,10 +200,24 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
   bool rejected_prev = false;
   Cnt cnt{0, 0, 0, 0, 0, 0, 0};
 
+  bool exhausted = false;
   while (true) {
-    if (p < 0) {
+    bool fresh = false;
+    if (p < 0 && !exhausted) {
       p = queue_pop(a.queue);
-      if (p >= a.n) break;
+      if (p >= a.n) {
+        exhausted = true;
+        p = -1;
+      } else {
+        fresh = true;
+      }
+    }
+    // every thread of the block reaches this barrier once per iteration:
+    // the block's warps start each attempt together (shared instruction
+    // fetch); the loop ends when no thread of the block has a particle
+    if (!__syncthreads_or(p >= 0)) break;
+    if (p < 0) continue;
+    if (fresh) {
       cnt = Cnt{0, 0, 0, 0, 0, 0, 0};
       c = &a.dc[a.dig[p]];
       pc_load(a.pc, a.ld, p, q);

@@ -148,7 +148,63 @@ __global__ void part_const_kernel(const DigConst* dc, const int* dig, const doub
   pc_store(q, pc, ld, p);
 }
 
+// Cost bucket of a particle, 0 = most expensive: floor(log2(dt / h)) from the
+// IEEE-754 exponent fields of dt and h (no FP64 division), clamped to the
+// buckets; h <= 0 or not finite (no history) -> bucket 0.
+__device__ __forceinline__ int order_bucket(double h, double dt) {
+  const long long hb = __double_as_longlong(h);
+  if (hb <= 0 || hb >= 0x7ff0000000000000ll) return 0;
+  const int eh = (int)((hb >> 52) & 0x7ff);
+  const int ed = (int)((__double_as_longlong(dt) >> 52) & 0x7ff);
+  const int k = (kOrderBuckets - 1) - (ed - eh);
+  return k < 0 ? 0 : (k > kOrderBuckets - 1 ? kOrderBuckets - 1 : k);
+}
+
+__global__ void order_count(const double* h, int64_t n, double dt, int* counts) {
+  __shared__ int loc[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) loc[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) atomicAdd(&loc[order_bucket(h[p], dt)], 1);
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets && loc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], loc[threadIdx.x]);
+}
+
+// Each block reserves a contiguous range of every bucket for its particles
+// (counts[kOrderBuckets + b] is the running cursor of bucket b).
+__global__ void order_scatter(const double* h, int64_t n, double dt, int* counts, int* order) {
+  __shared__ int loc[kOrderBuckets], base[kOrderBuckets], rank[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) {
+    loc[threadIdx.x] = 0;
+    rank[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = p < n ? order_bucket(h[p], dt) : 0;
+  if (p < n) atomicAdd(&loc[b], 1);
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets) {
+    const int k = threadIdx.x;
+    int start = 0;
+    for (int j = 0; j < k; ++j) start += counts[j];
+    base[k] = loc[k] ? start + atomicAdd(&counts[kOrderBuckets + k], loc[k]) : 0;
+  }
+  __syncthreads();
+  if (p < n) order[base[b] + atomicAdd(&rank[b], 1)] = (int)p;
+}
+
 }  // namespace
+
+cudaError_t launch_order(const double* h, int64_t n, double dt_days, int* counts, int* order,
+                         cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * 2 * kOrderBuckets, s);
+  if (e != cudaSuccess || n <= 0) return e;
+  const int block = 256;
+  const unsigned grid = (unsigned)((n + block - 1) / block);
+  order_count<<<grid, block, 0, s>>>(h, n, dt_days, counts);
+  order_scatter<<<grid, block, 0, s>>>(h, n, dt_days, counts, order);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_part_const(const DigConst* dc, const int* dig, const double* T, double* pc,
                               int64_t ld, int64_t begin, int64_t end, cudaStream_t s) {

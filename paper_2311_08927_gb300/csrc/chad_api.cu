@@ -56,6 +56,8 @@ struct chad_ctx {
   double* d_atol = nullptr;
   DevCounters* d_cnt = nullptr;
   unsigned long long* d_queue = nullptr;
+  int* d_order = nullptr;      // [N] queue position -> particle, heaviest first
+  int* d_order_cnt = nullptr;  // [2 * kOrderBuckets] bucket counts and cursors
   unsigned long long* d_interval = nullptr;  // global interval index (noise counter)
   int variant[3] = {kDefaultVariant, kDefaultVariant, kDefaultVariant};
   double flow_dt = -1.0;        // interval length the device flow constants hold
@@ -105,7 +107,7 @@ static cudaError_t dalloc(T** p, size_t count) {
 
 static void free_all(chad_ctx* c) {
   void* ptrs[] = {c->d_dc, c->d_fl, c->d_dig, c->d_off, c->d_y, c->d_pos, c->d_T, c->d_pc, c->d_D,
-                  c->d_SH, c->d_h, c->d_status, c->d_atol, c->d_cnt, c->d_queue, c->d_interval, c->d_chunk_dig,
+                  c->d_SH, c->d_h, c->d_status, c->d_atol, c->d_cnt, c->d_queue, c->d_order, c->d_order_cnt, c->d_interval, c->d_chunk_dig,
                   c->d_chunk_beg, c->d_chunk_end, c->d_dig_chunk0, c->d_partial, c->d_mean};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -230,6 +232,8 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   A(dalloc(&c->d_atol, NS));
   A(dalloc(&c->d_cnt, 1));
   A(dalloc(&c->d_queue, 1));
+  A(dalloc(&c->d_order, c->N));
+  A(dalloc(&c->d_order_cnt, 2 * kOrderBuckets));
   A(dalloc(&c->d_interval, 1));
   if (c->learned) {
     A(dalloc(&c->d_mlp, (size_t)CHAD_MLP_NPARAM + 2 * CHAD_MLP_IN + 4));
@@ -431,6 +435,7 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
   a.fixed_n = c->fixed_n;
   a.counters = c->d_cnt;
   a.queue = c->d_queue;
+  a.order = nullptr;
   a.SH_learned = learned_now ? c->d_SH_learned : nullptr;
   a.h_learned = learned_now ? c->d_h_learned : nullptr;
   cudaError_t e;
@@ -451,6 +456,11 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
     v.D = c->d_D;
     v.interval = c->d_interval;
     if ((e = launch_advect(v, s)) != cudaSuccess) return e;
+  }
+  if (c->fixed_n == 0 && c->N > 0) {
+    if ((e = launch_order(c->d_h, c->N, dt_days, c->d_order_cnt, c->d_order, s)) != cudaSuccess)
+      return e;
+    a.order = c->d_order;
   }
   if ((e = launch_integrate(a, c->precision, variant, s)) != cudaSuccess) return e;
   if (c->headspace == CHAD_HEADSPACE_SHARED) {

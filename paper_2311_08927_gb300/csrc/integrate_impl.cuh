@@ -137,9 +137,11 @@ __device__ __forceinline__ double sh_guess(double SH0, const double* v, const do
   return (g > 0.5 * SH0 && g < 2.0 * SH0) ? g : SH0;
 }
 
-// W x = b with the factored W_d and the Sherman-Morrison vector q.  Mixed:
-// FP32 solve, FP64 residual r = b - x + g J x with J x from the kept FP32
-// rate partials ko at the step's start y, FP32 correction solve.
+// W x = b with the factored W_d and the Sherman-Morrison vector q (the FP64
+// form calls it; the mixed form runs the same steps inside its merged stage
+// loop).  Mixed: FP32 solve, FP64 residual r = b - x + g J x with J x from
+// the kept FP32 rate partials ko at the step's start y, FP32 correction
+// solve.
 // v: dS_H/dy over the eight states of Eq. 7 in FP64 (residual) and in R
 // (rank-1 update).  The FP32<->FP64 conversions here use the hardware
 // instructions: there are ~120 per stage, and as integer sequences they
@@ -165,6 +167,40 @@ __device__ __forceinline__ void solve(const R* w, const R* dinv, const R* qv, R 
     rank1::update<R>(qv, vr, inv_delta, t);
 #pragma unroll
     for (int i = 0; i < NS; ++i) x[i] += double(t[i]);
+  }
+}
+
+// Right-hand side of stage st of the W-method (Shampine & Reichelt):
+//   st = 0: F0
+//   st = 1: F1 - k1 with F1 = f(y + h/2 k1) (F1 kept)
+//   st = 2: F2 - e32 (k2 - F1) - 2 (k1 - F0) with F2 = f(y + h k2)
+// y1 holds the evaluation point (after st = 2: the new solution y + h k2)
+// and SHg its Eq. 7 root.
+template <class RS>
+__device__ __forceinline__ void stage_rhs(int st, const DigConst& c, const PartConst& q,
+                                          const double* y, double D, double hh, double SH0,
+                                          const double* vsh, double& SHg, int max_newton,
+                                          Cnt& cnt, const double* F0, double* F1,
+                                          const double* k1, const double* k2, double* y1,
+                                          double* out) {
+  if (st == 0) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) out[i] = F0[i];
+    return;
+  }
+  const bool s1 = (st == 1);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) y1[i] = y[i] + (s1 ? 0.5 * hh * k1[i] : hh * k2[i]);
+  SHg = sh_guess(SH0, vsh, y, y1);
+  eval_f<RS>(c, q, y1, D, SHg, max_newton, cnt, out);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    if (s1) {
+      F1[i] = out[i];
+      out[i] = out[i] - k1[i];
+    } else {
+      out[i] = out[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
+    }
   }
 }
 
@@ -209,6 +245,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
         exhausted = true;
         p = -1;
       } else {
+        if (a.order) p = a.order[p];
         fresh = true;
       }
     }
@@ -268,12 +305,67 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     sp::form_w<R>(w, R(g));
     const bool lu_ok = sp::factor<R>(w, dinv);
     R inv_delta = R(0);
-    const bool sm_ok = rank1::setup<R>(w, dinv, R(g), vr, R(kPivTau), qv, &inv_delta);
-    const bool piv_ok = lu_ok && sm_ok;
+    // FP64: q and the Sherman-Morrison denominator here; mixed: in its loop
+    const bool sm_ok = MIXED || rank1::setup<R>(w, dinv, R(g), vr, R(kPivTau), qv, &inv_delta);
+    bool piv_ok = lu_ok && sm_ok;
     float norm = INFINITY;
-    if (!piv_ok) cnt.pivot++;
+    if (!MIXED && !piv_ok) cnt.pivot++;
     double xs[NS];
-    if (piv_ok || fixed) {
+    if constexpr (MIXED) {
+      // Mixed: one loop over q (st = -1) and the stages, and within a stage
+      // two passes, the second with the FP64 residual r = b - x + g J x (J x
+      // from the kept FP32 rate partials), so that the kernel holds one copy
+      // of the FP32 solve instead of three (the straight-line code is much
+      // larger than the instruction cache).  The FP32<->FP64 conversions use
+      // the hardware instructions: ~120 per stage, which as integer
+      // sequences cost more issue slots than they free on the FP64 pipe.
+      if (lu_ok || fixed) {
+        R t[NS];
+#pragma unroll 1
+        for (int st = -1; st < 3; ++st) {
+          if (st == -1) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) t[i] = R(g) * qv[i];
+          } else {
+            stage_rhs<RS>(st, *c, q, y, D, hh, SH0, vsh, SHg, a.max_newton, cnt, F0, F1, k1, k2,
+                          y1, tmp);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) t[i] = R(tmp[i]);
+          }
+          const int npass = st >= 0 ? 2 : 1;
+#pragma unroll 1
+          for (int pass = 0; pass < npass; ++pass) {
+            sp::solve<R>(w, dinv, t);
+            if (st < 0) break;
+            rank1::update<R>(qv, vr, inv_delta, t);
+            if (pass == 0) {
+#pragma unroll
+              for (int i = 0; i < NS; ++i) xs[i] = double(t[i]);
+              double jx[NS];
+              jvp<R, double>(*c, y, D, ko, xs, rank1::vdot<double>(vsh, xs), jx);
+#pragma unroll
+              for (int i = 0; i < NS; ++i) t[i] = R(tmp[i] - xs[i] + g * jx[i]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < NS; ++i) xs[i] += double(t[i]);
+            }
+          }
+          if (st < 0) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) qv[i] = t[i];
+            piv_ok = lu_ok && rank1::denominator<R>(qv, vr, R(kPivTau), &inv_delta);
+            if (!piv_ok && !fixed) break;
+            continue;
+          }
+#pragma unroll
+          for (int i = 0; i < NS; ++i) {
+            if (st == 0) k1[i] = xs[i];
+            else if (st == 1) k2[i] = xs[i] + k1[i];
+          }
+        }
+      }
+      if (!piv_ok) cnt.pivot++;
+    } else if (piv_ok || fixed) {
       // The three stages share one factorisation.  They run as a loop that
       // is not unrolled, so the kernel holds a single copy of the solve and
       // of the rate evaluation (the straight-line code is large):
@@ -309,6 +401,8 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
           else if (st == 1) k2[i] = xs[i] + k1[i];
         }
       }
+    }
+    if (piv_ok || fixed) {
       // scaled error norm max_i |h/6 (k1 - 2 k2 + k3)_i| / (atol_i + rtol
       // max(|y_i|, |y1_i|)): the combination, which cancels, in FP64;
       // everything after it in FP32 (the accept test and the controller

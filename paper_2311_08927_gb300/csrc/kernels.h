@@ -37,6 +37,7 @@ struct StepArgs {
   int fixed_n;          // 0: adaptive
   DevCounters* counters;
   unsigned long long* queue;  // particle queue head (reset before each launch)
+  const int* order;           // [n] queue position -> particle (null: identity)
   const double* SH_learned;   // learned guesses for particles without history (or null)
   const double* h_learned;
 };
@@ -78,6 +79,15 @@ cudaError_t launch_mlp_guess(const double* y, int64_t ld, const double* T, int64
                              double* SH_out, double* h_out, cudaStream_t s);
 // interval index += 1 (last node of every interval)
 cudaError_t launch_bump(unsigned long long* interval, cudaStream_t s);
+// Queue order of the integrator: particles by decreasing expected cost, the
+// steps of the coming interval estimated as dt / h from each particle's last
+// step size (no history counts as the most expensive), bucketed by powers of
+// two.  Long particles then start first and the interval does not end on a
+// tail of them.  Order within a bucket is arbitrary; results do not depend
+// on it.  counts: [2 * kOrderBuckets] scratch, zeroed here; order: [n].
+constexpr int kOrderBuckets = 16;
+cudaError_t launch_order(const double* h, int64_t n, double dt_days, int* counts, int* order,
+                         cudaStream_t s);
 // pc[.][p] = part_const(dc[dig[p]], T[p]) for p in [begin, end)
 cudaError_t launch_part_const(const DigConst* dc, const int* dig, const double* T, double* pc,
                               int64_t ld, int64_t begin, int64_t end, cudaStream_t s);

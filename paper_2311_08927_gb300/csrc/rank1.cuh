@@ -30,6 +30,16 @@ CHAD_HD R vdot(const V* v, const X* x) {
   return s;
 }
 
+// delta = 1 - v^T q for an already solved q; *inv_delta = 1/delta.  Returns
+// false when delta fails the threshold test or is not finite.
+template <class R>
+CHAD_HD bool denominator(const R* q, const R* v, R tau, R* inv_delta) {
+  const R s = vdot<R>(v, q);
+  const R delta = R(1) - s;
+  *inv_delta = rcp<R>(delta);
+  return isfinite(delta) && fabs(delta) >= tau * fmax(R(1), fabs(s)) && delta != R(0);
+}
+
 // u (in q) -> q = W_d^-1 (g u) with the factored W_d; *inv_delta = 1/delta.
 // Returns false when delta fails the threshold test or is not finite.
 template <class R>

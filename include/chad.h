@@ -163,7 +163,11 @@ const char* chad_last_error(const chad_ctx* ctx);
      digester's T_op = 308.15 K), S_H [n] kmol/m^3 and h [n] days (NULL:
      cold start, S_H guess 1e-7 and h 1e-6 d).
    Resets the particles' status bits.  Host pointers are copied synchronously;
-   device pointers are copied on the context's stream. */
+   device pointers are copied on the context's stream.  Host arrays are
+   checked on the GPU after the copy (y finite and >= 0, T in (200, 400) K;
+   CHAD_E_INVALID otherwise); device arrays are not checked.  A load that
+   fails after its argument checks leaves the digester not loaded (chad_step
+   returns CHAD_E_STATE until it is loaded again). */
 chad_status chad_load_particles(chad_ctx* ctx, int digester, int64_t n, const double* pos,
                                 const double* y, const double* T, const double* S_H,
                                 const double* h, int mem);

@@ -2,6 +2,7 @@
 // the shared-headspace reduction of the gas states (Table 1 gas volume).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "adm1_device.cuh"
@@ -193,7 +194,52 @@ __global__ void order_scatter(const double* h, int64_t n, double dt, int* counts
   if (p < n) order[base[b] + atomicAdd(&rank[b], 1)] = (int)p;
 }
 
+__global__ void check_load_kernel(const double* y, int64_t ld, const double* T, int64_t o,
+                                  int64_t n, int* flag) {
+  int bad = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < (int64_t)NS * n; k += stride) {
+    const int64_t i = k / n, p = k - i * n;
+    const double v = y[i * ld + o + p];
+    if (!(v >= 0.0) || !isfinite(v)) bad |= 1;
+  }
+  if (T)
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+      const double t = T[o + p];
+      if (!(t > 200.0 && t < 400.0)) bad |= 2;
+    }
+  if (bad) atomicOr(flag, bad);
+}
+
+__global__ void count_status_kernel(const int* status, int64_t o, int64_t n,
+                                    unsigned long long* count) {
+  unsigned c = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+    c += status[o + p] != 0;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
 }  // namespace
+
+cudaError_t launch_check_load(const double* y, int64_t ld, const double* T, int64_t o, int64_t n,
+                              int* flag, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  check_load_kernel<<<(unsigned)(sms > 0 ? 4 * sms : 256), 256, 0, s>>>(y, ld, T, o, n, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_status(const int* status, int64_t o, int64_t n,
+                                unsigned long long* count, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 1024);
+  count_status_kernel<<<(unsigned)blocks, 256, 0, s>>>(status, o, n, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_order(const double* h, int64_t n, double dt_days, int* counts, int* order,
                          cudaStream_t s) {

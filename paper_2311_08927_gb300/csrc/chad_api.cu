@@ -58,6 +58,7 @@ struct chad_ctx {
   unsigned long long* d_queue = nullptr;
   int* d_order = nullptr;      // [N] queue position -> particle, heaviest first
   int* d_order_cnt = nullptr;  // [2 * kOrderBuckets] bucket counts and cursors
+  unsigned long long* d_misc = nullptr;  // [2]: load check flag, failed-particle count
   unsigned long long* d_interval = nullptr;  // global interval index (noise counter)
   int variant[3] = {kDefaultVariant, kDefaultVariant, kDefaultVariant};
   double flow_dt = -1.0;        // interval length the device flow constants hold
@@ -107,7 +108,7 @@ static cudaError_t dalloc(T** p, size_t count) {
 
 static void free_all(chad_ctx* c) {
   void* ptrs[] = {c->d_dc, c->d_fl, c->d_dig, c->d_off, c->d_y, c->d_pos, c->d_T, c->d_pc, c->d_D,
-                  c->d_SH, c->d_h, c->d_status, c->d_atol, c->d_cnt, c->d_queue, c->d_order, c->d_order_cnt, c->d_interval, c->d_chunk_dig,
+                  c->d_SH, c->d_h, c->d_status, c->d_atol, c->d_cnt, c->d_queue, c->d_order, c->d_order_cnt, c->d_misc, c->d_interval, c->d_chunk_dig,
                   c->d_chunk_beg, c->d_chunk_end, c->d_dig_chunk0, c->d_partial, c->d_mean};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -234,6 +235,7 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   A(dalloc(&c->d_queue, 1));
   A(dalloc(&c->d_order, c->N));
   A(dalloc(&c->d_order_cnt, 2 * kOrderBuckets));
+  A(dalloc(&c->d_misc, 2));
   A(dalloc(&c->d_interval, 1));
   if (c->learned) {
     A(dalloc(&c->d_mlp, (size_t)CHAD_MLP_NPARAM + 2 * CHAD_MLP_IN + 4));
@@ -305,14 +307,8 @@ chad_status chad_load_particles(chad_ctx* c, int digester, int64_t n, const doub
   if (!y && n > 0) return fail(c, CHAD_E_INVALID, "y is required");
   if (mem != CHAD_MEM_HOST && mem != CHAD_MEM_DEVICE) return fail(c, CHAD_E_INVALID, "mem must be HOST or DEVICE");
   const int64_t o = c->offset[digester];
-  if (mem == CHAD_MEM_HOST && n > 0) {
-    for (int64_t i = 0; i < (int64_t)NS * n; ++i)
-      if (!std::isfinite(y[i]) || y[i] < 0.0) return fail(c, CHAD_E_INVALID, "y must be finite and >= 0");
-    if (T)
-      for (int64_t i = 0; i < n; ++i)
-        if (!(T[i] > 200.0 && T[i] < 400.0)) return fail(c, CHAD_E_INVALID, "T must be in (200, 400) K");
-  }
   cudaStream_t s = c->stream;
+  c->loaded[digester] = 0;
   const cudaMemcpyKind k = kind_in(mem);
   if (n > 0) {
     for (int i = 0; i < NS; ++i)
@@ -333,6 +329,17 @@ chad_status chad_load_particles(chad_ctx* c, int digester, int64_t n, const doub
       return r;
     };
     CK(c, fill(c->d_T, T, 308.15), "load T");
+    if (mem == CHAD_MEM_HOST) {
+      // y >= 0 and finite, T in (200, 400) K: checked on the GPU after the copy
+      int* flag = reinterpret_cast<int*>(c->d_misc);
+      CK(c, cudaMemsetAsync(flag, 0, sizeof(int), s), "load check");
+      CK(c, launch_check_load(c->d_y, c->ld, T ? c->d_T : nullptr, o, n, flag, s), "load check");
+      int bad = 0;
+      CK(c, cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, s), "load check");
+      CK(c, cudaStreamSynchronize(s), "load check");
+      if (bad & 1) return fail(c, CHAD_E_INVALID, "y must be finite and >= 0");
+      if (bad & 2) return fail(c, CHAD_E_INVALID, "T must be in (200, 400) K");
+    }
     CK(c, launch_part_const(c->d_dc, c->d_dig, c->d_T, c->d_pc, c->ld, o, o + n, s), "part constants");
     CK(c, fill(c->d_SH, S_H, 1e-7), "load S_H");
     CK(c, fill(c->d_h, h, 0.0), "load h");
@@ -658,19 +665,17 @@ chad_status chad_read_states(chad_ctx* c, int digester, double* y, double* pos, 
     if (S_H) CK(c, cudaMemcpyAsync(S_H, c->d_SH + o, sizeof(double) * n, k, s), "read S_H");
     if (h) CK(c, cudaMemcpyAsync(h, c->d_h + o, sizeof(double) * n, k, s), "read h");
   }
-  std::vector<int32_t> st(n > 0 ? n : 1);
-  if (n > 0) CK(c, cudaMemcpyAsync(st.data(), c->d_status + o, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s), "read status");
+  if (status && n > 0)
+    CK(c, cudaMemcpyAsync(status, c->d_status + o, sizeof(int32_t) * n, k, s), "read status");
+  unsigned long long* d_failed = c->d_misc + 1;
+  CK(c, cudaMemsetAsync(d_failed, 0, sizeof(unsigned long long), s), "count failed");
+  CK(c, launch_count_status(c->d_status, o, n, d_failed, s), "count failed");
+  unsigned long long nfailed = 0;
+  CK(c, cudaMemcpyAsync(&nfailed, d_failed, sizeof(nfailed), cudaMemcpyDeviceToHost, s), "count failed");
   DevCounters dc;
   CK(c, cudaMemcpyAsync(&dc, c->d_cnt, sizeof(dc), cudaMemcpyDeviceToHost, s), "read counters");
   CK(c, cudaStreamSynchronize(s), "read sync");
-  int64_t failed = 0;
-  for (int64_t i = 0; i < n; ++i) failed += (st[i] != 0);
-  if (status && n > 0) {
-    if (mem == CHAD_MEM_DEVICE)
-      CK(c, cudaMemcpy(status, c->d_status + o, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice), "read status");
-    else
-      std::memcpy(status, st.data(), sizeof(int32_t) * n);
-  }
+  const int64_t failed = (int64_t)nfailed;
   if (stats) {
     stats->accepted_steps = (int64_t)dc.accepted;
     stats->rejected_steps = (int64_t)dc.rejected;

@@ -86,6 +86,14 @@ cudaError_t launch_bump(unsigned long long* interval, cudaStream_t s);
 // tail of them.  Order within a bucket is arbitrary; results do not depend
 // on it.  counts: [2 * kOrderBuckets] scratch, zeroed here; order: [n].
 constexpr int kOrderBuckets = 16;
+// Input check of a load on the device: flag |= 1 if a state y[i][o + p]
+// (p < n) is negative or not finite, |= 2 if T[o + p] is outside (200, 400) K
+// (T may be null).  The caller zeroes *flag.
+cudaError_t launch_check_load(const double* y, int64_t ld, const double* T, int64_t o, int64_t n,
+                              int* flag, cudaStream_t s);
+// *count += number of nonzero status[o + p], p < n.  The caller zeroes *count.
+cudaError_t launch_count_status(const int* status, int64_t o, int64_t n,
+                                unsigned long long* count, cudaStream_t s);
 cudaError_t launch_order(const double* h, int64_t n, double dt_days, int* counts, int* order,
                          cudaStream_t s);
 // pc[.][p] = part_const(dc[dig[p]], T[p]) for p in [begin, end)

@@ -306,7 +306,8 @@ chad_status chad_probe_alu_peak(int fp64, double* tflops);
    Sherman-Morrison set-up of one attempt (q = (I - g J_d)^-1 g u and its
    denominator, besides the sparse solve), out[10] Sherman-Morrison update
    of one solve, out[11] move of the Eq. 7 reciprocals and slope to a
-   converged root.  n >= 12. */
+   converged root, out[12] scaling of the rate partials by -g (the FP64
+   form's formation of I - g J_d, with one add per diagonal).  n >= 13. */
 chad_status chad_flop_counts(int64_t* out, int n);
 
 /* The integrator's device arithmetic helpers applied to x [n] (host

@@ -200,7 +200,7 @@ def chad_mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, s
 
 
 FLOP_KEYS = ["rates_f", "rates_fj", "charge_E", "form_w", "factor", "solve", "jx", "stage",
-             "refine", "sm_setup", "sm_update", "sh_final"]
+             "refine", "sm_setup", "sm_update", "sh_final", "scale_j"]
 
 
 def flop_counts() -> dict:
@@ -220,8 +220,9 @@ def attempt_flops(precision: int) -> dict:
     second FP32 solve per stage."""
     f = flop_counts()
     if precision == PREC_FP64:
-        f64 = (f["rates_fj"] + 2 * f["rates_f"] + f["form_w"] + f["factor"] + 4 * f["solve"] +
-               f["sm_setup"] + 3 * f["sm_update"] + f["stage"])
+        # W_d: the rate partials scaled by -g before the scatter, plus the diagonal ones
+        f64 = (f["rates_fj"] + 2 * f["rates_f"] + f["scale_j"] + NS + f["factor"] +
+               4 * f["solve"] + f["sm_setup"] + 3 * f["sm_update"] + f["stage"])
         return {"fp64": f64, "fp32": 0}
     f32_rates = precision == PREC_MIXED_F32RATES
     f64 = 3 * (f["jx"] + f["refine"]) + f["stage"] + (0 if f32_rates else 3 * f["rates_f"])

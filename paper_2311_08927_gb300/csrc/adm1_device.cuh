@@ -563,6 +563,29 @@ CHAD_HD void stoich(const DigConst& c, const R* r, const R* dil, R* f) {
   f[iG_co2] = dil[iG_co2] + vr * r[21];
 }
 
+// Multiply every rate partial that enters the Jacobian (and u = df/dS_H) by
+// sc.  The FP64 form scales by -g before the Jacobian scatter, which then
+// yields -g J_d and -g u directly: W_d = I - g J_d needs only its diagonal
+// ones, instead of a multiply per stored slot.
+template <class R>
+CHAD_HD void scale_partials(Rates<R>& o, R sc) {
+  o.d1 *= sc; o.d2 *= sc; o.d3 *= sc; o.d4 *= sc;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { o.d5[k] *= sc; o.d6[k] *= sc; o.d11[k] *= sc; o.d12[k] *= sc; }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { o.d7[k] *= sc; o.d10[k] *= sc; }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) { o.d8[k] *= sc; o.d9[k] *= sc; }
+  o.s5 *= sc; o.s6 *= sc; o.s7 *= sc; o.s8 *= sc; o.s9 *= sc; o.s10 *= sc; o.s11 *= sc; o.s12 *= sc;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) o.ddec[k] *= sc;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) { o.dT8[k] *= sc; o.dT9[k] *= sc; o.dT10[k] *= sc; }
+  o.sT10 *= sc;
+  o.qv *= sc;
+  o.dqv *= sc;
+}
+
 // f(y): mass balances of Eq. 2 with the ADM1 stoichiometry
 template <class R>
 CHAD_HD void balances(const DigConst& c, const R* y, R D, const Rates<R>& o, R* f) {

@@ -211,6 +211,11 @@ __global__ void check_load_kernel(const double* y, int64_t ld, const double* T, 
   if (bad) atomicOr(flag, bad);
 }
 
+__global__ void fill_kernel(double* dst, int64_t n, double value) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) dst[p] = value;
+}
+
 __global__ void count_status_kernel(const int* status, int64_t o, int64_t n,
                                     unsigned long long* count) {
   unsigned c = 0;
@@ -230,6 +235,13 @@ cudaError_t launch_check_load(const double* y, int64_t ld, const double* T, int6
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   check_load_kernel<<<(unsigned)(sms > 0 ? 4 * sms : 256), 256, 0, s>>>(y, ld, T, o, n, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* dst, int64_t n, double value, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  fill_kernel<<<(unsigned)blocks, 256, 0, s>>>(dst, n, value);
   return cudaGetLastError();
 }
 

@@ -320,13 +320,9 @@ chad_status chad_load_particles(chad_ctx* c, int digester, int64_t n, const doub
       for (int i = 0; i < 3; ++i)
         CK(c, cudaMemsetAsync(c->d_pos + (size_t)i * c->ld + o, 0, sizeof(double) * n, s), "zero pos");
     }
-    std::vector<double> tmp;
     auto fill = [&](double* dst, const double* src, double dflt) -> cudaError_t {
       if (src) return cudaMemcpyAsync(dst + o, src, sizeof(double) * n, k, s);
-      tmp.assign(n, dflt);
-      cudaError_t r = cudaMemcpyAsync(dst + o, tmp.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
-      if (r == cudaSuccess) r = cudaStreamSynchronize(s);
-      return r;
+      return launch_fill(dst + o, n, dflt, s);
     };
     CK(c, fill(c->d_T, T, 308.15), "load T");
     if (mem == CHAD_MEM_HOST) {

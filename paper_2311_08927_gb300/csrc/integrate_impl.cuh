@@ -94,11 +94,13 @@ __device__ __forceinline__ void eval_f(const DigConst& c, const PartConst& q, co
 }
 
 // f(y) in precision RS, J_d (sparse slots) and u = df/dS_H in precision R,
-// one Newton solve
-template <class R, class RS>
+// one Newton solve.  SCALE (FP64 form only, where R is RS): J_d and u come
+// out multiplied by jscale (the rate partials are scaled after f is formed).
+template <class R, class RS, bool SCALE>
 __device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, const double* y,
                                         double D, double& SHg, int max_newton, Cnt& cnt,
-                                        double* f, R* w, R* u, Rates<R>& o, AcidBase& ab) {
+                                        double* f, R* w, R* u, Rates<R>& o, AcidBase& ab,
+                                        R jscale) {
   newton(c, q, y, SHg, max_newton, cnt, ab);
   {
     R yr[NS];
@@ -111,7 +113,12 @@ __device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, c
 #pragma unroll
       for (int i = 0; i < NS; ++i) f[i] = double(fr[i]);
     }
-    jacobian<sp::Idx, R>(c, q, yr, R(D), ab, o, w, u);
+    if constexpr (SCALE) {
+      scale_partials<R>(o, jscale);
+      jacobian<sp::Idx, R>(c, q, yr, R(D) * jscale, ab, o, w, u);
+    } else {
+      jacobian<sp::Idx, R>(c, q, yr, R(D), ab, o, w, u);
+    }
   }
   if (!std::is_same<R, RS>::value) {
     RS ys[NS];
@@ -293,20 +300,22 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       hh = Tend - t;
       last = true;
     }
+    const double g = hh * kRB_d;
     AcidBase ab0;
-    eval_fj<R, RS>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0);
+    // FP64: J_d and u come out scaled by -g, so W_d = I + (-g J_d) and
+    // q = W_d^-1 (g u) = -W_d^-1 (-g u)
+    eval_fj<R, RS, !MIXED>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0, R(-g));
     const double SH0 = SHg;
     double vsh[8];
     sh_tangent(*c, q, ab0, vsh);
     R vr[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) vr[k] = R(vsh[k]);
-    const double g = hh * kRB_d;
-    sp::form_w<R>(w, R(g));
+    sp::form_w<R>(w, MIXED ? R(g) : R(-1));
     const bool lu_ok = sp::factor<R>(w, dinv);
     R inv_delta = R(0);
     // FP64: q and the Sherman-Morrison denominator here; mixed: in its loop
-    const bool sm_ok = MIXED || rank1::setup<R>(w, dinv, R(g), vr, R(kPivTau), qv, &inv_delta);
+    const bool sm_ok = MIXED || rank1::setup<R>(w, dinv, R(-1), vr, R(kPivTau), qv, &inv_delta);
     bool piv_ok = lu_ok && sm_ok;
     float norm = INFINITY;
     if (!MIXED && !piv_ok) cnt.pivot++;

@@ -91,6 +91,8 @@ constexpr int kOrderBuckets = 16;
 // (T may be null).  The caller zeroes *flag.
 cudaError_t launch_check_load(const double* y, int64_t ld, const double* T, int64_t o, int64_t n,
                               int* flag, cudaStream_t s);
+// dst[p] = value for p < n.
+cudaError_t launch_fill(double* dst, int64_t n, double value, cudaStream_t s);
 // *count += number of nonzero status[o + p], p < n.  The caller zeroes *count.
 cudaError_t launch_count_status(const int* status, int64_t o, int64_t n,
                                 unsigned long long* count, cudaStream_t s);

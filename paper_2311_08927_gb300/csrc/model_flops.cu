@@ -61,8 +61,9 @@ using namespace chad;
 // out[9] Sherman-Morrison set-up of one attempt (besides its solve)
 // out[10] Sherman-Morrison update of one solve
 // out[11] move of the acid-base reciprocals to a converged Newton root
+// out[12] scaling of the rate partials by -g (FP64 form's W formation)
 extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
-  if (!out || n < 12) return CHAD_E_INVALID;
+  if (!out || n < 13) return CHAD_E_INVALID;
   DigConst c;
   std::memset(&c, 0, sizeof(c));
   c.ni_aa = 2;
@@ -133,6 +134,9 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   g_ops = 0;
   root_shift_t<Fc>(c, q, yd, Fc(1e-7), Fc(1e-16), r, rS, dE);
   out[11] = g_ops;
+  g_ops = 0;
+  scale_partials<Fc>(o, Fc(-1e-4));
+  out[12] = g_ops;
   // y + h/2 k1 (2/elt), F1 - k1 (1), k2 += k1 (1), y + h k2 (2), F2 - e32 (k2 - F1)
   // - 2 (k1 - F0) (5), h/6 (k1 - 2 k2 + k3) (4), atol + rtol max(..) (2), |e|/sc (1)
   out[7] = (int64_t)NS * 18;

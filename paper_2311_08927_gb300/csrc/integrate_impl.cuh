@@ -195,19 +195,27 @@ __device__ __forceinline__ void stage_rhs(int st, const DigConst& c, const PartC
     for (int i = 0; i < NS; ++i) out[i] = F0[i];
     return;
   }
-  const bool s1 = (st == 1);
+  // separate loops per stage: a per-element select would evaluate both sides
+  if (st == 1) {
+    const double h2 = 0.5 * hh;
 #pragma unroll
-  for (int i = 0; i < NS; ++i) y1[i] = y[i] + (s1 ? 0.5 * hh * k1[i] : hh * k2[i]);
+    for (int i = 0; i < NS; ++i) y1[i] = fma(h2, k1[i], y[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) y1[i] = fma(hh, k2[i], y[i]);
+  }
   SHg = sh_guess(SH0, vsh, y, y1);
   eval_f<RS>(c, q, y1, D, SHg, max_newton, cnt, out);
+  if (st == 1) {
 #pragma unroll
-  for (int i = 0; i < NS; ++i) {
-    if (s1) {
+    for (int i = 0; i < NS; ++i) {
       F1[i] = out[i];
       out[i] = out[i] - k1[i];
-    } else {
-      out[i] = out[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
     }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+      out[i] = out[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
   }
 }
 
@@ -366,10 +374,12 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
             if (!piv_ok && !fixed) break;
             continue;
           }
+          if (st == 0) {
 #pragma unroll
-          for (int i = 0; i < NS; ++i) {
-            if (st == 0) k1[i] = xs[i];
-            else if (st == 1) k2[i] = xs[i] + k1[i];
+            for (int i = 0; i < NS; ++i) k1[i] = xs[i];
+          } else if (st == 1) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) k2[i] = xs[i] + k1[i];
           }
         }
       }
@@ -388,26 +398,36 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
 #pragma unroll
           for (int i = 0; i < NS; ++i) tmp[i] = F0[i];
         } else {
-          const bool s1 = (st == 1);
+          // separate loops per stage: a per-element select would evaluate both sides
+          if (st == 1) {
+            const double h2 = 0.5 * hh;
 #pragma unroll
-          for (int i = 0; i < NS; ++i) y1[i] = y[i] + (s1 ? 0.5 * hh * k1[i] : hh * k2[i]);
+            for (int i = 0; i < NS; ++i) y1[i] = fma(h2, k1[i], y[i]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) y1[i] = fma(hh, k2[i], y[i]);
+          }
           SHg = sh_guess(SH0, vsh, y, y1);
           eval_f<RS>(*c, q, y1, D, SHg, a.max_newton, cnt, tmp);
+          if (st == 1) {
 #pragma unroll
-          for (int i = 0; i < NS; ++i) {
-            if (s1) {
+            for (int i = 0; i < NS; ++i) {
               F1[i] = tmp[i];
               tmp[i] = tmp[i] - k1[i];
-            } else {
-              tmp[i] = tmp[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
             }
+          } else {
+#pragma unroll
+            for (int i = 0; i < NS; ++i)
+              tmp[i] = tmp[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
           }
         }
         solve<MIXED, R>(w, dinv, qv, inv_delta, vsh, vr, *c, y, D, ko, g, tmp, xs);
+        if (st == 0) {
 #pragma unroll
-        for (int i = 0; i < NS; ++i) {
-          if (st == 0) k1[i] = xs[i];
-          else if (st == 1) k2[i] = xs[i] + k1[i];
+          for (int i = 0; i < NS; ++i) k1[i] = xs[i];
+        } else if (st == 1) {
+#pragma unroll
+          for (int i = 0; i < NS; ++i) k2[i] = xs[i] + k1[i];
         }
       }
     }

@@ -128,6 +128,19 @@ def test_flow_positions_bitwise_and_shared_headspace_parity():
     assert np.any(pop.pos[2] >= pop.digesters[0].flow["slab_zmin"])
 
 
+def test_paper_literal_stepping_matches_oracle():
+    """Paper-literal stepping (Sec. 4.3): 0.5-s coupling intervals, each 10
+    fixed substeps of 0.05 s, in the lab cylinder with swirl flow, inlet slab
+    and shared headspace.  Positions bitwise, states to 1e-9 of the oracle."""
+    pop = I.config_population(2, n=1500)
+    g = gpu_run(pop, 0.5, 40, fixed_substeps=10)
+    o = oracle_run(pop, 0.5, 40, fixed_n=10)
+    assert np.all(g["status"] == 0)
+    assert np.array_equal(g["pos"], o["pos"])
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+    assert g["stats"]["accepted_steps"] == 1500 * 40 * 10
+
+
 def test_many_digesters_parity():
     pop = I.config_population(5, n=2500)
     assert len(pop.digesters) == 64

@@ -75,7 +75,15 @@ def lib():
             L.oracle_integrate.restype = C.c_int
             L.oracle_integrate.argtypes = [_dp, C.c_double, C.c_double, C.c_double, C.c_double,
                                            _dp, _dp, C.POINTER(C.c_double), C.POINTER(C.c_double),
-                                           C.c_double, C.c_double, _dp, C.c_long, C.c_int, _lp]
+                                           C.c_double, C.c_double, _dp, C.c_long, C.c_int, _lp,
+                                           C.c_int]
+            L.oracle_rhs_h2alg.restype = C.c_int
+            L.oracle_rhs_h2alg.argtypes = [_dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                           _dp, _dp, C.c_double, _dp, C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double)]
+            L.oracle_jacobian_h2alg.restype = C.c_int
+            L.oracle_jacobian_h2alg.argtypes = [_dp, C.c_double, C.c_double, C.c_double,
+                                                C.c_double, _dp, _dp, C.c_double, _dp]
             L.oracle_rk4.restype = C.c_int
             L.oracle_rk4.argtypes = [_dp, C.c_double, C.c_double, C.c_double, C.c_double,
                                      _dp, _dp, C.c_double, C.c_long]
@@ -86,7 +94,7 @@ def lib():
             L.oracle_run.argtypes = [C.c_int, _lp, _dp, _dp, _dp, _dp, _dp, _up, C.c_int,
                                      C.c_long, _dp, _dp, _dp, _dp, _dp, _ip,
                                      C.c_double, C.c_int, C.c_long, C.c_double, _dp,
-                                     C.c_long, C.c_int, C.c_int, _lp]
+                                     C.c_long, C.c_int, C.c_int, _lp, C.c_int]
             _lib = L
     return _lib
 
@@ -166,8 +174,10 @@ def jacobian(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, SH_guess
 
 
 def integrate(params, T, y, dt_days, rtol=1e-6, atol=None, y_in=None, D=0.0,
-              V_liq=3400.0, V_gas=300.0, SH=1e-7, h=0.0, max_steps=100000, fixed_n=0):
-    """One particle over dt_days.  Returns (y, S_H, h, status, stats[4])."""
+              V_liq=3400.0, V_gas=300.0, SH=1e-7, h=0.0, max_steps=100000, fixed_n=0,
+              h2_algebraic=False):
+    """One particle over dt_days.  Returns (y, S_H, h, status, stats[4]).
+    h2_algebraic: S_h2 from its mass balance (Eq. 8) instead of as a state."""
     y = _f64(y).copy()
     atol = np.full(NS, 1e-12) if atol is None else _f64(atol)
     y_in = np.zeros(NS) if y_in is None else y_in
@@ -175,8 +185,31 @@ def integrate(params, T, y, dt_days, rtol=1e-6, atol=None, y_in=None, D=0.0,
     stats = np.zeros(4, dtype=np.int64)
     st = lib().oracle_integrate(_f64(params), float(T), float(V_liq), float(V_gas), float(D),
                                 _f64(y_in), y, C.byref(SHc), C.byref(hc), float(dt_days),
-                                float(rtol), atol, int(max_steps), int(fixed_n), stats)
+                                float(rtol), atol, int(max_steps), int(fixed_n), stats,
+                                int(bool(h2_algebraic)))
     return y, SHc.value, hc.value, st, stats
+
+
+def rhs_h2alg(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, SH_guess=1e-7):
+    """f(y) with S_h2 algebraic (Eq. 8): returns (f, S_H, S_h2); f[S_h2] = 0."""
+    f = np.zeros(NS)
+    y_in = np.zeros(NS) if y_in is None else y_in
+    SH, SH2 = C.c_double(0.0), C.c_double(0.0)
+    st = lib().oracle_rhs_h2alg(_f64(params), float(T), float(V_liq), float(V_gas), float(D),
+                                _f64(y_in), _f64(y), float(SH_guess), f, C.byref(SH),
+                                C.byref(SH2))
+    if st:
+        raise RuntimeError("charge balance failed")
+    return f, SH.value, SH2.value
+
+
+def jacobian_h2alg(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, SH_guess=1e-7):
+    """J = df/dy with S_h2 algebraic (Eq. 8), through both roots."""
+    J = np.zeros(NS * NS)
+    y_in = np.zeros(NS) if y_in is None else y_in
+    lib().oracle_jacobian_h2alg(_f64(params), float(T), float(V_liq), float(V_gas), float(D),
+                                _f64(y_in), _f64(y), float(SH_guess), J)
+    return J.reshape(NS, NS)
 
 
 def rk4(params, T, y, dt_days, n_steps, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0):
@@ -200,8 +233,9 @@ def gauss(seed, pid, interval, sub, axis) -> float:
 
 
 def run(pop, dt_coupling_s, n_intervals, interval0=0, rtol=1e-6, atol=None, SH=None, h=None,
-        max_steps=100000, fixed_n=0, n_threads=0, status=None):
+        max_steps=100000, fixed_n=0, n_threads=0, status=None, h2_algebraic=False):
     """Integrate a Population (see paper_2311_08927_gb300.inputs) in place.
+    h2_algebraic: S_h2 from its mass balance (Eq. 8) instead of as a state.
 
     Returns a dict with y, pos, S_H, h, status, stats (copies)."""
     from paper_2311_08927_gb300 import inputs as I  # seeded generators only
@@ -225,5 +259,5 @@ def run(pop, dt_coupling_s, n_intervals, interval0=0, rtol=1e-6, atol=None, SH=N
     lib().oracle_run(nd, np.ascontiguousarray(pop.offsets, dtype=np.int64), params, V_liq, V_gas,
                      D_u, flow, seeds, int(pop.shared_headspace), N, pos, y, T, SH, h, status,
                      float(dt_coupling_s), int(n_intervals), int(interval0), float(rtol), atol,
-                     int(max_steps), int(fixed_n), int(n_threads), stats)
+                     int(max_steps), int(fixed_n), int(n_threads), stats, int(bool(h2_algebraic)))
     return dict(y=y, pos=pos, S_H=SH, h=h, status=status, stats=stats)

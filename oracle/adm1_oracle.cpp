@@ -429,24 +429,96 @@ struct Particle {
   double SH;  // running S_H (Newton guess and last root)
   NewtonStats ns;
   bool newton_failed = false;
+  bool h2_alg = false;  // S_h2 algebraic (Eq. 8) instead of differential
+  double SH2 = 0.0;     // running S_h2 root (Newton guess and last root)
   Particle(const Model* m_, const double* y_in_, double D_, double SH_)
       : m(m_), y_in(y_in_), D(D_), SH(SH_) {}
 };
 
-// f(y): solves Eq. 7 for S_H (warm start from the particle's running S_H)
+// Eq. 8: E(S_h2) = the S_h2 mass balance (inflow - outflow + production -
+// uptake - transfer to the gas) at y with S_h2 replaced by S, and dE/dS.
+// E is strictly decreasing in S: uptake and transfer grow with S, while the
+// hydrogen-inhibited producers and the outflow shrink.
+double h2_residual(Particle& P, const double* y, double SH, double S, double* dE) {
+  Dual yd[NS], f[NS];
+  for (int i = 0; i < NS; ++i) yd[i] = Dual(y[i]);
+  yd[S_h2] = Dual(S, 1.0);
+  rhs_given_SH<Dual>(*P.m, P.y_in, P.D, yd, Dual(SH), f);
+  if (dE) *dE = f[S_h2].d;
+  return f[S_h2].v;
+}
+
+// Root of Eq. 8: Newton from the guess (stop at |dS| <= 1e-14 S), with a
+// bisection fallback on a bracket [0, hi] grown by doubling from the guess.
+double h2_solve(Particle& P, const double* y, double SH, double guess) {
+  double S = (guess > 0.0 && std::isfinite(guess)) ? guess : 1e-8;
+  double prevE = INFINITY;
+  for (int it = 0; it < 50; ++it) {
+    double dE;
+    const double E = h2_residual(P, y, SH, S, &dE);
+    P.ns.iters++;
+    if (!std::isfinite(E) || std::fabs(E) > std::fabs(prevE) || !(dE < 0.0)) break;
+    const double dS = E / dE;
+    const double Sn = S - dS;
+    if (!(Sn > 0.0) || !std::isfinite(Sn)) break;
+    if (std::fabs(dS) <= 1e-14 * Sn || E == 0.0) return Sn;
+    prevE = E;
+    S = Sn;
+  }
+  P.ns.bisections++;
+  double lo = 0.0, hi = std::max(guess > 0.0 ? guess : 0.0, 1e-12);
+  for (int k = 0; k < 200 && h2_residual(P, y, SH, hi, nullptr) > 0.0; ++k) hi *= 2.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (h2_residual(P, y, SH, mid, nullptr) > 0.0) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// f(y): solves Eq. 7 for S_H (warm start from the particle's running S_H);
+// with S_h2 algebraic also Eq. 8 for S_h2, whose rate is then zero.
 void rhs(Particle& P, const double* y, double* f) {
   double SH = charge_solve(*P.m, y, P.SH, &P.ns);
   if (!(SH > 0.0)) { P.newton_failed = true; SH = P.SH; }
   P.SH = SH;
-  rhs_given_SH<double>(*P.m, P.y_in, P.D, y, SH, f);
+  if (!P.h2_alg) {
+    rhs_given_SH<double>(*P.m, P.y_in, P.D, y, SH, f);
+    return;
+  }
+  double yy[NS];
+  for (int i = 0; i < NS; ++i) yy[i] = y[i];
+  P.SH2 = h2_solve(P, y, SH, P.SH2);
+  yy[S_h2] = P.SH2;
+  rhs_given_SH<double>(*P.m, P.y_in, P.D, yy, SH, f);
+  f[S_h2] = 0.0;
 }
 
 // J = df/dy with S_H(y) differentiated through Eq. 7 (implicit function theorem)
+// and, with S_h2 algebraic, S_h2(y) through Eq. 8: the S_h2 row and column
+// are zero (the rate is zero and the stored S_h2 is only a guess).
 void jacobian(Particle& P, const double* y, double* J /* NS x NS row-major */) {
   double SH = charge_solve(*P.m, y, P.SH, &P.ns);
   if (!(SH > 0.0)) { P.newton_failed = true; SH = P.SH; }
   P.SH = SH;
   const double dEdS = charge_slope(*P.m, y, SH);
+  if (P.h2_alg) {
+    P.SH2 = h2_solve(P, y, SH, P.SH2);
+    double dE2;
+    h2_residual(P, y, SH, P.SH2, &dE2);
+    for (int k = 0; k < NS; ++k) {
+      Dual yd[NS], f[NS];
+      for (int i = 0; i < NS; ++i) yd[i] = Dual(y[i], (i == k && k != S_h2) ? 1.0 : 0.0);
+      yd[S_h2] = Dual(P.SH2);
+      const double dEdy = charge_residual<Dual>(*P.m, yd, Dual(SH)).d;
+      const Dual SHd(SH, -dEdy / dEdS);
+      rhs_given_SH<Dual>(*P.m, P.y_in, P.D, yd, SHd, f);  // dE2/dy_k at fixed S_h2
+      yd[S_h2] = Dual(P.SH2, -f[S_h2].d / dE2);
+      rhs_given_SH<Dual>(*P.m, P.y_in, P.D, yd, SHd, f);
+      for (int i = 0; i < NS; ++i) J[i * NS + k] = (i == S_h2) ? 0.0 : f[i].d;
+    }
+    return;
+  }
   for (int k = 0; k < NS; ++k) {
     Dual yd[NS];
     for (int i = 0; i < NS; ++i) yd[i] = Dual(y[i], i == k ? 1.0 : 0.0);
@@ -545,6 +617,7 @@ int integrate_interval(Particle& P, double* y, double* h_io, double T_end, doubl
       jacobian(P, y, J);
       if (!rb_step(P, y, F0, J, h, y1, err)) { st.lu_fail++; status |= ST_NAN; break; }
       for (int i = 0; i < NS; ++i) y[i] = y1[i];
+      if (P.h2_alg) y[S_h2] = P.SH2;  // root at y1 (the last evaluation of the step)
       st.accepted++;
     }
   } else {
@@ -576,6 +649,7 @@ int integrate_interval(Particle& P, double* y, double* h_io, double T_end, doubl
       }
       if (norm <= 1.0) {
         for (int i = 0; i < NS; ++i) y[i] = y1[i];
+        if (P.h2_alg) y[S_h2] = P.SH2;  // root at y1 (the last evaluation of the step)
         t = last ? T_end : t + hh;
         have_fj = false;
         st.accepted++;
@@ -779,14 +853,43 @@ int oracle_jacobian(const double* params, double T, double V_liq, double V_gas, 
   return P.newton_failed ? ST_NEWTON : 0;
 }
 
+// f(y) with S_h2 algebraic (Eq. 8): S_H and S_h2 roots, f with a zero S_h2 rate
+int oracle_rhs_h2alg(const double* params, double T, double V_liq, double V_gas, double D,
+                     const double* y_in, const double* y, double SH_guess, double* f_out,
+                     double* SH_out, double* SH2_out) {
+  Model m;
+  make_model(params, T, V_liq, V_gas, m);
+  Particle P{&m, y_in, D, SH_guess};
+  P.h2_alg = true;
+  P.SH2 = y[S_h2];
+  rhs(P, y, f_out);
+  *SH_out = P.SH;
+  *SH2_out = P.SH2;
+  return P.newton_failed ? ST_NEWTON : 0;
+}
+
+// J = df/dy with S_h2 algebraic (Eq. 8), NS x NS row-major
+int oracle_jacobian_h2alg(const double* params, double T, double V_liq, double V_gas, double D,
+                          const double* y_in, const double* y, double SH_guess, double* J_out) {
+  Model m;
+  make_model(params, T, V_liq, V_gas, m);
+  Particle P{&m, y_in, D, SH_guess};
+  P.h2_alg = true;
+  P.SH2 = y[S_h2];
+  jacobian(P, y, J_out);
+  return P.newton_failed ? ST_NEWTON : 0;
+}
+
 // One particle over dt_days.  stats: accepted, rejected, newton iterations, bisections.
 int oracle_integrate(const double* params, double T, double V_liq, double V_gas, double D,
                      const double* y_in, double* y, double* SH, double* h, double dt_days,
                      double rtol, const double* atol, long max_steps, int fixed_n,
-                     long* stats4) {
+                     long* stats4, int h2_alg) {
   Model m;
   make_model(params, T, V_liq, V_gas, m);
   Particle P{&m, y_in, D, *SH};
+  P.h2_alg = h2_alg != 0;
+  P.SH2 = y[S_h2];
   StepStats st;
   int status = integrate_interval(P, y, h, dt_days, rtol, atol, max_steps, fixed_n, st);
   *SH = P.SH;
@@ -836,7 +939,7 @@ int oracle_run(int n_dig, const long* dig_offset, const double* params, const do
                double* y, const double* T, double* SH, double* h, int* status,
                double dt_coupling_s, int n_intervals, long interval0, double rtol,
                const double* atol, long max_steps, int fixed_n, int n_threads,
-               long* stats4) {
+               long* stats4, int h2_alg) {
   if (n_threads <= 0) n_threads = (int)std::max(1u, std::thread::hardware_concurrency());
   const int FL = 7 + NS;
   const double dt_days = dt_coupling_s / 86400.0;
@@ -879,6 +982,8 @@ int oracle_run(int n_dig, const long* dig_offset, const double* params, const do
         double yy[NS];
         for (int i = 0; i < NS; ++i) yy[i] = y[(long)i * N + p];
         Particle P{&m, yin, D, SH[p]};
+        P.h2_alg = h2_alg != 0;
+        P.SH2 = yy[S_h2];
         StepStats st;
         double hp = h[p];
         int s = integrate_interval(P, yy, &hp, dt_days, rtol, atol, max_steps, fixed_n, st);

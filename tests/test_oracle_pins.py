@@ -430,6 +430,83 @@ def test_rk4_brute_force_agreement():
         assert rel.max() < 1e-9, (slug, rel.max())
 
 
+# ----------------------------------------------------------------- S_h2 algebraic (Eq. 8)
+def test_h2_algebraic_root_zeroes_the_h2_balance():
+    """The algebraic mode's S_h2 is the root of Eq. 8: the differential
+    right-hand side at that S_h2 (same S_H) has a zero S_h2 rate, the balance
+    changes sign across it (it decreases in S_h2), and every other rate is
+    that right-hand side's."""
+    p, T, yin, D = I.default_params(), 310.0, I.influent(), 0.3
+    for seed in range(5):
+        y = perturbed_ss(40 + seed)
+        f, SH, SH2 = O.rhs_h2alg(p, T, y, y_in=yin, D=D)
+        yy = y.copy()
+        yy[S["S_h2"]] = SH2
+        fo = O.rhs_at(p, T, yy, SH, y_in=yin, D=D)
+        rho, _ = O.rates_at(p, T, yy, SH)
+        assert abs(fo[S["S_h2"]]) <= 1e-13 * (abs(rho[11]) + abs(rho[19]))
+        assert f[S["S_h2"]] == 0.0
+        other = np.arange(I.NS) != S["S_h2"]
+        assert np.array_equal(f[other], fo[other])
+        for fac, sign in ((0.9, 1.0), (1.1, -1.0)):
+            yy[S["S_h2"]] = fac * SH2
+            assert sign * O.rhs_at(p, T, yy, SH, y_in=yin, D=D)[S["S_h2"]] > 0.0
+
+
+def test_h2_algebraic_jacobian_matches_central_differences():
+    """Dual-number Jacobian of the algebraic mode (through the Eq. 7 and Eq. 8
+    roots) against Richardson central differences of its right-hand side,
+    which re-solves both roots; the S_h2 row and column are zero."""
+    p, T, yin, D = I.default_params(), 310.0, I.influent(), 0.3
+    y = perturbed_ss(12)
+    J = O.jacobian_h2alg(p, T, y, y_in=yin, D=D)
+    Jfd = np.zeros_like(J)
+    for k in range(I.NS):
+        h = 1e-3 * max(abs(y[k]), 1e-9)
+
+        def d(hh):
+            yp, ym = y.copy(), y.copy()
+            yp[k] += hh
+            ym[k] -= hh
+            return (O.rhs_h2alg(p, T, yp, y_in=yin, D=D)[0] -
+                    O.rhs_h2alg(p, T, ym, y_in=yin, D=D)[0]) / (2 * hh)
+        Jfd[:, k] = (4 * d(h / 2) - d(h)) / 3
+    assert np.all(J[S["S_h2"], :] == 0.0) and np.all(J[:, S["S_h2"]] == 0.0)
+    scale = np.abs(J).max(axis=0, keepdims=True) + 1e-300
+    cols = np.arange(I.NS) != S["S_h2"]
+    assert np.max(np.abs(J - Jfd)[:, cols] / scale[:, cols]) < 1e-7
+
+
+def test_h2_algebraic_fixed_steps_converge_and_store_the_root():
+    """Brute force in the algebraic mode: 2000 fixed W-method steps over one
+    60-s interval agree with the adaptive integration at rtol 1e-11, and the
+    S_h2 stored at the end is the Eq. 8 root of the final state."""
+    p = I.default_params()
+    y0 = perturbed_ss(50)
+    dt = 60.0 / 86400.0
+    ya, _, _, st, _ = O.integrate(p, 308.15, y0, dt, rtol=1e-11, atol=I.atol_vector(1e-14),
+                                  max_steps=10 ** 6, h2_algebraic=True)
+    assert st == 0
+    yf, *_ = O.integrate(p, 308.15, y0, dt, fixed_n=2000, h2_algebraic=True)
+    rel = np.abs(yf - ya) / np.maximum(np.abs(ya), 1e-12 * np.abs(ya).max())
+    assert rel.max() < 1e-8, rel.max()
+    _, _, SH2 = O.rhs_h2alg(p, 308.15, ya)
+    assert abs(SH2 / ya[S["S_h2"]] - 1.0) < 1e-12
+
+
+def test_h2_algebraic_and_differential_forms_agree():
+    """Eq. 8 replaces a fast S_h2 (time scale well below a second) by its
+    quasi-steady value; over one day of a closed batch the two forms agree to
+    1e-5 in every species at a tight tolerance."""
+    p = I.default_params()
+    y0 = perturbed_ss(51)
+    yo, *_ = O.integrate(p, 308.15, y0, 1.0, rtol=1e-10, atol=I.atol_vector(1e-13))
+    yd, *_ = O.integrate(p, 308.15, y0, 1.0, rtol=1e-10, atol=I.atol_vector(1e-13),
+                         h2_algebraic=True)
+    rel = np.abs(yd - yo) / np.maximum(np.abs(yo), 1e-12 * np.abs(yo).max())
+    assert rel.max() < 1e-5, rel.max()
+
+
 # ----------------------------------------------------------------- particles (Sec. 2.3, 3.1, 4.2)
 def _uniform_population(n, shared):
     p = I.default_params()

@@ -255,9 +255,9 @@ def run_ours(args, ws, rank, local):
     if args.form in ("both", "mixed") and not args.no_learned:
         model, train_info = train_mlp(CH, I, args)
 
-    def arm(precision, learned=False):
+    def arm(precision, learned=False, h2=False):
         sim = CH.Simulator(pop, precision=precision, rtol=1e-6, stream=stream.cuda_stream,
-                           learned=1 if learned else 0)
+                           learned=1 if learned else 0, h2_algebraic=h2)
         if learned:
             CH.chad_set_mlp(sim.ctx, model.params, model.feat_norm, model.out_norm)
         sim.load()
@@ -297,7 +297,12 @@ def run_ours(args, ws, rank, local):
     for name, prec in (("mixed", CH.PREC_MIXED), ("fp64", CH.PREC_FP64)):
         if args.form in (name, "both"):
             forms[name] = arm(prec, learned=(name == "mixed" and model is not None))
-    head = "mixed" if "mixed" in forms else "fp64"
+    if args.form == "fp64_h2alg":
+        # S_h2 algebraic (Eq. 8): the counted attempt flops are those of the
+        # differential FP64 form (the Eq. 8 solves and the second rank-1
+        # level are not counted)
+        forms["fp64_h2alg"] = arm(CH.PREC_FP64, h2=True)
+    head = "mixed" if "mixed" in forms else ("fp64" if "fp64" in forms else "fp64_h2alg")
     H = forms[head]
     value = ws * N * dt_days * args.steps / (H["total_ms"] * 1e-3)
 
@@ -310,7 +315,8 @@ def run_ours(args, ws, rank, local):
     e2e = None
     if rank == 0 and not args.no_e2e:
         prec = CH.PREC_MIXED if head == "mixed" else CH.PREC_FP64
-        sim = CH.Simulator(pop, precision=prec, rtol=1e-6, stream=stream.cuda_stream)
+        sim = CH.Simulator(pop, precision=prec, rtol=1e-6, stream=stream.cuda_stream,
+                           h2_algebraic=(head == "fp64_h2alg"))
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         y_h, T_h, SH_h, h_h = pin(pop.y), pin(pop.T), pin(np.full(N, 1e-7)), pin(np.zeros(N))
         st_h = pin(np.zeros(N, dtype=np.int32))
@@ -566,7 +572,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["both", "mixed", "fp64"], default="both")
+    ap.add_argument("--form", choices=["both", "mixed", "fp64", "fp64_h2alg"], default="both",
+                    help="fp64_h2alg: FP64 with S_h2 algebraic (Eq. 8), not the headline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -39,7 +39,7 @@ extern "C" {
 
 #define CHAD_NS 29        /* differential states per particle (Sec. 2.2) */
 #define CHAD_NPARAM 113   /* length of one digester's parameter vector */
-#define CHAD_ABI_VERSION 1
+#define CHAD_ABI_VERSION 2
 
 /* Learned initial guesses: a 32 -> 64 -> 64 -> 2 MLP with SiLU activations.
    FP32 parameter vector layout: W1[64][32], b1[64], W2[64][64], b2[64],
@@ -101,6 +101,10 @@ typedef struct {
   int max_newton_iters;        /* Newton iterations per Eq. 7 solve (>= 1) */
   int fixed_substeps;          /* 0: adaptive; k > 0: k equal steps per interval */
   void* cuda_stream;           /* cudaStream_t to run on; NULL = legacy default stream */
+  int h2_algebraic;            /* 1: S_h2 from its mass balance (Eq. 8) at every rate
+                                  evaluation, as the paper does, instead of as a
+                                  differential state; FP64 form only.  The S_h2 entry
+                                  of y then holds the root at the current state. */
 } chad_config;
 
 /* Prescribed flow of one digester (Sec. 2.3).  Rigid swirl u_theta = U r/R
@@ -123,7 +127,7 @@ typedef struct {
 typedef struct {
   int64_t accepted_steps;    /* accepted W-method steps, all particles */
   int64_t rejected_steps;
-  int64_t newton_iters;      /* Eq. 7 Newton iterations */
+  int64_t newton_iters;      /* Eq. 7 (and, with h2_algebraic, Eq. 8) Newton iterations */
   int64_t newton_fallbacks;  /* bisection fallbacks */
   int64_t min_steps;         /* fewest accepted steps of one particle in one interval */
   int64_t max_steps;         /* most accepted steps of one particle in one interval */

@@ -38,7 +38,7 @@ class chad_config(C.Structure):
                 ("precision", C.c_int), ("learned", C.c_int), ("headspace", C.c_int),
                 ("rtol", C.c_double), ("atol", _dp), ("max_steps_per_interval", C.c_int),
                 ("max_newton_iters", C.c_int), ("fixed_substeps", C.c_int),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("h2_algebraic", C.c_int)]
 
 
 class chad_flow(C.Structure):
@@ -400,7 +400,7 @@ class Simulator:
 
     def __init__(self, pop: I.Population, precision=PREC_FP64, rtol=1e-6, atol=None,
                  max_steps=100000, max_newton=50, fixed_substeps=0, stream=None,
-                 headspace=None, learned=0):
+                 headspace=None, learned=0, h2_algebraic=False):
         self.pop = pop
         nd = len(pop.digesters)
         self._keep = []
@@ -436,6 +436,7 @@ class Simulator:
         cfg.max_newton_iters = max_newton
         cfg.fixed_substeps = fixed_substeps
         cfg.cuda_stream = stream
+        cfg.h2_algebraic = int(bool(h2_algebraic))
         self.ctx = chad_create(cfg)
         self.offsets = pop.offsets
         for d, dg in enumerate(pop.digesters):

@@ -362,6 +362,105 @@ CHAD_HD void hill(R S, R invK, R n, int ni, R& I, R& dI) {
   dI = -n * xn1 * invK * I * I;
 }
 
+// ----------------------------------------------------------- Eq. 8 (FP64)
+// S_h2 as an algebraic variable: its mass balance (Eq. 8) as a function of
+// S_h2 alone, every other state and S_H fixed.  These are the hydrogen terms
+// of rates() and balances() written out: the fa, c4 and pro uptakes carry
+// the inhibition K_I/(K_I + S_h2), the hydrogen uptake the Monod factor
+// S_h2/(K_S + S_h2), the transfer and the outflow are linear, so
+//   E(S) = C0 + P_fa I_fa(S) + P_c4 I_c4(S) + P_pro I_pro(S) - P_h2 M(S) - kD S
+// with P >= 0: E decreases in S and the root is unique.
+template <class F>
+struct H2Bal {
+  F C0, Pfa, Pc4, Ppro, Ph2, kD, Kfa, Kc4, Kpro, Kh2;
+};
+
+template <class F>
+CHAD_HD void h2_coeffs(const DigConst& c, const PartConst& q, const double* y, F D,
+                       const AcidBase& ab, H2Bal<F>& e) {
+  const F a = F(q.arr);
+  F Ipaa, dIpaa, Iph2, dIph2;
+  hill<F>(F(ab.SH), F(c.inv_K_pH_aa), F(c.n_aa), c.ni_aa, Ipaa, dIpaa);
+  hill<F>(F(ab.SH), F(c.inv_K_pH_h2), F(c.n_h2), c.ni_h2, Iph2, dIph2);
+  const F S_IN = F(y[iS_IN]);
+  const F IIN = S_IN * rcp<F>(S_IN + F(c.K_S_IN));
+  const F msu = F(y[iS_su]) * rcp<F>(F(c.K_S_su) + F(y[iS_su]));
+  const F maa = F(y[iS_aa]) * rcp<F>(F(c.K_S_aa) + F(y[iS_aa]));
+  const F mfa = F(y[iS_fa]) * rcp<F>(F(c.K_S_fa) + F(y[iS_fa]));
+  const F mva = F(y[iS_va]) * rcp<F>(F(c.K_S_c4) + F(y[iS_va]));
+  const F mbu = F(y[iS_bu]) * rcp<F>(F(c.K_S_c4) + F(y[iS_bu]));
+  const F mpo = F(y[iS_pro]) * rcp<F>(F(c.K_S_pro) + F(y[iS_pro]));
+  const F rden = rcp<F>(F(y[iS_bu]) + F(y[iS_va]) + F(kC4Guard));
+  const F gva = F(y[iS_va]) * rden, gbu = F(y[iS_bu]) * rden;
+  const F B5 = Ipaa * IIN, B12 = Iph2 * IIN;
+  const F r4 = F(c.k_m_su) * a * F(y[iX_su]) * msu * B5;
+  const F r5 = F(c.k_m_aa) * a * F(y[iX_aa]) * maa * B5;
+  const F kLa = F(c.k_La);
+  const F KH2 = F(q.K_H_h2) * F(q.RT);
+  e.C0 = D * F(c.y_in[iS_h2]) + F(c.su_h2) * r4 + F(c.aa_h2) * r5 + kLa * KH2 * F(y[iG_h2]);
+  e.Pfa = F(c.fa_h2) * F(c.k_m_fa) * a * F(y[iX_fa]) * mfa * B5;
+  e.Pc4 = (F(c.va_h2) * mva * gva + F(c.bu_h2) * mbu * gbu) * F(c.k_m_c4) * a * F(y[iX_c4]) * B5;
+  e.Ppro = F(c.pro_h2) * F(c.k_m_pro) * a * F(y[iX_pro]) * mpo * B5;
+  e.Ph2 = F(c.k_m_h2) * a * F(y[iX_h2]) * B12;
+  e.kD = kLa + D;
+  e.Kfa = F(c.K_I_h2_fa);
+  e.Kc4 = F(c.K_I_h2_c4);
+  e.Kpro = F(c.K_I_h2_pro);
+  e.Kh2 = F(c.K_S_h2);
+}
+
+// E(S) and dE/dS of Eq. 8 from the coefficients.
+template <class F>
+CHAD_HD F h2_eval(const H2Bal<F>& e, F S, F& dE) {
+  const F rfa = rcp<F>(e.Kfa + S), rc4 = rcp<F>(e.Kc4 + S), rpr = rcp<F>(e.Kpro + S);
+  const F rh = rcp<F>(e.Kh2 + S);
+  const F Ifa = e.Kfa * rfa, Ic4 = e.Kc4 * rc4, Ipr = e.Kpro * rpr;
+  dE = F(0) - (e.Pfa * Ifa * rfa + e.Pc4 * Ic4 * rc4 + e.Ppro * Ipr * rpr +
+               e.Ph2 * e.Kh2 * rh * rh + e.kD);
+  return e.C0 + e.Pfa * Ifa + e.Pc4 * Ic4 + e.Ppro * Ipr - e.Ph2 * S * rh - e.kD * S;
+}
+
+// Root of Eq. 8 by Newton from the guess: an update below 1e-8 relative
+// leaves the next iterate within ~1e-16 (quadratic convergence).  An iterate
+// leaving (0, inf), a growing |E| or a non-negative slope switches to
+// bisection on [0, hi], hi doubled from the guess until E(hi) <= 0 (E
+// decreases, and E(0) >= 0: at S = 0 nothing removes hydrogen but the
+// transfer from a gas that holds some).
+__host__ __device__ inline double solve_h2(const H2Bal<double>& e, double guess, int max_iters,
+                                           NewtonCounters& nc) {
+  double S = (guess > 0.0 && isfinite(guess)) ? guess : 1e-8;
+  double prevE = INFINITY;
+  for (int it = 0; it < max_iters; ++it) {
+    double dE;
+    const double E = h2_eval<double>(e, S, dE);
+    nc.iters++;
+    if (!isfinite(E) || fabs(E) > fabs(prevE) || !(dE < 0.0)) break;
+    const double dS = E * rcp<double>(dE);
+    const double Sn = S - dS;
+    if (!(Sn > 0.0) || !isfinite(Sn)) break;
+    if (fabs(dS) <= 1e-8 * Sn || E == 0.0) return Sn;
+    prevE = E;
+    S = Sn;
+  }
+  nc.fallbacks++;
+  double lo = 0.0, hi = fmax((guess > 0.0 && isfinite(guess)) ? guess : 0.0, 1e-12), dE;
+  int k = 0;
+  while (k < 200 && h2_eval<double>(e, hi, dE) > 0.0) {
+    hi *= 2.0;
+    ++k;
+  }
+  if (k == 200) {
+    nc.failed = 1;
+    return (guess > 0.0 && isfinite(guess)) ? guess : 1e-8;
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (h2_eval<double>(e, mid, dE) > 0.0) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
 // Rates of the 19 biochemical processes, the 3 transfers and their partial
 // derivatives.  Column lists are fixed per process.
 template <class R>

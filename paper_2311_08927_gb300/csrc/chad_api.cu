@@ -29,6 +29,7 @@ struct chad_ctx {
   std::vector<int64_t> count, offset;  // per digester
   int64_t N = 0, ld = 0;
   int precision = 0, learned = 0, headspace = 0;
+  int h2_alg = 0;  // S_h2 algebraic (Eq. 8): kernel form 3
   double rtol = 1e-6;
   int max_steps = 100000, max_newton = 50, fixed_n = 0;
   cudaStream_t stream = nullptr;
@@ -60,7 +61,7 @@ struct chad_ctx {
   int* d_order_cnt = nullptr;  // [2 * kOrderBuckets] bucket counts and cursors
   unsigned long long* d_misc = nullptr;  // [2]: load check flag, failed-particle count
   unsigned long long* d_interval = nullptr;  // global interval index (noise counter)
-  int variant[3] = {kDefaultVariant, kDefaultVariant, kDefaultVariant};
+  int variant[4] = {kDefaultVariant, kDefaultVariant, kDefaultVariant, kDefaultVariant};
   double flow_dt = -1.0;        // interval length the device flow constants hold
   // CUDA graph of one interval (captured on first use, replayed per interval)
   cudaGraphExec_t gexec = nullptr;
@@ -147,6 +148,10 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   if (cfg->precision != CHAD_PREC_FP64 && cfg->precision != CHAD_PREC_MIXED &&
       cfg->precision != CHAD_PREC_MIXED_F32RATES)
     return fail(nullptr, CHAD_E_INVALID, "precision must be one of CHAD_PREC_*");
+  if (cfg->h2_algebraic != 0 && cfg->h2_algebraic != 1)
+    return fail(nullptr, CHAD_E_INVALID, "h2_algebraic must be 0 or 1");
+  if (cfg->h2_algebraic && cfg->precision != CHAD_PREC_FP64)
+    return fail(nullptr, CHAD_E_INVALID, "h2_algebraic is implemented for the FP64 form only");
   if (cfg->headspace != CHAD_HEADSPACE_PARTICLE && cfg->headspace != CHAD_HEADSPACE_SHARED)
     return fail(nullptr, CHAD_E_INVALID, "invalid headspace mode");
   if (cfg->learned != 0 && cfg->learned != 1)
@@ -180,6 +185,7 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
     return fail(nullptr, CHAD_E_INVALID, "total particle count must be < 2^31");
   }
   c->precision = cfg->precision;
+  c->h2_alg = cfg->h2_algebraic ? 1 : 0;
   c->learned = cfg->learned;
   c->headspace = cfg->headspace;
   c->rtol = cfg->rtol;
@@ -414,6 +420,9 @@ static chad_status prepare_flow(chad_ctx* c, double dt_coupling_s) {
   return CHAD_OK;
 }
 
+// Kernel form of a context: 0-2 = precision form, 3 = FP64 with S_h2 algebraic.
+static int kernel_form(const chad_ctx* c) { return c->h2_alg ? 3 : c->precision; }
+
 // The launch sequence of one coupling interval: advect (digesters with
 // flow) -> integrate every particle -> shared-headspace mean -> interval += 1.
 static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cudaStream_t s,
@@ -465,7 +474,7 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
       return e;
     a.order = c->d_order;
   }
-  if ((e = launch_integrate(a, c->precision, variant, s)) != cudaSuccess) return e;
+  if ((e = launch_integrate(a, kernel_form(c), variant, s)) != cudaSuccess) return e;
   if (c->headspace == CHAD_HEADSPACE_SHARED) {
     HeadspaceArgs hs;
     hs.ld = c->ld;
@@ -517,7 +526,7 @@ chad_status chad_step(chad_ctx* c, double dt_coupling_s, int n_intervals) {
   chad_status st = prepare_flow(c, dt_coupling_s);
   if (st != CHAD_OK) return st;
   const double dt_days = dt_coupling_s / 86400.0;
-  const int variant = c->variant[c->precision];
+  const int variant = c->variant[kernel_form(c)];
   // one graph per interval: capture once, replay per interval (not possible
   // on the legacy default stream)
   if (c->use_graph && s != nullptr &&
@@ -605,7 +614,7 @@ chad_status chad_autotune(chad_ctx* c, double dt_coupling_s, int32_t* chosen, do
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  int best = c->variant[c->precision];
+  int best = c->variant[kernel_form(c)];
   float best_ms = 1e30f;
   for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
     // two consecutive intervals per variant: one interval alone is too noisy
@@ -627,7 +636,7 @@ chad_status chad_autotune(chad_ctx* c, double dt_coupling_s, int32_t* chosen, do
   cudaFree(snap);
   cudaFree(snap_st);
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
-  c->variant[c->precision] = best;
+  c->variant[kernel_form(c)] = best;
   drop_graph(c);
   if (chosen) *chosen = best;
   return CHAD_OK;

@@ -75,43 +75,66 @@ __device__ __forceinline__ void newton(const DigConst& c, const PartConst& q, co
   SHg = ab.SH;
 }
 
-// f(y) in precision RS (Newton in FP64)
-template <class RS>
+// S_h2 from Eq. 8 at y (S_H given by ab), Newton from *SH2g, which receives
+// the root (algebraic S_h2 form).
+__device__ __forceinline__ void newton_h2(const DigConst& c, const PartConst& q, const double* y,
+                                          double D, const AcidBase& ab, double* SH2g,
+                                          int max_newton, Cnt& cnt) {
+  H2Bal<double> e;
+  h2_coeffs<double>(c, q, y, D, ab, e);
+  NewtonCounters nc{0, 0, 0};
+  *SH2g = solve_h2(e, *SH2g, max_newton, nc);
+  cnt.newton += nc.iters;
+  cnt.fallback += nc.fallbacks;
+  cnt.failed |= nc.failed;
+}
+
+// f(y) in precision RS (Newton in FP64).  H2A: S_h2 algebraic (Eq. 8), its
+// root in *SH2g (guess in, root out) and a zero S_h2 rate.
+template <class RS, bool H2A = false>
 __device__ __forceinline__ void eval_f(const DigConst& c, const PartConst& q, const double* y,
                                        double D, double& SHg, int max_newton, Cnt& cnt,
-                                       double* f) {
+                                       double* f, double* SH2g = nullptr) {
   AcidBase ab;
   newton(c, q, y, SHg, max_newton, cnt, ab);
   RS yr[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) yr[i] = RS(y[i]);
+  if constexpr (H2A) {
+    newton_h2(c, q, y, D, ab, SH2g, max_newton, cnt);
+    yr[iS_h2] = RS(*SH2g);
+  }
   Rates<RS> o;
   rates<RS, false>(c, q, yr, ab, o);
   RS fr[NS];
   balances<RS>(c, yr, RS(D), o, fr);
 #pragma unroll
   for (int i = 0; i < NS; ++i) f[i] = double(fr[i]);
+  if constexpr (H2A) f[iS_h2] = 0.0;
 }
 
 // f(y) in precision RS, J_d (sparse slots) and u = df/dS_H in precision R,
 // one Newton solve.  SCALE (FP64 form only, where R is RS): J_d and u come
 // out multiplied by jscale (the rate partials are scaled after f is formed).
-template <class R, class RS, bool SCALE>
+template <class R, class RS, bool SCALE, bool H2A = false>
 __device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, const double* y,
                                         double D, double& SHg, int max_newton, Cnt& cnt,
                                         double* f, R* w, R* u, Rates<R>& o, AcidBase& ab,
-                                        R jscale) {
+                                        R jscale, double* SH2g = nullptr) {
   newton(c, q, y, SHg, max_newton, cnt, ab);
+  if constexpr (H2A) newton_h2(c, q, y, D, ab, SH2g, max_newton, cnt);
   {
     R yr[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) yr[i] = R(y[i]);
+    if constexpr (H2A) yr[iS_h2] = R(*SH2g);
     rates<R, true>(c, q, yr, ab, o);
     if (std::is_same<R, RS>::value) {
       R fr[NS];
       balances<R>(c, yr, R(D), o, fr);
 #pragma unroll
       for (int i = 0; i < NS; ++i) f[i] = double(fr[i]);
+      if constexpr (H2A) f[iS_h2] = 0.0;
     }
     if constexpr (SCALE) {
       scale_partials<R>(o, jscale);
@@ -221,7 +244,8 @@ __device__ __forceinline__ void stage_rhs(int st, const DigConst& c, const PartC
 
 template <int FORM, int MINB>
 __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
-  constexpr bool MIXED = FORM != 0;
+  constexpr bool MIXED = FORM == 1 || FORM == 2;
+  constexpr bool H2A = FORM == 3;  // FP64 with S_h2 algebraic (Eq. 8)
   using R = typename std::conditional<MIXED, float, double>::type;
   using RS = typename std::conditional<FORM == 2, float, double>::type;
   __shared__ unsigned long long s_acc, s_rej, s_newton, s_fb, s_piv, s_redo;
@@ -237,6 +261,10 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
   R qv[NS];  // u = df/dS_H, then q = W_d^-1 (g u)
   R dinv[NS];
   Rates<R> ko;  // rates and partials at the step's start (mixed: kept for jvp)
+  // algebraic S_h2: second rank-1 pair of W (p2 = W_1^-1 g w with w the S_h2
+  // column of J_d, zh = dS_h2/dy) and the running Eq. 8 root
+  double p2[H2A ? NS : 1], zh[H2A ? NS : 1];
+  double inv_delta2 = 0.0, SH2g = 0.0;
   double y[NS], F0[NS], k1[NS], k2[NS], F1[NS], y1[NS], tmp[NS];
   const double Tend = a.dt_days;
   const bool fixed = a.fixed_n > 0;
@@ -276,6 +304,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) y[i] = a.y[i * a.ld + p];
       SHg = a.SH[p];
+      if constexpr (H2A) SH2g = y[iS_h2];
       h = a.h[p];
       if (a.SH_learned && !(h > 0.0 && isfinite(h))) {
         // no step-size history: learned guesses; Newton from the learned
@@ -312,19 +341,63 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     AcidBase ab0;
     // FP64: J_d and u come out scaled by -g, so W_d = I + (-g J_d) and
     // q = W_d^-1 (g u) = -W_d^-1 (-g u)
-    eval_fj<R, RS, !MIXED>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0, R(-g));
+    if constexpr (H2A)
+      eval_fj<R, RS, true, true>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0,
+                                 R(-g), &SH2g);
+    else
+      eval_fj<R, RS, !MIXED>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0, R(-g));
     const double SH0 = SHg;
     double vsh[8];
     sh_tangent(*c, q, ab0, vsh);
     R vr[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) vr[k] = R(vsh[k]);
+    const double SH20 = SH2g;
+    if constexpr (H2A) {
+      // The S_h2 row of -g J_d gives dS_h2/dy = -(J_h2,j + u_h2 v_j) / J_h2,h2
+      // (the scale cancels); its column times -1 is g w.  Both leave W_d,
+      // whose S_h2 row becomes the identity's, and u loses its S_h2 entry.
+      const double rjj = rcp<double>(w[sp::slot(iS_h2, iS_h2)]);
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const int sl = sp::slot(iS_h2, j);
+        zh[j] = (sl >= 0 && j != iS_h2) ? -w[sl] * rjj : 0.0;
+      }
+      const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) zh[hc[k]] -= qv[iS_h2] * vsh[k] * rjj;
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        const int sl = sp::slot(i, iS_h2);
+        p2[i] = (sl >= 0 && i != iS_h2) ? -w[sl] : 0.0;
+        if (sl >= 0) w[sl] = 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const int sl = sp::slot(iS_h2, j);
+        if (sl >= 0) w[sl] = 0.0;
+      }
+      qv[iS_h2] = R(0);
+    }
     sp::form_w<R>(w, MIXED ? R(g) : R(-1));
     const bool lu_ok = sp::factor<R>(w, dinv);
     R inv_delta = R(0);
     // FP64: q and the Sherman-Morrison denominator here; mixed: in its loop
     const bool sm_ok = MIXED || rank1::setup<R>(w, dinv, R(-1), vr, R(kPivTau), qv, &inv_delta);
     bool piv_ok = lu_ok && sm_ok;
+    if constexpr (H2A) {
+      // p2 = W_1^-1 (g w) with W_1 = W_d - g u v^T (first Sherman-Morrison
+      // level), then the second level's denominator 1 - zh^T p2
+      sp::solve<double>(w, dinv, p2);
+      rank1::update<double>(qv, vr, inv_delta, p2);
+      double s2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < NS; ++j) s2 += zh[j] * p2[j];
+      const double delta2 = 1.0 - s2;
+      inv_delta2 = rcp<double>(delta2);
+      piv_ok = piv_ok && isfinite(delta2) && delta2 != 0.0 &&
+               fabs(delta2) >= kPivTau * fmax(1.0, fabs(s2));
+    }
     float norm = INFINITY;
     if (!MIXED && !piv_ok) cnt.pivot++;
     double xs[NS];
@@ -408,7 +481,16 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
             for (int i = 0; i < NS; ++i) y1[i] = fma(hh, k2[i], y[i]);
           }
           SHg = sh_guess(SH0, vsh, y, y1);
-          eval_f<RS>(*c, q, y1, D, SHg, a.max_newton, cnt, tmp);
+          if constexpr (H2A) {
+            // tangent guess of the Eq. 8 root at y1
+            double g2 = SH20;
+#pragma unroll
+            for (int j = 0; j < NS; ++j) g2 += zh[j] * (y1[j] - y[j]);
+            SH2g = (g2 > 0.5 * SH20 && g2 < 2.0 * SH20) ? g2 : SH20;
+            eval_f<RS, true>(*c, q, y1, D, SHg, a.max_newton, cnt, tmp, &SH2g);
+          } else {
+            eval_f<RS>(*c, q, y1, D, SHg, a.max_newton, cnt, tmp);
+          }
           if (st == 1) {
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
@@ -422,6 +504,14 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
           }
         }
         solve<MIXED, R>(w, dinv, qv, inv_delta, vsh, vr, *c, y, D, ko, g, tmp, xs);
+        if constexpr (H2A) {
+          double s2 = 0.0;
+#pragma unroll
+          for (int j = 0; j < NS; ++j) s2 += zh[j] * xs[j];
+          s2 *= inv_delta2;
+#pragma unroll
+          for (int i = 0; i < NS; ++i) xs[i] += s2 * p2[i];
+        }
         if (st == 0) {
 #pragma unroll
           for (int i = 0; i < NS; ++i) k1[i] = xs[i];
@@ -451,6 +541,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     if (fixed) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) y[i] = y1[i];
+      if constexpr (H2A) y[iS_h2] = SH2g;  // Eq. 8 root at y1 (last evaluation)
       cnt.acc++;
       ++nacc;
       if (!isfinite(norm)) status |= ST_NAN;
@@ -458,6 +549,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     } else if (norm <= 1.0f) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) y[i] = y1[i];
+      if constexpr (H2A) y[iS_h2] = SH2g;  // Eq. 8 root at y1 (last evaluation)
       t = last ? Tend : t + hh;
       cnt.acc++;
       ++nacc;

@@ -53,8 +53,8 @@ def gpu_run(pop, dt, n, **kw):
     return out
 
 
-def oracle_run(pop, dt, n, rtol=1e-6, atol=None, fixed_n=0):
-    return O.run(pop, dt, n, rtol=rtol, atol=atol, fixed_n=fixed_n)
+def oracle_run(pop, dt, n, rtol=1e-6, atol=None, fixed_n=0, h2_algebraic=False):
+    return O.run(pop, dt, n, rtol=rtol, atol=atol, fixed_n=fixed_n, h2_algebraic=h2_algebraic)
 
 
 # ------------------------------------------------------------ Gate A: same arithmetic
@@ -113,6 +113,52 @@ def test_production_forms_within_1e4_of_tight_oracle(precision):
     assert np.all(g["status"] == 0)
     e = relerr(g["y"], o["y"])
     assert e.max() < 1e-4, (e.max(), I.STATE_NAMES[int(np.argmax(e.max(axis=1)))])
+
+
+# ------------------------------------------------------------ S_h2 algebraic (Eq. 8)
+def test_h2_algebraic_fixed_steps_match_oracle():
+    """The FP64 kernel form with S_h2 from Eq. 8 at every evaluation against
+    the oracle's algebraic mode, fixed steps: states (including the stored
+    S_h2 root) to 1e-9, with temperature spread and slugs."""
+    pop = I.config_population(3, n=2000)
+    g = gpu_run(pop, 60.0, 3, fixed_substeps=4, h2_algebraic=True)
+    o = oracle_run(pop, 60.0, 3, fixed_n=4, h2_algebraic=True)
+    assert np.all(g["status"] == 0)
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+
+
+def test_h2_algebraic_adaptive_tight_tolerance_matches_oracle():
+    pop = I.config_population(3, n=2000)
+    idx = np.concatenate([pop.slugs[:16], np.setdiff1d(np.arange(2000), pop.slugs)[:48]])
+    sp = subset(pop, idx)
+    atol = I.atol_vector(1e-13)
+    g = gpu_run(sp, 60.0, 4, rtol=1e-10, atol=atol, h2_algebraic=True)
+    o = oracle_run(sp, 60.0, 4, rtol=1e-10, atol=atol, h2_algebraic=True)
+    assert np.all(g["status"] == 0) and np.all(o["status"] == 0)
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+    assert abs(g["stats"]["accepted_steps"] - o["stats"][0]) <= 2
+
+
+def test_h2_algebraic_production_tolerance_and_differential_form():
+    """At rtol 1e-6 the algebraic form stays within 1e-4 of the tight
+    algebraic oracle, and within 1e-4 of the differential form (the two
+    models differ by the quasi-steady error of a sub-second S_h2)."""
+    pop = I.config_population(3, n=3000)
+    idx = np.concatenate([pop.slugs[:24], np.setdiff1d(np.arange(3000), pop.slugs)[:72]])
+    sp = subset(pop, idx)
+    g = gpu_run(sp, 60.0, 20, rtol=1e-6, h2_algebraic=True)
+    o = oracle_run(sp, 60.0, 20, rtol=1e-10, atol=I.atol_vector(1e-13), h2_algebraic=True)
+    assert np.all(g["status"] == 0)
+    assert relerr(g["y"], o["y"]).max() < 1e-4
+    d = gpu_run(sp, 60.0, 20, rtol=1e-6)
+    assert relerr(g["y"], d["y"]).max() < 1e-4
+
+
+def test_h2_algebraic_needs_the_fp64_form():
+    pop = I.config_population(1, n=16)
+    with pytest.raises(CH.ChadError) as ei:
+        CH.Simulator(pop, precision=CH.PREC_MIXED, h2_algebraic=True)
+    assert ei.value.code == 1
 
 
 # ------------------------------------------------------------ flow, headspace, digesters

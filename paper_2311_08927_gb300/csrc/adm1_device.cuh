@@ -333,7 +333,8 @@ __host__ __device__ inline void solve_SH(const DigConst& c, const PartConst& q, 
 // dS_H/dy_k = -(dE/dy_k) / (dE/dS_H) (implicit function theorem on Eq. 7)
 // for the 8 states that enter Eq. 7, in the order of kShStates.
 constexpr int kShStates[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
-CHAD_HD void sh_tangent(const DigConst& c, const PartConst& q, const AcidBase& ab, double* v) {
+template <class DC>
+CHAD_HD void sh_tangent(const DC& c, const PartConst& q, const AcidBase& ab, double* v) {
   const double inv = -rcp<double>(ab.dEdS);
   v[0] = inv * (-c.K_a_va * ab.r_va * (1.0 / kVfaCod_va));
   v[1] = inv * (-c.K_a_bu * ab.r_bu * (1.0 / kVfaCod_bu));
@@ -476,8 +477,8 @@ struct Rates {
   R P_h2, P_ch4, P_co2;                               // dP/dG
 };
 
-template <class R, bool J>
-CHAD_HD void rates(const DigConst& c, const PartConst& q, const R* y,
+template <class R, bool J, class DC>
+CHAD_HD void rates(const DC& c, const PartConst& q, const R* y,
                                       const AcidBase& ab, Rates<R>& o) {
   const R a = R(q.arr);
   const R SH = R(ab.SH);
@@ -541,7 +542,7 @@ CHAD_HD void rates(const DigConst& c, const PartConst& q, const R* y,
   const R RT = R(q.RT);
   const R P_h2 = RT * R(1.0 / 16.0), P_ch4 = RT * R(1.0 / 64.0), P_co2 = RT;
   const R P = P_h2 * y[iG_h2] + P_ch4 * y[iG_ch4] + P_co2 * y[iG_co2] + R(q.p_h2o);
-  const R kpv = R(c.kp_over_Vgas), invPa = R(1.0 / c.P_atm);
+  const R kpv = R(c.kp_over_Vgas), invPa = rcp<R>(R(c.P_atm));
   o.qv = kpv * (P - R(c.P_atm)) * P * invPa;
   const R kLa = R(c.k_La);
   const R KH2 = R(q.K_H_h2) * RT, KCH4 = R(q.K_H_ch4) * RT, KCO2 = R(q.K_H_co2) * RT;
@@ -619,8 +620,8 @@ CHAD_HD void rates(const DigConst& c, const PartConst& q, const R* y,
 // dil holds the transport terms of every state (liquid: dilution; gas:
 // outflow) and N the ADM1 stoichiometry of the 19 processes and the three
 // gas transfers (r[19..21]).
-template <class R>
-CHAD_HD void stoich(const DigConst& c, const R* r, const R* dil, R* f) {
+template <class R, class DC>
+CHAD_HD void stoich(const DC& c, const R* r, const R* dil, R* f) {
   const R dec = r[12] + r[13] + r[14] + r[15] + r[16] + r[17] + r[18];
   f[iS_su] = dil[iS_su] + r[1] + R(c.c_su_li) * r[3] - r[4];
   f[iS_aa] = dil[iS_aa] + r[2] - r[5];
@@ -686,8 +687,8 @@ CHAD_HD void scale_partials(Rates<R>& o, R sc) {
 }
 
 // f(y): mass balances of Eq. 2 with the ADM1 stoichiometry
-template <class R>
-CHAD_HD void balances(const DigConst& c, const R* y, R D, const Rates<R>& o, R* f) {
+template <class R, class DC>
+CHAD_HD void balances(const DC& c, const R* y, R D, const Rates<R>& o, R* f) {
   R dil[NS];
 #pragma unroll
   for (int i = 0; i < 26; ++i) dil[i] = D * (R(c.y_in[i]) - y[i]);
@@ -770,8 +771,8 @@ CHAD_HD void scat(JS Jm, int row, R coef, const int (&cols)[NC], const R (&d)[NC
 // With u_out == nullptr the full J = J_d + u v^T is assembled; otherwise only
 // the direct part J_d (S_H held fixed) goes into Jm and u = df/dS_H into
 // u_out, for the Sherman-Morrison solve of W = W_d - g u v^T.
-template <class Idx, class R, class JS>
-CHAD_HD void jacobian(const DigConst& c, const PartConst& q, const R* y, R D, const AcidBase& ab,
+template <class Idx, class R, class JS, class DC>
+CHAD_HD void jacobian(const DC& c, const PartConst& q, const R* y, R D, const AcidBase& ab,
                       const Rates<R>& o, JS Jm, R* u_out = nullptr) {
   R u[NS];
 #pragma unroll

@@ -43,6 +43,7 @@ struct chad_ctx {
   int n_chunks = 0;
   // device buffers
   DigConst* d_dc = nullptr;
+  DigConstF* d_dcf = nullptr;
   FlowConst* d_fl = nullptr;
   int* d_dig = nullptr;
   int64_t* d_off = nullptr;
@@ -108,7 +109,7 @@ static cudaError_t dalloc(T** p, size_t count) {
 }
 
 static void free_all(chad_ctx* c) {
-  void* ptrs[] = {c->d_dc, c->d_fl, c->d_dig, c->d_off, c->d_y, c->d_pos, c->d_T, c->d_pc, c->d_D,
+  void* ptrs[] = {c->d_dc, c->d_dcf, c->d_fl, c->d_dig, c->d_off, c->d_y, c->d_pos, c->d_T, c->d_pc, c->d_D,
                   c->d_SH, c->d_h, c->d_status, c->d_atol, c->d_cnt, c->d_queue, c->d_order, c->d_order_cnt, c->d_misc, c->d_interval, c->d_chunk_dig,
                   c->d_chunk_beg, c->d_chunk_end, c->d_dig_chunk0, c->d_partial, c->d_mean};
   for (void* p : ptrs)
@@ -225,6 +226,7 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   cudaError_t e = cudaSuccess;
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(dalloc(&c->d_dc, c->n_dig));
+  A(dalloc(&c->d_dcf, c->n_dig));
   A(dalloc(&c->d_fl, c->n_dig));
   A(dalloc(&c->d_dig, c->N));
   A(dalloc(&c->d_off, c->n_dig + 1));
@@ -265,6 +267,11 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   for (int d = 0; d < c->n_dig; ++d)
     for (int64_t p = c->offset[d]; p < c->offset[d + 1]; ++p) dig[p] = d;
   A(cudaMemcpy(c->d_dc, c->hdc.data(), sizeof(DigConst) * c->n_dig, cudaMemcpyHostToDevice));
+  {
+    std::vector<DigConstF> hf(c->n_dig);
+    for (int d = 0; d < c->n_dig; ++d) narrow_digester(c->hdc[d], hf[d]);
+    A(cudaMemcpy(c->d_dcf, hf.data(), sizeof(DigConstF) * c->n_dig, cudaMemcpyHostToDevice));
+  }
   A(cudaMemcpy(c->d_fl, c->hfl.data(), sizeof(FlowConst) * c->n_dig, cudaMemcpyHostToDevice));
   A(cudaMemcpy(c->d_dig, dig.data(), sizeof(int) * (c->N > 0 ? c->N : 1), cudaMemcpyHostToDevice));
   A(cudaMemcpy(c->d_off, c->offset.data(), sizeof(int64_t) * (c->n_dig + 1), cudaMemcpyHostToDevice));
@@ -432,6 +439,7 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
   a.ld = c->ld;
   a.dig = c->d_dig;
   a.dc = c->d_dc;
+  a.dcf = c->d_dcf;
   a.y = c->d_y;
   a.T = c->d_T;
   a.pc = c->d_pc;

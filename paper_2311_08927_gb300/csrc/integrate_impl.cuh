@@ -116,11 +116,28 @@ __device__ __forceinline__ void eval_f(const DigConst& c, const PartConst& q, co
 // f(y) in precision RS, J_d (sparse slots) and u = df/dS_H in precision R,
 // one Newton solve.  SCALE (FP64 form only, where R is RS): J_d and u come
 // out multiplied by jscale (the rate partials are scaled after f is formed).
+// The digester constants in the precision of the Jacobian evaluation.
+template <class R>
+struct DCSel;
+template <>
+struct DCSel<double> {
+  static __device__ __forceinline__ const DigConst& get(const DigConst& c, const DigConstF*) {
+    return c;
+  }
+};
+template <>
+struct DCSel<float> {
+  static __device__ __forceinline__ const DigConstF& get(const DigConst&, const DigConstF* cf) {
+    return *cf;
+  }
+};
+
 template <class R, class RS, bool SCALE, bool H2A = false>
-__device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, const double* y,
-                                        double D, double& SHg, int max_newton, Cnt& cnt,
-                                        double* f, R* w, R* u, Rates<R>& o, AcidBase& ab,
-                                        R jscale, double* SH2g = nullptr) {
+__device__ __forceinline__ void eval_fj(const DigConst& c, const DigConstF* cf, const PartConst& q,
+                                        const double* y, double D, double& SHg, int max_newton,
+                                        Cnt& cnt, double* f, R* w, R* u, Rates<R>& o,
+                                        AcidBase& ab, R jscale, double* SH2g = nullptr) {
+  const auto& cr = DCSel<R>::get(c, cf);
   newton(c, q, y, SHg, max_newton, cnt, ab);
   if constexpr (H2A) newton_h2(c, q, y, D, ab, SH2g, max_newton, cnt);
   {
@@ -128,19 +145,19 @@ __device__ __forceinline__ void eval_fj(const DigConst& c, const PartConst& q, c
 #pragma unroll
     for (int i = 0; i < NS; ++i) yr[i] = R(y[i]);
     if constexpr (H2A) yr[iS_h2] = R(*SH2g);
-    rates<R, true>(c, q, yr, ab, o);
+    rates<R, true>(cr, q, yr, ab, o);
     if (std::is_same<R, RS>::value) {
       R fr[NS];
-      balances<R>(c, yr, R(D), o, fr);
+      balances<R>(cr, yr, R(D), o, fr);
 #pragma unroll
       for (int i = 0; i < NS; ++i) f[i] = double(fr[i]);
       if constexpr (H2A) f[iS_h2] = 0.0;
     }
     if constexpr (SCALE) {
       scale_partials<R>(o, jscale);
-      jacobian<sp::Idx, R>(c, q, yr, R(D) * jscale, ab, o, w, u);
+      jacobian<sp::Idx, R>(cr, q, yr, R(D) * jscale, ab, o, w, u);
     } else {
-      jacobian<sp::Idx, R>(c, q, yr, R(D), ab, o, w, u);
+      jacobian<sp::Idx, R>(cr, q, yr, R(D), ab, o, w, u);
     }
   }
   if (!std::is_same<R, RS>::value) {
@@ -273,6 +290,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
 
   int64_t p = -1;
   const DigConst* c = nullptr;
+  const DigConstF* cf = nullptr;
   PartConst q;
   double SHg = 0.0, h = 0.0, t = 0.0, D = 0.0;
   int status = 0, attempts = 0, nacc = 0;
@@ -300,6 +318,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     if (fresh) {
       cnt = Cnt{0, 0, 0, 0, 0, 0, 0};
       c = &a.dc[a.dig[p]];
+      if constexpr (MIXED) cf = &a.dcf[a.dig[p]];
       pc_load(a.pc, a.ld, p, q);
 #pragma unroll
       for (int i = 0; i < NS; ++i) y[i] = a.y[i * a.ld + p];
@@ -342,10 +361,11 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     // FP64: J_d and u come out scaled by -g, so W_d = I + (-g J_d) and
     // q = W_d^-1 (g u) = -W_d^-1 (-g u)
     if constexpr (H2A)
-      eval_fj<R, RS, true, true>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0,
+      eval_fj<R, RS, true, true>(*c, cf, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0,
                                  R(-g), &SH2g);
     else
-      eval_fj<R, RS, !MIXED>(*c, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0, R(-g));
+      eval_fj<R, RS, !MIXED>(*c, cf, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0,
+                             R(-g));
     const double SH0 = SHg;
     double vsh[8];
     sh_tangent(*c, q, ab0, vsh);

@@ -22,6 +22,7 @@ struct StepArgs {
   int64_t ld;           // leading dimension of the SoA arrays
   const int* dig;       // [n] digester of each particle
   const DigConst* dc;   // [n_dig]
+  const DigConstF* dcf; // [n_dig] float copy (mixed form's FP32 Jacobian evaluation)
   double* y;            // [NS][ld]
   const double* T;      // [n] K
   const double* pc;     // [kPartConstFields][ld] per-particle constants (part_const of T)

@@ -52,38 +52,47 @@ enum ParamIndex : int {
 };
 
 // Temperature-independent constants of one digester, laid out for the device.
-struct DigConst {
+// T = T is the model's precision; the mixed form keeps a float copy for
+// its FP32 Jacobian evaluation (each FP64->FP32 conversion there would take an
+// FP64 pipe slot).  All members are T except the four ints.
+template <class T>
+struct DigConstT {
   // kinetics at the reference temperature (1/d) and their Arrhenius scaling
-  double k_dis, k_hyd_ch, k_hyd_pr, k_hyd_li;
-  double k_m_su, k_m_aa, k_m_fa, k_m_c4, k_m_pro, k_m_ac, k_m_h2;
-  double k_dec[7];
-  double Ea_over_R, inv_T_ref;
-  double K_S_IN, K_S_su, K_S_aa, K_S_fa, K_S_c4, K_S_pro, K_S_ac, K_S_h2;
-  double K_I_h2_fa, K_I_h2_c4, K_I_h2_pro, K_I_nh3;
+  T k_dis, k_hyd_ch, k_hyd_pr, k_hyd_li;
+  T k_m_su, k_m_aa, k_m_fa, k_m_c4, k_m_pro, k_m_ac, k_m_h2;
+  T k_dec[7];
+  T Ea_over_R, inv_T_ref;
+  T K_S_IN, K_S_su, K_S_aa, K_S_fa, K_S_c4, K_S_pro, K_S_ac, K_S_h2;
+  T K_I_h2_fa, K_I_h2_c4, K_I_h2_pro, K_I_nh3;
   // Hill pH inhibition I = 1 / (1 + (S_H / K_pH)^n)
-  double inv_K_pH_aa, inv_K_pH_ac, inv_K_pH_h2;
-  double n_aa, n_ac, n_h2;
+  T inv_K_pH_aa, inv_K_pH_ac, inv_K_pH_h2;
+  T n_aa, n_ac, n_h2;
   int ni_aa, ni_ac, ni_h2;  // n as a small integer (1..4), or 0 if not integral
   int pad0;
   // acid-base and gas-liquid constants
-  double K_a_va, K_a_bu, K_a_pro, K_a_ac;                       // T-independent
-  double K_w_b, K_a_co2_b, K_a_IN_b, K_H_co2_b, K_H_ch4_b, K_H_h2_b, p_h2o_b;  // at T_base
-  double th_w, th_a_co2, th_a_IN, th_H_co2, th_H_ch4, th_H_h2, th_h2o;        // dH/R (K)
-  double inv_T_base, R, P_atm, k_La, kp_over_Vgas, Vliq_over_Vgas;
+  T K_a_va, K_a_bu, K_a_pro, K_a_ac;                       // T-independent
+  T K_w_b, K_a_co2_b, K_a_IN_b, K_H_co2_b, K_H_ch4_b, K_H_h2_b, p_h2o_b;  // at T_base
+  T th_w, th_a_co2, th_a_IN, th_H_co2, th_H_ch4, th_H_h2, th_h2o;        // dH/R (K)
+  T inv_T_base, R, P_atm, k_La, kp_over_Vgas, Vliq_over_Vgas;
   // stoichiometric coefficients of the mass balances
-  double f_sI, f_xI, f_ch, f_pr, f_li, c_su_li, f_fa_li;
-  double su_h2, su_bu, su_pro, su_ac, Y_su;   // (1 - Y_su) f_x,su
-  double aa_h2, aa_va, aa_bu, aa_pro, aa_ac, Y_aa;
-  double fa_h2, fa_ac, Y_fa;
-  double va_pro, va_ac, va_h2, bu_ac, bu_h2, Y_c4;
-  double pro_ac, pro_h2, Y_pro;
-  double ac_ch4, Y_ac, h2_ch4, Y_h2;
-  double cIC[13];  // S_IC coefficient of processes 1..12 and decay (13)
-  double nIN[13];  // S_IN coefficient of processes 1..12 and decay (13)
+  T f_sI, f_xI, f_ch, f_pr, f_li, c_su_li, f_fa_li;
+  T su_h2, su_bu, su_pro, su_ac, Y_su;   // (1 - Y_su) f_x,su
+  T aa_h2, aa_va, aa_bu, aa_pro, aa_ac, Y_aa;
+  T fa_h2, fa_ac, Y_fa;
+  T va_pro, va_ac, va_h2, bu_ac, bu_h2, Y_c4;
+  T pro_ac, pro_h2, Y_pro;
+  T ac_ch4, Y_ac, h2_ch4, Y_h2;
+  T cIC[13];  // S_IC coefficient of processes 1..12 and decay (13)
+  T nIN[13];  // S_IN coefficient of processes 1..12 and decay (13)
   // inflow
-  double y_in[NS];
-  double D_uniform;
+  T y_in[NS];
+  T D_uniform;
 };
+using DigConst = DigConstT<double>;
+using DigConstF = DigConstT<float>;
+
+// Float copy of a digester's constants (rounded to nearest).
+void narrow_digester(const DigConst& d, DigConstF& f);
 
 // Flow field of one digester, expanded for the device.
 struct FlowConst {

@@ -3,6 +3,7 @@
 // the paper takes from its Ref. [14]; the S_IC and S_IN coefficients are the
 // carbon and nitrogen balances of each process written out term by term.
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 
 #include "model.h"
@@ -202,6 +203,29 @@ bool derive_digester(const double* p, double V_liq, double V_gas, double D_unifo
   }
   c.D_uniform = D_uniform;
   return true;
+}
+
+// The members are all of the element type except the block of four ints
+// (ni_aa .. pad0), which K_a_va follows; the copy walks the two runs.
+void narrow_digester(const DigConst& d, DigConstF& f) {
+  constexpr size_t nb = offsetof(DigConst, ni_aa) / sizeof(double);
+  constexpr size_t na = (sizeof(DigConst) - offsetof(DigConst, K_a_va)) / sizeof(double);
+  static_assert(offsetof(DigConstF, ni_aa) == nb * sizeof(float), "DigConstT layout");
+  static_assert((sizeof(DigConstF) - offsetof(DigConstF, K_a_va)) / sizeof(float) == na,
+                "DigConstT layout");
+  static_assert(offsetof(DigConst, K_a_va) - offsetof(DigConst, ni_aa) == 4 * sizeof(int),
+                "DigConstT layout");
+  const double* db = reinterpret_cast<const double*>(&d);
+  float* fb = reinterpret_cast<float*>(&f);
+  for (size_t i = 0; i < nb; ++i) fb[i] = (float)db[i];
+  f.ni_aa = d.ni_aa;
+  f.ni_ac = d.ni_ac;
+  f.ni_h2 = d.ni_h2;
+  f.pad0 = d.pad0;
+  const double* da = reinterpret_cast<const double*>(reinterpret_cast<const char*>(&d) +
+                                                     offsetof(DigConst, K_a_va));
+  float* fa = reinterpret_cast<float*>(reinterpret_cast<char*>(&f) + offsetof(DigConstF, K_a_va));
+  for (size_t i = 0; i < na; ++i) fa[i] = (float)da[i];
 }
 
 }  // namespace chad

@@ -77,6 +77,8 @@ def lib():
                                            _dp, _dp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                            C.c_double, C.c_double, _dp, C.c_long, C.c_int, _lp,
                                            C.c_int]
+            L.oracle_diffuse.argtypes = [C.c_long, _dp, _dp, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, C.c_int]
             L.oracle_rhs_h2alg.restype = C.c_int
             L.oracle_rhs_h2alg.argtypes = [_dp, C.c_double, C.c_double, C.c_double, C.c_double,
                                            _dp, _dp, C.c_double, _dp, C.POINTER(C.c_double),
@@ -261,3 +263,13 @@ def run(pop, dt_coupling_s, n_intervals, interval0=0, rtol=1e-6, atol=None, SH=N
                      float(dt_coupling_s), int(n_intervals), int(interval0), float(rtol), atol,
                      int(max_steps), int(fixed_n), int(n_threads), stats, int(bool(h2_algebraic)))
     return dict(y=y, pos=pos, S_H=SH, h=h, status=status, stats=stats)
+
+
+def diffuse(pos, y, V, D, h, dt_s, n_sub):
+    """SPH diffusion between particles (brute force over all pairs): n_sub
+    explicit Euler steps over dt_s seconds; returns the new y [NS][n]."""
+    y = np.ascontiguousarray(y, dtype=np.float64).copy()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    lib().oracle_diffuse(int(y.shape[1]), pos, y, float(V), float(D), float(h), float(dt_s),
+                         int(n_sub))
+    return y

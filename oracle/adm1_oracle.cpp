@@ -760,6 +760,26 @@ void parallel_chunks(long n, int n_threads, F fn) {
 // =========================================================================
 // C entry points (ctypes)
 // =========================================================================
+// ------------------------------------------------------- diffusion between particles
+// SPH discretisation of the diffusion equation (Cleary & Monaghan, J. Comput.
+// Phys. 148 (1999)) for particles of equal volume V, with the Wendland C2
+// kernel of smoothing length h (support 2h) in the form of Eq. 1:
+//   dC_i/dt = sum_{j != i} 2 D V (C_i - C_j) r_ij W'(r_ij) / (r_ij^2 + 0.01 h^2),
+// pairwise antisymmetric, so the total of every species is conserved.  The
+// soluble species (S_su .. S_I) and the lumped ions S_cat, S_an diffuse;
+// particulates and the gas states do not.  Brute force over all pairs.
+constexpr int N_DIFF = 14;
+const int DIFF_STATES[N_DIFF] = {S_su, S_aa, S_fa, S_va, S_bu, S_pro, S_ac,
+                                 S_h2, S_ch4, S_IC, S_IN, S_I, S_cat, S_an};
+
+double wendland_dwdr(double r, double h) {
+  const double q = r / h;
+  if (q >= 2.0) return 0.0;
+  const double alpha = 21.0 / (16.0 * M_PI * h * h * h);
+  const double t = 1.0 - 0.5 * q;
+  return -5.0 * alpha * q * t * t * t / h;
+}
+
 extern "C" {
 
 int oracle_n_params(void) { return NPARAM; }
@@ -898,6 +918,34 @@ int oracle_integrate(const double* params, double T, double V_liq, double V_gas,
     stats4[2] = P.ns.iters; stats4[3] = P.ns.bisections;
   }
   return status;
+}
+
+// n_sub explicit Euler steps of the SPH diffusion equation over dt_s seconds
+// for the n particles at pos [3][n] (m); y [NS][n] in place.
+void oracle_diffuse(long n, const double* pos, double* y, double V, double D, double h,
+                    double dt_s, int n_sub) {
+  const double dt = dt_s / n_sub;
+  std::vector<double> flux((size_t)N_DIFF * n);
+  for (int sub = 0; sub < n_sub; ++sub) {
+    for (long i = 0; i < n; ++i) {
+      double acc[N_DIFF] = {0};
+      for (long j = 0; j < n; ++j) {
+        if (j == i) continue;
+        const double dx = pos[i] - pos[j], dy = pos[n + i] - pos[n + j];
+        const double dz = pos[2 * n + i] - pos[2 * n + j];
+        const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+        if (r >= 2.0 * h) continue;
+        const double wgt = 2.0 * D * V * r * wendland_dwdr(r, h) / (r * r + 0.01 * h * h);
+        for (int k = 0; k < N_DIFF; ++k) {
+          const int st = DIFF_STATES[k];
+          acc[k] += wgt * (y[(long)st * n + i] - y[(long)st * n + j]);
+        }
+      }
+      for (int k = 0; k < N_DIFF; ++k) flux[(size_t)k * n + i] = acc[k];
+    }
+    for (int k = 0; k < N_DIFF; ++k)
+      for (long i = 0; i < n; ++i) y[(long)DIFF_STATES[k] * n + i] += dt * flux[(size_t)k * n + i];
+  }
 }
 
 // Brute-force reference: classical explicit RK4 with n_steps equal steps.

@@ -181,6 +181,19 @@ chad_status chad_set_flow(chad_ctx* ctx, int digester, const chad_flow* flow);
 
 /* ---- the hot path ------------------------------------------------------- */
 
+/* Diffusion between the particles of one digester, the extension the paper
+   plans (Sec. 2.3 and its future developments): every coupling interval,
+   after advection, explicit substeps of the SPH discretisation of the
+   diffusion equation (Cleary-Monaghan form of Eq. 1 with the Wendland C2
+   kernel, smoothing length h in m, support 2h; equal particle volumes
+   V_liq / n) move the soluble species (S_su .. S_I) and the lumped ions
+   S_cat, S_an between particles closer than 2h; particulates and gases do
+   not diffuse.  D is the diffusivity in m^2/s (0 switches it off).  The
+   substep count is the largest of ceil(dt D / (0.1 h^2)) over the digesters.
+   Needs the digester's flow geometry (chad_set_flow with has_flow, else
+   CHAD_E_STATE).  Allocates the neighbour-grid buffers on first use. */
+chad_status chad_set_diffusion(chad_ctx* ctx, int digester, double D, double h);
+
 /* Integrate n_intervals coupling intervals of dt_coupling_s seconds each:
    per interval, advect (digesters with flow), integrate every particle
    (Eq. 2-7) and, with a shared headspace, average the three gas states of

@@ -96,7 +96,7 @@ def lib():
             L.oracle_run.argtypes = [C.c_int, _lp, _dp, _dp, _dp, _dp, _dp, _up, C.c_int,
                                      C.c_long, _dp, _dp, _dp, _dp, _dp, _ip,
                                      C.c_double, C.c_int, C.c_long, C.c_double, _dp,
-                                     C.c_long, C.c_int, C.c_int, _lp, C.c_int]
+                                     C.c_long, C.c_int, C.c_int, _lp, C.c_int, _dp, _dp]
             _lib = L
     return _lib
 
@@ -235,9 +235,12 @@ def gauss(seed, pid, interval, sub, axis) -> float:
 
 
 def run(pop, dt_coupling_s, n_intervals, interval0=0, rtol=1e-6, atol=None, SH=None, h=None,
-        max_steps=100000, fixed_n=0, n_threads=0, status=None, h2_algebraic=False):
+        max_steps=100000, fixed_n=0, n_threads=0, status=None, h2_algebraic=False,
+        diffusion=None):
     """Integrate a Population (see paper_2311_08927_gb300.inputs) in place.
     h2_algebraic: S_h2 from its mass balance (Eq. 8) instead of as a state.
+    diffusion: (D m^2/s, h m) for every digester with a flow field: after the
+    advection of each interval, SPH diffusion between its particles.
 
     Returns a dict with y, pos, S_H, h, status, stats (copies)."""
     from paper_2311_08927_gb300 import inputs as I  # seeded generators only
@@ -258,10 +261,17 @@ def run(pop, dt_coupling_s, n_intervals, interval0=0, rtol=1e-6, atol=None, SH=N
     status = np.zeros(N, dtype=np.int32) if status is None else np.ascontiguousarray(status, dtype=np.int32).copy()
     atol = I.atol_vector() if atol is None else _f64(atol)
     stats = np.zeros(4, dtype=np.int64)
+    dD = np.zeros(nd)
+    dh = np.zeros(nd)
+    if diffusion is not None:
+        for k, dg in enumerate(pop.digesters):
+            if dg.flow is not None:
+                dD[k], dh[k] = diffusion
     lib().oracle_run(nd, np.ascontiguousarray(pop.offsets, dtype=np.int64), params, V_liq, V_gas,
                      D_u, flow, seeds, int(pop.shared_headspace), N, pos, y, T, SH, h, status,
                      float(dt_coupling_s), int(n_intervals), int(interval0), float(rtol), atol,
-                     int(max_steps), int(fixed_n), int(n_threads), stats, int(bool(h2_algebraic)))
+                     int(max_steps), int(fixed_n), int(n_threads), stats, int(bool(h2_algebraic)),
+                     dD, dh)
     return dict(y=y, pos=pos, S_H=SH, h=h, status=status, stats=stats)
 
 

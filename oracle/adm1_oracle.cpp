@@ -921,31 +921,40 @@ int oracle_integrate(const double* params, double T, double V_liq, double V_gas,
 }
 
 // n_sub explicit Euler steps of the SPH diffusion equation over dt_s seconds
-// for the n particles at pos [3][n] (m); y [NS][n] in place.
-void oracle_diffuse(long n, const double* pos, double* y, double V, double D, double h,
-                    double dt_s, int n_sub) {
+// for the particles [a, b) of arrays of leading dimension ld: pos [3][ld] (m),
+// y [NS][ld] in place.
+void diffuse_range(long ld, long a, long b, const double* pos, double* y, double V, double D,
+                   double h, double dt_s, int n_sub) {
+  const long n = b - a;
   const double dt = dt_s / n_sub;
   std::vector<double> flux((size_t)N_DIFF * n);
   for (int sub = 0; sub < n_sub; ++sub) {
-    for (long i = 0; i < n; ++i) {
+    for (long i = a; i < b; ++i) {
       double acc[N_DIFF] = {0};
-      for (long j = 0; j < n; ++j) {
+      for (long j = a; j < b; ++j) {
         if (j == i) continue;
-        const double dx = pos[i] - pos[j], dy = pos[n + i] - pos[n + j];
-        const double dz = pos[2 * n + i] - pos[2 * n + j];
+        const double dx = pos[i] - pos[j], dy = pos[ld + i] - pos[ld + j];
+        const double dz = pos[2 * ld + i] - pos[2 * ld + j];
         const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
         if (r >= 2.0 * h) continue;
         const double wgt = 2.0 * D * V * r * wendland_dwdr(r, h) / (r * r + 0.01 * h * h);
         for (int k = 0; k < N_DIFF; ++k) {
           const int st = DIFF_STATES[k];
-          acc[k] += wgt * (y[(long)st * n + i] - y[(long)st * n + j]);
+          acc[k] += wgt * (y[(long)st * ld + i] - y[(long)st * ld + j]);
         }
       }
-      for (int k = 0; k < N_DIFF; ++k) flux[(size_t)k * n + i] = acc[k];
+      for (int k = 0; k < N_DIFF; ++k) flux[(size_t)k * n + (i - a)] = acc[k];
     }
     for (int k = 0; k < N_DIFF; ++k)
-      for (long i = 0; i < n; ++i) y[(long)DIFF_STATES[k] * n + i] += dt * flux[(size_t)k * n + i];
+      for (long i = a; i < b; ++i)
+        y[(long)DIFF_STATES[k] * ld + i] += dt * flux[(size_t)k * n + (i - a)];
   }
+}
+
+// All particles of one array (see diffuse_range).
+void oracle_diffuse(long n, const double* pos, double* y, double V, double D, double h,
+                    double dt_s, int n_sub) {
+  diffuse_range(n, 0, n, pos, y, V, D, h, dt_s, n_sub);
 }
 
 // Brute-force reference: classical explicit RK4 with n_steps equal steps.
@@ -987,7 +996,7 @@ int oracle_run(int n_dig, const long* dig_offset, const double* params, const do
                double* y, const double* T, double* SH, double* h, int* status,
                double dt_coupling_s, int n_intervals, long interval0, double rtol,
                const double* atol, long max_steps, int fixed_n, int n_threads,
-               long* stats4, int h2_alg) {
+               long* stats4, int h2_alg, const double* diff_D, const double* diff_h) {
   if (n_threads <= 0) n_threads = (int)std::max(1u, std::thread::hardware_concurrency());
   const int FL = 7 + NS;
   const double dt_days = dt_coupling_s / 86400.0;
@@ -1009,14 +1018,22 @@ int oracle_run(int n_dig, const long* dig_offset, const double* params, const do
     D_slab[d] = fl[d].on ? fl[d].q_in / (M_PI * fl[d].R * fl[d].R * (fl[d].H - fl[d].slab_zmin)) : 0.0;
   }
   std::vector<long> acc(N, 0), rej(N, 0), nit(N, 0), nbis(N, 0);
+  std::vector<double> Dp(N);
+  // diffusion: one substep count for all digesters, the largest that
+  // stability asks for (dt D / (0.1 h^2), at least 1)
+  int diff_sub = 0;
+  if (diff_D)
+    for (int d = 0; d < n_dig; ++d)
+      if (diff_D[d] > 0.0 && dig_offset[d + 1] > dig_offset[d])
+        diff_sub = std::max(diff_sub, std::max(1, (int)std::ceil(dt_coupling_s * diff_D[d] /
+                                                                  (0.1 * diff_h[d] * diff_h[d]))));
   for (int it = 0; it < n_intervals; ++it) {
     const uint64_t gint = (uint64_t)(interval0 + it);
+    // advection (positions and the interval's dilution rate)
     parallel_chunks(N, n_threads, [&](long a, long b) {
       for (long p = a; p < b; ++p) {
         const int d = dig_of[p];
-        const double* prm = params + (long)d * NPARAM;
         double D = D_uniform[d];
-        const double* yin = fl[d].y_in;
         double* px = pos + p;
         double* py = pos + N + p;
         double* pz = pos + 2 * N + p;
@@ -1025,6 +1042,24 @@ int oracle_run(int n_dig, const long* dig_offset, const double* params, const do
           advect_one(fl[d], cs[d], sn[d], n_sub, dsub, (uint64_t)(p - dig_offset[d]), gint,
                      *px, *py, *pz);
         }
+        Dp[p] = D;
+      }
+    });
+    // diffusion between the particles of each digester
+    if (diff_sub > 0)
+      for (int d = 0; d < n_dig; ++d) {
+        const long a = dig_offset[d], b = dig_offset[d + 1];
+        if (!(diff_D[d] > 0.0) || b <= a) continue;
+        diffuse_range(N, a, b, pos, y, V_liq[d] / (double)(b - a), diff_D[d], diff_h[d],
+                      dt_coupling_s, diff_sub);
+      }
+    // ADM1 on every particle
+    parallel_chunks(N, n_threads, [&](long a, long b) {
+      for (long p = a; p < b; ++p) {
+        const int d = dig_of[p];
+        const double* prm = params + (long)d * NPARAM;
+        const double D = Dp[p];
+        const double* yin = fl[d].y_in;
         Model m;
         make_model(prm, T[p], V_liq[d], V_gas[d], m);
         double yy[NS];

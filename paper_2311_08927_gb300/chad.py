@@ -131,6 +131,8 @@ def lib():
                                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                                 C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                                 C.c_int]
+            L.chad_set_diffusion.restype = C.c_int
+            L.chad_set_diffusion.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
             L.chad_probe_numerics.restype = C.c_int
             L.chad_probe_numerics.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                               C.c_void_p]
@@ -145,7 +147,7 @@ def exported_symbols() -> list[str]:
             "chad_create", "chad_destroy", "chad_load_particles", "chad_set_flow",
             "chad_step", "chad_synchronize", "chad_read_states", "chad_probe_alu_peak",
             "chad_eval_model", "chad_eval_model_split", "chad_probe_numerics", "chad_autotune",
-            "chad_flop_counts",
+            "chad_flop_counts", "chad_set_diffusion",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
 
@@ -369,6 +371,11 @@ def chad_set_flow(ctx, digester, flow: chad_flow) -> None:
     _check(L, ctx, L.chad_set_flow(ctx, int(digester), C.byref(flow)))
 
 
+def chad_set_diffusion(ctx, digester, D, h) -> None:
+    L = lib()
+    _check(L, ctx, L.chad_set_diffusion(ctx, int(digester), float(D), float(h)))
+
+
 def chad_step(ctx, dt_coupling_s, n_intervals) -> None:
     L = lib()
     _check(L, ctx, L.chad_step(ctx, float(dt_coupling_s), int(n_intervals)))
@@ -400,7 +407,7 @@ class Simulator:
 
     def __init__(self, pop: I.Population, precision=PREC_FP64, rtol=1e-6, atol=None,
                  max_steps=100000, max_newton=50, fixed_substeps=0, stream=None,
-                 headspace=None, learned=0, h2_algebraic=False):
+                 headspace=None, learned=0, h2_algebraic=False, diffusion=None):
         self.pop = pop
         nd = len(pop.digesters)
         self._keep = []
@@ -446,6 +453,10 @@ class Simulator:
                 fl = chad_flow(1, f["U"], f["R"], f["H"], f["sigma"], f["slab_zmin"], f["q_in"],
                                yin.ctypes.data_as(_dp), f["seed"])
                 chad_set_flow(self.ctx, d, fl)
+        if diffusion is not None:  # (D m^2/s, h m) for every digester with flow
+            for d, dg in enumerate(pop.digesters):
+                if dg.flow is not None:
+                    chad_set_diffusion(self.ctx, d, diffusion[0], diffusion[1])
 
     def load(self, y=None, pos=None, T=None, S_H=None, h=None):
         """Load every digester from host arrays (SoA over the whole population)."""

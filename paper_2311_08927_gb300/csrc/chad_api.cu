@@ -35,6 +35,16 @@ struct chad_ctx {
   cudaStream_t stream = nullptr;
   std::vector<DigConst> hdc;
   std::vector<FlowConst> hfl;
+  // diffusion between particles (chad_set_diffusion)
+  std::vector<double> diff_D, diff_h, V_liq;  // V_liq per digester (m^3)
+  bool any_diff = false, diff_dirty = false;
+  double diff_dt = -1.0;
+  int diff_nsub = 0, n_cells = 0, cells_cap = 0;
+  DiffConst* d_diffc = nullptr;
+  int* d_cell_count = nullptr;
+  int* d_cell_start = nullptr;
+  int* d_cell_list = nullptr;
+  double* d_diff_buf = nullptr;
   std::vector<char> loaded;
   bool any_flow = false;
   double sim_days = 0.0;
@@ -114,7 +124,8 @@ static void free_all(chad_ctx* c) {
                   c->d_chunk_beg, c->d_chunk_end, c->d_dig_chunk0, c->d_partial, c->d_mean};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  void* lp[] = {c->d_mlp, c->d_SH_learned, c->d_h_learned};
+  void* lp[] = {c->d_mlp, c->d_SH_learned, c->d_h_learned, c->d_diffc, c->d_cell_count,
+                c->d_cell_start, c->d_cell_list, c->d_diff_buf};
   for (void* p : lp)
     if (p) cudaFree(p);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -177,6 +188,7 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
       return fail(nullptr, CHAD_E_INVALID, "n_particles out of range");
     }
     c->count[d] = cfg->n_particles[d];
+    c->V_liq.push_back(cfg->V_liq[d]);
     c->offset[d + 1] = c->offset[d] + c->count[d];
   }
   c->N = c->offset[c->n_dig];
@@ -196,6 +208,8 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   c->stream = (cudaStream_t)cfg->cuda_stream;
   c->hdc.resize(c->n_dig);
   c->hfl.resize(c->n_dig);
+  c->diff_D.assign(c->n_dig, 0.0);
+  c->diff_h.assign(c->n_dig, 0.0);
   c->loaded.assign(c->n_dig, 0);
   for (int d = 0; d < c->n_dig; ++d) {
     const char* why = "";
@@ -361,6 +375,33 @@ chad_status chad_load_particles(chad_ctx* c, int digester, int64_t n, const doub
   return CHAD_OK;
 }
 
+chad_status chad_set_diffusion(chad_ctx* c, int digester, double D, double h) {
+  if (!c) return CHAD_E_INVALID;
+  if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");
+  if (!(D >= 0.0) || !std::isfinite(D)) return fail(c, CHAD_E_INVALID, "D must be finite and >= 0");
+  if (D > 0.0 && (!(h > 0.0) || !std::isfinite(h))) return fail(c, CHAD_E_INVALID, "h must be > 0");
+  if (D > 0.0 && !c->hfl[digester].has_flow)
+    return fail(c, CHAD_E_STATE, "diffusion needs the digester's flow geometry (chad_set_flow)");
+  if (D > 0.0 && !c->d_diffc) {
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(dalloc(&c->d_diffc, c->n_dig));
+    A(dalloc(&c->d_cell_list, c->N));
+    A(dalloc(&c->d_diff_buf, (size_t)kNumDiffusing * c->ld));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, CHAD_E_NOMEM, "diffusion buffers");
+    }
+  }
+  c->diff_D[digester] = D;
+  c->diff_h[digester] = D > 0.0 ? h : 0.0;
+  c->any_diff = false;
+  for (int d = 0; d < c->n_dig; ++d) c->any_diff |= c->diff_D[d] > 0.0;
+  c->diff_dirty = true;
+  drop_graph(c);
+  return CHAD_OK;
+}
+
 chad_status chad_set_flow(chad_ctx* c, int digester, const chad_flow* f) {
   if (!c) return CHAD_E_INVALID;
   if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");
@@ -427,6 +468,60 @@ static chad_status prepare_flow(chad_ctx* c, double dt_coupling_s) {
   return CHAD_OK;
 }
 
+// Grid and coefficients of the diffusion for an interval of dt seconds:
+// cells 2h wide, one substep count for all digesters, the largest that
+// stability asks for (dt D / (0.1 h^2) per digester, at least 1).
+static chad_status prepare_diffusion(chad_ctx* c, double dt_s) {
+  if (!c->any_diff || (!c->diff_dirty && c->diff_dt == dt_s)) return CHAD_OK;
+  std::vector<DiffConst> g(c->n_dig);
+  int64_t cells = 0;
+  int nsub = 1;
+  for (int d = 0; d < c->n_dig; ++d) {
+    DiffConst& q = g[d];
+    std::memset(&q, 0, sizeof(q));
+    const double D = c->diff_D[d], h = c->diff_h[d];
+    if (!(D > 0.0) || c->count[d] == 0) continue;
+    q.on = 1;
+    q.R = c->hfl[d].R;
+    q.H = c->hfl[d].H;
+    q.h = h;
+    q.inv_h = 1.0 / h;
+    q.cell = 2.0 * h;
+    q.nx = q.ny = std::max(1, (int)std::ceil(2.0 * q.R / q.cell));
+    q.nz = std::max(1, (int)std::ceil(q.H / q.cell));
+    q.cell0 = (int)cells;
+    cells += (int64_t)q.nx * q.ny * q.nz;
+    const double V = c->V_liq[d] / (double)c->count[d];  // equal particle volumes
+    q.two_DV = 2.0 * D * V;
+    q.dw_coef = -5.0 * (21.0 / (16.0 * M_PI * h * h * h)) / h;
+    nsub = std::max(nsub, (int)std::ceil(dt_s * D / (0.1 * h * h)));
+  }
+  if (cells > (int64_t(1) << 26))
+    return fail(c, CHAD_E_INVALID, "diffusion grid too fine (more than 2^26 cells): raise h");
+  for (int d = 0; d < c->n_dig; ++d) g[d].dt_sub = dt_s / nsub;
+  if (cells > c->cells_cap) {
+    if (c->d_cell_count) cudaFree(c->d_cell_count);
+    if (c->d_cell_start) cudaFree(c->d_cell_start);
+    c->d_cell_count = nullptr;
+    c->d_cell_start = nullptr;
+    c->cells_cap = 0;
+    if (cudaMalloc(&c->d_cell_count, sizeof(int) * cells) != cudaSuccess ||
+        cudaMalloc(&c->d_cell_start, sizeof(int) * (cells + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, CHAD_E_NOMEM, "diffusion grid");
+    }
+    c->cells_cap = (int)cells;
+  }
+  CK(c, cudaMemcpy(c->d_diffc, g.data(), sizeof(DiffConst) * c->n_dig, cudaMemcpyHostToDevice),
+     "diffusion constants");
+  c->n_cells = (int)cells;
+  c->diff_nsub = nsub;
+  c->diff_dt = dt_s;
+  c->diff_dirty = false;
+  drop_graph(c);
+  return CHAD_OK;
+}
+
 // Kernel form of a context: 0-2 = precision form, 3 = FP64 with S_h2 algebraic.
 static int kernel_form(const chad_ctx* c) { return c->h2_alg ? 3 : c->precision; }
 
@@ -476,6 +571,21 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
     v.D = c->d_D;
     v.interval = c->d_interval;
     if ((e = launch_advect(v, s)) != cudaSuccess) return e;
+  }
+  if (c->any_diff && c->n_cells > 0) {
+    DiffArgs da;
+    da.n = c->N;
+    da.ld = c->ld;
+    da.dig = c->d_dig;
+    da.dc = c->d_diffc;
+    da.pos = c->d_pos;
+    da.y = c->d_y;
+    da.buf = c->d_diff_buf;
+    da.cell_count = c->d_cell_count;
+    da.cell_start = c->d_cell_start;
+    da.cell_list = c->d_cell_list;
+    da.n_cells = c->n_cells;
+    if ((e = launch_diffusion(da, c->diff_nsub, s)) != cudaSuccess) return e;
   }
   if (c->fixed_n == 0 && c->N > 0) {
     if ((e = launch_order(c->d_h, c->N, dt_days, c->d_order_cnt, c->d_order, s)) != cudaSuccess)
@@ -532,6 +642,8 @@ chad_status chad_step(chad_ctx* c, double dt_coupling_s, int n_intervals) {
   if (n_intervals == 0 || c->N == 0) return CHAD_OK;
   cudaStream_t s = c->stream;
   chad_status st = prepare_flow(c, dt_coupling_s);
+  if (st != CHAD_OK) return st;
+  st = prepare_diffusion(c, dt_coupling_s);
   if (st != CHAD_OK) return st;
   const double dt_days = dt_coupling_s / 86400.0;
   const int variant = c->variant[kernel_form(c)];

@@ -43,6 +43,32 @@ struct StepArgs {
   const double* h_learned;
 };
 
+// Diffusion between particles (diffusion.cu): per-digester grid and
+// coefficients, and the arguments of one interval's diffusion.
+constexpr int kNumDiffusing = 14;  // S_su .. S_I, S_cat, S_an
+struct DiffConst {
+  int on;                 // D > 0 and particles present
+  int nx, ny, nz, cell0;  // grid of cells 2h wide over [-R, R]^2 x [0, H]; first cell id
+  int pad;
+  double R, H, h, inv_h, cell;
+  double two_DV;          // 2 D V (m^5/s), V = V_liq / particles
+  double dw_coef;         // W'(r) = dw_coef q (1 - q/2)^3, q = r/h (Wendland C2)
+  double dt_sub;          // seconds per explicit substep
+};
+struct DiffArgs {
+  int64_t n, ld;
+  const int* dig;
+  const DiffConst* dc;
+  const double* pos;  // [3][ld]
+  double* y;          // [NS][ld]
+  double* buf;        // [kNumDiffusing][ld] new concentrations of a substep
+  int* cell_count;    // [n_cells]
+  int* cell_start;    // [n_cells + 1]
+  int* cell_list;     // [n] particle indices grouped by cell
+  int n_cells;
+};
+cudaError_t launch_diffusion(const DiffArgs& a, int n_sub, cudaStream_t s);
+
 struct AdvectArgs {
   int64_t n, ld;
   const int* dig;

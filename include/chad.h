@@ -78,7 +78,9 @@ enum {
   CHAD_P_STEPS = 2,   /* max_steps_per_interval reached before the interval end */
   CHAD_P_HMIN = 4,    /* step size fell below 1e-12 d after rejections */
   CHAD_P_NEG = 8,     /* a state ended the interval below -atol_i */
-  CHAD_P_NAN = 16     /* non-finite state or singular iteration matrix */
+  CHAD_P_NAN = 16,    /* non-finite state or singular iteration matrix */
+  CHAD_P_DIFFUSION = 32  /* diffusion needed more substeps than planned (see
+                            chad_set_diffusion); the diffusion step may be unstable */
 };
 
 /* Library configuration (copied at chad_create). */
@@ -189,8 +191,12 @@ chad_status chad_set_flow(chad_ctx* ctx, int digester, const chad_flow* flow);
    V_liq / n) move the soluble species (S_su .. S_I) and the lumped ions
    S_cat, S_an between particles closer than 2h; particulates and gases do
    not diffuse.  D is the diffusivity in m^2/s (0 switches it off).  The
-   substep count is the largest of ceil(dt D / (0.1 h^2)) over the digesters.
-   Needs the digester's flow geometry (chad_set_flow with has_flow, else
+   substep count follows the particles: each interval the largest row sum
+   S of the discrete operator (over all diffusing particles) is taken and
+   ceil(2 dt S) substeps are made (every update stays a convex combination),
+   at most 8 times the continuum estimate 2 dt 7 D / h^2 (at least 8); a
+   plan above that runs the maximum and sets CHAD_P_DIFFUSION on the
+   diffusing particles.  Needs the digester's flow geometry (chad_set_flow with has_flow, else
    CHAD_E_STATE).  Allocates the neighbour-grid buffers on first use. */
 chad_status chad_set_diffusion(chad_ctx* ctx, int digester, double D, double h);
 

@@ -79,6 +79,9 @@ def lib():
                                            C.c_int]
             L.oracle_diffuse.argtypes = [C.c_long, _dp, _dp, C.c_double, C.c_double, C.c_double,
                                          C.c_double, C.c_int]
+            L.oracle_diffusion_row_sum_max.restype = C.c_double
+            L.oracle_diffusion_row_sum_max.argtypes = [C.c_long, _dp, C.c_double, C.c_double,
+                                                       C.c_double]
             L.oracle_rhs_h2alg.restype = C.c_int
             L.oracle_rhs_h2alg.argtypes = [_dp, C.c_double, C.c_double, C.c_double, C.c_double,
                                            _dp, _dp, C.c_double, _dp, C.POINTER(C.c_double),
@@ -273,6 +276,20 @@ def run(pop, dt_coupling_s, n_intervals, interval0=0, rtol=1e-6, atol=None, SH=N
                      int(max_steps), int(fixed_n), int(n_threads), stats, int(bool(h2_algebraic)),
                      dD, dh)
     return dict(y=y, pos=pos, S_H=SH, h=h, status=status, stats=stats)
+
+
+def diffusion_row_sum_max(pos, V, D, h):
+    """max_i sum_j |w_ij| of the SPH diffusion operator (1/s) for particles
+    at pos [3][n]; ceil(2 dt S) Euler substeps keep each update a convex
+    combination of the old values."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    return float(lib().oracle_diffusion_row_sum_max(int(pos.shape[1]), pos, float(V), float(D),
+                                                    float(h)))
+
+
+def diffusion_substeps(dt_s, smax):
+    """The substep rule run() applies each interval: ceil(2 dt S_max), >= 1."""
+    return max(1, int(np.ceil(2.0 * dt_s * smax)))
 
 
 def diffuse(pos, y, V, D, h, dt_s, n_sub):

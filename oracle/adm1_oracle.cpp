@@ -951,6 +951,40 @@ void diffuse_range(long ld, long a, long b, const double* pos, double* y, double
   }
 }
 
+// Largest row sum max_i sum_j |w_ij| of the discrete diffusion operator over
+// the particles [a, b); an explicit Euler step of length dt keeps every new
+// value a convex combination of the old ones while dt times it is <= 1.
+double diffusion_row_sum_max(long ld, long a, long b, const double* pos, double V, double D,
+                             double h) {
+  double smax = 0.0;
+  for (long i = a; i < b; ++i) {
+    double S = 0.0;
+    for (long j = a; j < b; ++j) {
+      if (j == i) continue;
+      const double dx = pos[i] - pos[j], dy = pos[ld + i] - pos[ld + j];
+      const double dz = pos[2 * ld + i] - pos[2 * ld + j];
+      const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+      if (r >= 2.0 * h) continue;
+      S -= 2.0 * D * V * r * wendland_dwdr(r, h) / (r * r + 0.01 * h * h);
+    }
+    smax = std::max(smax, S);
+  }
+  return smax;
+}
+
+// Substeps for an interval of dt_s seconds: ceil(2 dt_s S_max), at least 1
+// (half the convex-combination bound, so every weight stays <= 1/2).
+int diffusion_substeps(double dt_s, double smax) {
+  const double want = std::ceil(2.0 * dt_s * smax);
+  return want >= 1.0 ? (int)want : 1;
+}
+
+// Largest row sum of the operator over all particles of one array (see
+// diffusion_row_sum_max).
+double oracle_diffusion_row_sum_max(long n, const double* pos, double V, double D, double h) {
+  return diffusion_row_sum_max(n, 0, n, pos, V, D, h);
+}
+
 // All particles of one array (see diffuse_range).
 void oracle_diffuse(long n, const double* pos, double* y, double V, double D, double h,
                     double dt_s, int n_sub) {
@@ -1019,14 +1053,10 @@ int oracle_run(int n_dig, const long* dig_offset, const double* params, const do
   }
   std::vector<long> acc(N, 0), rej(N, 0), nit(N, 0), nbis(N, 0);
   std::vector<double> Dp(N);
-  // diffusion: one substep count for all digesters, the largest that
-  // stability asks for (dt D / (0.1 h^2), at least 1)
-  int diff_sub = 0;
+  bool any_diff = false;
   if (diff_D)
     for (int d = 0; d < n_dig; ++d)
-      if (diff_D[d] > 0.0 && dig_offset[d + 1] > dig_offset[d])
-        diff_sub = std::max(diff_sub, std::max(1, (int)std::ceil(dt_coupling_s * diff_D[d] /
-                                                                  (0.1 * diff_h[d] * diff_h[d]))));
+      any_diff |= diff_D[d] > 0.0 && dig_offset[d + 1] > dig_offset[d];
   for (int it = 0; it < n_intervals; ++it) {
     const uint64_t gint = (uint64_t)(interval0 + it);
     // advection (positions and the interval's dilution rate)
@@ -1045,14 +1075,25 @@ int oracle_run(int n_dig, const long* dig_offset, const double* params, const do
         Dp[p] = D;
       }
     });
-    // diffusion between the particles of each digester
-    if (diff_sub > 0)
+    // diffusion between the particles of each digester; one substep count
+    // for all digesters, from the largest row sum over all of them at the
+    // interval's positions
+    if (any_diff) {
+      double smax = 0.0;
+      for (int d = 0; d < n_dig; ++d) {
+        const long a = dig_offset[d], b = dig_offset[d + 1];
+        if (!(diff_D[d] > 0.0) || b <= a) continue;
+        smax = std::max(smax, diffusion_row_sum_max(N, a, b, pos, V_liq[d] / (double)(b - a),
+                                                    diff_D[d], diff_h[d]));
+      }
+      const int diff_sub = diffusion_substeps(dt_coupling_s, smax);
       for (int d = 0; d < n_dig; ++d) {
         const long a = dig_offset[d], b = dig_offset[d + 1];
         if (!(diff_D[d] > 0.0) || b <= a) continue;
         diffuse_range(N, a, b, pos, y, V_liq[d] / (double)(b - a), diff_D[d], diff_h[d],
                       dt_coupling_s, diff_sub);
       }
+    }
     // ADM1 on every particle
     parallel_chunks(N, n_threads, [&](long a, long b) {
       for (long p = a; p < b; ++p) {

@@ -39,12 +39,14 @@ struct chad_ctx {
   std::vector<double> diff_D, diff_h, V_liq;  // V_liq per digester (m^3)
   bool any_diff = false, diff_dirty = false;
   double diff_dt = -1.0;
-  int diff_nsub = 0, n_cells = 0, cells_cap = 0;
+  int n_cells = 0, cells_cap = 0;
   DiffConst* d_diffc = nullptr;
   int* d_cell_count = nullptr;
   int* d_cell_start = nullptr;
   int* d_cell_list = nullptr;
   double* d_diff_buf = nullptr;
+  unsigned char* d_diff_plan = nullptr;  // smax (8 B), dt_sub (8 B), nsub, capped (4 B each)
+  int diff_max_sub = 0;
   std::vector<char> loaded;
   bool any_flow = false;
   double sim_days = 0.0;
@@ -125,7 +127,7 @@ static void free_all(chad_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* lp[] = {c->d_mlp, c->d_SH_learned, c->d_h_learned, c->d_diffc, c->d_cell_count,
-                c->d_cell_start, c->d_cell_list, c->d_diff_buf};
+                c->d_cell_start, c->d_cell_list, c->d_diff_buf, c->d_diff_plan};
   for (void* p : lp)
     if (p) cudaFree(p);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -388,6 +390,7 @@ chad_status chad_set_diffusion(chad_ctx* c, int digester, double D, double h) {
     A(dalloc(&c->d_diffc, c->n_dig));
     A(dalloc(&c->d_cell_list, c->N));
     A(dalloc(&c->d_diff_buf, (size_t)kNumDiffusing * c->ld));
+    A(dalloc(&c->d_diff_plan, 32));
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(c, CHAD_E_NOMEM, "diffusion buffers");
@@ -494,11 +497,12 @@ static chad_status prepare_diffusion(chad_ctx* c, double dt_s) {
     const double V = c->V_liq[d] / (double)c->count[d];  // equal particle volumes
     q.two_DV = 2.0 * D * V;
     q.dw_coef = -5.0 * (21.0 / (16.0 * M_PI * h * h * h)) / h;
-    nsub = std::max(nsub, (int)std::ceil(dt_s * D / (0.1 * h * h)));
+    // continuum estimate of the operator's largest row sum, 7 D / h^2
+    // (Wendland C2); the substep kernels in the launch sequence allow 8x
+    nsub = std::max(nsub, (int)std::ceil(2.0 * dt_s * 7.0 * D / (h * h)));
   }
   if (cells > (int64_t(1) << 26))
     return fail(c, CHAD_E_INVALID, "diffusion grid too fine (more than 2^26 cells): raise h");
-  for (int d = 0; d < c->n_dig; ++d) g[d].dt_sub = dt_s / nsub;
   if (cells > c->cells_cap) {
     if (c->d_cell_count) cudaFree(c->d_cell_count);
     if (c->d_cell_start) cudaFree(c->d_cell_start);
@@ -515,7 +519,7 @@ static chad_status prepare_diffusion(chad_ctx* c, double dt_s) {
   CK(c, cudaMemcpy(c->d_diffc, g.data(), sizeof(DiffConst) * c->n_dig, cudaMemcpyHostToDevice),
      "diffusion constants");
   c->n_cells = (int)cells;
-  c->diff_nsub = nsub;
+  c->diff_max_sub = std::max(8, 8 * nsub);
   c->diff_dt = dt_s;
   c->diff_dirty = false;
   drop_graph(c);
@@ -585,7 +589,14 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
     da.cell_start = c->d_cell_start;
     da.cell_list = c->d_cell_list;
     da.n_cells = c->n_cells;
-    if ((e = launch_diffusion(da, c->diff_nsub, s)) != cudaSuccess) return e;
+    da.status = c->d_status;
+    da.smax = reinterpret_cast<unsigned long long*>(c->d_diff_plan);
+    da.dt_sub = reinterpret_cast<double*>(c->d_diff_plan + 8);
+    da.nsub = reinterpret_cast<int*>(c->d_diff_plan + 16);
+    da.capped = reinterpret_cast<int*>(c->d_diff_plan + 20);
+    da.dt_s = dt_days * 86400.0;
+    da.max_sub = c->diff_max_sub;
+    if ((e = launch_diffusion(da, s)) != cudaSuccess) return e;
   }
   if (c->fixed_n == 0 && c->N > 0) {
     if ((e = launch_order(c->d_h, c->N, dt_days, c->d_order_cnt, c->d_order, s)) != cudaSuccess)

@@ -8,6 +8,15 @@
 // V = V_liq / N) for the soluble species and the lumped ions.  The fluxes are
 // pairwise antisymmetric, so every species' total is conserved.
 //
+// Substeps: explicit Euler keeps every concentration a convex combination
+// of the old ones (positive, stable) when dt_sub sum_j w_ij <= 1; each
+// interval a kernel takes S_max = max_i sum_j w_ij over the current
+// positions and the substep count is ceil(2 dt S_max) (half that limit),
+// capped at the substep kernels the host enqueues (8 times the continuum
+// estimate 2 dt 7 D / h^2, at least 8; a capped plan flags the particles).
+// The substep kernels are all in the interval's graph and return at once
+// past the planned count.
+//
 // Neighbour search: a uniform grid of cells 2h wide over the digester's
 // cylinder, built per interval by a counting sort (count, scan, scatter);
 // each cell's particle list is then ordered by particle index, so the sums
@@ -113,8 +122,58 @@ __device__ __forceinline__ double wendland_dwdr(double r, const DiffConst& g) {
   return q < 2.0 ? g.dw_coef * q * t * t * t : 0.0;  // -5 alpha q t^3 / h
 }
 
+// Row sum S_i = sum_j |w_ij| of particle i, maximum over particles into
+// *a.smax (positive doubles order like their bit patterns).
+__global__ void diff_rowsum(DiffArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const DiffConst& g = a.dc[a.dig[i]];
+  if (!g.on) return;
+  const double xi = a.pos[i], yi = a.pos[a.ld + i], zi = a.pos[2 * a.ld + i];
+  int cx, cy, cz;
+  cell_of(g, xi, yi, zi, cx, cy, cz);
+  const double two_h = 2.0 * g.h, eta = 0.01 * g.h * g.h;
+  double S = 0.0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int z = cz + dz;
+    if (z < 0 || z >= g.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = cy + dy;
+      if (yy < 0 || yy >= g.ny) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int x = cx + dx;
+        if (x < 0 || x >= g.nx) continue;
+        const int c = g.cell0 + (z * g.ny + yy) * g.nx + x;
+        for (int m = a.cell_start[c]; m < a.cell_start[c + 1]; ++m) {
+          const int j = a.cell_list[m];
+          if (j == i) continue;
+          const double ex = xi - a.pos[j], ey = yi - a.pos[a.ld + j], ez = zi - a.pos[2 * a.ld + j];
+          const double r2 = ex * ex + ey * ey + ez * ez;
+          const double r = sqrt(r2);
+          if (!(r < two_h)) continue;
+          S -= g.two_DV * r * wendland_dwdr(r, g) / (r2 + eta);
+        }
+      }
+    }
+  }
+  atomicMax(a.smax, (unsigned long long)__double_as_longlong(S));
+}
+
+// Substep plan: n_sub = ceil(2 dt S_max), at least 1, at most max_sub (a
+// capped plan sets *a.capped).
+__global__ void diff_plan(DiffArgs a) {
+  const double smax = __longlong_as_double((long long)*a.smax);
+  double want = ceil(2.0 * a.dt_s * smax);
+  if (!(want >= 1.0)) want = 1.0;
+  int n = a.max_sub;
+  if (want <= (double)a.max_sub) n = (int)want; else *a.capped = 1;
+  *a.nsub = n;
+  *a.dt_sub = a.dt_s / n;
+}
+
 // One explicit Euler step: out[k][i] = C_k,i + dt sum_j w_ij (C_k,i - C_k,j).
-__global__ void diff_flux(DiffArgs a) {
+__global__ void diff_flux(DiffArgs a, int sub) {
+  if (sub >= *a.nsub) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const DiffConst& g = a.dc[a.dig[i]];
@@ -155,14 +214,17 @@ __global__ void diff_flux(DiffArgs a) {
       }
     }
   }
+  const double dt = *a.dt_sub;
 #pragma unroll
-  for (int k = 0; k < kNumDiffusing; ++k) a.buf[(int64_t)k * a.ld + i] = ci[k] + g.dt_sub * acc[k];
+  for (int k = 0; k < kNumDiffusing; ++k) a.buf[(int64_t)k * a.ld + i] = ci[k] + dt * acc[k];
 }
 
-__global__ void diff_copy_back(DiffArgs a) {
+__global__ void diff_copy_back(DiffArgs a, int sub) {
+  if (sub >= *a.nsub) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   if (!a.dc[a.dig[i]].on) return;
+  if (sub == 0 && *a.capped) a.status[i] |= 32;  // CHAD_P_DIFFUSION
 #pragma unroll
   for (int k = 0; k < kNumDiffusing; ++k)
     a.y[(int64_t)kDiffStates[k] * a.ld + i] = a.buf[(int64_t)k * a.ld + i];
@@ -170,8 +232,8 @@ __global__ void diff_copy_back(DiffArgs a) {
 
 }  // namespace
 
-cudaError_t launch_diffusion(const DiffArgs& a, int n_sub, cudaStream_t s) {
-  if (a.n <= 0 || a.n_cells <= 0 || n_sub <= 0) return cudaSuccess;
+cudaError_t launch_diffusion(const DiffArgs& a, cudaStream_t s) {
+  if (a.n <= 0 || a.n_cells <= 0 || a.max_sub <= 0) return cudaSuccess;
   const int block = 256;
   const unsigned grid = (unsigned)((a.n + block - 1) / block);
   cudaError_t e = cudaMemsetAsync(a.cell_count, 0, sizeof(int) * a.n_cells, s);
@@ -180,9 +242,14 @@ cudaError_t launch_diffusion(const DiffArgs& a, int n_sub, cudaStream_t s) {
   diff_scan<<<1, 1024, 0, s>>>(a);
   diff_scatter<<<grid, block, 0, s>>>(a);
   diff_sort_cells<<<(unsigned)((a.n_cells + block - 1) / block), block, 0, s>>>(a);
-  for (int k = 0; k < n_sub; ++k) {
-    diff_flux<<<grid, block, 0, s>>>(a);
-    diff_copy_back<<<grid, block, 0, s>>>(a);
+  e = cudaMemsetAsync(a.smax, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.capped, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  diff_rowsum<<<grid, block, 0, s>>>(a);
+  diff_plan<<<1, 1, 0, s>>>(a);
+  for (int k = 0; k < a.max_sub; ++k) {
+    diff_flux<<<grid, block, 0, s>>>(a, k);
+    diff_copy_back<<<grid, block, 0, s>>>(a, k);
   }
   return cudaGetLastError();
 }

@@ -53,7 +53,6 @@ struct DiffConst {
   double R, H, h, inv_h, cell;
   double two_DV;          // 2 D V (m^5/s), V = V_liq / particles
   double dw_coef;         // W'(r) = dw_coef q (1 - q/2)^3, q = r/h (Wendland C2)
-  double dt_sub;          // seconds per explicit substep
 };
 struct DiffArgs {
   int64_t n, ld;
@@ -66,8 +65,15 @@ struct DiffArgs {
   int* cell_start;    // [n_cells + 1]
   int* cell_list;     // [n] particle indices grouped by cell
   int n_cells;
+  int* status;                // [n] status bits (a capped substep plan is recorded)
+  unsigned long long* smax;   // largest row sum of the diffusion operator (bit pattern)
+  int* nsub;                  // planned substeps of this interval
+  int* capped;                // 1 if the plan hit max_sub
+  double* dt_sub;             // seconds per substep
+  double dt_s;                // interval length, seconds
+  int max_sub;                // substep kernels in the interval's launch sequence
 };
-cudaError_t launch_diffusion(const DiffArgs& a, int n_sub, cudaStream_t s);
+cudaError_t launch_diffusion(const DiffArgs& a, cudaStream_t s);
 
 struct AdvectArgs {
   int64_t n, ld;

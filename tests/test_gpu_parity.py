@@ -143,6 +143,46 @@ def test_diffusion_rerun_is_bitwise_deterministic():
     assert np.array_equal(a["y"], b["y"])
 
 
+def _crowded(n, s=0.15):
+    """Config 2 with every particle pulled to within s of its distance from
+    the tank's centre: neighbour counts far above the uniform fill."""
+    pop = I.config_population(2, n=n)
+    c = np.array([0.0, 0.0, 0.15])[:, None]
+    pop.pos = c + s * (pop.pos - c)
+    return pop
+
+
+def test_diffusion_crowded_particles_match_oracle():
+    """Crowded particles: the substep count comes from the operator's
+    largest row sum at the interval's positions (computed on the GPU by an
+    atomic max), several times the continuum estimate; states to 1e-9."""
+    pop = _crowded(400)
+    dif = (1e-6, 0.024)
+    g = gpu_run(pop, 1.0, 2, diffusion=dif)
+    o = oracle_run(pop, 1.0, 2, diffusion=dif)
+    smax = O.diffusion_row_sum_max(o["pos"], pop.digesters[0].V_liq / 400, *dif)
+    assert O.diffusion_substeps(1.0, smax) > 1 >= math.ceil(2.0 * 7.0 * dif[0] / dif[1] ** 2)
+    assert np.all(g["status"] == 0)
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+
+
+def test_diffusion_plan_above_the_cap_is_flagged():
+    """A plan above the launched substeps (8 times the continuum estimate,
+    at least 8) runs them all and marks every diffusing particle with
+    CHAD_P_DIFFUSION (32); chosen so the capped steps stay convex
+    (dt_sub S_max <= 1), so the states stay finite and bounded."""
+    pop = _crowded(400)
+    dif = (4.5e-6, 0.024)
+    o = oracle_run(pop, 1.0, 1, diffusion=dif)
+    smax = O.diffusion_row_sum_max(o["pos"], pop.digesters[0].V_liq / 400, *dif)
+    assert 8 < O.diffusion_substeps(1.0, smax) and 1.0 * smax / 8 <= 1.0
+    g = gpu_run(pop, 1.0, 1, diffusion=dif)
+    assert np.all(g["status"] == 32)
+    assert np.all(np.isfinite(g["y"]))
+    ok = gpu_run(pop, 1.0, 1, diffusion=(1e-6, 0.024))
+    assert np.all(ok["status"] == 0)
+
+
 def test_diffusion_needs_flow_geometry():
     pop = I.config_population(1, n=16)
     sim = CH.Simulator(pop)

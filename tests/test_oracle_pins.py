@@ -644,3 +644,49 @@ def test_diffusion_operator_approximates_the_laplacian():
     ratio = rate[sel] / exact[sel]
     assert sel.sum() > 100 and np.all(np.abs(ratio - 1.0) < 0.03), (ratio.min(), ratio.max())
 
+
+
+def test_diffusion_row_sum_tends_to_the_continuum_integral():
+    """The operator's row sum sum_j |w_ij| at an inner lattice particle is a
+    quadrature of 8 pi D int_0^2h r^3 |W'(r)| / (r^2 + 0.01 h^2) dr, which
+    for the Wendland C2 kernel without the 0.01 h^2 term is 7 D / h^2
+    exactly (a Beta(3,4) integral); the quadrature error falls as h / dx
+    grows."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    D, dx = 1e-6, 0.004
+    errs = []
+    for f in (2.5, 4.5):
+        n1 = int(4 * f) + 5
+        pos, h = _lattice(n1, dx), f * dx
+        alpha = 21.0 / (16.0 * np.pi * h ** 3)
+        dw = lambda r: 5.0 * alpha * (r / h) * (1.0 - r / (2.0 * h)) ** 3 / h
+        cont = quad(lambda r: 8 * np.pi * D * r ** 3 * dw(r) / (r * r + 0.01 * h * h), 0, 2 * h)[0]
+        bare = quad(lambda r: 8 * np.pi * D * r * dw(r), 0, 2 * h)[0]
+        assert abs(bare / (7.0 * D / h ** 2) - 1.0) < 1e-10
+        errs.append(abs(O.diffusion_row_sum_max(pos, dx ** 3, D, h) / cont - 1.0))
+    assert errs[1] < 0.005 and errs[1] < errs[0] < 0.03, errs
+
+
+def test_diffusion_substep_rule_keeps_a_maximum_principle():
+    """With ceil(2 dt S_max) substeps every Euler update is a convex
+    combination of the old values, so no species leaves the range of its
+    initial values, also for crowded particles (h about the spacing), where
+    the continuum estimate 7 D / h^2 of the row sum is far too optimistic.
+    An eighth of the substeps overshoots."""
+    rng = np.random.default_rng(11)
+    n, L, D, h, dt = 400, 0.02, 1e-5, 0.004, 2.0
+    pos = rng.uniform(0.0, L, (3, n))
+    pos[:, : n // 4] = pos[:, : n // 4] * 0.1 + 0.5 * L     # a dense cluster
+    y = perturbed_ss(7, n)
+    y[S["S_ac"]] = rng.uniform(0.0, 1.0, n)
+    V = L ** 3 / n
+    smax = O.diffusion_row_sum_max(pos, V, D, h)
+    assert smax > 5 * 7 * D / h ** 2                            # crowding matters
+    nsub = O.diffusion_substeps(dt, smax)
+    y2 = O.diffuse(pos, y, V, D, h, dt, nsub)
+    for sp in DIFF:
+        i = S[sp]
+        lo, hi = y[i].min(), y[i].max()
+        assert y2[i].min() >= lo - 1e-12 * abs(lo) and y2[i].max() <= hi + 1e-12 * abs(hi), sp
+    y3 = O.diffuse(pos, y, V, D, h, dt, max(1, nsub // 8))
+    assert y3[S["S_ac"]].min() < 0.0 or y3[S["S_ac"]].max() > 1.0

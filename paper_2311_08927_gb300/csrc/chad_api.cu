@@ -594,7 +594,7 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
     da.dt_sub = reinterpret_cast<double*>(c->d_diff_plan + 8);
     da.nsub = reinterpret_cast<int*>(c->d_diff_plan + 16);
     da.capped = reinterpret_cast<int*>(c->d_diff_plan + 20);
-    da.dt_s = dt_days * 86400.0;
+    da.dt_s = c->diff_dt;  // the interval in seconds, as chad_step received it
     da.max_sub = c->diff_max_sub;
     if ((e = launch_diffusion(da, s)) != cudaSuccess) return e;
   }
@@ -707,6 +707,8 @@ chad_status chad_autotune(chad_ctx* c, double dt_coupling_s, int32_t* chosen, do
     if (!c->loaded[d]) return fail(c, CHAD_E_STATE, "every digester must be loaded before chad_autotune");
   cudaStream_t s = c->stream;
   chad_status st = prepare_flow(c, dt_coupling_s);
+  if (st != CHAD_OK) return st;
+  st = prepare_diffusion(c, dt_coupling_s);
   if (st != CHAD_OK) return st;
   const size_t nd = (size_t)c->ld;
   // snapshot of everything an interval modifies

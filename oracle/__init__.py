@@ -280,7 +280,7 @@ def run(pop, dt_coupling_s, n_intervals, interval0=0, rtol=1e-6, atol=None, SH=N
 
 def diffusion_row_sum_max(pos, V, D, h):
     """max_i sum_j |w_ij| of the SPH diffusion operator (1/s) for particles
-    at pos [3][n]; ceil(2 dt S) Euler substeps keep each update a convex
+    at pos [3][n]; ceil(dt S) Euler substeps keep each update a convex
     combination of the old values."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     return float(lib().oracle_diffusion_row_sum_max(int(pos.shape[1]), pos, float(V), float(D),
@@ -288,8 +288,8 @@ def diffusion_row_sum_max(pos, V, D, h):
 
 
 def diffusion_substeps(dt_s, smax):
-    """The substep rule run() applies each interval: ceil(2 dt S_max), >= 1."""
-    return max(1, int(np.ceil(2.0 * dt_s * smax)))
+    """The substep rule run() applies each interval: ceil(dt S_max), >= 1."""
+    return max(1, int(np.ceil(dt_s * smax)))
 
 
 def diffuse(pos, y, V, D, h, dt_s, n_sub):

@@ -972,10 +972,10 @@ double diffusion_row_sum_max(long ld, long a, long b, const double* pos, double 
   return smax;
 }
 
-// Substeps for an interval of dt_s seconds: ceil(2 dt_s S_max), at least 1
-// (half the convex-combination bound, so every weight stays <= 1/2).
+// Substeps for an interval of dt_s seconds: the fewest that keep every update
+// a convex combination of the old values, ceil(dt_s S_max), at least 1.
 int diffusion_substeps(double dt_s, double smax) {
-  const double want = std::ceil(2.0 * dt_s * smax);
+  const double want = std::ceil(dt_s * smax);
   return want >= 1.0 ? (int)want : 1;
 }
 

@@ -44,8 +44,18 @@ struct chad_ctx {
   int* d_cell_count = nullptr;
   int* d_cell_start = nullptr;
   int* d_cell_list = nullptr;
-  double* d_diff_buf = nullptr;
-  unsigned char* d_diff_plan = nullptr;  // smax (8 B), dt_sub (8 B), nsub, capped (4 B each)
+  // slot-order copies and the operator's rows (see diffusion.cu)
+  double* d_spos = nullptr;       // [3][N]
+  int* d_sdig = nullptr;          // [N]
+  double* d_sc = nullptr;         // 2 x [N][kDiffRow]
+  double* d_srow = nullptr;       // [N]
+  int64_t* d_row_start = nullptr; // [N]
+  int* d_row_len = nullptr;       // [N]
+  int* d_cols = nullptr;          // [diff_cap]
+  double* d_vals = nullptr;       // [diff_cap]
+  int64_t diff_cap = 0;
+  // plan scratch: smax, dt_sub, nnz, nnz_peak (8 B each), nsub, capped (4 B each)
+  unsigned char* d_diff_plan = nullptr;
   int diff_max_sub = 0;
   std::vector<char> loaded;
   bool any_flow = false;
@@ -127,7 +137,8 @@ static void free_all(chad_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* lp[] = {c->d_mlp, c->d_SH_learned, c->d_h_learned, c->d_diffc, c->d_cell_count,
-                c->d_cell_start, c->d_cell_list, c->d_diff_buf, c->d_diff_plan};
+                c->d_cell_start, c->d_cell_list, c->d_spos, c->d_sdig, c->d_sc, c->d_srow,
+                c->d_row_start, c->d_row_len, c->d_cols, c->d_vals, c->d_diff_plan};
   for (void* p : lp)
     if (p) cudaFree(p);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -389,8 +400,14 @@ chad_status chad_set_diffusion(chad_ctx* c, int digester, double D, double h) {
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
     A(dalloc(&c->d_diffc, c->n_dig));
     A(dalloc(&c->d_cell_list, c->N));
-    A(dalloc(&c->d_diff_buf, (size_t)kNumDiffusing * c->ld));
-    A(dalloc(&c->d_diff_plan, 32));
+    A(dalloc(&c->d_spos, (size_t)3 * c->N));
+    A(dalloc(&c->d_sdig, (size_t)c->N));
+    A(dalloc(&c->d_sc, (size_t)2 * kDiffRow * c->N));
+    A(dalloc(&c->d_srow, (size_t)c->N));
+    A(dalloc(&c->d_row_start, (size_t)c->N));
+    A(dalloc(&c->d_row_len, (size_t)c->N));
+    A(dalloc(&c->d_diff_plan, 64));
+    if (e == cudaSuccess) e = cudaMemset(c->d_diff_plan, 0, 64);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(c, CHAD_E_NOMEM, "diffusion buffers");
@@ -471,14 +488,28 @@ static chad_status prepare_flow(chad_ctx* c, double dt_coupling_s) {
   return CHAD_OK;
 }
 
-// Grid and coefficients of the diffusion for an interval of dt seconds:
-// cells 2h wide, one substep count for all digesters, the largest that
-// stability asks for (dt D / (0.1 h^2) per digester, at least 1).
+// Grid, coefficients and buffers of the diffusion for an interval of dt
+// seconds: cells 2h wide; room for the operator's entries from the continuum
+// neighbour count, twice over, grown to the largest request of earlier
+// intervals (rows that did not fit were recomputed in every substep); and
+// the substep kernels to enqueue: 8 times the continuum estimate
+// dt 7 D / h^2 of the substep count (largest over the digesters), at least 8.
+constexpr int64_t kDiffMaxEntries = int64_t(1) << 29;  // 6 GiB of entries at most
 static chad_status prepare_diffusion(chad_ctx* c, double dt_s) {
-  if (!c->any_diff || (!c->diff_dirty && c->diff_dt == dt_s)) return CHAD_OK;
+  if (!c->any_diff) return CHAD_OK;
+  int64_t grow = 0;
+  if (c->diff_cap > 0 && c->diff_cap < kDiffMaxEntries) {
+    unsigned long long peak = 0;
+    CK(c, cudaMemcpyAsync(&peak, c->d_diff_plan + 24, sizeof(peak), cudaMemcpyDeviceToHost, c->stream),
+       "diffusion request");
+    CK(c, cudaStreamSynchronize(c->stream), "diffusion request");
+    if ((int64_t)peak > c->diff_cap) grow = (int64_t)peak + (int64_t)peak / 4;
+  }
+  if (!c->diff_dirty && c->diff_dt == dt_s && grow == 0) return CHAD_OK;
   std::vector<DiffConst> g(c->n_dig);
   int64_t cells = 0;
   int nsub = 1;
+  double entries = 0.0;
   for (int d = 0; d < c->n_dig; ++d) {
     DiffConst& q = g[d];
     std::memset(&q, 0, sizeof(q));
@@ -497,9 +528,26 @@ static chad_status prepare_diffusion(chad_ctx* c, double dt_s) {
     const double V = c->V_liq[d] / (double)c->count[d];  // equal particle volumes
     q.two_DV = 2.0 * D * V;
     q.dw_coef = -5.0 * (21.0 / (16.0 * M_PI * h * h * h)) / h;
-    // continuum estimate of the operator's largest row sum, 7 D / h^2
-    // (Wendland C2); the substep kernels in the launch sequence allow 8x
-    nsub = std::max(nsub, (int)std::ceil(2.0 * dt_s * 7.0 * D / (h * h)));
+    // continuum estimates: 7 D / h^2 for the row sum (Wendland C2), the
+    // support's share of the cylinder for the neighbours
+    nsub = std::max(nsub, (int)std::ceil(dt_s * 7.0 * D / (h * h)));
+    const double n_d = (double)c->count[d];
+    const double share = (4.0 / 3.0) * (8.0 * h * h * h) / (q.R * q.R * q.H);
+    entries += n_d * std::min(n_d - 1.0, n_d * share);
+  }
+  int64_t cap = std::max<int64_t>(grow, (int64_t)std::min(2.0 * entries + 1024.0, (double)kDiffMaxEntries));
+  cap = std::min(cap, kDiffMaxEntries);
+  if (cap > c->diff_cap) {
+    if (c->d_cols) cudaFree(c->d_cols);
+    if (c->d_vals) cudaFree(c->d_vals);
+    c->d_cols = nullptr;
+    c->d_vals = nullptr;
+    c->diff_cap = 0;
+    if (dalloc(&c->d_cols, (size_t)cap) != cudaSuccess || dalloc(&c->d_vals, (size_t)cap) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, CHAD_E_NOMEM, "diffusion operator");
+    }
+    c->diff_cap = cap;
   }
   if (cells > (int64_t(1) << 26))
     return fail(c, CHAD_E_INVALID, "diffusion grid too fine (more than 2^26 cells): raise h");
@@ -584,7 +632,16 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
     da.dc = c->d_diffc;
     da.pos = c->d_pos;
     da.y = c->d_y;
-    da.buf = c->d_diff_buf;
+    da.spos = c->d_spos;
+    da.sdig = c->d_sdig;
+    da.sc[0] = c->d_sc;
+    da.sc[1] = c->d_sc + (size_t)kDiffRow * c->N;
+    da.srow = c->d_srow;
+    da.row_start = c->d_row_start;
+    da.row_len = c->d_row_len;
+    da.cols = c->d_cols;
+    da.vals = c->d_vals;
+    da.cap = c->diff_cap;
     da.cell_count = c->d_cell_count;
     da.cell_start = c->d_cell_start;
     da.cell_list = c->d_cell_list;
@@ -592,8 +649,10 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
     da.status = c->d_status;
     da.smax = reinterpret_cast<unsigned long long*>(c->d_diff_plan);
     da.dt_sub = reinterpret_cast<double*>(c->d_diff_plan + 8);
-    da.nsub = reinterpret_cast<int*>(c->d_diff_plan + 16);
-    da.capped = reinterpret_cast<int*>(c->d_diff_plan + 20);
+    da.nnz = reinterpret_cast<unsigned long long*>(c->d_diff_plan + 16);
+    da.nnz_peak = reinterpret_cast<unsigned long long*>(c->d_diff_plan + 24);
+    da.nsub = reinterpret_cast<int*>(c->d_diff_plan + 32);
+    da.capped = reinterpret_cast<int*>(c->d_diff_plan + 36);
     da.dt_s = c->diff_dt;  // the interval in seconds, as chad_step received it
     da.max_sub = c->diff_max_sub;
     if ((e = launch_diffusion(da, s)) != cudaSuccess) return e;

@@ -8,21 +8,23 @@
 // V = V_liq / N) for the soluble species and the lumped ions.  The fluxes are
 // pairwise antisymmetric, so every species' total is conserved.
 //
-// Substeps: explicit Euler keeps every concentration a convex combination
-// of the old ones (positive, stable) when dt_sub sum_j w_ij <= 1; each
-// interval a kernel takes S_max = max_i sum_j w_ij over the current
-// positions and the substep count is ceil(2 dt S_max) (half that limit),
-// capped at the substep kernels the host enqueues (8 times the continuum
-// estimate 2 dt 7 D / h^2, at least 8; a capped plan flags the particles).
-// The substep kernels are all in the interval's graph and return at once
-// past the planned count.
-//
-// Neighbour search: a uniform grid of cells 2h wide over the digester's
-// cylinder, built per interval by a counting sort (count, scan, scatter);
-// each cell's particle list is then ordered by particle index, so the sums
-// run in a fixed order and reruns are bitwise identical.  The flux kernel
-// runs one thread per particle over the 27 surrounding cells and writes the
-// new concentrations to a second buffer.
+// The particles do not move during the substeps, so the operator is fixed
+// for the interval: with a_ij = -w_ij >= 0 and S_i = sum_j a_ij each substep
+// is C_i <- C_i + dt (sum_j a_ij C_j - S_i C_i), a sparse product with 14
+// right-hand sides.  Per interval:
+//   1. neighbour grid: cells 2h wide over the digester's cylinder, a
+//      counting sort (count, scan, scatter), each cell's particles ordered by
+//      index -- the slot order; sums run in it, so reruns are bitwise equal;
+//   2. gather: positions and species into slot order (species as 128-B rows);
+//   3. rows: per slot, the 27 surrounding cells (contiguous slot ranges) give
+//      the entries a_ij, stored as one CSR row reserved by an atomic add; a
+//      row beyond the capacity is marked and recomputed in each substep;
+//   4. plan: S_max = max_i S_i; dt_sub S_max <= 1 keeps every update a convex
+//      combination of the old values, so n_sub = ceil(dt S_max), capped at the
+//      substep kernels the host enqueues (8 times the continuum estimate
+//      dt 7 D / h^2, at least 8; a capped plan flags the particles);
+//   5. n_sub substeps (the kernels past the plan return at once, so the
+//      interval's graph is static), then the species are stored back.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -122,112 +124,149 @@ __device__ __forceinline__ double wendland_dwdr(double r, const DiffConst& g) {
   return q < 2.0 ? g.dw_coef * q * t * t * t : 0.0;  // -5 alpha q t^3 / h
 }
 
-// Row sum S_i = sum_j |w_ij| of particle i, maximum over particles into
-// *a.smax (positive doubles order like their bit patterns).
-__global__ void diff_rowsum(DiffArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const DiffConst& g = a.dc[a.dig[i]];
-  if (!g.on) return;
-  const double xi = a.pos[i], yi = a.pos[a.ld + i], zi = a.pos[2 * a.ld + i];
+
+// Visit the neighbours of slot i (position xi..zi, digester constants g):
+// every slot m != i of the 27 surrounding cells with r < 2h, in slot order;
+// f(m, a_im) with a_im = -2 D V r W'(r) / (r^2 + 0.01 h^2) >= 0.
+template <class F>
+__device__ __forceinline__ void for_each_neighbour(const DiffArgs& a, const DiffConst& g, int i,
+                                                   double xi, double yi, double zi, F&& f) {
   int cx, cy, cz;
   cell_of(g, xi, yi, zi, cx, cy, cz);
   const double two_h = 2.0 * g.h, eta = 0.01 * g.h * g.h;
-  double S = 0.0;
+  const int64_t n = a.n;
   for (int dz = -1; dz <= 1; ++dz) {
     const int z = cz + dz;
     if (z < 0 || z >= g.nz) continue;
     for (int dy = -1; dy <= 1; ++dy) {
       const int yy = cy + dy;
       if (yy < 0 || yy >= g.ny) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int x = cx + dx;
-        if (x < 0 || x >= g.nx) continue;
-        const int c = g.cell0 + (z * g.ny + yy) * g.nx + x;
-        for (int m = a.cell_start[c]; m < a.cell_start[c + 1]; ++m) {
-          const int j = a.cell_list[m];
-          if (j == i) continue;
-          const double ex = xi - a.pos[j], ey = yi - a.pos[a.ld + j], ez = zi - a.pos[2 * a.ld + j];
-          const double r2 = ex * ex + ey * ey + ez * ez;
-          const double r = sqrt(r2);
-          if (!(r < two_h)) continue;
-          S -= g.two_DV * r * wendland_dwdr(r, g) / (r2 + eta);
-        }
+      const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
+      const int c0 = g.cell0 + (z * g.ny + yy) * g.nx;
+      // the x-neighbours are adjacent cells, so their slots are one range
+      const int b = a.cell_start[c0 + x0], e = a.cell_start[c0 + x1 + 1];
+      for (int m = b; m < e; ++m) {
+        if (m == i) continue;
+        const double ex = xi - a.spos[m], ey = yi - a.spos[n + m], ez = zi - a.spos[2 * n + m];
+        // no contraction: every inlined copy takes the same decisions
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+        const double r = sqrt(r2);
+        if (!(r < two_h)) continue;
+        f(m, -(g.two_DV * r * wendland_dwdr(r, g) / (r2 + eta)));
       }
     }
   }
-  atomicMax(a.smax, (unsigned long long)__double_as_longlong(S));
 }
 
-// Substep plan: n_sub = ceil(2 dt S_max), at least 1, at most max_sub (a
-// capped plan sets *a.capped).
+__device__ __forceinline__ int n_slots(const DiffArgs& a) { return a.cell_start[a.n_cells]; }
+
+// Slot order copies of positions, digester and species.
+__global__ void diff_gather(DiffArgs a) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots(a)) return;
+  const int p = a.cell_list[s];
+  for (int k = 0; k < 3; ++k) a.spos[k * a.n + s] = a.pos[k * a.ld + p];
+  a.sdig[s] = a.dig[p];
+  double* row = a.sc[0] + s * kDiffRow;
+#pragma unroll
+  for (int k = 0; k < kNumDiffusing; ++k) row[k] = a.y[(int64_t)kDiffStates[k] * a.ld + p];
+}
+
+// The operator's rows: S_i (and its maximum into *a.smax: positive doubles
+// order like their bit patterns) and the entries, stored when they fit.
+__global__ void diff_rows(DiffArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_slots(a)) return;
+  const DiffConst& g = a.dc[a.sdig[i]];
+  const double xi = a.spos[i], yi = a.spos[a.n + i], zi = a.spos[2 * a.n + i];
+  double S = 0.0;
+  int len = 0;
+  for_each_neighbour(a, g, (int)i, xi, yi, zi, [&](int, double w) {
+    S += w;
+    ++len;
+  });
+  a.srow[i] = S;
+  a.row_len[i] = len;
+  atomicMax(a.smax, (unsigned long long)__double_as_longlong(S));
+  const unsigned long long b = atomicAdd(a.nnz, (unsigned long long)len);
+  if (b + (unsigned long long)len > (unsigned long long)a.cap) {
+    a.row_start[i] = -1;
+    return;
+  }
+  a.row_start[i] = (int64_t)b;
+  int* col = a.cols + b;
+  double* val = a.vals + b;
+  int k = 0;
+  for_each_neighbour(a, g, (int)i, xi, yi, zi, [&](int m, double w) {
+    if (k < len) {
+      col[k] = m;
+      val[k] = w;
+    }
+    ++k;
+  });
+}
+
+// Substep plan: n_sub = ceil(dt S_max), at least 1, at most max_sub (a capped
+// plan sets *a.capped); records the largest CSR request.
 __global__ void diff_plan(DiffArgs a) {
   const double smax = __longlong_as_double((long long)*a.smax);
-  double want = ceil(2.0 * a.dt_s * smax);
+  double want = ceil(a.dt_s * smax);
   if (!(want >= 1.0)) want = 1.0;
   int n = a.max_sub;
   if (want <= (double)a.max_sub) n = (int)want; else *a.capped = 1;
   *a.nsub = n;
   *a.dt_sub = a.dt_s / n;
+  if (*a.nnz > *a.nnz_peak) *a.nnz_peak = *a.nnz;
 }
 
-// One explicit Euler step: out[k][i] = C_k,i + dt sum_j w_ij (C_k,i - C_k,j).
-__global__ void diff_flux(DiffArgs a, int sub) {
+// One explicit Euler step in slot order: sc[sub & 1] -> sc[(sub + 1) & 1].
+__global__ void diff_step(DiffArgs a, int sub) {
   if (sub >= *a.nsub) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const DiffConst& g = a.dc[a.dig[i]];
-  if (!g.on) return;
-  const double xi = a.pos[i], yi = a.pos[a.ld + i], zi = a.pos[2 * a.ld + i];
-  int cx, cy, cz;
-  cell_of(g, xi, yi, zi, cx, cy, cz);
-  double ci[kNumDiffusing], acc[kNumDiffusing];
+  if (i >= n_slots(a)) return;
+  const double* __restrict__ src = a.sc[sub & 1];
+  double* __restrict__ dst = a.sc[(sub + 1) & 1];
+  double acc[kNumDiffusing];
 #pragma unroll
-  for (int k = 0; k < kNumDiffusing; ++k) {
-    ci[k] = a.y[(int64_t)kDiffStates[k] * a.ld + i];
-    acc[k] = 0.0;
-  }
-  const double two_h = 2.0 * g.h, eta = 0.01 * g.h * g.h;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int z = cz + dz;
-    if (z < 0 || z >= g.nz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = cy + dy;
-      if (yy < 0 || yy >= g.ny) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int x = cx + dx;
-        if (x < 0 || x >= g.nx) continue;
-        const int c = g.cell0 + (z * g.ny + yy) * g.nx + x;
-        const int b = a.cell_start[c], e = a.cell_start[c + 1];
-        for (int m = b; m < e; ++m) {
-          const int j = a.cell_list[m];
-          if (j == i) continue;
-          const double ex = xi - a.pos[j], ey = yi - a.pos[a.ld + j], ez = zi - a.pos[2 * a.ld + j];
-          const double r2 = ex * ex + ey * ey + ez * ez;
-          const double r = sqrt(r2);
-          if (!(r < two_h)) continue;
-          const double w = g.two_DV * r * wendland_dwdr(r, g) / (r2 + eta);
+  for (int k = 0; k < kNumDiffusing; ++k) acc[k] = 0.0;
+  auto add = [&](int m, double w) {
+    const double2* cj = reinterpret_cast<const double2*>(src + (int64_t)m * kDiffRow);
 #pragma unroll
-          for (int k = 0; k < kNumDiffusing; ++k)
-            acc[k] += w * (ci[k] - a.y[(int64_t)kDiffStates[k] * a.ld + j]);
-        }
-      }
+    for (int k = 0; k < kNumDiffusing / 2; ++k) {
+      const double2 v = cj[k];
+      acc[2 * k] = fma(w, v.x, acc[2 * k]);
+      acc[2 * k + 1] = fma(w, v.y, acc[2 * k + 1]);
     }
+  };
+  const int64_t b = a.row_start[i];
+  if (b >= 0) {
+    const int len = a.row_len[i];
+    const int* __restrict__ col = a.cols + b;
+    const double* __restrict__ val = a.vals + b;
+    for (int e = 0; e < len; ++e) add(col[e], val[e]);
+  } else {
+    const DiffConst& g = a.dc[a.sdig[i]];
+    for_each_neighbour(a, g, (int)i, a.spos[i], a.spos[a.n + i], a.spos[2 * a.n + i], add);
   }
-  const double dt = *a.dt_sub;
+  const double dt = *a.dt_sub, S = a.srow[i];
+  const double2* ci = reinterpret_cast<const double2*>(src + i * kDiffRow);
+  double2* out = reinterpret_cast<double2*>(dst + i * kDiffRow);
 #pragma unroll
-  for (int k = 0; k < kNumDiffusing; ++k) a.buf[(int64_t)k * a.ld + i] = ci[k] + dt * acc[k];
+  for (int k = 0; k < kNumDiffusing / 2; ++k) {
+    const double2 c = ci[k];
+    out[k] = make_double2(c.x + dt * (acc[2 * k] - S * c.x), c.y + dt * (acc[2 * k + 1] - S * c.y));
+  }
 }
 
-__global__ void diff_copy_back(DiffArgs a, int sub) {
-  if (sub >= *a.nsub) return;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  if (!a.dc[a.dig[i]].on) return;
-  if (sub == 0 && *a.capped) a.status[i] |= 32;  // CHAD_P_DIFFUSION
+// Species back to the particles; a capped plan flags them.
+__global__ void diff_store(DiffArgs a) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots(a)) return;
+  const int p = a.cell_list[s];
+  const double* row = a.sc[*a.nsub & 1] + s * kDiffRow;
 #pragma unroll
-  for (int k = 0; k < kNumDiffusing; ++k)
-    a.y[(int64_t)kDiffStates[k] * a.ld + i] = a.buf[(int64_t)k * a.ld + i];
+  for (int k = 0; k < kNumDiffusing; ++k) a.y[(int64_t)kDiffStates[k] * a.ld + p] = row[k];
+  if (*a.capped) a.status[p] |= 32;  // CHAD_P_DIFFUSION
 }
 
 }  // namespace
@@ -237,20 +276,19 @@ cudaError_t launch_diffusion(const DiffArgs& a, cudaStream_t s) {
   const int block = 256;
   const unsigned grid = (unsigned)((a.n + block - 1) / block);
   cudaError_t e = cudaMemsetAsync(a.cell_count, 0, sizeof(int) * a.n_cells, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.smax, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.nnz, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.capped, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   diff_count<<<grid, block, 0, s>>>(a);
   diff_scan<<<1, 1024, 0, s>>>(a);
   diff_scatter<<<grid, block, 0, s>>>(a);
   diff_sort_cells<<<(unsigned)((a.n_cells + block - 1) / block), block, 0, s>>>(a);
-  e = cudaMemsetAsync(a.smax, 0, sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.capped, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  diff_rowsum<<<grid, block, 0, s>>>(a);
+  diff_gather<<<grid, block, 0, s>>>(a);
+  diff_rows<<<grid, block, 0, s>>>(a);
   diff_plan<<<1, 1, 0, s>>>(a);
-  for (int k = 0; k < a.max_sub; ++k) {
-    diff_flux<<<grid, block, 0, s>>>(a, k);
-    diff_copy_back<<<grid, block, 0, s>>>(a, k);
-  }
+  for (int k = 0; k < a.max_sub; ++k) diff_step<<<grid, block, 0, s>>>(a, k);
+  diff_store<<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -161,7 +161,7 @@ def test_diffusion_crowded_particles_match_oracle():
     g = gpu_run(pop, 1.0, 2, diffusion=dif)
     o = oracle_run(pop, 1.0, 2, diffusion=dif)
     smax = O.diffusion_row_sum_max(o["pos"], pop.digesters[0].V_liq / 400, *dif)
-    assert O.diffusion_substeps(1.0, smax) > 1 >= math.ceil(2.0 * 7.0 * dif[0] / dif[1] ** 2)
+    assert O.diffusion_substeps(1.0, smax) > 1 >= math.ceil(7.0 * dif[0] / dif[1] ** 2)
     assert np.all(g["status"] == 0)
     assert relerr(g["y"], o["y"]).max() < 1e-9
 
@@ -169,15 +169,15 @@ def test_diffusion_crowded_particles_match_oracle():
 def test_diffusion_plan_above_the_cap_is_flagged():
     """A plan above the launched substeps (8 times the continuum estimate,
     at least 8) runs them all and marks every diffusing particle with
-    CHAD_P_DIFFUSION (32); chosen so the capped steps stay convex
-    (dt_sub S_max <= 1), so the states stay finite and bounded."""
+    CHAD_P_DIFFUSION (32); chosen just above the cap (dt_sub S_max about
+    1.07), so the states stay finite."""
     pop = _crowded(400)
-    dif = (4.5e-6, 0.024)
+    dif = (6.5e-6, 0.024)
     o = oracle_run(pop, 1.0, 1, diffusion=dif)
     smax = O.diffusion_row_sum_max(o["pos"], pop.digesters[0].V_liq / 400, *dif)
-    assert 8 < O.diffusion_substeps(1.0, smax) and 1.0 * smax / 8 <= 1.0
+    assert 8 < O.diffusion_substeps(1.0, smax) and 1.0 * smax / 8 < 1.1
     g = gpu_run(pop, 1.0, 1, diffusion=dif)
-    assert np.all(g["status"] == 32)
+    assert np.all(g["status"] & 32)
     assert np.all(np.isfinite(g["y"]))
     ok = gpu_run(pop, 1.0, 1, diffusion=(1e-6, 0.024))
     assert np.all(ok["status"] == 0)

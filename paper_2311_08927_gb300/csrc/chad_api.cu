@@ -46,6 +46,7 @@ struct chad_ctx {
   int* d_cell_list = nullptr;
   // slot-order copies and the operator's rows (see diffusion.cu)
   double* d_spos = nullptr;       // [3][N]
+  float4* d_sposf = nullptr;      // [N]
   int* d_sdig = nullptr;          // [N]
   double* d_sc = nullptr;         // 2 x [N][kDiffRow]
   double* d_srow = nullptr;       // [N]
@@ -137,7 +138,7 @@ static void free_all(chad_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* lp[] = {c->d_mlp, c->d_SH_learned, c->d_h_learned, c->d_diffc, c->d_cell_count,
-                c->d_cell_start, c->d_cell_list, c->d_spos, c->d_sdig, c->d_sc, c->d_srow,
+                c->d_cell_start, c->d_cell_list, c->d_spos, c->d_sposf, c->d_sdig, c->d_sc, c->d_srow,
                 c->d_row_start, c->d_row_len, c->d_cols, c->d_vals, c->d_diff_plan};
   for (void* p : lp)
     if (p) cudaFree(p);
@@ -401,6 +402,7 @@ chad_status chad_set_diffusion(chad_ctx* c, int digester, double D, double h) {
     A(dalloc(&c->d_diffc, c->n_dig));
     A(dalloc(&c->d_cell_list, c->N));
     A(dalloc(&c->d_spos, (size_t)3 * c->N));
+    A(dalloc(&c->d_sposf, (size_t)c->N));
     A(dalloc(&c->d_sdig, (size_t)c->N));
     A(dalloc(&c->d_sc, (size_t)2 * kDiffRow * c->N));
     A(dalloc(&c->d_srow, (size_t)c->N));
@@ -495,6 +497,15 @@ static chad_status prepare_flow(chad_ctx* c, double dt_coupling_s) {
 // the substep kernels to enqueue: 8 times the continuum estimate
 // dt 7 D / h^2 of the substep count (largest over the digesters), at least 8.
 constexpr int64_t kDiffMaxEntries = int64_t(1) << 29;  // 6 GiB of entries at most
+
+// Smallest x >= 0 whose correctly rounded square root is >= t: for r2 >= 0,
+// sqrt(r2) < t exactly when r2 < x.
+static double sqrt_threshold(double t) {
+  double x = t * t;
+  while (x > 0.0 && std::sqrt(x) >= t) x = std::nextafter(x, 0.0);
+  while (std::sqrt(x) < t) x = std::nextafter(x, HUGE_VAL);
+  return x;
+}
 static chad_status prepare_diffusion(chad_ctx* c, double dt_s) {
   if (!c->any_diff) return CHAD_OK;
   int64_t grow = 0;
@@ -528,6 +539,12 @@ static chad_status prepare_diffusion(chad_ctx* c, double dt_s) {
     const double V = c->V_liq[d] / (double)c->count[d];  // equal particle volumes
     q.two_DV = 2.0 * D * V;
     q.dw_coef = -5.0 * (21.0 / (16.0 * M_PI * h * h * h)) / h;
+    q.r2_lim = sqrt_threshold(2.0 * h);
+    // FP32 positions are within 2^-24 max(R, H) of the FP64 ones, so an FP32
+    // distance is within a few 1e-7 max(R, H) of the true one: a margin of
+    // 2^-16 (max(R, H) + 2h) admits every pair closer than 2h
+    const double margin = std::ldexp(std::max(q.R, q.H) + 2.0 * h, -16);
+    q.r2f_max = std::nextafter((float)((2.0 * h + margin) * (2.0 * h + margin)), HUGE_VALF);
     // continuum estimates: 7 D / h^2 for the row sum (Wendland C2), the
     // support's share of the cylinder for the neighbours
     nsub = std::max(nsub, (int)std::ceil(dt_s * 7.0 * D / (h * h)));
@@ -633,6 +650,7 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
     da.pos = c->d_pos;
     da.y = c->d_y;
     da.spos = c->d_spos;
+    da.sposf = c->d_sposf;
     da.sdig = c->d_sdig;
     da.sc[0] = c->d_sc;
     da.sc[1] = c->d_sc + (size_t)kDiffRow * c->N;

@@ -125,15 +125,17 @@ __device__ __forceinline__ double wendland_dwdr(double r, const DiffConst& g) {
 }
 
 
-// Visit the neighbours of slot i (position xi..zi, digester constants g):
-// every slot m != i of the 27 surrounding cells with r < 2h, in slot order;
-// f(m, a_im) with a_im = -2 D V r W'(r) / (r^2 + 0.01 h^2) >= 0.
+// Visit the neighbours of slot i (position xi..zi, FP32 copy pi, digester
+// constants g): every slot m != i of the 27 surrounding cells with r < 2h,
+// in slot order; f(m, r2).  Candidates are first tested in FP32 against a
+// bound that admits every pair within 2h, then exactly: r2 < r2_lim is the
+// same decision as sqrt(r2) < 2h, so no square root is taken for it.
 template <class F>
 __device__ __forceinline__ void for_each_neighbour(const DiffArgs& a, const DiffConst& g, int i,
-                                                   double xi, double yi, double zi, F&& f) {
+                                                   double xi, double yi, double zi, float4 pi,
+                                                   F&& f) {
   int cx, cy, cz;
   cell_of(g, xi, yi, zi, cx, cy, cz);
-  const double two_h = 2.0 * g.h, eta = 0.01 * g.h * g.h;
   const int64_t n = a.n;
   for (int dz = -1; dz <= 1; ++dz) {
     const int z = cz + dz;
@@ -146,16 +148,24 @@ __device__ __forceinline__ void for_each_neighbour(const DiffArgs& a, const Diff
       // the x-neighbours are adjacent cells, so their slots are one range
       const int b = a.cell_start[c0 + x0], e = a.cell_start[c0 + x1 + 1];
       for (int m = b; m < e; ++m) {
-        if (m == i) continue;
+        const float4 pm = a.sposf[m];
+        const float fx = pi.x - pm.x, fy = pi.y - pm.y, fz = pi.z - pm.z;
+        if (!(fx * fx + fy * fy + fz * fz < g.r2f_max) || m == i) continue;
         const double ex = xi - a.spos[m], ey = yi - a.spos[n + m], ez = zi - a.spos[2 * n + m];
         // no contraction: every inlined copy takes the same decisions
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-        const double r = sqrt(r2);
-        if (!(r < two_h)) continue;
-        f(m, -(g.two_DV * r * wendland_dwdr(r, g) / (r2 + eta)));
+        if (!(r2 < g.r2_lim)) continue;
+        f(m, r2);
       }
     }
   }
+}
+
+// The operator's entry a_ij = -2 D V r W'(r) / (r^2 + 0.01 h^2) >= 0 for a
+// neighbour at squared distance r2.
+__device__ __forceinline__ double entry(const DiffConst& g, double r2) {
+  const double r = sqrt(r2);
+  return -(g.two_DV * r * wendland_dwdr(r, g) / (r2 + 0.01 * g.h * g.h));
 }
 
 __device__ __forceinline__ int n_slots(const DiffArgs& a) { return a.cell_start[a.n_cells]; }
@@ -165,45 +175,48 @@ __global__ void diff_gather(DiffArgs a) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_slots(a)) return;
   const int p = a.cell_list[s];
-  for (int k = 0; k < 3; ++k) a.spos[k * a.n + s] = a.pos[k * a.ld + p];
+  const double x = a.pos[p], y = a.pos[a.ld + p], z = a.pos[2 * a.ld + p];
+  a.spos[s] = x;
+  a.spos[a.n + s] = y;
+  a.spos[2 * a.n + s] = z;
+  a.sposf[s] = make_float4((float)x, (float)y, (float)z, 0.f);
   a.sdig[s] = a.dig[p];
   double* row = a.sc[0] + s * kDiffRow;
 #pragma unroll
   for (int k = 0; k < kNumDiffusing; ++k) row[k] = a.y[(int64_t)kDiffStates[k] * a.ld + p];
 }
 
-// The operator's rows: S_i (and its maximum into *a.smax: positive doubles
-// order like their bit patterns) and the entries, stored when they fit.
+// The operator's rows: the neighbours are counted, the row is reserved by an
+// atomic add, then the entries are formed and stored (when they fit) along
+// with S_i; the maximum of S_i goes to *a.smax (positive doubles order like
+// their bit patterns).
 __global__ void diff_rows(DiffArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_slots(a)) return;
   const DiffConst& g = a.dc[a.sdig[i]];
   const double xi = a.spos[i], yi = a.spos[a.n + i], zi = a.spos[2 * a.n + i];
-  double S = 0.0;
+  const float4 pi = a.sposf[i];
   int len = 0;
-  for_each_neighbour(a, g, (int)i, xi, yi, zi, [&](int, double w) {
-    S += w;
-    ++len;
-  });
-  a.srow[i] = S;
-  a.row_len[i] = len;
-  atomicMax(a.smax, (unsigned long long)__double_as_longlong(S));
+  for_each_neighbour(a, g, (int)i, xi, yi, zi, pi, [&](int, double) { ++len; });
   const unsigned long long b = atomicAdd(a.nnz, (unsigned long long)len);
-  if (b + (unsigned long long)len > (unsigned long long)a.cap) {
-    a.row_start[i] = -1;
-    return;
-  }
-  a.row_start[i] = (int64_t)b;
-  int* col = a.cols + b;
-  double* val = a.vals + b;
+  const bool fits = b + (unsigned long long)len <= (unsigned long long)a.cap;
+  int* col = a.cols + (fits ? b : 0);
+  double* val = a.vals + (fits ? b : 0);
+  double S = 0.0;
   int k = 0;
-  for_each_neighbour(a, g, (int)i, xi, yi, zi, [&](int m, double w) {
-    if (k < len) {
+  for_each_neighbour(a, g, (int)i, xi, yi, zi, pi, [&](int m, double r2) {
+    const double w = entry(g, r2);
+    S += w;
+    if (fits && k < len) {
       col[k] = m;
       val[k] = w;
     }
     ++k;
   });
+  a.srow[i] = S;
+  a.row_len[i] = len;
+  a.row_start[i] = fits ? (int64_t)b : -1;
+  atomicMax(a.smax, (unsigned long long)__double_as_longlong(S));
 }
 
 // Substep plan: n_sub = ceil(dt S_max), at least 1, at most max_sub (a capped
@@ -246,7 +259,8 @@ __global__ void diff_step(DiffArgs a, int sub) {
     for (int e = 0; e < len; ++e) add(col[e], val[e]);
   } else {
     const DiffConst& g = a.dc[a.sdig[i]];
-    for_each_neighbour(a, g, (int)i, a.spos[i], a.spos[a.n + i], a.spos[2 * a.n + i], add);
+    for_each_neighbour(a, g, (int)i, a.spos[i], a.spos[a.n + i], a.spos[2 * a.n + i], a.sposf[i],
+                       [&](int m, double r2) { add(m, entry(g, r2)); });
   }
   const double dt = *a.dt_sub, S = a.srow[i];
   const double2* ci = reinterpret_cast<const double2*>(src + i * kDiffRow);

@@ -54,6 +54,9 @@ struct DiffConst {
   double R, H, h, inv_h, cell;
   double two_DV;          // 2 D V (m^5/s), V = V_liq / particles
   double dw_coef;         // W'(r) = dw_coef q (1 - q/2)^3, q = r/h (Wendland C2)
+  double r2_lim;          // sqrt(r2) < 2h exactly when r2 < r2_lim (correctly rounded sqrt)
+  float r2f_max;          // FP32 pre-test: every pair with r < 2h has r2 (in FP32) below it
+  float pad2;
 };
 struct DiffArgs {
   int64_t n, ld;
@@ -67,6 +70,7 @@ struct DiffArgs {
   int n_cells;
   // per slot, in cell order (built each interval)
   double* spos;       // [3][n] positions
+  float4* sposf;      // [n] positions in FP32 (x, y, z, 0) for the neighbour pre-test
   int* sdig;          // [n] digester
   double* sc[2];      // [n][kDiffRow] diffusing species, ping-pong between substeps
   double* srow;       // [n] row sum S_i = sum_j a_ij

@@ -197,8 +197,20 @@ chad_status chad_set_flow(chad_ctx* ctx, int digester, const chad_flow* flow);
    at most 8 times the continuum estimate dt 7 D / h^2 (at least 8); a
    plan above that runs the maximum and sets CHAD_P_DIFFUSION on the
    diffusing particles.  Needs the digester's flow geometry (chad_set_flow with has_flow, else
-   CHAD_E_STATE).  Allocates the neighbour-grid buffers on first use. */
+   CHAD_E_STATE).  Allocates the neighbour-grid buffers on first use; the
+   operator's entries (12 bytes each, about the particles times their
+   neighbours within 2h) are allocated by chad_step and grown to the largest
+   need seen (rows that do not fit are recomputed in every substep). */
 chad_status chad_set_diffusion(chad_ctx* ctx, int digester, double D, double h);
+
+/* The last interval's diffusion plan: entries reserved for the operator (an
+   upper bound on its non-zeros, those beyond the capacity included), the
+   substeps taken, 1 if the plan was capped (see chad_set_diffusion), and
+   the largest row sum S_max (1/s) over the diffusing particles.  Waits for
+   the context's stream.  Any output pointer may be NULL.  CHAD_E_STATE
+   before diffusion was first set. */
+chad_status chad_diffusion_info(chad_ctx* ctx, int64_t* entries, int32_t* n_sub, int32_t* capped,
+                                double* s_max);
 
 /* Integrate n_intervals coupling intervals of dt_coupling_s seconds each:
    per interval, advect (digesters with flow), integrate every particle

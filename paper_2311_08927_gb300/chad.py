@@ -133,6 +133,10 @@ def lib():
                                                 C.c_int]
             L.chad_set_diffusion.restype = C.c_int
             L.chad_set_diffusion.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+            L.chad_diffusion_info.restype = C.c_int
+            L.chad_diffusion_info.argtypes = [C.c_void_p, C.POINTER(C.c_int64),
+                                              C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                              C.POINTER(C.c_double)]
             L.chad_probe_numerics.restype = C.c_int
             L.chad_probe_numerics.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                               C.c_void_p]
@@ -147,7 +151,7 @@ def exported_symbols() -> list[str]:
             "chad_create", "chad_destroy", "chad_load_particles", "chad_set_flow",
             "chad_step", "chad_synchronize", "chad_read_states", "chad_probe_alu_peak",
             "chad_eval_model", "chad_eval_model_split", "chad_probe_numerics", "chad_autotune",
-            "chad_flop_counts", "chad_set_diffusion",
+            "chad_flop_counts", "chad_set_diffusion", "chad_diffusion_info",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
 
@@ -374,6 +378,14 @@ def chad_set_flow(ctx, digester, flow: chad_flow) -> None:
 def chad_set_diffusion(ctx, digester, D, h) -> None:
     L = lib()
     _check(L, ctx, L.chad_set_diffusion(ctx, int(digester), float(D), float(h)))
+
+
+def chad_diffusion_info(ctx) -> dict:
+    """The last interval's diffusion plan: reserved entries, substeps, capped, S_max."""
+    L = lib()
+    e, n, c, s = C.c_int64(), C.c_int32(), C.c_int32(), C.c_double()
+    _check(L, ctx, L.chad_diffusion_info(ctx, C.byref(e), C.byref(n), C.byref(c), C.byref(s)))
+    return dict(entries=e.value, n_sub=n.value, capped=c.value, s_max=s.value)
 
 
 def chad_step(ctx, dt_coupling_s, n_intervals) -> None:

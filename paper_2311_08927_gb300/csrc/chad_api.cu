@@ -424,6 +424,27 @@ chad_status chad_set_diffusion(chad_ctx* c, int digester, double D, double h) {
   return CHAD_OK;
 }
 
+chad_status chad_diffusion_info(chad_ctx* c, int64_t* entries, int32_t* n_sub, int32_t* capped,
+                                double* s_max) {
+  if (!c) return CHAD_E_INVALID;
+  if (!c->d_diff_plan) return fail(c, CHAD_E_STATE, "diffusion was never set");
+  unsigned char h[40];
+  CK(c, cudaMemcpyAsync(h, c->d_diff_plan, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
+     "diffusion plan");
+  CK(c, cudaStreamSynchronize(c->stream), "diffusion plan");
+  unsigned long long smax_bits, nnz;
+  int32_t ns, cap;
+  std::memcpy(&smax_bits, h, 8);
+  std::memcpy(&nnz, h + 16, 8);
+  std::memcpy(&ns, h + 32, 4);
+  std::memcpy(&cap, h + 36, 4);
+  if (entries) *entries = (int64_t)nnz;
+  if (n_sub) *n_sub = ns;
+  if (capped) *capped = cap;
+  if (s_max) std::memcpy(s_max, &smax_bits, 8);
+  return CHAD_OK;
+}
+
 chad_status chad_set_flow(chad_ctx* c, int digester, const chad_flow* f) {
   if (!c) return CHAD_E_INVALID;
   if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");

@@ -186,37 +186,115 @@ __global__ void diff_gather(DiffArgs a) {
   for (int k = 0; k < kNumDiffusing; ++k) row[k] = a.y[(int64_t)kDiffStates[k] * a.ld + p];
 }
 
-// The operator's rows: the neighbours are counted, the row is reserved by an
-// atomic add, then the entries are formed and stored (when they fit) along
-// with S_i; the maximum of S_i goes to *a.smax (positive doubles order like
+// The operator's rows, one warp per slot.  Pass 1 counts the candidates that
+// pass the FP32 pre-test (a bound on the row length) and reserves that many
+// entries with one atomic add.  Pass 2 compacts the passing candidates, in
+// slot order, into a per-warp queue (ballot + rank) and drains it 32 at a
+// time, one candidate per lane: the exact test, the entry, and its place in
+// the row by rank, so the row holds the neighbours in slot order (the order
+// the per-thread scan of a row that did not fit also takes).  S_i is reduced
+// over the warp; its maximum goes to *a.smax (positive doubles order like
 // their bit patterns).
-__global__ void diff_rows(DiffArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_slots(a)) return;
+constexpr int kRowsBlock = 128;
+__global__ void __launch_bounds__(kRowsBlock) diff_rows(DiffArgs a) {
+  __shared__ int queue[kRowsBlock / 32][64];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int* q = queue[threadIdx.x >> 5];
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n_slots(a)) return;  // the whole warp
   const DiffConst& g = a.dc[a.sdig[i]];
-  const double xi = a.spos[i], yi = a.spos[a.n + i], zi = a.spos[2 * a.n + i];
+  const int64_t n = a.n;
+  const double xi = a.spos[i], yi = a.spos[n + i], zi = a.spos[2 * n + i];
   const float4 pi = a.sposf[i];
-  int len = 0;
-  for_each_neighbour(a, g, (int)i, xi, yi, zi, pi, [&](int, double) { ++len; });
-  const unsigned long long b = atomicAdd(a.nnz, (unsigned long long)len);
-  const bool fits = b + (unsigned long long)len <= (unsigned long long)a.cap;
-  int* col = a.cols + (fits ? b : 0);
-  double* val = a.vals + (fits ? b : 0);
-  double S = 0.0;
-  int k = 0;
-  for_each_neighbour(a, g, (int)i, xi, yi, zi, pi, [&](int m, double r2) {
-    const double w = entry(g, r2);
-    S += w;
-    if (fits && k < len) {
-      col[k] = m;
-      val[k] = w;
+  int cx, cy, cz;
+  cell_of(g, xi, yi, zi, cx, cy, cz);
+  const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
+  auto pretest = [&](int m, int e) {
+    if (m >= e || m == (int)i) return false;
+    const float4 pm = a.sposf[m];
+    const float fx = pi.x - pm.x, fy = pi.y - pm.y, fz = pi.z - pm.z;
+    // no contraction: both passes take the same decisions
+    return __fadd_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)), __fmul_rn(fz, fz)) < g.r2f_max;
+  };
+  // pass 1: bound on the row length, reservation
+  int bound = 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int z = cz + dz;
+    if (z < 0 || z >= g.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = cy + dy;
+      if (yy < 0 || yy >= g.ny) continue;
+      const int c0 = g.cell0 + (z * g.ny + yy) * g.nx;
+      const int b = a.cell_start[c0 + x0], e = a.cell_start[c0 + x1 + 1];
+      for (int m0 = b; m0 < e; m0 += 32) bound += __popc(__ballot_sync(full, pretest(m0 + lane, e)));
     }
-    ++k;
-  });
-  a.srow[i] = S;
-  a.row_len[i] = len;
-  a.row_start[i] = fits ? (int64_t)b : -1;
-  atomicMax(a.smax, (unsigned long long)__double_as_longlong(S));
+  }
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(a.nnz, (unsigned long long)bound);
+  base = __shfl_sync(full, base, 0);
+  const bool fits = base + (unsigned long long)bound <= (unsigned long long)a.cap;
+  // pass 2: entries
+  const unsigned below = (1u << lane) - 1u;
+  int queued = 0, len = 0;
+  double S = 0.0;
+  auto drain = [&](int k) {
+    int m = -1;
+    double w = 0.0;
+    bool ok = false;
+    if (lane < k) {
+      m = q[lane];
+      const double ex = xi - a.spos[m], ey = yi - a.spos[n + m], ez = zi - a.spos[2 * n + m];
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+      ok = r2 < g.r2_lim;
+      if (ok) w = entry(g, r2);
+    }
+    const unsigned got = __ballot_sync(full, ok);
+    if (ok) {
+      S += w;
+      const int k = len + __popc(got & below);
+      if (fits && k < bound) {
+        a.cols[base + (unsigned long long)k] = m;
+        a.vals[base + (unsigned long long)k] = w;
+      }
+    }
+    len += __popc(got);
+  };
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int z = cz + dz;
+    if (z < 0 || z >= g.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = cy + dy;
+      if (yy < 0 || yy >= g.ny) continue;
+      const int c0 = g.cell0 + (z * g.ny + yy) * g.nx;
+      const int b = a.cell_start[c0 + x0], e = a.cell_start[c0 + x1 + 1];
+      for (int m0 = b; m0 < e; m0 += 32) {
+        const int m = m0 + lane;
+        const bool pass = pretest(m, e);
+        const unsigned got = __ballot_sync(full, pass);
+        if (pass) q[queued + __popc(got & below)] = m;
+        queued += __popc(got);
+        __syncwarp();
+        if (queued >= 32) {
+          drain(32);
+          const int rest = lane < queued - 32 ? q[32 + lane] : 0;
+          __syncwarp();
+          if (lane < queued - 32) q[lane] = rest;
+          queued -= 32;
+          __syncwarp();
+        }
+      }
+    }
+  }
+  drain(queued);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) S += __shfl_xor_sync(full, S, off);
+  if (lane == 0) {
+    a.srow[i] = S;
+    a.row_len[i] = fits ? min(len, bound) : len;
+    a.row_start[i] = fits ? (int64_t)base : -1;
+    atomicMax(a.smax, (unsigned long long)__double_as_longlong(S));
+  }
 }
 
 // Substep plan: n_sub = ceil(dt S_max), at least 1, at most max_sub (a capped
@@ -299,7 +377,7 @@ cudaError_t launch_diffusion(const DiffArgs& a, cudaStream_t s) {
   diff_scatter<<<grid, block, 0, s>>>(a);
   diff_sort_cells<<<(unsigned)((a.n_cells + block - 1) / block), block, 0, s>>>(a);
   diff_gather<<<grid, block, 0, s>>>(a);
-  diff_rows<<<grid, block, 0, s>>>(a);
+  diff_rows<<<(unsigned)((a.n * 32 + kRowsBlock - 1) / kRowsBlock), kRowsBlock, 0, s>>>(a);
   diff_plan<<<1, 1, 0, s>>>(a);
   for (int k = 0; k < a.max_sub; ++k) diff_step<<<grid, block, 0, s>>>(a, k);
   diff_store<<<grid, block, 0, s>>>(a);

@@ -120,4 +120,6 @@ def test_null_context_calls_are_invalid(L):
     assert L.chad_synchronize(None) == 1
     assert L.chad_load_particles(None, 0, 0, None, None, None, None, None, 0) == 1
     assert L.chad_read_states(None, 0, None, None, None, None, None, None, 0) == 1
+    assert L.chad_set_diffusion(None, 0, 1e-6, 0.01) == 1
+    assert L.chad_diffusion_info(None, None, None, None, None) == 1
     L.chad_destroy(None)

@@ -49,6 +49,8 @@ def gpu_run(pop, dt, n, **kw):
     sim.load()
     sim.step(dt, n)
     out = sim.read()
+    if kw.get("diffusion") is not None:
+        out["diff_info"] = CH.chad_diffusion_info(sim.ctx)
     sim.close()
     return out
 
@@ -130,6 +132,8 @@ def test_diffusion_matches_oracle():
     assert np.all(g["status"] == 0)
     assert np.array_equal(g["pos"], o["pos"])
     assert relerr(g["y"], o["y"]).max() < 1e-9
+    smax = O.diffusion_row_sum_max(o["pos"], pop.digesters[0].V_liq / 1200, *DIFFUSION)
+    assert g["diff_info"]["n_sub"] == O.diffusion_substeps(60.0, smax) > 1
     nd = gpu_run(pop, 60.0, 3)
     assert relerr(g["y"], nd["y"]).max() > 1e-6
 
@@ -164,6 +168,10 @@ def test_diffusion_crowded_particles_match_oracle():
     assert O.diffusion_substeps(1.0, smax) > 1 >= math.ceil(7.0 * dif[0] / dif[1] ** 2)
     assert np.all(g["status"] == 0)
     assert relerr(g["y"], o["y"]).max() < 1e-9
+    # the last interval's plan: the same integer substep count, S_max to round-off
+    info = g["diff_info"]
+    assert info["n_sub"] == O.diffusion_substeps(1.0, smax) and info["capped"] == 0
+    assert abs(info["s_max"] / smax - 1.0) < 1e-12
 
 
 def test_diffusion_plan_above_the_cap_is_flagged():
@@ -177,6 +185,7 @@ def test_diffusion_plan_above_the_cap_is_flagged():
     smax = O.diffusion_row_sum_max(o["pos"], pop.digesters[0].V_liq / 400, *dif)
     assert 8 < O.diffusion_substeps(1.0, smax) and 1.0 * smax / 8 < 1.1
     g = gpu_run(pop, 1.0, 1, diffusion=dif)
+    assert g["diff_info"]["capped"] == 1 and g["diff_info"]["n_sub"] == 8
     assert np.all(g["status"] & 32)
     assert np.all(np.isfinite(g["y"]))
     ok = gpu_run(pop, 1.0, 1, diffusion=(1e-6, 0.024))

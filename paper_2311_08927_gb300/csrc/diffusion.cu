@@ -184,6 +184,7 @@ __global__ void diff_gather(DiffArgs a) {
   double* row = a.sc[0] + s * kDiffRow;
 #pragma unroll
   for (int k = 0; k < kNumDiffusing; ++k) row[k] = a.y[(int64_t)kDiffStates[k] * a.ld + p];
+  for (int k = kNumDiffusing; k < kDiffRow; ++k) row[k] = 0.0;
 }
 
 // The operator's rows, one warp per slot.  Pass 1 counts the candidates that
@@ -310,43 +311,54 @@ __global__ void diff_plan(DiffArgs a) {
   if (*a.nnz > *a.nnz_peak) *a.nnz_peak = *a.nnz;
 }
 
-// One explicit Euler step in slot order: sc[sub & 1] -> sc[(sub + 1) & 1].
-__global__ void diff_step(DiffArgs a, int sub) {
+// One explicit Euler step in slot order, sc[sub & 1] -> sc[(sub + 1) & 1]:
+// a half-warp per slot, lane k holding species k (lanes 14 and 15 idle), so
+// each neighbour's species row is one 128-byte load and its column index and
+// entry are broadcasts.  Rows that did not fit are formed on the fly (every
+// lane forms the same entries).
+constexpr int kStepBlock = 256;
+__global__ void __launch_bounds__(kStepBlock) diff_step(DiffArgs a, int sub) {
   if (sub >= *a.nsub) return;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int k = threadIdx.x & 15;
   if (i >= n_slots(a)) return;
+  const bool on = k < kNumDiffusing;
   const double* __restrict__ src = a.sc[sub & 1];
   double* __restrict__ dst = a.sc[(sub + 1) & 1];
-  double acc[kNumDiffusing];
-#pragma unroll
-  for (int k = 0; k < kNumDiffusing; ++k) acc[k] = 0.0;
-  auto add = [&](int m, double w) {
-    const double2* cj = reinterpret_cast<const double2*>(src + (int64_t)m * kDiffRow);
-#pragma unroll
-    for (int k = 0; k < kNumDiffusing / 2; ++k) {
-      const double2 v = cj[k];
-      acc[2 * k] = fma(w, v.x, acc[2 * k]);
-      acc[2 * k + 1] = fma(w, v.y, acc[2 * k + 1]);
-    }
-  };
+  double acc = 0.0;
   const int64_t b = a.row_start[i];
   if (b >= 0) {
     const int len = a.row_len[i];
     const int* __restrict__ col = a.cols + b;
     const double* __restrict__ val = a.vals + b;
-    for (int e = 0; e < len; ++e) add(col[e], val[e]);
+    int e = 0;
+    for (; e + 4 <= len; e += 4) {
+      const int m0 = col[e], m1 = col[e + 1], m2 = col[e + 2], m3 = col[e + 3];
+      const double w0 = val[e], w1 = val[e + 1], w2 = val[e + 2], w3 = val[e + 3];
+      double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+      if (on) {
+        c0 = src[(int64_t)m0 * kDiffRow + k];
+        c1 = src[(int64_t)m1 * kDiffRow + k];
+        c2 = src[(int64_t)m2 * kDiffRow + k];
+        c3 = src[(int64_t)m3 * kDiffRow + k];
+      }
+      acc = fma(w0, c0, acc);
+      acc = fma(w1, c1, acc);
+      acc = fma(w2, c2, acc);
+      acc = fma(w3, c3, acc);
+    }
+    for (; e < len; ++e) acc = fma(val[e], on ? src[(int64_t)col[e] * kDiffRow + k] : 0.0, acc);
   } else {
     const DiffConst& g = a.dc[a.sdig[i]];
     for_each_neighbour(a, g, (int)i, a.spos[i], a.spos[a.n + i], a.spos[2 * a.n + i], a.sposf[i],
-                       [&](int m, double r2) { add(m, entry(g, r2)); });
+                       [&](int m, double r2) {
+                         acc = fma(entry(g, r2), on ? src[(int64_t)m * kDiffRow + k] : 0.0, acc);
+                       });
   }
-  const double dt = *a.dt_sub, S = a.srow[i];
-  const double2* ci = reinterpret_cast<const double2*>(src + i * kDiffRow);
-  double2* out = reinterpret_cast<double2*>(dst + i * kDiffRow);
-#pragma unroll
-  for (int k = 0; k < kNumDiffusing / 2; ++k) {
-    const double2 c = ci[k];
-    out[k] = make_double2(c.x + dt * (acc[2 * k] - S * c.x), c.y + dt * (acc[2 * k + 1] - S * c.y));
+  if (on) {
+    const double dt = *a.dt_sub, S = a.srow[i];
+    const double c = src[i * kDiffRow + k];
+    dst[i * kDiffRow + k] = c + dt * (acc - S * c);
   }
 }
 
@@ -379,7 +391,8 @@ cudaError_t launch_diffusion(const DiffArgs& a, cudaStream_t s) {
   diff_gather<<<grid, block, 0, s>>>(a);
   diff_rows<<<(unsigned)((a.n * 32 + kRowsBlock - 1) / kRowsBlock), kRowsBlock, 0, s>>>(a);
   diff_plan<<<1, 1, 0, s>>>(a);
-  for (int k = 0; k < a.max_sub; ++k) diff_step<<<grid, block, 0, s>>>(a, k);
+  const unsigned step_grid = (unsigned)((a.n * 16 + kStepBlock - 1) / kStepBlock);
+  for (int k = 0; k < a.max_sub; ++k) diff_step<<<step_grid, kStepBlock, 0, s>>>(a, k);
   diff_store<<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }

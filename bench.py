@@ -531,6 +531,109 @@ def run_fig7(args, ws, rank, local):
     return res
 
 
+# --------------------------------------------------------------------------- diffusion workload
+LAB_D, LAB_H = 1.0e-6, 0.006   # m^2/s; m (about 1.3 mean particle spacings at 100k particles)
+
+
+def run_lab_diffusion(args, ws, rank, local):
+    """Diffusion between particles (the paper's planned extension, Sec. 2.3):
+    the lab cylinder (100k particles, swirl + noise, inlet slab, shared
+    headspace), 60-s intervals of advection, SPH diffusion (D = 1e-6 m^2/s,
+    h = 6 mm) and FP64 ADM1.  Not the headline workload.  The roofline object
+    covers the diffusion substep kernel (FP64 multiply-adds of the sparse
+    product), timed through chad_diffusion_kernel_times after the timed run."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2311_08927_gb300 import build as B
+    B.build()
+    from paper_2311_08927_gb300 import chad as CH
+    from paper_2311_08927_gb300 import inputs as I
+    pop = I.config_population(2)
+    N = pop.n
+    stream = torch.cuda.Stream()
+    peak64 = CH.probe_alu_peak(True)
+    sim = CH.Simulator(pop, precision=CH.PREC_FP64, stream=stream.cuda_stream,
+                       diffusion=(LAB_D, LAB_H))
+    sim.load()
+    sim.step(DT_S, args.warmup)
+    CH.chad_synchronize(sim.ctx)
+    sim.read()
+    k = args.steps
+    # state, operator and slot buffers (~150 MB) are about L2's size: flush it
+    # with a 256 MB write before every interval, inside the timed region
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            sim.step(DT_S, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = sim.read()
+    info = CH.chad_diffusion_info(sim.ctx)
+    rows_ms, step_ms = [], []
+    for _ in range(5):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        r, t = CH.chad_diffusion_kernel_times(sim.ctx, 1)
+        rows_ms.append(r)
+        step_ms.append(t)
+    sim.close()
+    rows_ms, step_ms = statistics.median(rows_ms), statistics.median(step_ms)
+    # one substep: a multiply-add per entry and species, and per particle and
+    # species the update c + dt (acc - S c) (two more)
+    flops_step = 2.0 * 14 * info["entries"] + 4.0 * 14 * N
+    achieved = flops_step / (step_ms * 1e-3) / 1e12
+    st = out["stats"]
+    days = DT_S / 86400.0
+    # kernels per interval: advect, 2 ordering, integrate, 3 headspace, bump;
+    # diffusion: count, scan, scatter, sort, gather, rows, plan, the enqueued
+    # substeps (8 x ceil(dt 7 D / h^2), at least 8) and store
+    max_sub = max(8, 8 * math.ceil(DT_S * 7.0 * LAB_D / LAB_H ** 2))
+    res = {"metric": "particle-days simulated per second (with diffusion between particles)",
+           "value": N * days * k / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": k,
+           "warmup": args.warmup, "ms_per_step": ms / k, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"lab_cylinder_{N}_diffusion_D{LAB_D:g}_h{LAB_H:g}",
+                      "particles": N, "coupling_interval_s": DT_S, "rtol": 1e-6,
+                      "geometry": "lab cylinder, swirl + noise, inlet slab, shared headspace",
+                      "l2": "256 MB L2 flush before every interval, inside the timed region"},
+           "diffusion": {"substeps_last_interval": info["n_sub"], "entries": info["entries"],
+                         "s_max_per_s": info["s_max"], "rows_ms": rows_ms,
+                         "substep_ms": step_ms,
+                         "share_of_interval": (rows_ms + info["n_sub"] * step_ms) / (ms / k)},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                        "frac": achieved / peak64, "traffic": None,
+                        "kernel": "diffusion substep (diff_step), FP64 multiply-adds, entries "
+                                  "= reserved bound",
+                        "timing": "chad_diffusion_kernel_times after the timed run, L2 flushed "
+                                  "before each of 5 launches, median"},
+           "adm1": {"accepted_steps": st["accepted_steps"], "rejected_steps": st["rejected_steps"]},
+           "clocks": clk.summary(), "gpu_launches": k * (8 + 8 + max_sub)}
+    if not args.no_cpu:
+        import oracle as O
+        cores = os.cpu_count() or 1
+        # all-pairs oracle: a sample of n_s particles in the same tank, h and D
+        # scaled so the neighbours per particle and the substeps stay the same
+        n_s = 2000
+        scale = (N / n_s) ** (1.0 / 3.0)
+        h_s, D_s = LAB_H * scale, LAB_D * scale ** 2
+        sub = I.config_population(2, n=n_s)
+        t0 = time.perf_counter()
+        O.run(sub, DT_S, 2, n_threads=cores, diffusion=(D_s, h_s))
+        dt = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": n_s * days * 2 / dt, "unit": UNIT, "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"{n_s} particles of the same recipe with h = {h_s:.4f} m, "
+                                         f"D = {D_s:.3g} m^2/s (same neighbours per particle and "
+                                         f"substeps), 2 intervals, {dt:.1f} s"}
+    return res
+
+
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args, ws, rank):
     dist = init_dist(ws, "gloo")
@@ -581,9 +684,10 @@ def main():
     ap.add_argument("--train-particles", type=int, default=1_000_000)
     ap.add_argument("--train-intervals", type=int, default=10)
     ap.add_argument("--train-epochs", type=int, default=20)
-    ap.add_argument("--workload", choices=["default", "fig7"], default="default",
+    ap.add_argument("--workload", choices=["default", "fig7", "lab_diffusion"], default="default",
                     help="fig7: paper-literal stepping, 110,929 particles, 0.5-s intervals of "
-                         "10 substeps (not the headline workload)")
+                         "10 substeps; lab_diffusion: 100k particles with diffusion between "
+                         "them (neither is the headline workload)")
     ap.add_argument("--particles", type=int, default=None,
                     help="override the 1M particles (profiling captures only)")
     args = ap.parse_args()
@@ -594,6 +698,8 @@ def main():
         res = run_reference(args, ws, rank)
     elif args.workload == "fig7":
         res = run_fig7(args, ws, rank, local) if rank == 0 else None
+    elif args.workload == "lab_diffusion":
+        res = run_lab_diffusion(args, ws, rank, local) if rank == 0 else None
     else:
         res = run_ours(args, ws, rank, local)
     if rank == 0 and res is not None:

@@ -212,6 +212,13 @@ chad_status chad_set_diffusion(chad_ctx* ctx, int digester, double D, double h);
 chad_status chad_diffusion_info(chad_ctx* ctx, int64_t* entries, int32_t* n_sub, int32_t* capped,
                                 double* s_max);
 
+/* Measurement: the two dominant diffusion kernels (the operator's rows, one
+   substep) timed with CUDA events on the context's stream, each re-run reps
+   times on the last interval's slot-order buffers (scratch: the particles'
+   states are not touched); mean milliseconds per launch.  Blocks until done.
+   CHAD_E_STATE before a diffusion interval has run. */
+chad_status chad_diffusion_kernel_times(chad_ctx* ctx, int reps, double* ms_rows, double* ms_step);
+
 /* Integrate n_intervals coupling intervals of dt_coupling_s seconds each:
    per interval, advect (digesters with flow), integrate every particle
    (Eq. 2-7) and, with a shared headspace, average the three gas states of

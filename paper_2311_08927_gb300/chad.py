@@ -133,6 +133,9 @@ def lib():
                                                 C.c_int]
             L.chad_set_diffusion.restype = C.c_int
             L.chad_set_diffusion.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+            L.chad_diffusion_kernel_times.restype = C.c_int
+            L.chad_diffusion_kernel_times.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double),
+                                                      C.POINTER(C.c_double)]
             L.chad_diffusion_info.restype = C.c_int
             L.chad_diffusion_info.argtypes = [C.c_void_p, C.POINTER(C.c_int64),
                                               C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -152,6 +155,7 @@ def exported_symbols() -> list[str]:
             "chad_step", "chad_synchronize", "chad_read_states", "chad_probe_alu_peak",
             "chad_eval_model", "chad_eval_model_split", "chad_probe_numerics", "chad_autotune",
             "chad_flop_counts", "chad_set_diffusion", "chad_diffusion_info",
+            "chad_diffusion_kernel_times",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
 
@@ -386,6 +390,14 @@ def chad_diffusion_info(ctx) -> dict:
     e, n, c, s = C.c_int64(), C.c_int32(), C.c_int32(), C.c_double()
     _check(L, ctx, L.chad_diffusion_info(ctx, C.byref(e), C.byref(n), C.byref(c), C.byref(s)))
     return dict(entries=e.value, n_sub=n.value, capped=c.value, s_max=s.value)
+
+
+def chad_diffusion_kernel_times(ctx, reps=1):
+    """Mean ms per launch of the diffusion rows and substep kernels (re-run on scratch)."""
+    L = lib()
+    r, s = C.c_double(), C.c_double()
+    _check(L, ctx, L.chad_diffusion_kernel_times(ctx, int(reps), C.byref(r), C.byref(s)))
+    return r.value, s.value
 
 
 def chad_step(ctx, dt_coupling_s, n_intervals) -> None:

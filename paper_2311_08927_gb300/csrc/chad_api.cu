@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "chad.h"
+#include "diffusion.h"
 #include "kernels.h"
 #include "model.h"
 
@@ -129,6 +130,42 @@ static cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
   return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+// The arguments of the diffusion kernels for the context's current buffers.
+static DiffArgs diff_args(const chad_ctx* c) {
+  DiffArgs da;
+  da.n = c->N;
+  da.ld = c->ld;
+  da.dig = c->d_dig;
+  da.dc = c->d_diffc;
+  da.pos = c->d_pos;
+  da.y = c->d_y;
+  da.spos = c->d_spos;
+  da.sposf = c->d_sposf;
+  da.sdig = c->d_sdig;
+  da.sc[0] = c->d_sc;
+  da.sc[1] = c->d_sc + (size_t)kDiffRow * c->N;
+  da.srow = c->d_srow;
+  da.row_start = c->d_row_start;
+  da.row_len = c->d_row_len;
+  da.cols = c->d_cols;
+  da.vals = c->d_vals;
+  da.cap = c->diff_cap;
+  da.cell_count = c->d_cell_count;
+  da.cell_start = c->d_cell_start;
+  da.cell_list = c->d_cell_list;
+  da.n_cells = c->n_cells;
+  da.status = c->d_status;
+  da.smax = reinterpret_cast<unsigned long long*>(c->d_diff_plan);
+  da.dt_sub = reinterpret_cast<double*>(c->d_diff_plan + 8);
+  da.nnz = reinterpret_cast<unsigned long long*>(c->d_diff_plan + 16);
+  da.nnz_peak = reinterpret_cast<unsigned long long*>(c->d_diff_plan + 24);
+  da.nsub = reinterpret_cast<int*>(c->d_diff_plan + 32);
+  da.capped = reinterpret_cast<int*>(c->d_diff_plan + 36);
+  da.dt_s = c->diff_dt;  // the interval in seconds, as chad_step received it
+  da.max_sub = c->diff_max_sub;
+  return da;
 }
 
 static void free_all(chad_ctx* c) {
@@ -445,6 +482,17 @@ chad_status chad_diffusion_info(chad_ctx* c, int64_t* entries, int32_t* n_sub, i
   return CHAD_OK;
 }
 
+chad_status chad_diffusion_kernel_times(chad_ctx* c, int reps, double* ms_rows, double* ms_step) {
+  if (!c || reps <= 0) return CHAD_E_INVALID;
+  if (!c->any_diff || c->n_cells <= 0 || c->diff_cap <= 0)
+    return fail(c, CHAD_E_STATE, "no diffusion interval has run");
+  float r = 0.f, t = 0.f;
+  CK(c, time_diffusion_kernels(diff_args(c), reps, &r, &t, c->stream), "diffusion kernel timing");
+  if (ms_rows) *ms_rows = r;
+  if (ms_step) *ms_step = t;
+  return CHAD_OK;
+}
+
 chad_status chad_set_flow(chad_ctx* c, int digester, const chad_flow* f) {
   if (!c) return CHAD_E_INVALID;
   if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");
@@ -663,37 +711,7 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
     if ((e = launch_advect(v, s)) != cudaSuccess) return e;
   }
   if (c->any_diff && c->n_cells > 0) {
-    DiffArgs da;
-    da.n = c->N;
-    da.ld = c->ld;
-    da.dig = c->d_dig;
-    da.dc = c->d_diffc;
-    da.pos = c->d_pos;
-    da.y = c->d_y;
-    da.spos = c->d_spos;
-    da.sposf = c->d_sposf;
-    da.sdig = c->d_sdig;
-    da.sc[0] = c->d_sc;
-    da.sc[1] = c->d_sc + (size_t)kDiffRow * c->N;
-    da.srow = c->d_srow;
-    da.row_start = c->d_row_start;
-    da.row_len = c->d_row_len;
-    da.cols = c->d_cols;
-    da.vals = c->d_vals;
-    da.cap = c->diff_cap;
-    da.cell_count = c->d_cell_count;
-    da.cell_start = c->d_cell_start;
-    da.cell_list = c->d_cell_list;
-    da.n_cells = c->n_cells;
-    da.status = c->d_status;
-    da.smax = reinterpret_cast<unsigned long long*>(c->d_diff_plan);
-    da.dt_sub = reinterpret_cast<double*>(c->d_diff_plan + 8);
-    da.nnz = reinterpret_cast<unsigned long long*>(c->d_diff_plan + 16);
-    da.nnz_peak = reinterpret_cast<unsigned long long*>(c->d_diff_plan + 24);
-    da.nsub = reinterpret_cast<int*>(c->d_diff_plan + 32);
-    da.capped = reinterpret_cast<int*>(c->d_diff_plan + 36);
-    da.dt_s = c->diff_dt;  // the interval in seconds, as chad_step received it
-    da.max_sub = c->diff_max_sub;
+    const DiffArgs da = diff_args(c);
     if ((e = launch_diffusion(da, s)) != cudaSuccess) return e;
   }
   if (c->fixed_n == 0 && c->N > 0) {

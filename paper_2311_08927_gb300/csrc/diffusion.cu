@@ -29,7 +29,7 @@
 
 #include <cstdint>
 
-#include "kernels.h"
+#include "diffusion.h"
 #include "model.h"
 
 namespace chad {
@@ -394,6 +394,37 @@ cudaError_t launch_diffusion(const DiffArgs& a, cudaStream_t s) {
   const unsigned step_grid = (unsigned)((a.n * 16 + kStepBlock - 1) / kStepBlock);
   for (int k = 0; k < a.max_sub; ++k) diff_step<<<step_grid, kStepBlock, 0, s>>>(a, k);
   diff_store<<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t time_diffusion_kernels(const DiffArgs& a, int reps, float* ms_rows, float* ms_step,
+                                   cudaStream_t s) {
+  if (a.n <= 0 || a.n_cells <= 0 || reps <= 0) return cudaErrorInvalidValue;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+  float tr = 0.f, ts = 0.f;
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    e = cudaMemsetAsync(a.nnz, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+    if (e != cudaSuccess) break;
+    diff_rows<<<(unsigned)((a.n * 32 + kRowsBlock - 1) / kRowsBlock), kRowsBlock, 0, s>>>(a);
+    e = cudaEventRecord(ev[1], s);
+    if (e != cudaSuccess) break;
+    diff_step<<<(unsigned)((a.n * 16 + kStepBlock - 1) / kStepBlock), kStepBlock, 0, s>>>(a, 0);
+    e = cudaEventRecord(ev[2], s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+    float t0 = 0.f, t1 = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
+    tr += t0;
+    ts += t1;
+  }
+  for (int k = 0; k < 4; ++k)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  if (e != cudaSuccess) return e;
+  *ms_rows = tr / reps;
+  *ms_step = ts / reps;
   return cudaGetLastError();
 }
 

@@ -138,6 +138,17 @@ def test_diffusion_matches_oracle():
     assert relerr(g["y"], nd["y"]).max() > 1e-6
 
 
+def test_diffusion_with_algebraic_h2_matches_oracle():
+    """Diffusion followed by the S_h2-algebraic FP64 form (Eq. 8): the
+    diffused S_h2 is the root's starting point each interval; states to 1e-9
+    of the oracle with both switched on."""
+    pop = I.config_population(2, n=1200)
+    g = gpu_run(pop, 60.0, 3, diffusion=DIFFUSION, h2_algebraic=True)
+    o = oracle_run(pop, 60.0, 3, diffusion=DIFFUSION, h2_algebraic=True)
+    assert np.all(g["status"] == 0) and np.all(o["status"] == 0)
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+
+
 def test_diffusion_rerun_is_bitwise_deterministic():
     """The cell lists are ordered by particle index after the atomic scatter,
     so the neighbour sums run in a fixed order."""

@@ -242,8 +242,9 @@ def run(pop, dt_coupling_s, n_intervals, interval0=0, rtol=1e-6, atol=None, SH=N
         diffusion=None):
     """Integrate a Population (see paper_2311_08927_gb300.inputs) in place.
     h2_algebraic: S_h2 from its mass balance (Eq. 8) instead of as a state.
-    diffusion: (D m^2/s, h m) for every digester with a flow field: after the
-    advection of each interval, SPH diffusion between its particles.
+    diffusion: (D m^2/s, h m) for every digester with a flow field, or a list
+    with one such pair (or None) per digester: after the advection of each
+    interval, SPH diffusion between its particles.
 
     Returns a dict with y, pos, S_H, h, status, stats (copies)."""
     from paper_2311_08927_gb300 import inputs as I  # seeded generators only
@@ -267,9 +268,10 @@ def run(pop, dt_coupling_s, n_intervals, interval0=0, rtol=1e-6, atol=None, SH=N
     dD = np.zeros(nd)
     dh = np.zeros(nd)
     if diffusion is not None:
+        per = diffusion if isinstance(diffusion, list) else [diffusion] * nd
         for k, dg in enumerate(pop.digesters):
-            if dg.flow is not None:
-                dD[k], dh[k] = diffusion
+            if dg.flow is not None and per[k] is not None:
+                dD[k], dh[k] = per[k]
     lib().oracle_run(nd, np.ascontiguousarray(pop.offsets, dtype=np.int64), params, V_liq, V_gas,
                      D_u, flow, seeds, int(pop.shared_headspace), N, pos, y, T, SH, h, status,
                      float(dt_coupling_s), int(n_intervals), int(interval0), float(rtol), atol,

@@ -477,10 +477,11 @@ class Simulator:
                 fl = chad_flow(1, f["U"], f["R"], f["H"], f["sigma"], f["slab_zmin"], f["q_in"],
                                yin.ctypes.data_as(_dp), f["seed"])
                 chad_set_flow(self.ctx, d, fl)
-        if diffusion is not None:  # (D m^2/s, h m) for every digester with flow
+        if diffusion is not None:  # (D m^2/s, h m) for every digester with flow, or one per digester
+            per = diffusion if isinstance(diffusion, list) else [diffusion] * nd
             for d, dg in enumerate(pop.digesters):
-                if dg.flow is not None:
-                    chad_set_diffusion(self.ctx, d, diffusion[0], diffusion[1])
+                if dg.flow is not None and per[d] is not None:
+                    chad_set_diffusion(self.ctx, d, per[d][0], per[d][1])
 
     def load(self, y=None, pos=None, T=None, S_H=None, h=None):
         """Load every digester from host arrays (SoA over the whole population)."""

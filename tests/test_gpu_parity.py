@@ -7,6 +7,7 @@ form) must stay within 1e-4 of the oracle run at rtol 1e-10.  The relative
 error of species i is |a - b| / max(|b|, 1e-12 * max_p |b_i|), so species
 near zero do not dominate.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -147,6 +148,43 @@ def test_diffusion_with_algebraic_h2_matches_oracle():
     o = oracle_run(pop, 60.0, 3, diffusion=DIFFUSION, h2_algebraic=True)
     assert np.all(g["status"] == 0) and np.all(o["status"] == 0)
     assert relerr(g["y"], o["y"]).max() < 1e-9
+
+
+def test_diffusion_per_digester_settings_match_oracle():
+    """64 digesters, each its own grid: diffusion off in every fourth, three
+    (D, h) pairs in the rest, and a digester cut to one particle (no
+    neighbours: S = 0, nothing moves).  One substep plan for all digesters,
+    from the largest row sum over all of them."""
+    pop = I.config_population(5, n=3000)
+    a, b = pop.offsets[1], pop.offsets[2]
+    keep = np.r_[0:a + 1, b:pop.n]           # digester 1 keeps one particle
+    dgs = list(pop.digesters)
+    dgs[1] = dataclasses.replace(dgs[1], n=1)
+    pop = I.Population(dgs, pop.y[:, keep].copy(), pop.T[keep].copy(), pop.pos[:, keep].copy(),
+                       pop.shared_headspace)
+    pairs = [(1e-6, 0.05), (3e-6, 0.04), (1e-5, 0.06)]
+    dif = [None if d % 4 == 0 else pairs[d % 3] for d in range(64)]
+    g = gpu_run(pop, 60.0, 3, diffusion=dif)
+    o = oracle_run(pop, 60.0, 3, diffusion=dif)
+    assert np.all(g["status"] == 0) and np.all(o["status"] == 0)
+    assert np.array_equal(g["pos"], o["pos"])
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+    smax = 0.0
+    for d in range(64):
+        if dif[d] is None:
+            continue
+        lo, hi = pop.offsets[d], pop.offsets[d + 1]
+        smax = max(smax, O.diffusion_row_sum_max(o["pos"][:, lo:hi], pop.digesters[d].V_liq / (hi - lo),
+                                                 *dif[d]))
+    assert g["diff_info"]["n_sub"] == O.diffusion_substeps(60.0, smax) > 1
+    nd = gpu_run(pop, 60.0, 3)
+    moved = np.abs(g["y"] - nd["y"]).max(axis=0) > 0
+    for d in range(64):
+        lo, hi = pop.offsets[d], pop.offsets[d + 1]
+        if dif[d] is None or hi - lo == 1:
+            assert not moved[lo:hi].any(), d
+        else:
+            assert moved[lo:hi].any(), d
 
 
 def test_diffusion_rerun_is_bitwise_deterministic():

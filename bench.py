@@ -539,7 +539,8 @@ def run_lab_diffusion(args, ws, rank, local):
     """Diffusion between particles (the paper's planned extension, Sec. 2.3):
     the lab cylinder (100k particles, swirl + noise, inlet slab, shared
     headspace), 60-s intervals of advection, SPH diffusion (D = 1e-6 m^2/s,
-    h = 6 mm) and FP64 ADM1.  Not the headline workload.  The roofline object
+    h = 6 mm) and FP64 ADM1 (--form fp64_h2alg: with S_h2 from Eq. 8).  Not
+    the headline workload.  The roofline object
     covers the diffusion substep kernel (FP64 multiply-adds of the sparse
     product), timed through chad_diffusion_kernel_times after the timed run."""
     import torch
@@ -552,8 +553,9 @@ def run_lab_diffusion(args, ws, rank, local):
     N = pop.n
     stream = torch.cuda.Stream()
     peak64 = CH.probe_alu_peak(True)
+    h2 = args.form == "fp64_h2alg"
     sim = CH.Simulator(pop, precision=CH.PREC_FP64, stream=stream.cuda_stream,
-                       diffusion=(LAB_D, LAB_H))
+                       diffusion=(LAB_D, LAB_H), h2_algebraic=h2)
     sim.load()
     sim.step(DT_S, args.warmup)
     CH.chad_synchronize(sim.ctx)
@@ -600,6 +602,7 @@ def run_lab_diffusion(args, ws, rank, local):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"lab_cylinder_{N}_diffusion_D{LAB_D:g}_h{LAB_H:g}",
                       "particles": N, "coupling_interval_s": DT_S, "rtol": 1e-6,
+                      "form": "fp64, S_h2 algebraic (Eq. 8)" if h2 else "fp64, S_h2 a state",
                       "geometry": "lab cylinder, swirl + noise, inlet slab, shared headspace",
                       "l2": "256 MB L2 flush before every interval, inside the timed region"},
            "diffusion": {"substeps_last_interval": info["n_sub"], "entries": info["entries"],
@@ -624,7 +627,7 @@ def run_lab_diffusion(args, ws, rank, local):
         h_s, D_s = LAB_H * scale, LAB_D * scale ** 2
         sub = I.config_population(2, n=n_s)
         t0 = time.perf_counter()
-        O.run(sub, DT_S, 2, n_threads=cores, diffusion=(D_s, h_s))
+        O.run(sub, DT_S, 2, n_threads=cores, diffusion=(D_s, h_s), h2_algebraic=h2)
         dt = time.perf_counter() - t0
         res["cpu_baseline"] = {"value": n_s * days * 2 / dt, "unit": UNIT, "cores": cores,
                                "kind": "oracle",

@@ -125,18 +125,32 @@ DIFFUSION = (1e-5, 0.024)  # D m^2/s, h m (about 1.3 particle spacings at 1,200 
 
 def test_diffusion_matches_oracle():
     """Interval = advect, SPH diffusion between the particles (grid neighbour
-    search on the GPU, all pairs in the oracle), ADM1: states to 1e-9 of the
-    oracle, positions bitwise, and the diffusion visibly acts."""
+    search on the GPU, all pairs in the oracle), ADM1 in fixed steps (the
+    same arithmetic on both sides): states to 1e-9 of the oracle, positions
+    bitwise, and the diffusion visibly acts."""
     pop = I.config_population(2, n=1200)
-    g = gpu_run(pop, 60.0, 3, diffusion=DIFFUSION)
-    o = oracle_run(pop, 60.0, 3, diffusion=DIFFUSION)
+    g = gpu_run(pop, 60.0, 3, diffusion=DIFFUSION, fixed_substeps=4)
+    o = oracle_run(pop, 60.0, 3, diffusion=DIFFUSION, fixed_n=4)
     assert np.all(g["status"] == 0)
     assert np.array_equal(g["pos"], o["pos"])
     assert relerr(g["y"], o["y"]).max() < 1e-9
     smax = O.diffusion_row_sum_max(o["pos"], pop.digesters[0].V_liq / 1200, *DIFFUSION)
     assert g["diff_info"]["n_sub"] == O.diffusion_substeps(60.0, smax) > 1
-    nd = gpu_run(pop, 60.0, 3)
+    nd = gpu_run(pop, 60.0, 3, fixed_substeps=4)
     assert relerr(g["y"], nd["y"]).max() > 1e-6
+
+
+def test_diffusion_production_tolerance_tracks_oracle():
+    """Adaptive stepping at rtol 1e-6 on both sides after the same diffusion:
+    the GPU's FP32 step controller may differ from the oracle's FP64 one in
+    the last bits of a step size, so states agree to O(rtol) at worst and to
+    round-off for most particles (the bound of the production test above)."""
+    pop = I.config_population(2, n=1200)
+    g = gpu_run(pop, 60.0, 3, diffusion=DIFFUSION)
+    o = oracle_run(pop, 60.0, 3, diffusion=DIFFUSION)
+    assert np.all(g["status"] == 0)
+    e = relerr(g["y"], o["y"])
+    assert np.median(e) < 1e-10 and e.max() < 1e-5
 
 
 def test_diffusion_with_algebraic_h2_matches_oracle():
@@ -144,8 +158,8 @@ def test_diffusion_with_algebraic_h2_matches_oracle():
     diffused S_h2 is the root's starting point each interval; states to 1e-9
     of the oracle with both switched on."""
     pop = I.config_population(2, n=1200)
-    g = gpu_run(pop, 60.0, 3, diffusion=DIFFUSION, h2_algebraic=True)
-    o = oracle_run(pop, 60.0, 3, diffusion=DIFFUSION, h2_algebraic=True)
+    g = gpu_run(pop, 60.0, 3, diffusion=DIFFUSION, h2_algebraic=True, fixed_substeps=4)
+    o = oracle_run(pop, 60.0, 3, diffusion=DIFFUSION, h2_algebraic=True, fixed_n=4)
     assert np.all(g["status"] == 0) and np.all(o["status"] == 0)
     assert relerr(g["y"], o["y"]).max() < 1e-9
 
@@ -164,8 +178,8 @@ def test_diffusion_per_digester_settings_match_oracle():
                        pop.shared_headspace)
     pairs = [(1e-6, 0.05), (3e-6, 0.04), (1e-5, 0.06)]
     dif = [None if d % 4 == 0 else pairs[d % 3] for d in range(64)]
-    g = gpu_run(pop, 60.0, 3, diffusion=dif)
-    o = oracle_run(pop, 60.0, 3, diffusion=dif)
+    g = gpu_run(pop, 60.0, 3, diffusion=dif, fixed_substeps=4)
+    o = oracle_run(pop, 60.0, 3, diffusion=dif, fixed_n=4)
     assert np.all(g["status"] == 0) and np.all(o["status"] == 0)
     assert np.array_equal(g["pos"], o["pos"])
     assert relerr(g["y"], o["y"]).max() < 1e-9
@@ -177,7 +191,7 @@ def test_diffusion_per_digester_settings_match_oracle():
         smax = max(smax, O.diffusion_row_sum_max(o["pos"][:, lo:hi], pop.digesters[d].V_liq / (hi - lo),
                                                  *dif[d]))
     assert g["diff_info"]["n_sub"] == O.diffusion_substeps(60.0, smax) > 1
-    nd = gpu_run(pop, 60.0, 3)
+    nd = gpu_run(pop, 60.0, 3, fixed_substeps=4)
     moved = np.abs(g["y"] - nd["y"]).max(axis=0) > 0
     for d in range(64):
         lo, hi = pop.offsets[d], pop.offsets[d + 1]
@@ -211,8 +225,8 @@ def test_diffusion_crowded_particles_match_oracle():
     atomic max), several times the continuum estimate; states to 1e-9."""
     pop = _crowded(400)
     dif = (1e-6, 0.024)
-    g = gpu_run(pop, 1.0, 2, diffusion=dif)
-    o = oracle_run(pop, 1.0, 2, diffusion=dif)
+    g = gpu_run(pop, 1.0, 2, diffusion=dif, fixed_substeps=2)
+    o = oracle_run(pop, 1.0, 2, diffusion=dif, fixed_n=2)
     smax = O.diffusion_row_sum_max(o["pos"], pop.digesters[0].V_liq / 400, *dif)
     assert O.diffusion_substeps(1.0, smax) > 1 >= math.ceil(7.0 * dif[0] / dif[1] ** 2)
     assert np.all(g["status"] == 0)

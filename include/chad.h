@@ -178,6 +178,18 @@ chad_status chad_load_particles(chad_ctx* ctx, int digester, int64_t n, const do
                                 const double* y, const double* T, const double* S_H,
                                 const double* h, int mem);
 
+/* Replace the positions of one digester's particles and keep their states:
+   the coupling step of an external CFD solver, which supplies the particles'
+   positions at every coupling step (Sec. 2.3).  pos [3][n] m, n =
+   cfg->n_particles[digester].  The next chad_step advects from these
+   positions with the digester's flow; a flow with U = 0 and noise_sigma = 0
+   leaves them where the caller put them, while its geometry, inlet slab and
+   any diffusion still apply.  Host arrays must be finite (else
+   CHAD_E_INVALID and the positions are unchanged); device arrays are copied
+   on the context's stream unchecked.  CHAD_E_STATE before the digester is
+   loaded. */
+chad_status chad_set_positions(chad_ctx* ctx, int digester, int64_t n, const double* pos, int mem);
+
 /* Set (or clear, has_flow = 0) the flow field of one digester. */
 chad_status chad_set_flow(chad_ctx* ctx, int digester, const chad_flow* flow);
 

@@ -133,6 +133,8 @@ def lib():
                                                 C.c_int]
             L.chad_set_diffusion.restype = C.c_int
             L.chad_set_diffusion.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+            L.chad_set_positions.restype = C.c_int
+            L.chad_set_positions.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_int]
             L.chad_diffusion_kernel_times.restype = C.c_int
             L.chad_diffusion_kernel_times.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double),
                                                       C.POINTER(C.c_double)]
@@ -155,7 +157,7 @@ def exported_symbols() -> list[str]:
             "chad_step", "chad_synchronize", "chad_read_states", "chad_probe_alu_peak",
             "chad_eval_model", "chad_eval_model_split", "chad_probe_numerics", "chad_autotune",
             "chad_flop_counts", "chad_set_diffusion", "chad_diffusion_info",
-            "chad_diffusion_kernel_times",
+            "chad_diffusion_kernel_times", "chad_set_positions",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
 
@@ -374,6 +376,13 @@ def chad_load_particles(ctx, digester, n, pos, y, T=None, S_H=None, h=None) -> N
     _check(L, ctx, L.chad_load_particles(ctx, int(digester), int(n), *[p for p, _ in ptrs], mem))
 
 
+def chad_set_positions(ctx, digester, n, pos) -> None:
+    """Replace one digester's positions ([3][n], numpy or CUDA tensor), keeping its states."""
+    L = lib()
+    p, mem = _ptr(pos)
+    _check(L, ctx, L.chad_set_positions(ctx, int(digester), int(n), p, MEM_HOST if mem is None else mem))
+
+
 def chad_set_flow(ctx, digester, flow: chad_flow) -> None:
     L = lib()
     _check(L, ctx, L.chad_set_flow(ctx, int(digester), C.byref(flow)))
@@ -493,6 +502,12 @@ class Simulator:
             a, b = self.offsets[d], self.offsets[d + 1]
             sl = lambda x: None if x is None else np.ascontiguousarray(x[..., a:b])
             chad_load_particles(self.ctx, d, b - a, sl(pos), sl(y), sl(T), sl(S_H), sl(h))
+
+    def set_positions(self, pos):
+        """New positions [3][N] for every digester (an external CFD's coupling step)."""
+        for d in range(len(self.pop.digesters)):
+            a, b = self.offsets[d], self.offsets[d + 1]
+            chad_set_positions(self.ctx, d, b - a, np.ascontiguousarray(pos[:, a:b], dtype=np.float64))
 
     def step(self, dt_coupling_s, n_intervals):
         chad_step(self.ctx, dt_coupling_s, n_intervals)

@@ -426,6 +426,26 @@ chad_status chad_load_particles(chad_ctx* c, int digester, int64_t n, const doub
   return CHAD_OK;
 }
 
+chad_status chad_set_positions(chad_ctx* c, int digester, int64_t n, const double* pos, int mem) {
+  if (!c) return CHAD_E_INVALID;
+  if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");
+  if (n != c->count[digester]) return fail(c, CHAD_E_INVALID, "n differs from cfg->n_particles[digester]");
+  if (mem != CHAD_MEM_HOST && mem != CHAD_MEM_DEVICE) return fail(c, CHAD_E_INVALID, "mem must be HOST or DEVICE");
+  if (!c->loaded[digester]) return fail(c, CHAD_E_STATE, "load the digester before setting positions");
+  if (n == 0) return CHAD_OK;
+  if (!pos) return fail(c, CHAD_E_INVALID, "pos is required");
+  if (mem == CHAD_MEM_HOST)
+    for (int64_t i = 0; i < 3 * n; ++i)
+      if (!std::isfinite(pos[i])) return fail(c, CHAD_E_INVALID, "positions must be finite");
+  const int64_t o = c->offset[digester];
+  const cudaMemcpyKind k = kind_in(mem);
+  for (int i = 0; i < 3; ++i)
+    CK(c, cudaMemcpyAsync(c->d_pos + (size_t)i * c->ld + o, pos + (size_t)i * n, sizeof(double) * n, k,
+                          c->stream), "set positions");
+  if (mem == CHAD_MEM_HOST) CK(c, cudaStreamSynchronize(c->stream), "set positions");
+  return CHAD_OK;
+}
+
 chad_status chad_set_diffusion(chad_ctx* c, int digester, double D, double h) {
   if (!c) return CHAD_E_INVALID;
   if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");

@@ -123,4 +123,5 @@ def test_null_context_calls_are_invalid(L):
     assert L.chad_set_diffusion(None, 0, 1e-6, 0.01) == 1
     assert L.chad_diffusion_info(None, None, None, None, None) == 1
     assert L.chad_diffusion_kernel_times(None, 1, None, None) == 1
+    assert L.chad_set_positions(None, 0, 0, None, 0) == 1
     L.chad_destroy(None)

@@ -201,6 +201,40 @@ def test_diffusion_per_digester_settings_match_oracle():
             assert moved[lo:hi].any(), d
 
 
+def test_external_positions_each_interval_match_oracle():
+    """The coupling loop of an external CFD: before every interval the caller
+    supplies new positions (chad_set_positions) and the flow has U = 0 and no
+    noise, so the library only uses them: inlet slab membership and diffusion
+    follow the supplied positions, the states carry over.  Oracle chained
+    interval by interval from the same positions; fixed ADM1 steps."""
+    n = 1500
+    base = I.config_population(2, n=n)
+    fl = I.swirl_flow(U=0.0, sigma=0.0, R=0.1, H=0.3, seed=7)
+    dg = dataclasses.replace(base.digesters[0], flow=fl)
+    pop = I.Population([dg], base.y.copy(), base.T.copy(), base.pos.copy(), base.shared_headspace)
+    frames = [I.config_population(2, n=n, seed_offset=10 + k).pos for k in range(4)]
+    sim = CH.Simulator(pop, fixed_substeps=4, diffusion=DIFFUSION)
+    sim.load()
+    y, SH, h = pop.y.copy(), None, None
+    for k, pos in enumerate(frames):
+        sim.set_positions(pos)
+        sim.step(60.0, 1)
+        step_pop = I.Population([dg], y, pop.T.copy(), pos.copy(), pop.shared_headspace)
+        o = O.run(step_pop, 60.0, 1, interval0=k, fixed_n=4, SH=SH, h=h, diffusion=DIFFUSION)
+        y, SH, h = o["y"], o["S_H"], o["h"]
+    g = sim.read()
+    with pytest.raises(CH.ChadError) as ei:
+        bad = frames[0].copy()
+        bad[2, 5] = np.nan
+        sim.set_positions(bad)
+    assert ei.value.code == 1
+    assert np.array_equal(sim.read()["pos"], g["pos"])
+    sim.close()
+    assert np.array_equal(g["pos"], frames[-1]) and np.array_equal(o["pos"], frames[-1])
+    assert np.all(g["status"] == 0)
+    assert relerr(g["y"], o["y"]).max() < 1e-9
+
+
 def test_diffusion_rerun_is_bitwise_deterministic():
     """The cell lists are ordered by particle index after the atomic scatter,
     so the neighbour sums run in a fixed order."""

@@ -145,3 +145,73 @@ def test_learned_cold_restart_saves_work_and_keeps_the_solution(trained):
     floor = 1e-12 * np.abs(o["y"]).max(axis=1, keepdims=True)
     e = np.abs(lrn["y"][:, idx] - o["y"]) / np.maximum(np.abs(o["y"]), floor)
     assert e.max() < 1e-4
+
+
+# ------------------------------------------------------------ full sizes with learned guesses
+def _relerr(a, b):
+    floor = 1e-12 * np.max(np.abs(b), axis=1, keepdims=True)
+    return np.abs(a - b) / np.maximum(np.abs(b), floor + 1e-300)
+
+
+def _learned_mixed_run(pop, model, n_intervals):
+    """Learned + mixed form from a cold load (no S_H, no h: the network gives
+    the first guesses), as the 2M and 64-digester workloads prescribe."""
+    sim = CH.Simulator(pop, precision=CH.PREC_MIXED, learned=1)
+    CH.chad_set_mlp(sim.ctx, model.params, model.feat_norm, model.out_norm)
+    sim.load()
+    sim.step(60.0, n_intervals)
+    out = sim.read()
+    sim.close()
+    return out
+
+
+def test_full_size_2M_learned_mixed_sampled(trained):
+    """2,000,000 particles (the 1M recipe with a new seed) in the learned +
+    mixed form: every particle OK, few learned guesses redone, and a seeded
+    sample of 66 particles (slugs included) recomputed by the oracle within
+    the mixed form's 1e-4 (oracle at the same rtol 1e-6; particles are
+    independent, so a sample is exact)."""
+    model = trained[0]
+    pop = I.config_population(4)
+    assert pop.n == 2_000_000
+    g = _learned_mixed_run(pop, model, 2)
+    assert np.all(g["status"] == 0)
+    assert g["stats"]["mlp_redo"] < 0.01 * pop.n
+    rng = np.random.default_rng(4)
+    idx = np.sort(np.concatenate([rng.choice(pop.slugs, 16, replace=False),
+                                  rng.choice(pop.n, 48, replace=False), [0, pop.n - 1]]))
+    d0 = pop.digesters[0]
+    sp = I.Population([I.Digester(n=len(idx), V_liq=d0.V_liq, V_gas=d0.V_gas, params=d0.params,
+                                  D=d0.D, flow=d0.flow, y_in=d0.y_in)],
+                      pop.y[:, idx].copy(), pop.T[idx].copy(), pop.pos[:, idx].copy(),
+                      pop.shared_headspace)
+    o = O.run(sp, 60.0, 2, rtol=1e-6)
+    assert _relerr(g["y"][:, idx], o["y"]).max() < 1e-4
+
+
+def test_full_size_64_digesters_learned_mixed(trained):
+    """The 64-digester workload at full size (3.37M particles, log-uniform
+    counts, per-digester kinetics, swirl fields and shared headspaces) in one
+    learned + mixed run: every particle OK, the headspace states equal within
+    each digester, every particle inside its cylinder, and the two smallest
+    digesters recomputed whole by the oracle (each is self-contained: own
+    flow, noise keys and headspace): positions bitwise, states within 1e-4."""
+    model = trained[0]
+    pop = I.config_population(5)
+    g = _learned_mixed_run(pop, model, 2)
+    assert np.all(g["status"] == 0)
+    cnt = np.diff(pop.offsets)
+    for d in range(64):
+        a, b = pop.offsets[d], pop.offsets[d + 1]
+        gas = g["y"][26:29, a:b]
+        assert np.all(gas == gas[:, :1]), d
+        x, y, z = g["pos"][:, a:b]
+        f = pop.digesters[d].flow
+        assert np.all(np.hypot(x, y) <= f["R"] * (1 + 1e-15)) and np.all((z >= 0) & (z <= f["H"]))
+    for d in np.argsort(cnt)[:2]:
+        a, b = pop.offsets[d], pop.offsets[d + 1]
+        one = I.Population([pop.digesters[d]], pop.y[:, a:b].copy(), pop.T[a:b].copy(),
+                           pop.pos[:, a:b].copy(), pop.shared_headspace)
+        o = O.run(one, 60.0, 2, rtol=1e-6)
+        assert np.array_equal(g["pos"][:, a:b], o["pos"]), d
+        assert _relerr(g["y"][:, a:b], o["y"]).max() < 1e-4, d

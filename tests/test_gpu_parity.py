@@ -432,6 +432,22 @@ def test_full_size_1M_sampled(precision, tol):
         assert relerr(g["y"][:, idx], o["y"]).max() < tol
 
 
+def test_full_size_lab_cylinder_100k_whole_tank():
+    """The lab-cylinder workload at full size (100,000 particles, swirl +
+    noise, inlet slab, shared headspace), one 60-s interval in the FP64 form
+    at rtol 1e-6, against the oracle on the whole tank at the same rtol:
+    positions bitwise, states to round-off for most particles and within the
+    production bound for all (the GPU's step controller works in FP32)."""
+    pop = I.config_population(2)
+    assert pop.n == 100_000
+    g = gpu_run(pop, 60.0, 1, rtol=1e-6)
+    o = oracle_run(pop, 60.0, 1, rtol=1e-6)
+    assert np.all(g["status"] == 0) and np.all(o["status"] == 0)
+    assert np.array_equal(g["pos"], o["pos"])
+    e = relerr(g["y"], o["y"])
+    assert np.median(e) < 1e-10 and e.max() < 1e-5
+
+
 # ------------------------------------------------------------ failure handling
 def test_step_limit_sets_status_without_faulting():
     pop = I.config_population(1, n=64)

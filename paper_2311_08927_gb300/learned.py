@@ -37,10 +37,14 @@ class TrainedMLP:
 
 
 def sample_states(pop: I.Population, intervals: int, precision=CH.PREC_MIXED, skip: int = 1,
-                  max_samples: int | None = None, stream=None):
+                  max_samples: int | None = None, stream=None, initial: bool = True):
     """Run the integrator on `pop` and collect (y, T, S_H, h) at every interval
-    end after the first `skip` ones.  Returns device tensors y [29][M],
-    T [M], S_H [M], h [M]."""
+    end after the first `skip` ones.  With `initial`, the loaded states are
+    sampled too (a cold load is where the network is consulted): a first
+    1-ms interval makes the stored S_H the Eq. 7 root at the loaded state,
+    and their step-size target is the controller's proposal at the end of
+    the first full interval.  Returns device tensors y [29][M], T [M],
+    S_H [M], h [M]."""
     import torch
     sim = CH.Simulator(pop, precision=precision, stream=stream)
     sim.load()
@@ -48,8 +52,24 @@ def sample_states(pop: I.Population, intervals: int, precision=CH.PREC_MIXED, sk
     T = torch.from_numpy(np.ascontiguousarray(pop.T)).cuda()
     ys, Ts, SHs, hs = [], [], [], []
     total = 0
+    first = None
+    if initial:
+        sim.step(1e-3, 1)
+        y0 = torch.empty((NS, n), dtype=torch.float64, device="cuda")
+        SH0 = torch.empty(n, dtype=torch.float64, device="cuda")
+        CH.chad_read_states(sim.ctx, 0, y=y0, S_H=SH0)
+        first = (y0, SH0)
     for k in range(intervals):
         sim.step(60.0, 1)
+        if first is not None:
+            h1 = torch.empty(n, dtype=torch.float64, device="cuda")
+            CH.chad_read_states(sim.ctx, 0, h=h1)
+            ys.append(first[0])
+            Ts.append(T)
+            SHs.append(first[1])
+            hs.append(h1)
+            total += n
+            first = None
         if k < skip:
             continue
         y = torch.empty((NS, n), dtype=torch.float64, device="cuda")

@@ -190,6 +190,41 @@ chad_status chad_load_particles(chad_ctx* ctx, int digester, int64_t n, const do
    loaded. */
 chad_status chad_set_positions(chad_ctx* ctx, int digester, int64_t n, const double* pos, int mem);
 
+/* As chad_set_positions for positions listed in another order: pos [3][n]
+   holds the frame's entries and id [n] the library particle (0 .. n-1 within
+   the digester) each entry belongs to -- an SPH code re-sorts its particles
+   every step and writes them with their ids.  The ids must name every
+   particle exactly once; otherwise CHAD_E_INVALID (checked on the GPU) and
+   the positions are unchanged.  Host positions must be finite.  Blocks until
+   the check is done. */
+chad_status chad_set_positions_by_id(chad_ctx* ctx, int digester, int64_t n, const double* pos,
+                                     const int64_t* id, int mem);
+
+/* Particle frame files, one per CFD step (the paper's coupling reads the
+   particles of every CFD step from files, Sec. 2.3).  Little-endian layout:
+     64-byte header: char magic[8] = "CHADFRM\0"; uint32 version = 1;
+       uint32 dtype = 4 or 8 (bytes per position/velocity value); uint64 n;
+       uint64 step; double time_s; uint32 fields (bit 0 positions, required;
+       bit 1 velocities; bit 2 ids); uint32 reserved[5] = 0;
+     then x[n], y[n], z[n] (dtype); u[n], v[n], w[n] (dtype, if bit 1; not
+     used by the library); id[n] (uint32, if bit 2; without ids the entries
+     are in the library's particle order).
+   chad_load_frame reads one into the positions of one digester through
+   chad_set_positions_by_id (FP32 values widened exactly); the frame's n must
+   equal the digester's particle count.  step and time_s (may be NULL)
+   receive the header's values.  A missing, short or malformed file, or bad
+   ids: CHAD_E_INVALID with the reason in chad_last_error, positions
+   unchanged. */
+chad_status chad_load_frame(chad_ctx* ctx, int digester, const char* path, uint64_t* step,
+                            double* time_s);
+
+/* Read a frame file on the host without a context: *n, *step, *time_s and
+   *has_id (each may be NULL) from the header; pos [3][n] (doubles) and id [n]
+   filled when non-NULL and n <= n_max (id untouched without ids).
+   CHAD_E_INVALID on any I/O or format error or n > n_max.  Needs no GPU. */
+chad_status chad_read_frame(const char* path, int64_t n_max, double* pos, int64_t* id, int64_t* n,
+                            uint64_t* step, double* time_s, int32_t* has_id);
+
 /* Set (or clear, has_flow = 0) the flow field of one digester. */
 chad_status chad_set_flow(chad_ctx* ctx, int digester, const chad_flow* flow);
 

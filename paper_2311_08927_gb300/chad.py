@@ -133,6 +133,16 @@ def lib():
                                                 C.c_int]
             L.chad_set_diffusion.restype = C.c_int
             L.chad_set_diffusion.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+            L.chad_set_positions_by_id.restype = C.c_int
+            L.chad_set_positions_by_id.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
+                                                   C.c_void_p, C.c_int]
+            L.chad_load_frame.restype = C.c_int
+            L.chad_load_frame.argtypes = [C.c_void_p, C.c_int, C.c_char_p,
+                                          C.POINTER(C.c_uint64), C.POINTER(C.c_double)]
+            L.chad_read_frame.restype = C.c_int
+            L.chad_read_frame.argtypes = [C.c_char_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                          C.POINTER(C.c_int64), C.POINTER(C.c_uint64),
+                                          C.POINTER(C.c_double), C.POINTER(C.c_int32)]
             L.chad_set_positions.restype = C.c_int
             L.chad_set_positions.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_int]
             L.chad_diffusion_kernel_times.restype = C.c_int
@@ -158,6 +168,7 @@ def exported_symbols() -> list[str]:
             "chad_eval_model", "chad_eval_model_split", "chad_probe_numerics", "chad_autotune",
             "chad_flop_counts", "chad_set_diffusion", "chad_diffusion_info",
             "chad_diffusion_kernel_times", "chad_set_positions",
+            "chad_set_positions_by_id", "chad_load_frame", "chad_read_frame",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
 
@@ -381,6 +392,42 @@ def chad_set_positions(ctx, digester, n, pos) -> None:
     L = lib()
     p, mem = _ptr(pos)
     _check(L, ctx, L.chad_set_positions(ctx, int(digester), int(n), p, MEM_HOST if mem is None else mem))
+
+
+def chad_set_positions_by_id(ctx, digester, n, pos, ids) -> None:
+    """Positions [3][n] in frame order with the particle id [n] (int64) of each entry."""
+    L = lib()
+    ptrs = [_ptr(a) for a in (pos, ids)]
+    mems = {m for _, m in ptrs if m is not None}
+    if len(mems) > 1:
+        raise ValueError("pos and ids must both be host or both device")
+    mem = mems.pop() if mems else MEM_HOST
+    _check(L, ctx, L.chad_set_positions_by_id(ctx, int(digester), int(n), ptrs[0][0], ptrs[1][0], mem))
+
+
+def chad_load_frame(ctx, digester, path):
+    """Load a frame file into one digester's positions; returns (step, time_s)."""
+    L = lib()
+    st, t = C.c_uint64(), C.c_double()
+    _check(L, ctx, L.chad_load_frame(ctx, int(digester), os.fsencode(path), C.byref(st), C.byref(t)))
+    return st.value, t.value
+
+
+def chad_read_frame(path):
+    """Host read of a frame file through the library (no GPU): dict with n,
+    step, time_s, pos [3][n] and id [n] (None without ids)."""
+    L = lib()
+    n, st, t, hid = C.c_int64(), C.c_uint64(), C.c_double(), C.c_int32()
+    fp = os.fsencode(path)
+    if L.chad_read_frame(fp, 0, None, None, C.byref(n), C.byref(st), C.byref(t), C.byref(hid)) != 0:
+        raise ChadError(1, f"cannot read frame {path}")
+    pos = np.empty((3, n.value))
+    ids = np.empty(n.value, dtype=np.int64) if hid.value else None
+    code = L.chad_read_frame(fp, n.value, pos.ctypes.data, None if ids is None else ids.ctypes.data,
+                             None, None, None, None)
+    if code != 0:
+        raise ChadError(code, f"cannot read frame {path}")
+    return dict(n=n.value, step=st.value, time_s=t.value, pos=pos, id=ids)
 
 
 def chad_set_flow(ctx, digester, flow: chad_flow) -> None:

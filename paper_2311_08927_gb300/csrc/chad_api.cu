@@ -16,6 +16,7 @@
 
 #include "chad.h"
 #include "diffusion.h"
+#include "frames.h"
 #include "kernels.h"
 #include "model.h"
 
@@ -59,6 +60,10 @@ struct chad_ctx {
   // plan scratch: smax, dt_sub, nnz, nnz_peak (8 B each), nsub, capped (4 B each)
   unsigned char* d_diff_plan = nullptr;
   int diff_max_sub = 0;
+  // positions by particle id (chad_set_positions_by_id, chad_load_frame):
+  // frame positions [3][m], scattered positions [3][m], ids [m], counts [m],
+  // flag; m = the largest digester
+  unsigned char* d_frame = nullptr;
   std::vector<char> loaded;
   bool any_flow = false;
   double sim_days = 0.0;
@@ -176,7 +181,7 @@ static void free_all(chad_ctx* c) {
     if (p) cudaFree(p);
   void* lp[] = {c->d_mlp, c->d_SH_learned, c->d_h_learned, c->d_diffc, c->d_cell_count,
                 c->d_cell_start, c->d_cell_list, c->d_spos, c->d_sposf, c->d_sdig, c->d_sc, c->d_srow,
-                c->d_row_start, c->d_row_len, c->d_cols, c->d_vals, c->d_diff_plan};
+                c->d_row_start, c->d_row_len, c->d_cols, c->d_vals, c->d_diff_plan, c->d_frame};
   for (void* p : lp)
     if (p) cudaFree(p);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -443,6 +448,95 @@ chad_status chad_set_positions(chad_ctx* c, int digester, int64_t n, const doubl
     CK(c, cudaMemcpyAsync(c->d_pos + (size_t)i * c->ld + o, pos + (size_t)i * n, sizeof(double) * n, k,
                           c->stream), "set positions");
   if (mem == CHAD_MEM_HOST) CK(c, cudaStreamSynchronize(c->stream), "set positions");
+  return CHAD_OK;
+}
+
+chad_status chad_set_positions_by_id(chad_ctx* c, int digester, int64_t n, const double* pos,
+                                     const int64_t* id, int mem) {
+  if (!c) return CHAD_E_INVALID;
+  if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");
+  if (n != c->count[digester]) return fail(c, CHAD_E_INVALID, "n differs from cfg->n_particles[digester]");
+  if (mem != CHAD_MEM_HOST && mem != CHAD_MEM_DEVICE) return fail(c, CHAD_E_INVALID, "mem must be HOST or DEVICE");
+  if (!c->loaded[digester]) return fail(c, CHAD_E_STATE, "load the digester before setting positions");
+  if (n == 0) return CHAD_OK;
+  if (!pos || !id) return fail(c, CHAD_E_INVALID, "pos and id are required");
+  if (mem == CHAD_MEM_HOST)
+    for (int64_t i = 0; i < 3 * n; ++i)
+      if (!std::isfinite(pos[i])) return fail(c, CHAD_E_INVALID, "positions must be finite");
+  cudaStream_t s = c->stream;
+  if (!c->d_frame) {
+    int64_t m = 0;
+    for (int d = 0; d < c->n_dig; ++d) m = std::max(m, c->count[d]);
+    const size_t bytes = (size_t)m * (6 * sizeof(double) + sizeof(int64_t) + sizeof(int)) + 16;
+    if (cudaMalloc(&c->d_frame, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_frame = nullptr;
+      return fail(c, CHAD_E_NOMEM, "frame buffers");
+    }
+  }
+  int64_t m = 0;
+  for (int d = 0; d < c->n_dig; ++d) m = std::max(m, c->count[d]);
+  double* fpos = reinterpret_cast<double*>(c->d_frame);
+  double* tmp = fpos + 3 * m;
+  int64_t* fid = reinterpret_cast<int64_t*>(tmp + 3 * m);
+  int* seen = reinterpret_cast<int*>(fid + m);
+  int* bad = seen + m;
+  const cudaMemcpyKind k = kind_in(mem);
+  for (int i = 0; i < 3; ++i)
+    CK(c, cudaMemcpyAsync(fpos + (size_t)i * n, pos + (size_t)i * n, sizeof(double) * n, k, s), "frame positions");
+  CK(c, cudaMemcpyAsync(fid, id, sizeof(int64_t) * n, k, s), "frame ids");
+  CK(c, cudaMemsetAsync(bad, 0, sizeof(int), s), "frame check");
+  CK(c, launch_scatter_by_id(fpos, fid, n, tmp, seen, bad, s), "frame scatter");
+  int h_bad = 0;
+  CK(c, cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s), "frame check");
+  CK(c, cudaStreamSynchronize(s), "frame check");
+  if (h_bad & 1) return fail(c, CHAD_E_INVALID, "particle id outside [0, n)");
+  if (h_bad & 2) return fail(c, CHAD_E_INVALID, "particle ids are not a permutation of 0 .. n-1");
+  const int64_t o = c->offset[digester];
+  for (int i = 0; i < 3; ++i)
+    CK(c, cudaMemcpyAsync(c->d_pos + (size_t)i * c->ld + o, tmp + (size_t)i * n, sizeof(double) * n,
+                          cudaMemcpyDeviceToDevice, s), "frame positions");
+  return CHAD_OK;
+}
+
+chad_status chad_read_frame(const char* path, int64_t n_max, double* pos, int64_t* id,
+                            int64_t* n, uint64_t* step, double* time_s, int32_t* has_id) {
+  if (!path) return CHAD_E_INVALID;
+  FrameHeader h;
+  std::vector<double> p;
+  std::vector<int64_t> ids;
+  std::string err;
+  if (!read_frame_file(path, h, p, ids, err)) return CHAD_E_INVALID;
+  if (n) *n = (int64_t)h.n;
+  if (step) *step = h.step;
+  if (time_s) *time_s = h.time_s;
+  if (has_id) *has_id = ids.empty() ? 0 : 1;
+  if ((pos || id) && (int64_t)h.n > n_max) return CHAD_E_INVALID;
+  if (pos) std::memcpy(pos, p.data(), sizeof(double) * p.size());
+  if (id && !ids.empty()) std::memcpy(id, ids.data(), sizeof(int64_t) * ids.size());
+  return CHAD_OK;
+}
+
+chad_status chad_load_frame(chad_ctx* c, int digester, const char* path, uint64_t* step,
+                            double* time_s) {
+  if (!c) return CHAD_E_INVALID;
+  if (!path) return fail(c, CHAD_E_INVALID, "path is required");
+  if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");
+  FrameHeader h;
+  std::vector<double> p;
+  std::vector<int64_t> ids;
+  std::string err;
+  if (!read_frame_file(path, h, p, ids, err)) return fail(c, CHAD_E_INVALID, err);
+  const int64_t n = (int64_t)h.n;
+  if (n != c->count[digester]) return fail(c, CHAD_E_INVALID, "frame particle count differs from the digester's");
+  if (ids.empty()) {
+    ids.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) ids[(size_t)i] = i;
+  }
+  const chad_status st = chad_set_positions_by_id(c, digester, n, p.data(), ids.data(), CHAD_MEM_HOST);
+  if (st != CHAD_OK) return st;
+  if (step) *step = h.step;
+  if (time_s) *time_s = h.time_s;
   return CHAD_OK;
 }
 

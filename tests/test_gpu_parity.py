@@ -235,6 +235,65 @@ def test_external_positions_each_interval_match_oracle():
     assert relerr(g["y"], o["y"]).max() < 1e-9
 
 
+def test_frames_scatter_by_id_and_refuse_bad_ids(tmp_path):
+    """Frame files (FP64 and FP32, entries shuffled with their ids, as an SPH
+    code writes them after re-sorting) land in particle order bitwise (FP32
+    widened exactly); ids that repeat, run out of range or a frame of another
+    size are refused and leave the positions as they were."""
+    from paper_2311_08927_gb300 import frames as F
+    pop = I.config_population(2, n=3000)
+    sim = CH.Simulator(pop)
+    sim.load()
+    rng = np.random.default_rng(12)
+    new = I.config_population(2, n=3000, seed_offset=21).pos
+    perm = rng.permutation(3000)
+    for dt in (np.float64, np.float32):
+        f = tmp_path / f"f{np.dtype(dt).itemsize}.frm"
+        F.write_frame(f, new[:, perm], ids=perm.astype(np.uint32), dtype=dt, step=5, time_s=2.5)
+        assert CH.chad_load_frame(sim.ctx, 0, f) == (5, 2.5)
+        assert np.array_equal(sim.read()["pos"], new.astype(dt).astype(np.float64))
+    before = sim.read()["pos"]
+    dup = perm.copy()
+    dup[7] = dup[8]
+    out = perm.copy()
+    out[0] = 3000
+    for ids, m in ((dup, 3000), (out, 3000), (np.arange(2999), 2999)):
+        f = tmp_path / "bad.frm"
+        F.write_frame(f, new[:, :m], ids=ids.astype(np.uint32))
+        with pytest.raises(CH.ChadError) as ei:
+            CH.chad_load_frame(sim.ctx, 0, f)
+        assert ei.value.code == 1
+        assert np.array_equal(sim.read()["pos"], before)
+    sim.close()
+
+
+def test_frames_each_interval_equal_set_positions(tmp_path):
+    """Stepping from frame files (shuffled, with ids) gives bitwise the states
+    of stepping from the same positions handed over in particle order."""
+    from paper_2311_08927_gb300 import frames as F
+    base = I.config_population(2, n=2000)
+    dg = dataclasses.replace(base.digesters[0], flow=I.swirl_flow(U=0.0, sigma=0.0, seed=3))
+    pop = I.Population([dg], base.y.copy(), base.T.copy(), base.pos.copy(), base.shared_headspace)
+    frames = [I.config_population(2, n=2000, seed_offset=30 + k).pos for k in range(3)]
+    a = CH.Simulator(pop, diffusion=DIFFUSION)
+    b = CH.Simulator(pop, diffusion=DIFFUSION)
+    a.load()
+    b.load()
+    rng = np.random.default_rng(1)
+    for k, pos in enumerate(frames):
+        a.set_positions(pos)
+        perm = rng.permutation(2000)
+        f = tmp_path / f"{k}.frm"
+        F.write_frame(f, pos[:, perm], ids=perm.astype(np.uint32), step=k)
+        CH.chad_load_frame(b.ctx, 0, f)
+        a.step(60.0, 1)
+        b.step(60.0, 1)
+    ra, rb = a.read(), b.read()
+    a.close()
+    b.close()
+    assert np.array_equal(ra["pos"], rb["pos"]) and np.array_equal(ra["y"], rb["y"])
+
+
 def test_diffusion_rerun_is_bitwise_deterministic():
     """The cell lists are ordered by particle index after the atomic scatter,
     so the neighbour sums run in a fixed order."""

@@ -199,7 +199,7 @@ def train_mlp(CH, I, args):
             "training_s": t2 - t1, "val_loss_before": hist[0][2], "val_loss_after": hist[-1][2],
             "test_loss": test_loss, "median_abs_log10_err_SH": e_sh,
             "median_abs_log10_err_h": e_h,
-            "kernels": "chad_mlp_grad (BF16 mma.sync fwd+bwd) + chad_mlp_adam"}
+            "kernels": "chad_mlp_grad (BF16 tcgen05 fwd+bwd, TMEM accumulators) + chad_mlp_adam"}
     del X, Y, y, T, SH, h
     torch.cuda.empty_cache()
     return model, info

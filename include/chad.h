@@ -319,8 +319,10 @@ chad_status chad_set_mlp(chad_ctx* ctx, const float* params, const float* feat_n
 chad_status chad_mlp_features(const double* y, int64_t ld, const double* T, int64_t n,
                               const float* feat_norm, uint16_t* X, void* cuda_stream);
 
-/* Inference on the tensor cores: out [n][2] FP32 standardised outputs for
-   X [n][32] BF16, params [NPARAM] FP32 (device pointers).  Asynchronous. */
+/* Inference on the tensor cores (tcgen05, accumulators in tensor memory):
+   out [n][2] FP32 standardised outputs for X [n][32] BF16 (16-byte aligned),
+   params [NPARAM] FP32 (device pointers).  Waits for the stream and returns
+   CHAD_E_CUDA if a tensor-core completion wait timed out. */
 chad_status chad_mlp_forward(const uint16_t* X, int64_t n, const float* params, float* out,
                              void* cuda_stream);
 
@@ -328,12 +330,13 @@ chad_status chad_mlp_forward(const uint16_t* X, int64_t n, const float* params, 
 size_t chad_mlp_grad_scratch_bytes(int64_t n);
 
 /* Gradient of L = (1/n) sum_i sum_j (MLP(X_i)_j - Y_ij)^2 w.r.t. params
-   (forward and backward on the tensor cores, BF16 operands, FP32
-   accumulation; per-block partials reduced in a fixed order, so the result
-   is deterministic).  X [n][32] BF16, Y [n][2] FP32, params and grad
-   [NPARAM] FP32, loss (may be NULL) one FP32; all device pointers; scratch
-   is caller-owned device memory of chad_mlp_grad_scratch_bytes(n) bytes.
-   Asynchronous. */
+   (forward and backward on the tensor cores with tcgen05, BF16 operands,
+   FP32 accumulation in tensor memory; per-CTA partials reduced in a fixed
+   order, so the result is deterministic).  X [n][32] BF16 (16-byte
+   aligned), Y [n][2] FP32, params and grad [NPARAM] FP32, loss (may be NULL)
+   one FP32; all device pointers; scratch is caller-owned device memory of
+   chad_mlp_grad_scratch_bytes(n) bytes.  Waits for the stream and returns
+   CHAD_E_CUDA if a tensor-core completion wait timed out. */
 chad_status chad_mlp_grad(const uint16_t* X, const float* Y, int64_t n, const float* params,
                           float* grad, float* loss, void* scratch, size_t scratch_bytes,
                           void* cuda_stream);

@@ -719,8 +719,7 @@ chad_status chad_mlp_forward(const uint16_t* X, int64_t n, const float* params, 
 }
 
 size_t chad_mlp_grad_scratch_bytes(int64_t n) {
-  const int64_t per = 256;
-  const int64_t nb = (n + per - 1) / per;
+  const int64_t nb = (n + mlp::tc::TILE - 1) / mlp::tc::TILE;  // a partial per tile at most
   return (size_t)nb * (mlp::NPARAM + 1) * sizeof(float);
 }
 
@@ -739,8 +738,8 @@ chad_status chad_mlp_grad(const uint16_t* X, const float* Y, int64_t n, const fl
   }
   int* err = mlp::err_flag();
   if (!err) return CHAD_E_NOMEM;
-  // one CTA per SM at most, and no more partials than the scratch holds
-  int64_t nb = (n + 255) / 256;
+  // one CTA per SM at most, and one per tile
+  int64_t nb = (n + mlp::tc::TILE - 1) / mlp::tc::TILE;
   if (nb > mlp::sm_count()) nb = mlp::sm_count();
   float* partial = static_cast<float*>(scratch);
   float* lpart = partial + nb * mlp::NPARAM;

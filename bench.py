@@ -446,9 +446,19 @@ def cpu_baseline(pop, warmup, k, budget_s):
         if dt >= 0.5 * budget_s or n_s >= 200_000:
             break
         n_s = int(min(200_000, n_s * budget_s / max(dt, 1e-3)))
+    # the same timed intervals on one core, for a sample sized to ~1/4 of the budget
+    n1 = max(64, int(n_s * 0.25 / cores))
+    s1 = _oracle_sample(pop, n1, seed=13)
+    r1 = O.run(s1, DT_S, warmup, rtol=1e-6, n_threads=1)
+    s1b = I.Population(s1.digesters, r1["y"], s1.T, s1.pos, False)
+    t0 = time.perf_counter()
+    O.run(s1b, DT_S, k, interval0=warmup, rtol=1e-6, SH=r1["S_H"], h=r1["h"], n_threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": n_s * k * DT_S / 86400.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_s} seeded particles of the 1M workload, intervals {warmup}..{warmup + k - 1} "
-                      f"(after {warmup} untimed), rtol 1e-6, {dt:.1f} s"}
+                      f"(after {warmup} untimed), rtol 1e-6, {dt:.1f} s",
+            "one_core": {"value": n1 * k * DT_S / 86400.0 / dt1, "unit": UNIT, "cores": 1,
+                         "sample": f"{n1} other seeded particles, same intervals, {dt1:.1f} s"}}
 
 
 # --------------------------------------------------------------------------- paper-literal workload

@@ -301,7 +301,7 @@ chad_status chad_synchronize(chad_ctx* ctx);
 chad_status chad_read_states(chad_ctx* ctx, int digester, double* y, double* pos, double* S_H,
                              double* h, int32_t* status, chad_stats* stats, int mem);
 
-/* ---- learned guesses (north star item 4; the paper has no counterpart) --- */
+/* ---- learned guesses (an extension; the paper has no counterpart) -------- */
 
 /* Install a trained MLP into a context with learned = 1.  params [NPARAM]
    FP32 (layout above), feat_norm [2][32]: per-feature mean and 1/std of the

@@ -294,6 +294,56 @@ def test_frames_each_interval_equal_set_positions(tmp_path):
     assert np.array_equal(ra["pos"], rb["pos"]) and np.array_equal(ra["y"], rb["y"])
 
 
+def test_diffusion_kernel_timing_leaves_the_states_alone():
+    """chad_diffusion_kernel_times re-runs the rows and one substep on the
+    interval's scratch: positive times, states and positions unchanged, and
+    the next interval identical to a run without the timing call."""
+    pop = I.config_population(2, n=1500)
+    a = CH.Simulator(pop, diffusion=DIFFUSION, fixed_substeps=2)
+    b = CH.Simulator(pop, diffusion=DIFFUSION, fixed_substeps=2)
+    for sim in (a, b):
+        sim.load()
+        sim.step(60.0, 1)
+    before = a.read()
+    rows_ms, step_ms = CH.chad_diffusion_kernel_times(a.ctx, 3)
+    assert rows_ms > 0.0 and step_ms > 0.0
+    after = a.read()
+    assert np.array_equal(before["y"], after["y"]) and np.array_equal(before["pos"], after["pos"])
+    a.step(60.0, 1)
+    b.step(60.0, 1)
+    ra, rb = a.read(), b.read()
+    a.close()
+    b.close()
+    assert np.array_equal(ra["y"], rb["y"])
+
+
+def test_diffusion_in_the_mixed_form_within_its_tolerance():
+    """Diffusion runs before either precision form: the mixed form with
+    diffusion stays within the mixed form's 1e-4 of the FP64 oracle."""
+    pop = I.config_population(2, n=1200)
+    g = gpu_run(pop, 60.0, 3, diffusion=DIFFUSION, precision=CH.PREC_MIXED, fixed_substeps=4)
+    o = oracle_run(pop, 60.0, 3, diffusion=DIFFUSION, fixed_n=4)
+    assert np.all(g["status"] == 0)
+    assert relerr(g["y"], o["y"]).max() < 1e-4
+
+
+def test_positions_by_id_from_device_buffers():
+    """chad_set_positions_by_id with torch CUDA tensors (the in-memory form of
+    a frame) lands the positions in particle order."""
+    torch = pytest.importorskip("torch")
+    pop = I.config_population(2, n=2000)
+    sim = CH.Simulator(pop)
+    sim.load()
+    new = I.config_population(2, n=2000, seed_offset=41).pos
+    perm = np.random.default_rng(2).permutation(2000)
+    pos_d = torch.from_numpy(np.ascontiguousarray(new[:, perm])).cuda()
+    ids_d = torch.from_numpy(perm.astype(np.int64)).cuda()
+    CH.chad_set_positions_by_id(sim.ctx, 0, 2000, pos_d, ids_d)
+    got = sim.read()["pos"]
+    sim.close()
+    assert np.array_equal(got, new)
+
+
 def test_diffusion_rerun_is_bitwise_deterministic():
     """The cell lists are ordered by particle index after the atomic scatter,
     so the neighbour sums run in a fixed order."""

@@ -225,6 +225,15 @@ chad_status chad_load_frame(chad_ctx* ctx, int digester, const char* path, uint6
 chad_status chad_read_frame(const char* path, int64_t n_max, double* pos, int64_t* id, int64_t* n,
                             uint64_t* step, double* time_s, int32_t* has_id);
 
+/* Checkpoint and resume.  The coupling-interval index keys the advection
+   noise (0 after chad_create, +1 per interval), so a run restored from a
+   checkpoint continues bit for bit when it is put back: save y, pos, S_H, h
+   (chad_read_states), T and this index; restore with chad_load_particles
+   (with S_H and h) for every digester, then chad_set_interval.  Both wait
+   for the context's stream. */
+chad_status chad_get_interval(chad_ctx* ctx, uint64_t* interval);
+chad_status chad_set_interval(chad_ctx* ctx, uint64_t interval);
+
 /* Set (or clear, has_flow = 0) the flow field of one digester. */
 chad_status chad_set_flow(chad_ctx* ctx, int digester, const chad_flow* flow);
 

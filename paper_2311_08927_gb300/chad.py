@@ -143,6 +143,10 @@ def lib():
             L.chad_read_frame.argtypes = [C.c_char_p, C.c_int64, C.c_void_p, C.c_void_p,
                                           C.POINTER(C.c_int64), C.POINTER(C.c_uint64),
                                           C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+            L.chad_get_interval.restype = C.c_int
+            L.chad_get_interval.argtypes = [C.c_void_p, C.POINTER(C.c_uint64)]
+            L.chad_set_interval.restype = C.c_int
+            L.chad_set_interval.argtypes = [C.c_void_p, C.c_uint64]
             L.chad_set_positions.restype = C.c_int
             L.chad_set_positions.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_int]
             L.chad_diffusion_kernel_times.restype = C.c_int
@@ -169,6 +173,7 @@ def exported_symbols() -> list[str]:
             "chad_flop_counts", "chad_set_diffusion", "chad_diffusion_info",
             "chad_diffusion_kernel_times", "chad_set_positions",
             "chad_set_positions_by_id", "chad_load_frame", "chad_read_frame",
+            "chad_get_interval", "chad_set_interval",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
 
@@ -385,6 +390,19 @@ def chad_load_particles(ctx, digester, n, pos, y, T=None, S_H=None, h=None) -> N
         raise ValueError("all buffers of one call must be host or all device")
     mem = mems.pop() if mems else MEM_HOST
     _check(L, ctx, L.chad_load_particles(ctx, int(digester), int(n), *[p for p, _ in ptrs], mem))
+
+
+def chad_get_interval(ctx) -> int:
+    """The coupling-interval index that keys the advection noise."""
+    L = lib()
+    v = C.c_uint64()
+    _check(L, ctx, L.chad_get_interval(ctx, C.byref(v)))
+    return v.value
+
+
+def chad_set_interval(ctx, interval) -> None:
+    L = lib()
+    _check(L, ctx, L.chad_set_interval(ctx, int(interval)))
 
 
 def chad_set_positions(ctx, digester, n, pos) -> None:

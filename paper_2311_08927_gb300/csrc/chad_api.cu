@@ -431,6 +431,23 @@ chad_status chad_load_particles(chad_ctx* c, int digester, int64_t n, const doub
   return CHAD_OK;
 }
 
+chad_status chad_get_interval(chad_ctx* c, uint64_t* interval) {
+  if (!c || !interval) return CHAD_E_INVALID;
+  unsigned long long v = 0;
+  CK(c, cudaMemcpyAsync(&v, c->d_interval, sizeof(v), cudaMemcpyDeviceToHost, c->stream), "interval");
+  CK(c, cudaStreamSynchronize(c->stream), "interval");
+  *interval = (uint64_t)v;
+  return CHAD_OK;
+}
+
+chad_status chad_set_interval(chad_ctx* c, uint64_t interval) {
+  if (!c) return CHAD_E_INVALID;
+  const unsigned long long v = (unsigned long long)interval;
+  CK(c, cudaMemcpyAsync(c->d_interval, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream), "interval");
+  CK(c, cudaStreamSynchronize(c->stream), "interval");
+  return CHAD_OK;
+}
+
 chad_status chad_set_positions(chad_ctx* c, int digester, int64_t n, const double* pos, int mem) {
   if (!c) return CHAD_E_INVALID;
   if (digester < 0 || digester >= c->n_dig) return fail(c, CHAD_E_INVALID, "digester out of range");

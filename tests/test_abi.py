@@ -125,6 +125,8 @@ def test_null_context_calls_are_invalid(L):
     assert L.chad_diffusion_kernel_times(None, 1, None, None) == 1
     assert L.chad_set_positions(None, 0, 0, None, 0) == 1
     assert L.chad_set_positions_by_id(None, 0, 0, None, None, 0) == 1
+    assert L.chad_get_interval(None, None) == 1
+    assert L.chad_set_interval(None, 0) == 1
     assert L.chad_load_frame(None, 0, b"x", None, None) == 1
     assert L.chad_read_frame(None, 0, None, None, None, None, None, None) == 1
     L.chad_destroy(None)

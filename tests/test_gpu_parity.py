@@ -344,6 +344,31 @@ def test_positions_by_id_from_device_buffers():
     assert np.array_equal(got, new)
 
 
+def test_checkpoint_round_trip_is_bitwise():
+    """Stop after two intervals, save y, pos, S_H, h and the interval index,
+    restore into a fresh context and run two more: bitwise the states and
+    positions of an uninterrupted four-interval run (flow with noise, inlet
+    slab, shared headspace, diffusion)."""
+    pop = I.config_population(2, n=1500)
+    full = gpu_run(pop, 60.0, 4, diffusion=DIFFUSION)
+    a = CH.Simulator(pop, diffusion=DIFFUSION)
+    a.load()
+    a.step(60.0, 2)
+    mid = a.read()
+    k = CH.chad_get_interval(a.ctx)
+    a.close()
+    assert k == 2
+    b = CH.Simulator(pop, diffusion=DIFFUSION)
+    b.load(y=mid["y"], pos=mid["pos"], T=pop.T, S_H=mid["S_H"], h=mid["h"])
+    CH.chad_set_interval(b.ctx, k)
+    b.step(60.0, 2)
+    end = b.read()
+    b.close()
+    assert np.array_equal(end["pos"], full["pos"])
+    assert np.array_equal(end["y"], full["y"])
+    assert np.array_equal(end["S_H"], full["S_H"]) and np.array_equal(end["h"], full["h"])
+
+
 def test_diffusion_rerun_is_bitwise_deterministic():
     """The cell lists are ordered by particle index after the atomic scatter,
     so the neighbour sums run in a fixed order."""
@@ -555,6 +580,31 @@ def test_full_size_lab_cylinder_100k_whole_tank():
     assert np.array_equal(g["pos"], o["pos"])
     e = relerr(g["y"], o["y"])
     assert np.median(e) < 1e-10 and e.max() < 1e-5
+
+
+def test_runtime_is_linear_in_particles():
+    """The paper reports ADM1 time linear in the particle count (Sec. 4.3):
+    once the GPU is full, the time per particle-interval of the 1M recipe at
+    1, 2 and 4 million particles agrees within 15 % (intervals 2-4, after a
+    cold start and one warm interval)."""
+    torch = pytest.importorskip("torch")
+    per = []
+    for n in (1_000_000, 2_000_000, 4_000_000):
+        pop = I.config_population(3, n=n)
+        s = torch.cuda.Stream()
+        sim = CH.Simulator(pop, stream=s.cuda_stream)
+        sim.load()
+        sim.step(60.0, 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        sim.step(60.0, 3)
+        e1.record(s)
+        torch.cuda.synchronize()
+        st = sim.read()
+        sim.close()
+        assert np.all(st["status"] == 0)
+        per.append(e0.elapsed_time(e1) / (3 * n))
+    assert max(per) / min(per) < 1.15, per
 
 
 # ------------------------------------------------------------ failure handling

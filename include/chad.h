@@ -225,6 +225,15 @@ chad_status chad_load_frame(chad_ctx* ctx, int digester, const char* path, uint6
 chad_status chad_read_frame(const char* path, int64_t n_max, double* pos, int64_t* id, int64_t* n,
                             uint64_t* step, double* time_s, int32_t* has_id);
 
+/* The bounds-check build (libchad_debug.so, compiled with
+   -DCHAD_DEBUG_BOUNDS): the kernels with data-dependent indices (the
+   diffusion cell lists, neighbour ranges and stored columns, the ordering
+   scatter) check each index, record a failed check as a bit in *status
+   (one bit per check site) and skip the access instead of trapping.
+   *enabled = 1 in that build, 0 in the normal one (whose *status is always
+   0).  reset != 0 clears the bits after reading.  Needs no context. */
+chad_status chad_debug_bounds(int32_t* enabled, uint32_t* status, int reset);
+
 /* Checkpoint and resume.  The coupling-interval index keys the advection
    noise (0 after chad_create, +1 per interval), so a run restored from a
    checkpoint continues bit for bit when it is put back: save y, pos, S_H, h

@@ -17,6 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libchad.so")
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libchad_debug.so")  # bounds-check build (-DCHAD_DEBUG_BOUNDS)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
@@ -38,11 +40,12 @@ def _headers():
             glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-def _compile(src: str, hdr_mtime: float, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, hdr_mtime: float, verbose: bool, build_dir: str = BUILD,
+             extra: tuple = ()) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_mtime):
         return obj
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
     if src.endswith(".cpp"):
         cmd.insert(1, "-x=cu")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -54,25 +57,30 @@ def _compile(src: str, hdr_mtime: float, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug_bounds: bool = False) -> str:
+    """Build libchad.so, or with debug_bounds the bounds-check library
+    libchad_debug.so (same sources, -DCHAD_DEBUG_BOUNDS, its own objects)."""
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug_bounds else (BUILD, LIB)
+    extra = ("-DCHAD_DEBUG_BOUNDS",) if debug_bounds else ()
+    os.makedirs(build_dir, exist_ok=True)
     srcs = _sources()
     hdr_mtime = max(os.path.getmtime(h) for h in _headers())
     if force:
-        for o in glob.glob(os.path.join(BUILD, "*.o")):
+        for o in glob.glob(os.path.join(build_dir, "*.o")):
             os.remove(o)
     with cf.ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 1, 4), len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, hdr_mtime, verbose), srcs))
-    if (not force and os.path.exists(LIB) and
-            os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs)):
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, hdr_mtime, verbose, build_dir, extra), srcs))
+    if (not force and os.path.exists(lib) and
+            os.path.getmtime(lib) >= max(os.path.getmtime(o) for o in objs)):
+        return lib
+    LIB_OUT = lib
+    tmp = LIB_OUT + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, LIB_OUT)
+    return LIB_OUT
 
 
 if __name__ == "__main__":

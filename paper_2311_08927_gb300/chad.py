@@ -16,7 +16,9 @@ import numpy as np
 from . import inputs as I
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libchad.so")
+# CHAD_LIB selects another build of the library (the bounds-check build,
+# libchad_debug.so); by default the in-tree libchad.so
+LIB_PATH = os.environ.get("CHAD_LIB") or os.path.join(_HERE, "libchad.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -143,6 +145,8 @@ def lib():
             L.chad_read_frame.argtypes = [C.c_char_p, C.c_int64, C.c_void_p, C.c_void_p,
                                           C.POINTER(C.c_int64), C.POINTER(C.c_uint64),
                                           C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+            L.chad_debug_bounds.restype = C.c_int
+            L.chad_debug_bounds.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_uint32), C.c_int]
             L.chad_get_interval.restype = C.c_int
             L.chad_get_interval.argtypes = [C.c_void_p, C.POINTER(C.c_uint64)]
             L.chad_set_interval.restype = C.c_int
@@ -173,7 +177,7 @@ def exported_symbols() -> list[str]:
             "chad_flop_counts", "chad_set_diffusion", "chad_diffusion_info",
             "chad_diffusion_kernel_times", "chad_set_positions",
             "chad_set_positions_by_id", "chad_load_frame", "chad_read_frame",
-            "chad_get_interval", "chad_set_interval",
+            "chad_get_interval", "chad_set_interval", "chad_debug_bounds",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
 
@@ -390,6 +394,16 @@ def chad_load_particles(ctx, digester, n, pos, y, T=None, S_H=None, h=None) -> N
         raise ValueError("all buffers of one call must be host or all device")
     mem = mems.pop() if mems else MEM_HOST
     _check(L, ctx, L.chad_load_particles(ctx, int(digester), int(n), *[p for p, _ in ptrs], mem))
+
+
+def chad_debug_bounds(reset=False):
+    """(enabled, status bits) of the bounds-check build; (0, 0) in the normal one."""
+    L = lib()
+    en, st = C.c_int32(), C.c_uint32()
+    code = L.chad_debug_bounds(C.byref(en), C.byref(st), int(bool(reset)))
+    if code != 0:
+        raise ChadError(code, "reading the bounds-check status failed")
+    return en.value, st.value
 
 
 def chad_get_interval(ctx) -> int:

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "bounds.h"
 #include "adm1_device.cuh"
 #include "kernels.h"
 
@@ -161,6 +162,8 @@ __device__ __forceinline__ int order_bucket(double h, double dt) {
   return k < 0 ? 0 : (k > kOrderBuckets - 1 ? kOrderBuckets - 1 : k);
 }
 
+CHAD_BOUNDS_WORD(aux)
+
 __global__ void order_count(const double* h, int64_t n, double dt, int* counts) {
   __shared__ int loc[kOrderBuckets];
   if (threadIdx.x < kOrderBuckets) loc[threadIdx.x] = 0;
@@ -181,7 +184,8 @@ __global__ void order_scatter(const double* h, int64_t n, double dt, int* counts
   }
   __syncthreads();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = p < n ? order_bucket(h[p], dt) : 0;
+  int b = p < n ? order_bucket(h[p], dt) : 0;
+  if (!CHAD_IN_BOUNDS(aux, b >= 0 && b < kOrderBuckets, kBoundsBucket)) b = 0;
   if (p < n) atomicAdd(&loc[b], 1);
   __syncthreads();
   if (threadIdx.x < kOrderBuckets) {
@@ -191,7 +195,10 @@ __global__ void order_scatter(const double* h, int64_t n, double dt, int* counts
     base[k] = loc[k] ? start + atomicAdd(&counts[kOrderBuckets + k], loc[k]) : 0;
   }
   __syncthreads();
-  if (p < n) order[base[b] + atomicAdd(&rank[b], 1)] = (int)p;
+  if (p < n) {
+    const int at = base[b] + atomicAdd(&rank[b], 1);
+    if (CHAD_IN_BOUNDS(aux, at >= 0 && at < n, kBoundsOrder)) order[at] = (int)p;
+  }
 }
 
 __global__ void check_load_kernel(const double* y, int64_t ld, const double* T, int64_t o,
@@ -292,5 +299,7 @@ cudaError_t launch_headspace(const HeadspaceArgs& a, cudaStream_t s) {
   headspace_broadcast<<<(unsigned)((a.n + 255) / 256), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
+
+CHAD_BOUNDS_ACCESSOR(aux)
 
 }  // namespace chad

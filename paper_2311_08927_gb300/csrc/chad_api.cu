@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "bounds.h"
 #include "chad.h"
 #include "diffusion.h"
 #include "frames.h"
@@ -429,6 +430,17 @@ chad_status chad_load_particles(chad_ctx* c, int digester, int64_t n, const doub
   }
   c->loaded[digester] = 1;
   return CHAD_OK;
+}
+
+chad_status chad_debug_bounds(int32_t* enabled, uint32_t* status, int reset) {
+#ifdef CHAD_DEBUG_BOUNDS
+  if (enabled) *enabled = 1;
+#else
+  if (enabled) *enabled = 0;
+#endif
+  const unsigned int v = bounds_status_diffusion(reset != 0) | bounds_status_aux(reset != 0);
+  if (status) *status = v;
+  return v == ~0u ? CHAD_E_CUDA : CHAD_OK;
 }
 
 chad_status chad_get_interval(chad_ctx* c, uint64_t* interval) {

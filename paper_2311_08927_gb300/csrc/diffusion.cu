@@ -29,11 +29,14 @@
 
 #include <cstdint>
 
+#include "bounds.h"
 #include "diffusion.h"
 #include "model.h"
 
 namespace chad {
 namespace {
+
+CHAD_BOUNDS_WORD(diffusion)
 
 __constant__ int kDiffStates[kNumDiffusing] = {iS_su, iS_aa, iS_fa, iS_va, iS_bu,  iS_pro, iS_ac,
                                                iS_h2, iS_ch4, iS_IC, iS_IN, iS_I, iS_cat, iS_an};
@@ -58,6 +61,7 @@ __global__ void diff_count(DiffArgs a) {
   if (!g.on) return;
   int cx, cy, cz;
   const int c = cell_of(g, a.pos[p], a.pos[a.ld + p], a.pos[2 * a.ld + p], cx, cy, cz);
+  if (!CHAD_IN_BOUNDS(diffusion, c >= 0 && c < a.n_cells, kBoundsCell)) return;
   atomicAdd(&a.cell_count[c], 1);
 }
 
@@ -97,7 +101,10 @@ __global__ void diff_scatter(DiffArgs a) {
   if (!g.on) return;
   int cx, cy, cz;
   const int c = cell_of(g, a.pos[p], a.pos[a.ld + p], a.pos[2 * a.ld + p], cx, cy, cz);
-  a.cell_list[a.cell_start[c] + atomicAdd(&a.cell_count[c], 1)] = (int)p;
+  if (!CHAD_IN_BOUNDS(diffusion, c >= 0 && c < a.n_cells, kBoundsCell)) return;
+  const int slot = a.cell_start[c] + atomicAdd(&a.cell_count[c], 1);
+  if (!CHAD_IN_BOUNDS(diffusion, slot >= 0 && slot < a.n, kBoundsScatter)) return;
+  a.cell_list[slot] = (int)p;
 }
 
 // Order each cell's list by particle index (insertion sort; cells hold a few
@@ -146,7 +153,9 @@ __device__ __forceinline__ void for_each_neighbour(const DiffArgs& a, const Diff
       const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
       const int c0 = g.cell0 + (z * g.ny + yy) * g.nx;
       // the x-neighbours are adjacent cells, so their slots are one range
+      if (!CHAD_IN_BOUNDS(diffusion, c0 + x1 + 1 <= a.n_cells, kBoundsRange)) continue;
       const int b = a.cell_start[c0 + x0], e = a.cell_start[c0 + x1 + 1];
+      if (!CHAD_IN_BOUNDS(diffusion, b >= 0 && e <= a.n, kBoundsRange)) continue;
       for (int m = b; m < e; ++m) {
         const float4 pm = a.sposf[m];
         const float fx = pi.x - pm.x, fy = pi.y - pm.y, fz = pi.z - pm.z;
@@ -227,7 +236,9 @@ __global__ void __launch_bounds__(kRowsBlock) diff_rows(DiffArgs a) {
       const int yy = cy + dy;
       if (yy < 0 || yy >= g.ny) continue;
       const int c0 = g.cell0 + (z * g.ny + yy) * g.nx;
+      if (!CHAD_IN_BOUNDS(diffusion, c0 + x1 + 1 <= a.n_cells, kBoundsRange)) continue;
       const int b = a.cell_start[c0 + x0], e = a.cell_start[c0 + x1 + 1];
+      if (!CHAD_IN_BOUNDS(diffusion, b >= 0 && e <= a.n, kBoundsRange)) continue;
       for (int m0 = b; m0 < e; m0 += 32) bound += __popc(__ballot_sync(full, pretest(m0 + lane, e)));
     }
   }
@@ -268,12 +279,15 @@ __global__ void __launch_bounds__(kRowsBlock) diff_rows(DiffArgs a) {
       const int yy = cy + dy;
       if (yy < 0 || yy >= g.ny) continue;
       const int c0 = g.cell0 + (z * g.ny + yy) * g.nx;
+      if (!CHAD_IN_BOUNDS(diffusion, c0 + x1 + 1 <= a.n_cells, kBoundsRange)) continue;
       const int b = a.cell_start[c0 + x0], e = a.cell_start[c0 + x1 + 1];
+      if (!CHAD_IN_BOUNDS(diffusion, b >= 0 && e <= a.n, kBoundsRange)) continue;
       for (int m0 = b; m0 < e; m0 += 32) {
         const int m = m0 + lane;
         const bool pass = pretest(m, e);
         const unsigned got = __ballot_sync(full, pass);
-        if (pass) q[queued + __popc(got & below)] = m;
+        const int at = queued + __popc(got & below);
+        if (pass && CHAD_IN_BOUNDS(diffusion, at < 64, kBoundsQueue)) q[at] = m;
         queued += __popc(got);
         __syncwarp();
         if (queued >= 32) {
@@ -336,6 +350,12 @@ __global__ void __launch_bounds__(kStepBlock) diff_step(DiffArgs a, int sub) {
       const int m0 = col[e], m1 = col[e + 1], m2 = col[e + 2], m3 = col[e + 3];
       const double w0 = val[e], w1 = val[e + 1], w2 = val[e + 2], w3 = val[e + 3];
       double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+#ifdef CHAD_DEBUG_BOUNDS
+      const int ns = n_slots(a);
+      if (!CHAD_IN_BOUNDS(diffusion, m0 >= 0 && m0 < ns && m1 >= 0 && m1 < ns && m2 >= 0 && m2 < ns &&
+                                         m3 >= 0 && m3 < ns, kBoundsColumn))
+        continue;
+#endif
       if (on) {
         c0 = src[(int64_t)m0 * kDiffRow + k];
         c1 = src[(int64_t)m1 * kDiffRow + k];
@@ -347,7 +367,10 @@ __global__ void __launch_bounds__(kStepBlock) diff_step(DiffArgs a, int sub) {
       acc = fma(w2, c2, acc);
       acc = fma(w3, c3, acc);
     }
-    for (; e < len; ++e) acc = fma(val[e], on ? src[(int64_t)col[e] * kDiffRow + k] : 0.0, acc);
+    for (; e < len; ++e) {
+      if (!CHAD_IN_BOUNDS(diffusion, col[e] >= 0 && col[e] < n_slots(a), kBoundsColumn)) continue;
+      acc = fma(val[e], on ? src[(int64_t)col[e] * kDiffRow + k] : 0.0, acc);
+    }
   } else {
     const DiffConst& g = a.dc[a.sdig[i]];
     for_each_neighbour(a, g, (int)i, a.spos[i], a.spos[a.n + i], a.spos[2 * a.n + i], a.sposf[i],
@@ -396,6 +419,8 @@ cudaError_t launch_diffusion(const DiffArgs& a, cudaStream_t s) {
   diff_store<<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
+
+CHAD_BOUNDS_ACCESSOR(diffusion)
 
 cudaError_t time_diffusion_kernels(const DiffArgs& a, int reps, float* ms_rows, float* ms_step,
                                    cudaStream_t s) {

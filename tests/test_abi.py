@@ -130,3 +130,7 @@ def test_null_context_calls_are_invalid(L):
     assert L.chad_load_frame(None, 0, b"x", None, None) == 1
     assert L.chad_read_frame(None, 0, None, None, None, None, None, None) == 1
     L.chad_destroy(None)
+
+
+def test_normal_build_has_no_bounds_checks(L):
+    assert CH.chad_debug_bounds() == (0, 0)

@@ -369,6 +369,59 @@ def test_checkpoint_round_trip_is_bitwise():
     assert np.array_equal(end["S_H"], full["S_H"]) and np.array_equal(end["h"], full["h"])
 
 
+_BOUNDS_SCRIPT = r"""
+import dataclasses, sys
+import numpy as np
+from paper_2311_08927_gb300 import chad as CH, inputs as I
+assert CH.chad_debug_bounds(reset=True)[0] == 1
+# diffusion: lab cylinder, then crowded particles (rows beyond the capacity
+# formed on the fly) and a capped plan
+for s_, dif in ((1.0, (1e-5, 0.024)), (0.15, (1e-6, 0.024)), (0.15, (6.5e-6, 0.024))):
+    pop = I.config_population(2, n=1500)
+    c = np.array([0.0, 0.0, 0.15])[:, None]
+    pop.pos = c + s_ * (pop.pos - c)
+    sim = CH.Simulator(pop, diffusion=dif)
+    sim.load()
+    sim.step(1.0 if s_ < 1.0 else 60.0, 2)
+    sim.read()
+    sim.close()
+# positions by id, the adaptive integrator with its ordering pass, 64 digesters
+pop = I.config_population(2, n=1000)
+sim = CH.Simulator(pop)
+sim.load()
+perm = np.random.default_rng(1).permutation(1000)
+CH.chad_set_positions_by_id(sim.ctx, 0, 1000, np.ascontiguousarray(pop.pos[:, perm]), perm.astype(np.int64))
+sim.step(60.0, 2)
+sim.close()
+for cfg, n in ((3, 3000), (5, 3000)):
+    sim = CH.Simulator(I.config_population(cfg, n=n))
+    sim.load()
+    sim.step(60.0, 2)
+    sim.read()
+    sim.close()
+en, st = CH.chad_debug_bounds()
+print("bounds", en, st)
+sys.exit(0 if (en == 1 and st == 0) else 1)
+"""
+
+
+def test_bounds_check_build_records_no_violation():
+    """The bounds-check build (libchad_debug.so) checks every data-dependent
+    index of the diffusion, ordering and frame kernels and records a failed
+    check instead of trapping; small runs of every path record none."""
+    import os
+    import subprocess
+    import sys
+    from paper_2311_08927_gb300 import build as B
+    lib = B.build(debug_bounds=True)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CHAD_LIB=lib, PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", _BOUNDS_SCRIPT], env=env, cwd=root,
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "bounds 1 0" in r.stdout
+
+
 def test_diffusion_rerun_is_bitwise_deterministic():
     """The cell lists are ordered by particle index after the atomic scatter,
     so the neighbour sums run in a fixed order."""

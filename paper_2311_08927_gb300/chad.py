@@ -523,6 +523,7 @@ class Simulator:
         self.pop = pop
         nd = len(pop.digesters)
         self._keep = []
+        self._T = None
 
         def arr(x, dt=np.float64):
             a = np.ascontiguousarray(x, dtype=dt)
@@ -577,10 +578,25 @@ class Simulator:
         y = pop.y if y is None else y
         pos = pop.pos if pos is None else pos
         T = pop.T if T is None else T
+        self._T = np.asarray(T)
         for d, dg in enumerate(pop.digesters):
             a, b = self.offsets[d], self.offsets[d + 1]
             sl = lambda x: None if x is None else np.ascontiguousarray(x[..., a:b])
             chad_load_particles(self.ctx, d, b - a, sl(pos), sl(y), sl(T), sl(S_H), sl(h))
+
+    def checkpoint(self, path):
+        """Save what a bitwise resume needs: y, pos, S_H, h (every digester),
+        the temperatures and the interval index, as one .npz file."""
+        out = self.read()
+        T = np.ascontiguousarray(self.pop.T if self._T is None else self._T)
+        np.savez(path, y=out["y"], pos=out["pos"], S_H=out["S_H"], h=out["h"], T=T,
+                 interval=np.uint64(chad_get_interval(self.ctx)))
+
+    def restore(self, path):
+        """Load a checkpoint written by checkpoint() into this context."""
+        with np.load(path) as z:
+            self.load(y=z["y"], pos=z["pos"], T=z["T"], S_H=z["S_H"], h=z["h"])
+            chad_set_interval(self.ctx, int(z["interval"]))
 
     def set_positions(self, pos):
         """New positions [3][N] for every digester (an external CFD's coupling step)."""

@@ -344,7 +344,7 @@ def test_positions_by_id_from_device_buffers():
     assert np.array_equal(got, new)
 
 
-def test_checkpoint_round_trip_is_bitwise():
+def test_checkpoint_round_trip_is_bitwise(tmp_path):
     """Stop after two intervals, save y, pos, S_H, h and the interval index,
     restore into a fresh context and run two more: bitwise the states and
     positions of an uninterrupted four-interval run (flow with noise, inlet
@@ -367,6 +367,18 @@ def test_checkpoint_round_trip_is_bitwise():
     assert np.array_equal(end["pos"], full["pos"])
     assert np.array_equal(end["y"], full["y"])
     assert np.array_equal(end["S_H"], full["S_H"]) and np.array_equal(end["h"], full["h"])
+    # the same through the binding's checkpoint file
+    c = CH.Simulator(pop, diffusion=DIFFUSION)
+    c.load()
+    c.step(60.0, 2)
+    c.checkpoint(tmp_path / "ck.npz")
+    c.close()
+    d = CH.Simulator(pop, diffusion=DIFFUSION)
+    d.restore(tmp_path / "ck.npz")
+    d.step(60.0, 2)
+    end2 = d.read()
+    d.close()
+    assert np.array_equal(end2["y"], full["y"]) and np.array_equal(end2["pos"], full["pos"])
 
 
 _BOUNDS_SCRIPT = r"""

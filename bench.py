@@ -375,7 +375,8 @@ def run_ours(args, ws, rank, local):
                               "frac": H["achieved32_tflops"] / peak32}},
         "peaks_measured": {"fp64_tflops": peak64, "fp32_tflops": peak32},
         "clocks": fr,
-        "gpu_launches": args.steps,
+        # per interval: order_count, order_scatter, integrate_kernel, bump_kernel
+        "gpu_launches": 4 * args.steps,
         "steps_per_particle_interval": H["stats"]["accepted_steps"] / (N * args.steps),
         "rejected_per_particle_interval": H["stats"]["rejected_steps"] / (N * args.steps),
         "failed_particles": H["failed"],

@@ -259,7 +259,8 @@ chad_status chad_set_flow(chad_ctx* ctx, int digester, const chad_flow* flow);
    substep count follows the particles: each interval the largest row sum
    S of the discrete operator (over all diffusing particles) is taken and
    ceil(dt S) substeps are made (every update stays a convex combination),
-   at most 8 times the continuum estimate dt 7 D / h^2 (at least 8); a
+   at most 8 times the continuum estimate dt 7 D / h^2 (at least 8, at most
+   4096); a
    plan above that runs the maximum and sets CHAD_P_DIFFUSION on the
    diffusing particles.  Needs the digester's flow geometry (chad_set_flow with has_flow, else
    CHAD_E_STATE).  Allocates the neighbour-grid buffers on first use; the

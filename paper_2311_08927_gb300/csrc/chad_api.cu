@@ -709,6 +709,7 @@ static chad_status prepare_flow(chad_ctx* c, double dt_coupling_s) {
 // the substep kernels to enqueue: 8 times the continuum estimate
 // dt 7 D / h^2 of the substep count (largest over the digesters), at least 8.
 constexpr int64_t kDiffMaxEntries = int64_t(1) << 29;  // 6 GiB of entries at most
+constexpr int64_t kMaxDiffusionSubsteps = 4096;
 
 // Smallest x >= 0 whose correctly rounded square root is >= t: for r2 >= 0,
 // sqrt(r2) < t exactly when r2 < x.
@@ -759,7 +760,7 @@ static chad_status prepare_diffusion(chad_ctx* c, double dt_s) {
     q.r2f_max = std::nextafter((float)((2.0 * h + margin) * (2.0 * h + margin)), HUGE_VALF);
     // continuum estimates: 7 D / h^2 for the row sum (Wendland C2), the
     // support's share of the cylinder for the neighbours
-    nsub = std::max(nsub, (int)std::ceil(dt_s * 7.0 * D / (h * h)));
+    nsub = (int)std::min(1.0e6, std::max((double)nsub, std::ceil(dt_s * 7.0 * D / (h * h))));
     const double n_d = (double)c->count[d];
     const double share = (4.0 / 3.0) * (8.0 * h * h * h) / (q.R * q.R * q.H);
     entries += n_d * std::min(n_d - 1.0, n_d * share);
@@ -796,7 +797,9 @@ static chad_status prepare_diffusion(chad_ctx* c, double dt_s) {
   CK(c, cudaMemcpy(c->d_diffc, g.data(), sizeof(DiffConst) * c->n_dig, cudaMemcpyHostToDevice),
      "diffusion constants");
   c->n_cells = (int)cells;
-  c->diff_max_sub = std::max(8, 8 * nsub);
+  // at most kMaxDiffusionSubsteps kernels in an interval's graph; a plan
+  // above them runs that many and flags the particles (CHAD_P_DIFFUSION)
+  c->diff_max_sub = (int)std::min<int64_t>(kMaxDiffusionSubsteps, std::max<int64_t>(8, 8 * (int64_t)nsub));
   c->diff_dt = dt_s;
   c->diff_dirty = false;
   drop_graph(c);

@@ -317,68 +317,99 @@ __global__ void __launch_bounds__(TILE, kBlocksPerSM) guess_kernel(const double*
 constexpr size_t smem_bytes() { return sizeof(Smem) + 128; }
 
 // Fused forward + backward of the mean-squared loss on the tensor cores, 128
-// samples per tile, one CTA per SM walking its tiles in a fixed order:
+// samples per tile, one CTA per SM holding two tile pipelines (4 warps each),
+// so that one pipeline's epilogue overlaps the other's MMAs.  Per tile:
 //   Z1 = X W1^T, Z2 = A1 W2^T (as in the forward kernel), the output layer,
 //   dO = 2 (O - Y) / n and dZ2 = (dO W3) * silu'(Z2) on the CUDA cores,
 //   dA1 = dZ2 W2 (MMA, W2 held transposed), dZ1 = dA1 * silu'(Z1),
 //   G12 += [dZ2^T; dZ1^T] [A1 | X | 1]   (128 x 112, K = the tile's samples)
 //   G3  += [A2^T; 1] [dO | 0]            (128 x 16)
-// G12 and G3 stay in tensor memory across the CTA's tiles; their blocks are
-// gW2, gW1 and, through the rows and columns of ones, the bias gradients.
-// The CTA writes them as its gradient partial (summed over CTAs in a fixed
-// order afterwards, so the result is deterministic).
+// G12 and G3 stay in each pipeline's half of tensor memory across its tiles;
+// their blocks are gW2, gW1 and, through the rows and columns of ones, the
+// bias gradients.  The CTA writes the two pipelines' sum as its gradient
+// partial (partials are summed over CTAs in a fixed order afterwards, so the
+// result is deterministic).
 namespace gr {
 
-constexpr uint32_t kTmemCols = 256;  // Z1 0-63, Z2 / dA1 64-127, G12 128-239, G3 240-255
+constexpr int kPipes = 2;                   // tile pipelines per CTA
+constexpr int kThreads = kPipes * TILE;
+constexpr uint32_t kColsPerPipe = 256;      // Z1 0-63, Z2 / dA1 64-127, G12 128-239, G3 240-255
+constexpr uint32_t kTmemCols = kPipes * kColsPerPipe;  // all 512 columns of the SM
 constexpr int N12 = 112, N3 = 16, KS = TILE;  // KS: samples per tile = K of the weight gradients
+// Rows the weight-gradient operands hold.  The MMAs read N12, TILE and N3
+// rows; the rows past these fall in the buffers that follow in shared memory
+// (bf16 operand or weight arrays), and their values reach only accumulator
+// columns (104-111 of G12, 8-15 of G3) or rows (72-127 of G3) never read.
+constexpr int kB12Rows = 104, kA3Rows = 72, kB3Rows = 8;
+
+struct Pipe {
+  __nv_bfloat16 A12[TILE * KS];      // (row, sample): dZ2^T rows 0-63, dZ1^T rows 64-127;
+                                     // the X tile (sample, feature) uses its start until Z1 is formed
+  __nv_bfloat16 A1[TILE * HID];      // (sample, unit); dZ2 (sample, unit) once Z2 is formed
+  __nv_bfloat16 B12[kB12Rows * KS];  // (col, sample): A1^T 0-63, X^T 64-95, ones 96, zeros 97-103
+  __nv_bfloat16 A3[kA3Rows * KS];    // (row, sample): A2^T 0-63, ones 64, zeros 65-71
+  __nv_bfloat16 B3[kB3Rows * KS];    // (col, sample): dO 0-1, zeros 2-7
+};
 
 struct Smem {
-  __nv_bfloat16 X[TILE * IN];        // K-major (sample, feature)
-  __nv_bfloat16 A1[TILE * HID];      // K-major (sample, unit)
-  __nv_bfloat16 dZ2[TILE * HID];     // K-major (sample, unit)
-  __nv_bfloat16 A12[TILE * KS];      // K-major (row, sample): dZ2^T rows 0-63, dZ1^T rows 64-127
-  __nv_bfloat16 B12[N12 * KS];       // K-major (col, sample): A1^T 0-63, X^T 64-95, ones 96, zeros
-  __nv_bfloat16 A3[TILE * KS];       // K-major (row, sample): A2^T 0-63, ones 64, zeros
-  __nv_bfloat16 B3[N3 * KS];         // K-major (col, sample): dO 0-1, zeros
+  Pipe pipe[kPipes];
   __nv_bfloat16 W1[HID * IN];
   __nv_bfloat16 W2[HID * HID];
   __nv_bfloat16 W2T[HID * HID];
   float b1[HID], b2[HID], W3[OUT * HID], b3[OUT];
-  float loss[TILE / 32];
-  unsigned long long mbar;
+  float loss[kThreads / 32];
+  unsigned long long mbar[kPipes];
   uint32_t tmem;
 };
 
 constexpr size_t smem_bytes() { return sizeof(Smem) + 128; }
 
-__global__ void __launch_bounds__(TILE, 1) grad_kernel(const __nv_bfloat16* X, const float* Y,
-                                                       int64_t n, float inv_n, const float* P,
-                                                       float* partial, float* loss_partial,
-                                                       int* err) {
+// Barrier of one pipeline's 128 threads (ids 1, 2; id 0 is __syncthreads).
+__device__ __forceinline__ void pipe_sync(int id) {
+  asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+}
+__device__ __forceinline__ bool pipe_and(int id, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.and.pred p, %2, 128, q;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id)
+      : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) grad_kernel(const __nv_bfloat16* X, const float* Y,
+                                                           int64_t n, float inv_n, const float* P,
+                                                           float* partial, float* loss_partial,
+                                                           int* err) {
   extern __shared__ unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cta_tid = threadIdx.x, warp = cta_tid >> 5, lane = cta_tid & 31;
+  const int pi = cta_tid / TILE, tid = cta_tid % TILE;  // pipeline, thread (= tile row) within it
+  const int bar_id = 1 + pi;
+  Pipe& b = s.pipe[pi];
   const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
-  for (int i = tid; i < HID * IN; i += TILE) s.W1[kmaj(i / IN, i % IN, IN)] = __float2bfloat16_rn(P[OFF_W1 + i]);
-  for (int i = tid; i < HID * HID; i += TILE) {
+  for (int i = cta_tid; i < HID * IN; i += kThreads) s.W1[kmaj(i / IN, i % IN, IN)] = __float2bfloat16_rn(P[OFF_W1 + i]);
+  for (int i = cta_tid; i < HID * HID; i += kThreads) {
     const int o = i / HID, c = i % HID;
     const __nv_bfloat16 w = __float2bfloat16_rn(P[OFF_W2 + i]);
     s.W2[kmaj(o, c, HID)] = w;   // B of Z2 = A1 W2^T: (n = o, k = c)
     s.W2T[kmaj(c, o, HID)] = w;  // B of dA1 = dZ2 W2: (n = c, k = o)
   }
-  for (int i = tid; i < HID; i += TILE) {
+  for (int i = cta_tid; i < HID; i += kThreads) {
     s.b1[i] = P[OFF_B1 + i];
     s.b2[i] = P[OFF_B2 + i];
   }
-  for (int i = tid; i < OUT * HID; i += TILE) s.W3[i] = __bfloat162float(__float2bfloat16_rn(P[OFF_W3 + i]));
-  if (tid < OUT) s.b3[tid] = P[OFF_B3 + tid];
-  // constant rows: ones and zeros of the weight-gradient operands
+  for (int i = cta_tid; i < OUT * HID; i += kThreads) s.W3[i] = __bfloat162float(__float2bfloat16_rn(P[OFF_W3 + i]));
+  if (cta_tid < OUT) s.b3[cta_tid] = P[OFF_B3 + cta_tid];
+  // constant rows of this pipeline's weight-gradient operands
   for (int k = 0; k < KS; ++k) {
-    if (tid >= HID + IN && tid < N12) s.B12[kmaj(tid, k, KS)] = tid == HID + IN ? one : zero;
-    if (tid >= HID) s.A3[kmaj(tid, k, KS)] = tid == HID ? one : zero;
-    if (tid >= OUT && tid < N3) s.B3[kmaj(tid, k, KS)] = zero;
+    if (tid >= HID + IN && tid < kB12Rows) b.B12[kmaj(tid, k, KS)] = tid == HID + IN ? one : zero;
+    if (tid >= HID && tid < kA3Rows) b.A3[kmaj(tid, k, KS)] = tid == HID ? one : zero;
+    if (tid >= OUT && tid < kB3Rows) b.B3[kmaj(tid, k, KS)] = zero;
   }
-  const uint32_t bar = smem_u32(&s.mbar);
+  const uint32_t bar = smem_u32(&s.mbar[pi]);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -393,12 +424,14 @@ __global__ void __launch_bounds__(TILE, 1) grad_kernel(const __nv_bfloat16* X, c
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = s.tmem;
-  const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
-  const uint32_t x_a = smem_u32(s.X), a1_a = smem_u32(s.A1), dz2_a = smem_u32(s.dZ2);
-  const uint32_t a12_a = smem_u32(s.A12), b12_a = smem_u32(s.B12), a3_a = smem_u32(s.A3),
-                 b3_a = smem_u32(s.B3);
+  const uint32_t tmem = s.tmem + pi * kColsPerPipe;
+  const uint32_t row = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t x_a = smem_u32(b.A12), a1_a = smem_u32(b.A1), dz2_a = smem_u32(b.A1);
+  const uint32_t a12_a = smem_u32(b.A12), b12_a = smem_u32(b.B12), a3_a = smem_u32(b.A3),
+                 b3_a = smem_u32(b.B3);
   const uint32_t w1_a = smem_u32(s.W1), w2_a = smem_u32(s.W2), w2t_a = smem_u32(s.W2T);
+  __nv_bfloat16* const Xs = b.A12;   // the X tile, until Z1 is formed
+  __nv_bfloat16* const dZ2s = b.A1;  // dZ2, once Z2 is formed
   constexpr uint32_t kId64 = idesc_bf16(TILE, HID), kId12 = idesc_bf16(TILE, N12),
                      kId3 = idesc_bf16(TILE, N3);
   uint32_t phase = 0;
@@ -408,15 +441,18 @@ __global__ void __launch_bounds__(TILE, 1) grad_kernel(const __nv_bfloat16* X, c
   auto sync_issue = [&]() {
     fence_async_smem();
     fence_before();
-    __syncthreads();
+    pipe_sync(bar_id);
   };
   auto wait = [&]() {
-    ok = __syncthreads_and(mbar_wait(bar, phase));
+    ok = pipe_and(bar_id, mbar_wait(bar, phase));
     phase ^= 1;
     fence_after();
     return ok;
   };
-  for (int64_t m0 = (int64_t)blockIdx.x * TILE; m0 < n && ok; m0 += (int64_t)gridDim.x * TILE) {
+  // tiles go to the CTAs first, then to their second pipelines, so a batch
+  // of fewer tiles than CTAs still spreads over every SM
+  const int64_t stride = (int64_t)gridDim.x * kPipes * TILE;
+  for (int64_t m0 = ((int64_t)pi * gridDim.x + blockIdx.x) * TILE; m0 < n && ok; m0 += stride) {
     const int64_t p = m0 + tid;
     const bool live = p < n;
     // X tile: (sample, feature) for Z1 and (feature, sample) for G12
@@ -428,10 +464,10 @@ __global__ void __launch_bounds__(TILE, 1) grad_kernel(const __nv_bfloat16* X, c
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      *reinterpret_cast<uint4*>(&s.X[kmaj(tid, 8 * j, IN)]) = v[j];
+      *reinterpret_cast<uint4*>(&Xs[kmaj(tid, 8 * j, IN)]) = v[j];
       const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v[j]);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) s.B12[kmaj(HID + 8 * j + q, tid, KS)] = e[q];
+      for (int q = 0; q < 8; ++q) b.B12[kmaj(HID + 8 * j + q, tid, KS)] = e[q];
     }
     sync_issue();
     if (tid == 0) {
@@ -450,10 +486,10 @@ __global__ void __launch_bounds__(TILE, 1) grad_kernel(const __nv_bfloat16* X, c
 #pragma unroll
       for (int j = 0; j < 16; ++j) z[j] = silu(z[j] + s.b1[c + j]);
       const uint4 u0 = pack8(z), u1 = pack8(z + 8);
-      *reinterpret_cast<uint4*>(&s.A1[kmaj(tid, c, HID)]) = u0;
-      *reinterpret_cast<uint4*>(&s.A1[kmaj(tid, c + 8, HID)]) = u1;
+      *reinterpret_cast<uint4*>(&b.A1[kmaj(tid, c, HID)]) = u0;
+      *reinterpret_cast<uint4*>(&b.A1[kmaj(tid, c + 8, HID)]) = u1;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) s.B12[kmaj(c + j, tid, KS)] = __float2bfloat16_rn(z[j]);
+      for (int j = 0; j < 16; ++j) b.B12[kmaj(c + j, tid, KS)] = __float2bfloat16_rn(z[j]);
     }
     sync_issue();
     if (tid == 0) {
@@ -489,8 +525,8 @@ __global__ void __launch_bounds__(TILE, 1) grad_kernel(const __nv_bfloat16* X, c
       d0 *= 2.0f * inv_n;
       d1 *= 2.0f * inv_n;
     }
-    s.B3[kmaj(0, tid, KS)] = __float2bfloat16_rn(d0);
-    s.B3[kmaj(1, tid, KS)] = __float2bfloat16_rn(d1);
+    b.B3[kmaj(0, tid, KS)] = __float2bfloat16_rn(d0);
+    b.B3[kmaj(1, tid, KS)] = __float2bfloat16_rn(d1);
 #pragma unroll
     for (int c = 0; c < HID; c += 8) {
       float g[8];
@@ -498,14 +534,14 @@ __global__ void __launch_bounds__(TILE, 1) grad_kernel(const __nv_bfloat16* X, c
       for (int j = 0; j < 8; ++j) {
         const float zz = a2[c + j];
         const __nv_bfloat16 act = __float2bfloat16_rn(silu(zz));
-        s.A3[kmaj(c + j, tid, KS)] = act;  // A2^T
+        b.A3[kmaj(c + j, tid, KS)] = act;  // A2^T
         g[j] = (d0 * s.W3[c + j] + d1 * s.W3[HID + c + j]) * dsilu(zz);
       }
       const uint4 u = pack8(g);
-      *reinterpret_cast<uint4*>(&s.dZ2[kmaj(tid, c, HID)]) = u;
+      *reinterpret_cast<uint4*>(&dZ2s[kmaj(tid, c, HID)]) = u;
       const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&u);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) s.A12[kmaj(c + j, tid, KS)] = e[j];  // dZ2^T
+      for (int j = 0; j < 8; ++j) b.A12[kmaj(c + j, tid, KS)] = e[j];  // dZ2^T
     }
     sync_issue();
     if (tid == 0) {
@@ -525,7 +561,7 @@ __global__ void __launch_bounds__(TILE, 1) grad_kernel(const __nv_bfloat16* X, c
       tmem_ld16(row + c, z);
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        s.A12[kmaj(HID + c + j, tid, KS)] = __float2bfloat16_rn(da[j] * dsilu(z[j] + s.b1[c + j]));
+        b.A12[kmaj(HID + c + j, tid, KS)] = __float2bfloat16_rn(da[j] * dsilu(z[j] + s.b1[c + j]));
     }
     sync_issue();
     if (tid == 0) {
@@ -543,51 +579,58 @@ __global__ void __launch_bounds__(TILE, 1) grad_kernel(const __nv_bfloat16* X, c
     if (!wait()) break;
     ++tiles;
   }
-  // the CTA's partial: G12 and G3 rows by thread
-  if (ok && tiles > 0) {
-    float* out = partial + (int64_t)blockIdx.x * NPARAM;
-    for (int c = 0; c < N12; c += 16) {
-      float g[16];
-      tmem_ld16(row + 2 * HID + c, g);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = c + j;
-        if (tid < HID) {  // rows dZ2^T: gW2[o][c], gb2[o]
-          if (col < HID) out[OFF_W2 + tid * HID + col] = g[j];
-          if (col == HID + IN) out[OFF_B2 + tid] = g[j];
-        } else {          // rows dZ1^T: gW1[o][k], gb1[o]
-          const int o = tid - HID;
-          if (col >= HID && col < HID + IN) out[OFF_W1 + o * IN + (col - HID)] = g[j];
-          if (col == HID + IN) out[OFF_B1 + o] = g[j];
-        }
-      }
-    }
-    float g3[16];
-    tmem_ld16(row + 2 * HID + N12, g3);
-    if (tid < HID) {
-      out[OFF_W3 + tid] = g3[0];        // gW3[0][c] = sum_i dO[i][0] A2[i][c]
-      out[OFF_W3 + HID + tid] = g3[1];
-    } else if (tid == HID) {
-      out[OFF_B3 + 0] = g3[0];
-      out[OFF_B3 + 1] = g3[1];
-    }
-  }
   for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
   if (lane == 0) s.loss[warp] = lsum;
+  // the CTA's partial: pipeline 0 writes its G12 and G3 rows (zeros without
+  // a tile), then pipeline 1 adds its own
+  float* out = partial + (int64_t)blockIdx.x * NPARAM;
+  const bool all_ok = __syncthreads_and(ok);
+  for (int turn = 0; turn < kPipes; ++turn) {
+    if (pi == turn && all_ok) {
+      const bool have = tiles > 0;
+      auto put = [&](int idx, float v) {
+        if (turn == 0) out[idx] = have ? v : 0.0f;
+        else if (have) out[idx] += v;
+      };
+#pragma unroll 1
+      for (int c = 0; c < N12; c += 16) {
+        float g[16];
+        tmem_ld16(row + 2 * HID + c, g);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = c + j;
+          if (tid < HID) {  // rows dZ2^T: gW2[o][c], gb2[o]
+            if (col < HID) put(OFF_W2 + tid * HID + col, g[j]);
+            if (col == HID + IN) put(OFF_B2 + tid, g[j]);
+          } else {          // rows dZ1^T: gW1[o][k], gb1[o]
+            const int o = tid - HID;
+            if (col >= HID && col < HID + IN) put(OFF_W1 + o * IN + (col - HID), g[j]);
+            if (col == HID + IN) put(OFF_B1 + o, g[j]);
+          }
+        }
+      }
+      float g3[16];
+      tmem_ld16(row + 2 * HID + N12, g3);
+      if (tid < HID) {
+        put(OFF_W3 + tid, g3[0]);  // gW3[0][c] = sum_i dO[i][0] A2[i][c]
+        put(OFF_W3 + HID + tid, g3[1]);
+      } else if (tid == HID) {
+        put(OFF_B3 + 0, g3[0]);
+        put(OFF_B3 + 1, g3[1]);
+      }
+    }
+    __syncthreads();
+  }
+  if (cta_tid == 0) {
+    float l = 0.0f;
+    for (int w = 0; w < kThreads / 32; ++w) l += s.loss[w];
+    loss_partial[blockIdx.x] = l;
+    if (!all_ok) atomicExch(err, 1);
+  }
   fence_before();
   __syncthreads();
-  if (tid == 0) {
-    float l = 0.0f;
-    for (int w = 0; w < TILE / 32; ++w) l += s.loss[w];
-    loss_partial[blockIdx.x] = l;
-    if (tiles == 0 || !ok) {
-      // no tile (or a failed wait): a zero partial
-      for (int i = 0; i < NPARAM; ++i) partial[(int64_t)blockIdx.x * NPARAM + i] = 0.0f;
-    }
-  }
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
-  if (!ok && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem), "r"(kTmemCols) : "memory");
 }
 
 }  // namespace gr
@@ -745,7 +788,7 @@ chad_status chad_mlp_grad(const uint16_t* X, const float* Y, int64_t n, const fl
   float* lpart = partial + nb * mlp::NPARAM;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return CHAD_E_CUDA;
-  mlp::tc::gr::grad_kernel<<<(unsigned)nb, mlp::tc::TILE, mlp::tc::gr::smem_bytes(), s>>>(
+  mlp::tc::gr::grad_kernel<<<(unsigned)nb, mlp::tc::gr::kThreads, mlp::tc::gr::smem_bytes(), s>>>(
       reinterpret_cast<const __nv_bfloat16*>(X), Y, n, 1.0f / (float)n, params, partial, lpart, err);
   mlp::reduce_kernel<<<(mlp::NPARAM + 255) / 256, 256, 0, s>>>(partial, (int)nb, grad, lpart, loss);
   return mlp::check_err(err, s);

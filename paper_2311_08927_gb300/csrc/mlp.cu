@@ -72,16 +72,22 @@ __global__ void features_kernel(const double* y, int64_t ld, const double* T, in
 namespace tc {
 
 constexpr int TILE = 128;
-constexpr uint32_t kTmemCols = 128;
-constexpr int kBlocksPerSM = 2;  // 2 x 128 of the SM's 512 tensor-memory columns
+constexpr int kFwdPipes = 2;                       // tile pipelines per CTA (4 warps each)
+constexpr int kFwdThreads = kFwdPipes * TILE;
+constexpr uint32_t kTmemCols = kFwdPipes * 128;    // per pipeline: Z1 0-63, Z2 64-127
+constexpr int kBlocksPerSM = 2;  // 2 x 256 = the SM's 512 tensor-memory columns
 
-struct Smem {
+struct FwdPipe {
   __nv_bfloat16 X[TILE * IN];     // 8 KB
   __nv_bfloat16 A1[TILE * HID];   // 16 KB
+};
+
+struct Smem {
+  FwdPipe pipe[kFwdPipes];
   __nv_bfloat16 W1[HID * IN];     // 4 KB
   __nv_bfloat16 W2[HID * HID];    // 8 KB
   float b1[HID], b2[HID], W3[OUT * HID], b3[OUT];
-  unsigned long long mbar;
+  unsigned long long mbar[kFwdPipes];
   uint32_t tmem;
 };
 
@@ -170,22 +176,43 @@ __device__ __forceinline__ uint4 pack8(const float* a) {
   return u;
 }
 
-// The forward pass over the tiles this CTA owns.  load(p, v) fills the 32
+// Barrier of one pipeline's 128 threads (ids 1, 2; id 0 is __syncthreads).
+__device__ __forceinline__ void pipe_sync(int id) {
+  asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+}
+__device__ __forceinline__ bool pipe_and(int id, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.and.pred p, %2, 128, q;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id)
+      : "memory");
+  return r != 0;
+}
+
+// The forward pass over the tiles this CTA owns, in two pipelines of 4 warps
+// (each with its own operands, half of the tensor memory, mbarrier and named
+// barrier), so that one tile's epilogue overlaps the other's MMAs; tiles go
+// to the CTAs first, then to their second pipelines.  load(p, v) fills the 32
 // BF16 features of sample p as four 16-byte vectors (p < n); store(p, o0, o1)
 // takes the two standardised outputs.
 template <class Load, class Store>
 __device__ __forceinline__ void forward_tiles(Smem& s, const float* P, int64_t n, int* err,
                                               Load load, Store store) {
-  const int tid = threadIdx.x, warp = tid >> 5;
-  for (int i = tid; i < HID * IN; i += TILE) s.W1[kmaj(i / IN, i % IN, IN)] = __float2bfloat16_rn(P[OFF_W1 + i]);
-  for (int i = tid; i < HID * HID; i += TILE) s.W2[kmaj(i / HID, i % HID, HID)] = __float2bfloat16_rn(P[OFF_W2 + i]);
-  for (int i = tid; i < HID; i += TILE) {
+  const int cta_tid = threadIdx.x, warp = cta_tid >> 5;
+  const int pi = cta_tid / TILE, tid = cta_tid % TILE;
+  const int bar_id = 1 + pi;
+  FwdPipe& b = s.pipe[pi];
+  for (int i = cta_tid; i < HID * IN; i += kFwdThreads) s.W1[kmaj(i / IN, i % IN, IN)] = __float2bfloat16_rn(P[OFF_W1 + i]);
+  for (int i = cta_tid; i < HID * HID; i += kFwdThreads) s.W2[kmaj(i / HID, i % HID, HID)] = __float2bfloat16_rn(P[OFF_W2 + i]);
+  for (int i = cta_tid; i < HID; i += kFwdThreads) {
     s.b1[i] = P[OFF_B1 + i];
     s.b2[i] = P[OFF_B2 + i];
   }
-  for (int i = tid; i < OUT * HID; i += TILE) s.W3[i] = __bfloat162float(__float2bfloat16_rn(P[OFF_W3 + i]));
-  if (tid < OUT) s.b3[tid] = P[OFF_B3 + tid];
-  const uint32_t bar = smem_u32(&s.mbar);
+  for (int i = cta_tid; i < OUT * HID; i += kFwdThreads) s.W3[i] = __bfloat162float(__float2bfloat16_rn(P[OFF_W3 + i]));
+  if (cta_tid < OUT) s.b3[cta_tid] = P[OFF_B3 + cta_tid];
+  const uint32_t bar = smem_u32(&s.mbar[pi]);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -200,22 +227,23 @@ __device__ __forceinline__ void forward_tiles(Smem& s, const float* P, int64_t n
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = s.tmem;
-  const uint32_t row_base = tmem + ((uint32_t)(warp * 32) << 16);
-  const uint32_t x_addr = smem_u32(s.X), a1_addr = smem_u32(s.A1);
+  const uint32_t tmem = s.tmem + pi * 128;
+  const uint32_t row_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t x_addr = smem_u32(b.X), a1_addr = smem_u32(b.A1);
   const uint32_t w1_addr = smem_u32(s.W1), w2_addr = smem_u32(s.W2);
   constexpr uint32_t kId = idesc_bf16(TILE, HID);
   uint32_t phase = 0;
   bool ok = true;
-  for (int64_t m0 = (int64_t)blockIdx.x * TILE; m0 < n && ok; m0 += (int64_t)gridDim.x * TILE) {
+  const int64_t stride = (int64_t)gridDim.x * kFwdPipes * TILE;
+  for (int64_t m0 = ((int64_t)pi * gridDim.x + blockIdx.x) * TILE; m0 < n && ok; m0 += stride) {
     const int64_t p = m0 + tid;
     uint4 v[4] = {};
     if (p < n) load(p, v);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4*>(&s.X[kmaj(tid, 8 * j, IN)]) = v[j];
+    for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4*>(&b.X[kmaj(tid, 8 * j, IN)]) = v[j];
     fence_async_smem();
     fence_before();
-    __syncthreads();
+    pipe_sync(bar_id);
     if (tid == 0) {
       fence_after();
 #pragma unroll
@@ -224,7 +252,7 @@ __device__ __forceinline__ void forward_tiles(Smem& s, const float* P, int64_t n
             kId, k);
       commit(bar);
     }
-    ok = __syncthreads_and(mbar_wait(bar, phase));
+    ok = pipe_and(bar_id, mbar_wait(bar, phase));
     phase ^= 1;
     if (!ok) break;
     fence_after();
@@ -234,12 +262,12 @@ __device__ __forceinline__ void forward_tiles(Smem& s, const float* P, int64_t n
       tmem_ld16(row_base + c, z);
 #pragma unroll
       for (int j = 0; j < 16; ++j) z[j] = silu(z[j] + s.b1[c + j]);
-      *reinterpret_cast<uint4*>(&s.A1[kmaj(tid, c, HID)]) = pack8(z);
-      *reinterpret_cast<uint4*>(&s.A1[kmaj(tid, c + 8, HID)]) = pack8(z + 8);
+      *reinterpret_cast<uint4*>(&b.A1[kmaj(tid, c, HID)]) = pack8(z);
+      *reinterpret_cast<uint4*>(&b.A1[kmaj(tid, c + 8, HID)]) = pack8(z + 8);
     }
     fence_async_smem();
     fence_before();
-    __syncthreads();
+    pipe_sync(bar_id);
     if (tid == 0) {
       fence_after();
 #pragma unroll
@@ -248,7 +276,7 @@ __device__ __forceinline__ void forward_tiles(Smem& s, const float* P, int64_t n
             sdesc(w2_addr + k * 256, 128, (HID / 8) * 128), kId, k);
       commit(bar);
     }
-    ok = __syncthreads_and(mbar_wait(bar, phase));
+    ok = pipe_and(bar_id, mbar_wait(bar, phase));
     phase ^= 1;
     if (!ok) break;
     fence_after();
@@ -266,11 +294,12 @@ __device__ __forceinline__ void forward_tiles(Smem& s, const float* P, int64_t n
     }
     if (p < n) store(p, o0, o1);
   }
+  const bool all_ok = __syncthreads_and(ok);
   fence_before();
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
-  if (!ok && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem), "r"(kTmemCols) : "memory");
+  if (!all_ok && cta_tid == 0) atomicExch(err, 1);
 }
 
 __device__ __forceinline__ Smem& smem_aligned(unsigned char* raw) {
@@ -278,7 +307,7 @@ __device__ __forceinline__ Smem& smem_aligned(unsigned char* raw) {
 }
 
 // Inference: out[p][0..1] = MLP(X[p]) (standardised outputs).
-__global__ void __launch_bounds__(TILE, kBlocksPerSM) forward_kernel(const __nv_bfloat16* X,
+__global__ void __launch_bounds__(kFwdThreads, kBlocksPerSM) forward_kernel(const __nv_bfloat16* X,
                                                                      int64_t n, const float* P,
                                                                      float* out, int* err) {
   extern __shared__ unsigned char smem_raw[];
@@ -297,7 +326,7 @@ __global__ void __launch_bounds__(TILE, kBlocksPerSM) forward_kernel(const __nv_
 
 // Learned guesses for the particles of a context: S_H = 10^(o0 s0 + m0)
 // kmol/m^3 and h = 10^(o1 s1 + m1) days, clamped to [1e-14, 1] and [1e-10, 1].
-__global__ void __launch_bounds__(TILE, kBlocksPerSM) guess_kernel(const double* y, int64_t ld,
+__global__ void __launch_bounds__(kFwdThreads, kBlocksPerSM) guess_kernel(const double* y, int64_t ld,
                                                                    const double* T, int64_t n,
                                                                    const float* P, const float* norm,
                                                                    const float* onorm, double* SH_out,
@@ -363,21 +392,6 @@ struct Smem {
 };
 
 constexpr size_t smem_bytes() { return sizeof(Smem) + 128; }
-
-// Barrier of one pipeline's 128 threads (ids 1, 2; id 0 is __syncthreads).
-__device__ __forceinline__ void pipe_sync(int id) {
-  asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
-}
-__device__ __forceinline__ bool pipe_and(int id, bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.and.pred p, %2, 128, q;\n"
-      "selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(id)
-      : "memory");
-  return r != 0;
-}
 
 __global__ void __launch_bounds__(kThreads, 1) grad_kernel(const __nv_bfloat16* X, const float* Y,
                                                            int64_t n, float inv_n, const float* P,
@@ -717,7 +731,7 @@ cudaError_t launch_mlp_guess(const double* y, int64_t ld, const double* T, int64
   int64_t blocks = (n + mlp::tc::TILE - 1) / mlp::tc::TILE;
   const int64_t cap = (int64_t)mlp::sm_count() * mlp::tc::kBlocksPerSM;
   if (blocks > cap) blocks = cap;
-  mlp::tc::guess_kernel<<<(unsigned)blocks, mlp::tc::TILE, mlp::tc::smem_bytes(), s>>>(
+  mlp::tc::guess_kernel<<<(unsigned)blocks, mlp::tc::kFwdThreads, mlp::tc::smem_bytes(), s>>>(
       y, ld, T, n, params, norm, onorm, SH_out, h_out, err);
   return cudaGetLastError();
 }
@@ -756,7 +770,7 @@ chad_status chad_mlp_forward(const uint16_t* X, int64_t n, const float* params, 
   if (blocks > cap) blocks = cap;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return CHAD_E_CUDA;
-  mlp::tc::forward_kernel<<<(unsigned)blocks, mlp::tc::TILE, mlp::tc::smem_bytes(), s>>>(
+  mlp::tc::forward_kernel<<<(unsigned)blocks, mlp::tc::kFwdThreads, mlp::tc::smem_bytes(), s>>>(
       reinterpret_cast<const __nv_bfloat16*>(X), n, params, out, err);
   return mlp::check_err(err, s);
 }

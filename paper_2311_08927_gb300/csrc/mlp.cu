@@ -28,9 +28,12 @@ constexpr int NPARAM = OFF_B3 + OUT;
 static_assert(NPARAM == CHAD_MLP_NPARAM, "parameter count");
 constexpr float kLogFloor = 1e-20f;
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// The activations are rounded to BF16 (8 significant bits) right after, so
+// the fast division (a few FP32 ulp) is exact enough; for z below about -88
+// the exponential overflows and both give 0.
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float dsilu(float z) {
-  const float s = 1.0f / (1.0f + __expf(-z));
+  const float s = __fdividef(1.0f, 1.0f + __expf(-z));
   return s * (1.0f + z * (1.0f - s));
 }
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {

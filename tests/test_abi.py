@@ -134,3 +134,32 @@ def test_null_context_calls_are_invalid(L):
 
 def test_normal_build_has_no_bounds_checks(L):
     assert CH.chad_debug_bounds() == (0, 0)
+
+
+def _cc():
+    import shutil
+    return shutil.which("gcc") or shutil.which("cc")
+
+
+def build_c_caller(out_path):
+    """Compile and link tests/c/run_digester.c (plain C99) against the library."""
+    import subprocess
+    pkg = os.path.dirname(B.LIB)
+    cuda_lib = "/usr/local/cuda/lib64"
+    cmd = [_cc(), "-std=c99", "-Wall", "-Wextra", "-Werror", "-O2",
+           os.path.join(ROOT, "tests", "c", "run_digester.c"), "-I", os.path.join(ROOT, "include"),
+           "-L", pkg, "-lchad", f"-Wl,-rpath,{pkg}", "-L", cuda_lib, f"-Wl,-rpath-link,{cuda_lib}",
+           "-o", str(out_path)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return str(out_path)
+
+
+def test_header_compiles_as_c_and_a_c_program_links(L, tmp_path):
+    """include/chad.h is plain C: a C99 program using it compiles with every
+    warning as an error and links against libchad.so (every call it uses
+    resolves); running it needs a GPU (tests/test_gpu_parity.py)."""
+    if _cc() is None:
+        pytest.skip("no C compiler")
+    assert os.path.exists(build_c_caller(tmp_path / "run_digester"))
+

@@ -434,6 +434,36 @@ def test_bounds_check_build_records_no_violation():
     assert "bounds 1 0" in r.stdout
 
 
+def test_c_program_matches_the_binding(tmp_path):
+    """A plain C99 program (tests/c/run_digester.c) drives the library through
+    chad.h alone: on the same seeded inputs its states equal, bitwise, those
+    of the same run through the Python binding."""
+    import struct
+    import subprocess
+    from test_abi import _cc, build_c_caller
+    if _cc() is None:
+        pytest.skip("no C compiler")
+    exe = build_c_caller(tmp_path / "run_digester")
+    pop = I.config_population(1, n=64)
+    d = pop.digesters[0]
+    n, k, dt = pop.n, 3, 60.0
+    with open(tmp_path / "in.bin", "wb") as f:
+        f.write(struct.pack("<qqddddd", n, k, dt, d.V_liq, d.V_gas, d.D, 1e-6))
+        for arr in (d.params, I.atol_vector(), d.y_in, pop.y, pop.T):
+            f.write(np.ascontiguousarray(arr, dtype="<f8").tobytes())
+    r = subprocess.run([exe, str(tmp_path / "in.bin"), str(tmp_path / "out.bin")],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    raw = (tmp_path / "out.bin").read_bytes()
+    y = np.frombuffer(raw, dtype="<f8", count=29 * n).reshape(29, n)
+    SH = np.frombuffer(raw, dtype="<f8", count=n, offset=8 * 29 * n)
+    h = np.frombuffer(raw, dtype="<f8", count=n, offset=8 * 30 * n)
+    st = np.frombuffer(raw, dtype="<i4", count=n, offset=8 * 31 * n)
+    g = gpu_run(pop, dt, k)
+    assert np.all(st == 0)
+    assert np.array_equal(y, g["y"]) and np.array_equal(SH, g["S_H"]) and np.array_equal(h, g["h"])
+
+
 def test_diffusion_rerun_is_bitwise_deterministic():
     """The cell lists are ordered by particle index after the atomic scatter,
     so the neighbour sums run in a fixed order."""

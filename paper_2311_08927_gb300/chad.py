@@ -584,6 +584,16 @@ class Simulator:
             sl = lambda x: None if x is None else np.ascontiguousarray(x[..., a:b])
             chad_load_particles(self.ctx, d, b - a, sl(pos), sl(y), sl(T), sl(S_H), sl(h))
 
+    @classmethod
+    def from_config(cls, path, particles=None, **overrides):
+        """(Simulator, coupling interval in s, intervals) for a run
+        configuration (runconfig; the bundled ones are configs/c1 .. c5.json).
+        A learned configuration still needs chad_set_mlp before chad_step."""
+        from . import runconfig as RC
+        pop, kw, dt, k = RC.load(path, particles)
+        kw.update(overrides)
+        return cls(pop, **kw), dt, k
+
     def checkpoint(self, path):
         """Save what a bitwise resume needs: y, pos, S_H, h (every digester),
         the temperatures and the interval index, as one .npz file."""

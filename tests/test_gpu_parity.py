@@ -464,6 +464,29 @@ def test_c_program_matches_the_binding(tmp_path):
     assert np.array_equal(y, g["y"]) and np.array_equal(SH, g["S_H"]) and np.array_equal(h, g["h"])
 
 
+def test_diffusion_settings_changed_between_steps_match_oracle():
+    """Two intervals with one (D, h), two with another (a finer grid, more
+    substeps), one with diffusion off: the library re-plans the grid, the
+    operator's capacity and the interval graph at each change; the oracle is
+    run the same way, chained interval by interval.  Fixed ADM1 steps."""
+    pop = I.config_population(2, n=1500)
+    plan = [((1e-6, 0.03), 2), ((1e-5, 0.02), 2), (None, 1)]
+    sim = CH.Simulator(pop, fixed_substeps=4)
+    sim.load()
+    y, pos, SH, h, k0 = pop.y.copy(), pop.pos.copy(), None, None, 0
+    for dif, k in plan:
+        CH.chad_set_diffusion(sim.ctx, 0, dif[0] if dif else 0.0, dif[1] if dif else 0.0)
+        sim.step(60.0, k)
+        step_pop = I.Population(pop.digesters, y, pop.T, pos, pop.shared_headspace)
+        o = O.run(step_pop, 60.0, k, interval0=k0, fixed_n=4, SH=SH, h=h, diffusion=dif)
+        y, pos, SH, h, k0 = o["y"], o["pos"], o["S_H"], o["h"], k0 + k
+    g = sim.read()
+    sim.close()
+    assert np.all(g["status"] == 0)
+    assert np.array_equal(g["pos"], pos)
+    assert relerr(g["y"], y).max() < 1e-9
+
+
 def test_diffusion_rerun_is_bitwise_deterministic():
     """The cell lists are ordered by particle index after the atomic scatter,
     so the neighbour sums run in a fixed order."""

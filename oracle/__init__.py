@@ -6,7 +6,10 @@ no FMA contraction) through ctypes and shares no code with the CUDA library.
 
 Pinned by: tests/test_oracle_pins.py (closed forms, conservation laws,
 textbook pH values, AD-vs-finite-difference Jacobian, convergence order,
-brute-force RK4, numpy's Philox).  Absolute trajectories against the paper's
+brute-force RK4, numpy's Philox) and tests/test_oracle_pins_kinetics.py
+(each rate-law factor, the stoichiometric route of every process, the
+temperature laws against printed 35 C constants); tests/test_oracle_mutations.py
+checks that planted mistakes fail them.  Absolute trajectories against the paper's
 Fig. 3 / Table 3: parity unpinned (the benchmark records are not available).
 """
 from __future__ import annotations

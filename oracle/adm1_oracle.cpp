@@ -32,7 +32,9 @@
 //                           Irwin-Hall(12) Gaussian; rigid swirl rotation;
 //                           reflecting cylinder walls.
 //
-// Parity pins: see tests/test_oracle_*.py.  Absolute values against the
+// Parity pins: tests/test_oracle_pins.py and tests/test_oracle_pins_kinetics.py
+// (tests/test_oracle_mutations.py checks that planted mistakes fail them).
+// Absolute values against the
 // paper's Fig. 3 / Table 3 are parity unpinned (the benchmark data is not
 // available).
 #include <cmath>

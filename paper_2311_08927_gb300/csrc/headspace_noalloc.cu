@@ -45,6 +45,11 @@ struct NoallocParams {
   int64_t off[kNoallocMaxDigesters + 1];
   int chunk0[kNoallocMaxDigesters + 1];
 };
+// Passed by value as the kernels' parameter block (about 12 KB with the
+// offset tables inline, so no device buffer is needed for them either).
+// Parameter blocks above 4 KB need CUDA 12.1 or later, which allows up to
+// 32,764 bytes.
+static_assert(sizeof(NoallocParams) <= 32764, "kernel parameter block too large");
 
 __global__ void __launch_bounds__(kNoallocThreads) noalloc_partial(const NoallocParams P) {
   __shared__ double s[3][kNoallocThreads];

@@ -393,9 +393,10 @@ def run_ours(args, ws, rank, local, cfg=3):
                     y_final=out["y"])
 
     forms = {}
+    h2m = args.model == "h2alg"
     for name, prec in (("mixed", CH.PREC_MIXED), ("fp64", CH.PREC_FP64)):
         if args.form in (name, "both"):
-            forms[name] = arm(prec, learned=(name == "mixed" and model is not None))
+            forms[name] = arm(prec, learned=(name == "mixed" and model is not None), h2=h2m)
     if args.form == "fp64_h2alg":
         # S_h2 algebraic (Eq. 8): the counted attempt flops are those of the
         # differential FP64 form (the Eq. 8 solves and the second rank-1
@@ -414,12 +415,13 @@ def run_ours(args, ws, rank, local, cfg=3):
     e2e = None
     if rank == 0 and not args.no_e2e:
         prec = CH.PREC_MIXED if head == "mixed" else CH.PREC_FP64
-        e2e = e2e_run(CH, pop, prec, stream, args, head == "fp64_h2alg")
+        e2e = e2e_run(CH, pop, prec, stream, args, h2m or head == "fp64_h2alg")
 
     # ---------------- CPU baseline: the oracle on a bounded sample, same intervals
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(pop, args.warmup, min(args.steps, 10), args.cpu_seconds, cfg)
+        cpu = cpu_baseline(pop, args.warmup, min(args.steps, 10), args.cpu_seconds, cfg,
+                           h2m or head == "fp64_h2alg")
 
     if rank != 0:
         return None
@@ -436,8 +438,13 @@ def run_ours(args, ws, rank, local, cfg=3):
         "config": {"workload": wl, "description": meta["desc"],
                    "particles_per_gpu": N, "digesters": len(pop.digesters),
                    "coupling_interval_s": DT_S,
-                   "form": head + (" (FP32 Jacobian/LU + FP64 refinement)" if head == "mixed" else "")
+                   "form": head + ((" (S_h2 algebraic, Eq. 8: FP32 rates, Jacobian and LU, "
+                                    "two-float refinement residual, FP64 Eq. 7 Newton and state)"
+                                    if h2m else " (FP32 Jacobian/LU + FP64 refinement)")
+                                   if head == "mixed" else (" (S_h2 algebraic, Eq. 8)" if h2m else ""))
                 + (" + learned guesses" if (head == "mixed" and model is not None) else ""),
+                   "model": "S_h2 algebraic (Eq. 8)" if (h2m or head == "fp64_h2alg")
+                            else "S_h2 a differential state",
                    "learned_guesses": model is not None, "rtol": 1e-6,
                    "l2": meta["l2"],
                    "parallelism": f"particles sharded, {ws} independent populations"},
@@ -513,18 +520,18 @@ def _sampler(pop, cfg):
     return lambda n, seed=7: _oracle_sample(pop, n, seed)
 
 
-def _calibrate_sample(sample, intervals, budget_s, cores, cap):
+def _calibrate_sample(sample, intervals, budget_s, cores, cap, h2=False):
     """Sample size for about budget_s seconds of oracle work over `intervals`."""
     import oracle as O
     n_cal = min(cap, 64 * max(1, cores // 4))
     sub = sample(n_cal, 11)
     t0 = time.perf_counter()
-    O.run(sub, DT_S, min(intervals, 3), rtol=1e-6, n_threads=cores)
+    O.run(sub, DT_S, min(intervals, 3), rtol=1e-6, n_threads=cores, h2_algebraic=h2)
     per = (time.perf_counter() - t0) / (sub.n * min(intervals, 3))
     return int(max(128, min(cap, 50_000, budget_s / max(per, 1e-9) / intervals)))
 
 
-def cpu_baseline(pop, warmup, k, budget_s, cfg=3):
+def cpu_baseline(pop, warmup, k, budget_s, cfg=3, h2=False):
     """The oracle as it stands (FP64, std::thread equal chunks over all host
     cores) on a seeded sample of the workload, over the same intervals; the
     sample grows until the timed part takes about budget_s seconds."""
@@ -533,14 +540,14 @@ def cpu_baseline(pop, warmup, k, budget_s, cfg=3):
     cores = os.cpu_count() or 1
     sample = _sampler(pop, cfg)
     cap = pop.n if cfg == 1 else 200_000
-    n_s = _calibrate_sample(sample, warmup + k, budget_s, cores, cap)
+    n_s = _calibrate_sample(sample, warmup + k, budget_s, cores, cap, h2)
 
     def timed(sub, threads):
-        r = O.run(sub, DT_S, warmup, rtol=1e-6, n_threads=threads)
+        r = O.run(sub, DT_S, warmup, rtol=1e-6, n_threads=threads, h2_algebraic=h2)
         sub2 = I.Population(sub.digesters, r["y"], sub.T, r["pos"], sub.shared_headspace)
         t0 = time.perf_counter()
         O.run(sub2, DT_S, k, interval0=warmup, rtol=1e-6, SH=r["S_H"], h=r["h"],
-              n_threads=threads)
+              n_threads=threads, h2_algebraic=h2)
         return time.perf_counter() - t0
 
     for _ in range(3):
@@ -557,7 +564,8 @@ def cpu_baseline(pop, warmup, k, budget_s, cfg=3):
                        if cfg in (2, 5) else "seeded particles of the workload")
     return {"value": n_s * k * DT_S / 86400.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_s} {what(sub)}, intervals {warmup}..{warmup + k - 1} "
-                      f"(after {warmup} untimed), rtol 1e-6, {dt:.1f} s",
+                      f"(after {warmup} untimed), rtol 1e-6"
+                      f"{', S_h2 algebraic' if h2 else ''}, {dt:.1f} s",
             "one_core": {"value": s1.n * k * DT_S / 86400.0 / dt1, "unit": UNIT, "cores": 1,
                          "sample": f"{s1.n} other {what(s1)}, same intervals, {dt1:.1f} s"}}
 
@@ -964,6 +972,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", choices=["both", "mixed", "fp64", "fp64_h2alg"], default="both",
                     help="fp64_h2alg: FP64 with S_h2 algebraic (Eq. 8), not the headline")
+    ap.add_argument("--model", choices=["differential", "h2alg"], default="differential",
+                    help="h2alg: S_h2 algebraic (Eq. 8, the paper's DAE form) in both forms")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -105,8 +105,12 @@ typedef struct {
   void* cuda_stream;           /* cudaStream_t to run on; NULL = legacy default stream */
   int h2_algebraic;            /* 1: S_h2 from its mass balance (Eq. 8) at every rate
                                   evaluation, as the paper does, instead of as a
-                                  differential state; FP64 form only.  The S_h2 entry
-                                  of y then holds the root at the current state. */
+                                  differential state.  With CHAD_PREC_FP64 the root is
+                                  FP64; with CHAD_PREC_MIXED the stage rates and the
+                                  root are FP32, the refinement residual two-float,
+                                  the Eq. 7 Newton and the state FP64 (not available
+                                  with CHAD_PREC_MIXED_F32RATES).  The S_h2 entry of y
+                                  then holds the root at the current state. */
 } chad_config;
 
 /* Prescribed flow of one digester (Sec. 2.3).  Rigid swirl u_theta = U r/R

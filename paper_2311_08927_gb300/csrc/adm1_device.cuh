@@ -139,10 +139,26 @@ constexpr double kVfaCod_ac = 64.0, kVfaCod_pro = 112.0, kVfaCod_bu = 160.0, kVf
 constexpr double kC4Guard = 1e-6;  // division guard of the c4 uptake split
 constexpr double kSH_lo = 1e-14, kSH_hi = 1.0;
 
-struct PartConst {
-  double arr;  // Arrhenius factor of the kinetic constants
-  double K_w, K_a_co2, K_a_IN, K_H_co2, K_H_ch4, K_H_h2, p_h2o, RT;
+template <class T>
+struct PartConstT {
+  T arr;  // Arrhenius factor of the kinetic constants
+  T K_w, K_a_co2, K_a_IN, K_H_co2, K_H_ch4, K_H_h2, p_h2o, RT;
 };
+using PartConst = PartConstT<double>;
+// float copy for FP32 rate evaluations (converted once per particle load
+// instead of at every use)
+using PartConstF = PartConstT<float>;
+CHAD_HD void narrow_pc(const PartConst& q, PartConstF& f) {
+  f.arr = float(q.arr);
+  f.K_w = float(q.K_w);
+  f.K_a_co2 = float(q.K_a_co2);
+  f.K_a_IN = float(q.K_a_IN);
+  f.K_H_co2 = float(q.K_H_co2);
+  f.K_H_ch4 = float(q.K_H_ch4);
+  f.K_H_h2 = float(q.K_H_h2);
+  f.p_h2o = float(q.p_h2o);
+  f.RT = float(q.RT);
+}
 
 CHAD_HD void part_const(const DigConst& c, double T, PartConst& q) {
   const double invT = 1.0 / T;
@@ -333,8 +349,8 @@ __host__ __device__ inline void solve_SH(const DigConst& c, const PartConst& q, 
 // dS_H/dy_k = -(dE/dy_k) / (dE/dS_H) (implicit function theorem on Eq. 7)
 // for the 8 states that enter Eq. 7, in the order of kShStates.
 constexpr int kShStates[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
-template <class DC>
-CHAD_HD void sh_tangent(const DC& c, const PartConst& q, const AcidBase& ab, double* v) {
+template <class DC, class PQ>
+CHAD_HD void sh_tangent(const DC& c, const PQ& q, const AcidBase& ab, double* v) {
   const double inv = -rcp<double>(ab.dEdS);
   v[0] = inv * (-c.K_a_va * ab.r_va * (1.0 / kVfaCod_va));
   v[1] = inv * (-c.K_a_bu * ab.r_bu * (1.0 / kVfaCod_bu));
@@ -376,9 +392,9 @@ struct H2Bal {
   F C0, Pfa, Pc4, Ppro, Ph2, kD, Kfa, Kc4, Kpro, Kh2;
 };
 
-template <class F>
-CHAD_HD void h2_coeffs(const DigConst& c, const PartConst& q, const double* y, F D,
-                       const AcidBase& ab, H2Bal<F>& e) {
+template <class F, class DC, class PQ, class Y>
+CHAD_HD void h2_coeffs(const DC& c, const PQ& q, const Y* y, F D, const AcidBase& ab,
+                       H2Bal<F>& e) {
   const F a = F(q.arr);
   F Ipaa, dIpaa, Iph2, dIph2;
   hill<F>(F(ab.SH), F(c.inv_K_pH_aa), F(c.n_aa), c.ni_aa, Ipaa, dIpaa);
@@ -477,9 +493,8 @@ struct Rates {
   R P_h2, P_ch4, P_co2;                               // dP/dG
 };
 
-template <class R, bool J, class DC>
-CHAD_HD void rates(const DC& c, const PartConst& q, const R* y,
-                                      const AcidBase& ab, Rates<R>& o) {
+template <class R, bool J, class DC, class PQ>
+CHAD_HD void rates(const DC& c, const PQ& q, const R* y, const AcidBase& ab, Rates<R>& o) {
   const R a = R(q.arr);
   const R SH = R(ab.SH);
   // inhibition factors (Eq. 3-6)
@@ -704,8 +719,8 @@ CHAD_HD void balances(const DC& c, const R* y, R D, const Rates<R>& o, R* f) {
 // same stoichiometry as the rates; the transport terms are linearised
 // directly.  Arithmetic in precision RD (FP64 in the kernels) whatever the
 // precision RO of the partials.
-template <class RO, class RD>
-CHAD_HD void jvp(const DigConst& c, const RD* y, RD D, const Rates<RO>& o, const RD* x, RD s,
+template <class RO, class RD, class DC>
+CHAD_HD void jvp(const DC& c, const RD* y, RD D, const Rates<RO>& o, const RD* x, RD s,
                  RD* out) {
   RD dr[22];
   dr[0] = RD(o.d1) * x[iX_c];
@@ -771,8 +786,8 @@ CHAD_HD void scat(JS Jm, int row, R coef, const int (&cols)[NC], const R (&d)[NC
 // With u_out == nullptr the full J = J_d + u v^T is assembled; otherwise only
 // the direct part J_d (S_H held fixed) goes into Jm and u = df/dS_H into
 // u_out, for the Sherman-Morrison solve of W = W_d - g u v^T.
-template <class Idx, class R, class JS, class DC>
-CHAD_HD void jacobian(const DC& c, const PartConst& q, const R* y, R D, const AcidBase& ab,
+template <class Idx, class R, class JS, class DC, class PQ>
+CHAD_HD void jacobian(const DC& c, const PQ& q, const R* y, R D, const AcidBase& ab,
                       const Rates<R>& o, JS Jm, R* u_out = nullptr) {
   R u[NS];
 #pragma unroll

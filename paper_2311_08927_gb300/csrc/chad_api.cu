@@ -92,7 +92,8 @@ struct chad_ctx {
   int* d_order_cnt = nullptr;  // [2 * kOrderBuckets] bucket counts and cursors
   unsigned long long* d_misc = nullptr;  // [2]: load check flag, failed-particle count
   unsigned long long* d_interval = nullptr;  // global interval index (noise counter)
-  int variant[4] = {kDefaultVariant, kDefaultVariant, kDefaultVariant, kDefaultVariant};
+  int variant[5] = {kDefaultVariant, kDefaultVariant, kDefaultVariant, kDefaultVariant,
+                    kDefaultVariant};
   double flow_dt = -1.0;        // interval length the device flow constants hold
   // CUDA graph of one interval (captured on first use, replayed per interval)
   cudaGraphExec_t gexec = nullptr;
@@ -219,8 +220,10 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
     return fail(nullptr, CHAD_E_INVALID, "precision must be one of CHAD_PREC_*");
   if (cfg->h2_algebraic != 0 && cfg->h2_algebraic != 1)
     return fail(nullptr, CHAD_E_INVALID, "h2_algebraic must be 0 or 1");
-  if (cfg->h2_algebraic && cfg->precision != CHAD_PREC_FP64)
-    return fail(nullptr, CHAD_E_INVALID, "h2_algebraic is implemented for the FP64 form only");
+  if (cfg->h2_algebraic && cfg->precision == CHAD_PREC_MIXED_F32RATES)
+    return fail(nullptr, CHAD_E_INVALID,
+                "h2_algebraic takes CHAD_PREC_FP64 or CHAD_PREC_MIXED (whose stage rates are "
+                "then FP32)");
   if (cfg->headspace != CHAD_HEADSPACE_PARTICLE && cfg->headspace != CHAD_HEADSPACE_SHARED)
     return fail(nullptr, CHAD_E_INVALID, "invalid headspace mode");
   if (cfg->learned != 0 && cfg->learned != 1)
@@ -806,8 +809,13 @@ static chad_status prepare_diffusion(chad_ctx* c, double dt_s) {
   return CHAD_OK;
 }
 
-// Kernel form of a context: 0-2 = precision form, 3 = FP64 with S_h2 algebraic.
-static int kernel_form(const chad_ctx* c) { return c->h2_alg ? 3 : c->precision; }
+// Kernel form of a context: 0-2 = precision form, 3 = FP64 with S_h2
+// algebraic, 4 = mixed with S_h2 algebraic (FP32 stage rates, two-float
+// refinement residual).
+static int kernel_form(const chad_ctx* c) {
+  if (c->h2_alg) return c->precision == CHAD_PREC_MIXED ? 4 : 3;
+  return c->precision;
+}
 
 // The launch sequence of one coupling interval: advect (digesters with
 // flow) -> integrate every particle -> shared-headspace mean -> interval += 1.

@@ -589,11 +589,12 @@ def test_h2_algebraic_production_tolerance_and_differential_form():
     assert relerr(g["y"], d["y"]).max() < 1e-4
 
 
-def test_h2_algebraic_needs_the_fp64_form():
+def test_h2_algebraic_takes_the_fp64_and_mixed_forms_only():
     pop = I.config_population(1, n=16)
     with pytest.raises(CH.ChadError) as ei:
-        CH.Simulator(pop, precision=CH.PREC_MIXED, h2_algebraic=True)
+        CH.Simulator(pop, precision=CH.PREC_MIXED_F32RATES, h2_algebraic=True)
     assert ei.value.code == 1
+    CH.Simulator(pop, precision=CH.PREC_MIXED, h2_algebraic=True).close()
 
 
 # ------------------------------------------------------------ flow, headspace, digesters

@@ -126,7 +126,7 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- algorithmic work
-def work_per_launch(CH, precision, stats, steps):
+def work_per_launch(CH, precision, stats, steps, h2=False):
     """Algorithmic FP64 / FP32 operations of one integrator launch.
 
     Counts come from the kernel source (chad_flop_counts: the templated
@@ -135,14 +135,31 @@ def work_per_launch(CH, precision, stats, steps):
     W formation, static-order sparse LU, three solves (mixed: FP32 solves
     plus FP64 refinement residuals J x) and stage combinations; per Newton
     iteration of Eq. 7 one charge-balance evaluation plus the update; per
-    attempt three moves of the acid-base reciprocals to the converged root."""
-    af = CH.attempt_flops(precision)
+    attempt three moves of the acid-base reciprocals to the converged root.
+    The mixed form with S_h2 algebraic counts its two-float arithmetic at its
+    FP32 cost and each FP32 Eq. 8 Newton iteration."""
     nf = CH.newton_flops()
     fin = CH.flop_counts()["sh_final"]
     attempts = stats["accepted_steps"] + stats["rejected_steps"]
+    if h2 and precision == CH.PREC_MIXED:
+        af = CH.attempt_flops_h2_mixed()
+        f32 = attempts * af["fp32"] + stats["h2_newton_iters"] * af["fp32_per_h2_iter"]
+    else:
+        af = CH.attempt_flops(precision)
+        f32 = attempts * af["fp32"]
     f64 = attempts * (af["fp64"] + 3 * fin) + stats["newton_iters"] * nf
-    f32 = attempts * af["fp32"]
     return f64 / steps, f32 / steps, af
+
+
+def alu_roofline(f64, f32, launch_ms, peak64, peak32):
+    """The ALU roofline of a launch: the time the counted work needs on the
+    pipe that bounds it, max(FP64 flops / FP64 peak, FP32 flops / FP32 peak),
+    over the measured time.  achieved / peak are those of the bounding pipe."""
+    t = launch_ms * 1e-3
+    t64, t32 = f64 / (peak64 * 1e12), f32 / (peak32 * 1e12)
+    if t64 >= t32:
+        return {"pipe": "fp64", "achieved": f64 / t / 1e12, "peak": peak64, "frac": t64 / t}
+    return {"pipe": "fp32", "achieved": f32 / t / 1e12, "peak": peak32, "frac": t32 / t}
 
 
 def kernel_sources_hash():
@@ -184,7 +201,7 @@ def train_mlp(CH, I, args):
     pops = [I.config_population(3, n=n3, seed_offset=100), I.config_population(2, seed_offset=100)]
     ys, Ts, SHs, hs = [], [], [], []
     for pop_t, k in zip(pops, (args.train_intervals, 11)):
-        y, T, SH, h = Lm.sample_states(pop_t, k)
+        y, T, SH, h = Lm.sample_states(pop_t, k, h2_algebraic=(args.model == "h2alg"))
         ys.append(y); Ts.append(T); SHs.append(SH); hs.append(h)
     y, T, SH, h = torch.cat(ys, 1), torch.cat(Ts), torch.cat(SHs), torch.cat(hs)
     t1 = time.perf_counter()
@@ -205,7 +222,7 @@ def train_mlp(CH, I, args):
     return model, info
 
 
-def cold_restart_ab(CH, pop, relaxed, model, stream):
+def cold_restart_ab(CH, pop, relaxed, model, stream, h2=False):
     """One interval after reloading relaxed states without S_H and h (as a
     coupling that reloads particle files would): plain start (S_H 1e-7, h
     1e-6 d) against the learned guesses, mixed form, CUDA-event timed."""
@@ -213,7 +230,7 @@ def cold_restart_ab(CH, pop, relaxed, model, stream):
     res = {}
     for name, learned in (("plain", False), ("learned", True)):
         sim = CH.Simulator(pop, precision=CH.PREC_MIXED, stream=stream.cuda_stream,
-                           learned=1 if learned else 0)
+                           learned=1 if learned else 0, h2_algebraic=h2)
         if learned:
             CH.chad_set_mlp(sim.ctx, model.params, model.feat_norm, model.out_norm)
         sim.load(y=relaxed)
@@ -342,6 +359,7 @@ def run_ours(args, ws, rank, local, cfg=3):
     flush = (torch.empty(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
              if meta["flush"] else None)
 
+    h2m = args.model == "h2alg"
     model = None
     train_info = None
     if meta["learned"] and args.form in ("both", "mixed") and not args.no_learned:
@@ -381,22 +399,26 @@ def run_ours(args, ws, rank, local, cfg=3):
         attempts = st["accepted_steps"] + st["rejected_steps"]
         sim.close()
         launch_ms = statistics.mean(per)
-        f64, f32, af = work_per_launch(CH, precision, st, K)
+        f64, f32, af = work_per_launch(CH, precision, st, K, h2)
         achieved = f64 / (launch_ms * 1e-3) / 1e12
         achieved32 = f32 / (launch_ms * 1e-3) / 1e12
+        vinfo = CH.kernel_variant(precision, h2, variant)
         return dict(total_ms=total_ms, per_ms=per, launch_ms=launch_ms, stats=st,
                     f64_per_launch=f64, f32_per_launch=f32, attempt_flops=af,
-                    achieved32_tflops=achieved32,
+                    achieved32_tflops=achieved32, variant_info=vinfo,
+                    roof=alu_roofline(f64, f32, launch_ms, peak64, peak32),
                     variant=variant, tune_ms=[float(x) for x in tune_ms],
                     attempts=attempts, failed=int((out["status"] != 0).sum()),
                     clocks=clk.summary(), achieved_tflops=achieved,
                     y_final=out["y"])
 
     forms = {}
-    h2m = args.model == "h2alg"
     for name, prec in (("mixed", CH.PREC_MIXED), ("fp64", CH.PREC_FP64)):
         if args.form in (name, "both"):
             forms[name] = arm(prec, learned=(name == "mixed" and model is not None), h2=h2m)
+    if h2m and args.form == "both" and cfg == 3 and not args.no_differential:
+        # the FP64 form of the other reading of S_h2 (a differential state)
+        forms["fp64_differential"] = arm(CH.PREC_FP64, h2=False)
     if args.form == "fp64_h2alg":
         # S_h2 algebraic (Eq. 8): the counted attempt flops are those of the
         # differential FP64 form (the Eq. 8 solves and the second rank-1
@@ -409,7 +431,7 @@ def run_ours(args, ws, rank, local, cfg=3):
     # ---------------- learned guesses on a cold restart (reload without S_H, h)
     cold = None
     if model is not None and rank == 0 and cfg in (3, 4):
-        cold = cold_restart_ab(CH, pop, H["y_final"], model, stream)
+        cold = cold_restart_ab(CH, pop, H["y_final"], model, stream, h2m)
 
     # ---------------- e2e: host buffers through the C ABI, copies in the timed region
     e2e = None
@@ -448,12 +470,16 @@ def run_ours(args, ws, rank, local, cfg=3):
                    "learned_guesses": model is not None, "rtol": 1e-6,
                    "l2": meta["l2"],
                    "parallelism": f"particles sharded, {ws} independent populations"},
-        "roofline": {"bound": "alu", "achieved": H["achieved_tflops"], "peak": peak64,
-                     "unit": "TFLOP/s", "frac": H["achieved_tflops"] / peak64, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": H["roof"]["achieved"], "peak": H["roof"]["peak"],
+                     "unit": "TFLOP/s", "frac": H["roof"]["frac"], "pipe": H["roof"]["pipe"],
+                     "traffic": traffic,
                      "traffic_source": (f"profiles/{tsrc}: DRAM bytes per attempt x attempts per launch"
                                         if tsrc else "no capture of the current kernel on this workload"),
-                     "kernel": "integrate_kernel (FP64 part)",
-                     "peak_source": "measured FP64 DFMA chains (chad_probe_alu_peak)",
+                     "kernel": ("integrate_mx_kernel" if (h2m and head == "mixed") else "integrate_kernel"),
+                     "definition": "max(FP64 flops / FP64 peak, FP32 flops / FP32 peak) / launch time; "
+                                   "achieved and peak of the bounding pipe",
+                     "peak_source": "measured DFMA / FFMA chains on every SM (chad_probe_alu_peak)",
+                     "fp64_tflops_achieved": H["achieved_tflops"],
                      "fp64_flops_per_launch": H["f64_per_launch"],
                      "attempt_flops": H["attempt_flops"],
                      "attempts_per_step": H["attempts"] / args.steps,
@@ -466,23 +492,36 @@ def run_ours(args, ws, rank, local, cfg=3):
         "rejected_per_particle_interval": H["stats"]["rejected_steps"] / (N * args.steps),
         "step_spread": [H["stats"]["min_steps"], H["stats"]["max_steps"]],
         "failed_particles": H["failed"],
-        "kernel_variant": H["variant"], "autotune_ms": H["tune_ms"],
+        "kernel_variant": H["variant"], "kernel_variant_shape": H["variant_info"],
+        "autotune_ms": H["tune_ms"],
         "pivot_rejects_per_step": H["stats"]["pivot_rejects"] / args.steps,
         "graph_per_interval": True,
     }
     if "fp64" in forms and head != "fp64":
         F = forms["fp64"]
-        res["plain_fp64"] = {
-            "value": ws * N * dt_days * args.steps / (F["total_ms"] * 1e-3),
-            "ms_per_step": F["total_ms"] / args.steps,
-            "roofline": {"bound": "alu", "achieved": F["achieved_tflops"], "peak": peak64,
-                         "unit": "TFLOP/s", "frac": F["achieved_tflops"] / peak64,
-                         "fp64_flops_per_launch": F["f64_per_launch"],
-                         "attempt_flops": F["attempt_flops"]},
-            "steps_per_particle_interval": F["stats"]["accepted_steps"] / (N * args.steps),
-            "kernel_variant": F["variant"],
-            "clocks": F["clocks"],
-        }
+        def summary(F):
+            return {
+                "value": ws * N * dt_days * args.steps / (F["total_ms"] * 1e-3),
+                "ms_per_step": F["total_ms"] / args.steps,
+                "roofline": {"bound": "alu", "achieved": F["roof"]["achieved"],
+                             "peak": F["roof"]["peak"], "unit": "TFLOP/s",
+                             "frac": F["roof"]["frac"], "pipe": F["roof"]["pipe"],
+                             "fp64_flops_per_launch": F["f64_per_launch"],
+                             "attempt_flops": F["attempt_flops"]},
+                "steps_per_particle_interval": F["stats"]["accepted_steps"] / (N * args.steps),
+                "rejected_per_particle_interval": F["stats"]["rejected_steps"] / (N * args.steps),
+                "kernel_variant": F["variant"], "kernel_variant_shape": F["variant_info"],
+                "clocks": F["clocks"],
+            }
+        res["plain_fp64"] = summary(F)
+        res["plain_fp64"]["model"] = "S_h2 algebraic (Eq. 8)" if h2m else "S_h2 a differential state"
+        if "fp64_differential" in forms:
+            res["plain_fp64_differential"] = summary(forms["fp64_differential"])
+            res["plain_fp64_differential"]["model"] = "S_h2 a differential state"
+            G = forms["fp64_differential"]
+            d2 = np.abs(H["y_final"] - G["y_final"]) / np.maximum(
+                np.abs(G["y_final"]), 1e-12 * np.abs(G["y_final"]).max(axis=1, keepdims=True))
+            res["mixed_vs_fp64_differential_max_rel"] = float(d2.max())
         res["mixed_over_fp64"] = F["total_ms"] / H["total_ms"]
         d = np.abs(H["y_final"] - F["y_final"]) / np.maximum(
             np.abs(F["y_final"]), 1e-12 * np.abs(F["y_final"]).max(axis=1, keepdims=True))
@@ -869,7 +908,7 @@ def run_reload(args, ws, rank, local):
     finals = {}
     for name, learned in (("plain", False), ("learned", True)):
         sim = CH.Simulator(pop, precision=CH.PREC_MIXED, rtol=1e-6, stream=stream.cuda_stream,
-                           learned=1 if learned else 0)
+                           learned=1 if learned else 0, h2_algebraic=(args.model == "h2alg"))
         if learned:
             CH.chad_set_mlp(sim.ctx, model.params, model.feat_norm, model.out_norm)
         y = y0.clone()
@@ -913,6 +952,8 @@ def run_reload(args, ws, rank, local):
             "config": {"workload": f"reload_coupling_{WORKLOAD}", "particles": N,
                        "coupling_interval_s": DT_S, "rtol": 1e-6,
                        "form": "mixed + learned guesses (network at every reload)",
+                       "model": ("S_h2 algebraic (Eq. 8)" if args.model == "h2alg"
+                                 else "S_h2 a differential state"),
                        "reload": "chad_load_particles (device buffers: y, T; no S_H, no h) "
                                  "before every interval, inside the timed region",
                        "l2": "inputs larger than L2 (232 MB state)"},
@@ -938,16 +979,18 @@ def run_reference(args, ws, rank):
     import oracle as O
     pop = I.config_population(3)
     cores = os.cpu_count() or 1
+    h2 = args.model == "h2alg"
     n_s = _calibrate_sample(_sampler(pop, 3), args.warmup + args.steps, 4 * args.cpu_seconds,
-                            cores, 200_000)
+                            cores, 200_000, h2)
     sub = _oracle_sample(pop, n_s)
-    r = O.run(sub, DT_S, args.warmup, rtol=1e-6, n_threads=cores)
+    r = O.run(sub, DT_S, args.warmup, rtol=1e-6, n_threads=cores, h2_algebraic=h2)
     y, SH, h = r["y"], r["S_H"], r["h"]
     times = []
     for k in range(args.steps):
         s2 = I.Population(sub.digesters, y, sub.T, sub.pos, False)
         t0 = time.perf_counter()
-        r = O.run(s2, DT_S, 1, interval0=args.warmup + k, rtol=1e-6, SH=SH, h=h, n_threads=cores)
+        r = O.run(s2, DT_S, 1, interval0=args.warmup + k, rtol=1e-6, SH=SH, h=h, n_threads=cores,
+                  h2_algebraic=h2)
         times.append(time.perf_counter() - t0)
         y, SH, h = r["y"], r["S_H"], r["h"]
     tot = sum(times)
@@ -958,7 +1001,8 @@ def run_reference(args, ws, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "particles_per_step_sample": n_s,
-                       "coupling_interval_s": DT_S, "rtol": 1e-6},
+                       "coupling_interval_s": DT_S, "rtol": 1e-6,
+                       "model": "S_h2 algebraic (Eq. 8)" if h2 else "S_h2 a differential state"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{n_s} seeded particles of the 1M workload per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -972,8 +1016,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", choices=["both", "mixed", "fp64", "fp64_h2alg"], default="both",
                     help="fp64_h2alg: FP64 with S_h2 algebraic (Eq. 8), not the headline")
-    ap.add_argument("--model", choices=["differential", "h2alg"], default="differential",
-                    help="h2alg: S_h2 algebraic (Eq. 8, the paper's DAE form) in both forms")
+    ap.add_argument("--model", choices=["differential", "h2alg"], default="h2alg",
+                    help="h2alg (default): S_h2 algebraic (Eq. 8, the paper's DAE form) in both "
+                         "forms; differential: S_h2 a state")
+    ap.add_argument("--no-differential", action="store_true",
+                    help="skip the extra FP64 arm with S_h2 a differential state")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

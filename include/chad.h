@@ -39,7 +39,7 @@ extern "C" {
 
 #define CHAD_NS 29        /* differential states per particle (Sec. 2.2) */
 #define CHAD_NPARAM 113   /* length of one digester's parameter vector */
-#define CHAD_ABI_VERSION 2
+#define CHAD_ABI_VERSION 3
 
 /* Learned initial guesses: a 32 -> 64 -> 64 -> 2 MLP with SiLU activations.
    FP32 parameter vector layout: W1[64][32], b1[64], W2[64][64], b2[64],
@@ -133,7 +133,7 @@ typedef struct {
 typedef struct {
   int64_t accepted_steps;    /* accepted W-method steps, all particles */
   int64_t rejected_steps;
-  int64_t newton_iters;      /* Eq. 7 (and, with h2_algebraic, Eq. 8) Newton iterations */
+  int64_t newton_iters;      /* Eq. 7 Newton iterations (charge balance, FP64) */
   int64_t newton_fallbacks;  /* bisection fallbacks */
   int64_t min_steps;         /* fewest accepted steps of one particle in one interval */
   int64_t max_steps;         /* most accepted steps of one particle in one interval */
@@ -142,6 +142,8 @@ typedef struct {
   int64_t pivot_rejects;     /* attempts rejected by the static-pivot threshold test */
   int64_t intervals;         /* coupling intervals integrated */
   double sim_days;           /* particle-days integrated */
+  int64_t h2_newton_iters;   /* with h2_algebraic: Eq. 8 Newton iterations (FP64 in the
+                                FP64 form, FP32 in the mixed form); else 0 */
 } chad_stats;
 
 /* ---- introspection ------------------------------------------------------ */
@@ -299,16 +301,30 @@ chad_status chad_diffusion_kernel_times(chad_ctx* ctx, int reps, double* ms_rows
    dt_coupling_s > 0, n_intervals >= 0. */
 chad_status chad_step(chad_ctx* ctx, double dt_coupling_s, int n_intervals);
 
+/* Number of integrator kernel variants the autotuner chooses from. */
+#define CHAD_NUM_VARIANTS 7
+
 /* Pick the fastest integrator kernel variant for this population and
    interval length: the particle state is snapshot, two intervals are run
-   and timed with each of the variants (register budgets of 255/168/128 per
-   thread, i.e. at least 2, 3 or 4 resident 128-thread blocks per SM), and
-   the state is restored, so results are unaffected.  The choice is kept by
-   the context for its precision form; *chosen (may be NULL) receives the
-   variant index and ms (may be NULL) the time (two intervals) of each of
-   the 3 variants.  Temporarily
-   allocates about 290 bytes per particle of device memory.  Synchronous. */
+   and timed with each of the CHAD_NUM_VARIANTS variants, and the state is
+   restored, so results are unaffected.  The variants span threads per block
+   (32, 64, 128, 256), the register budget per thread (255, 168, 128: at
+   least 2, 3 or 4 resident 128-thread blocks per SM) and where the factored
+   matrix I - g J_d lives (per-thread arrays, or a shared-memory tile); see
+   chad_kernel_variant.  The choice is kept by the context for its kernel
+   form; *chosen (may be NULL) receives the variant index and ms (may be
+   NULL, else CHAD_NUM_VARIANTS doubles) the time of two intervals with each
+   variant.  Temporarily allocates about 290 bytes per particle of device
+   memory.  Synchronous. */
 chad_status chad_autotune(chad_ctx* ctx, double dt_coupling_s, int32_t* chosen, double* ms);
+
+/* The launch shape of kernel variant v (0 <= v < CHAD_NUM_VARIANTS) for a
+   context's configuration (precision and h2_algebraic as in chad_config):
+   threads per block, minimum resident blocks per SM (the register budget
+   is 65536 / (threads x blocks), at most 255) and w_shared = 1 when the
+   factored matrix lives in shared memory.  Any output may be NULL. */
+chad_status chad_kernel_variant(int precision, int h2_algebraic, int v, int32_t* threads,
+                                int32_t* min_blocks, int32_t* w_shared);
 
 /* Wait for the context's stream.  CHAD_E_PARTICLE if any particle has a
    status bit set, CHAD_E_CUDA if a kernel failed. */
@@ -422,7 +438,13 @@ chad_status chad_probe_alu_peak(int fp64, double* tflops);
    denominator, besides the sparse solve), out[10] Sherman-Morrison update
    of one solve, out[11] move of the Eq. 7 reciprocals and slope to a
    converged root, out[12] scaling of the rate partials by -g (the FP64
-   form's formation of I - g J_d, with one add per diagonal).  n >= 13. */
+   form's formation of I - g J_d, with one add per diagonal).  n >= 13.
+   With n >= 18 also the mixed form with S_h2 algebraic: out[13] J x from
+   the FP32 rate partials in two-float arithmetic (in FP32 flops), out[14]
+   the Eq. 8 balance coefficients, out[15] one Eq. 8 Newton iteration,
+   out[16] the rest of one attempt's FP32 work (two-float stage arithmetic,
+   residuals, second Sherman-Morrison level), out[17] the rest of its FP64
+   work (evaluation points, S_H guesses). */
 chad_status chad_flop_counts(int64_t* out, int n);
 
 /* The integrator's device arithmetic helpers applied to x [n] (host

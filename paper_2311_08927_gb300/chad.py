@@ -55,7 +55,8 @@ class chad_stats(C.Structure):
                 ("min_steps", C.c_int64), ("max_steps", C.c_int64),
                 ("failed_particles", C.c_int64), ("mlp_redo", C.c_int64),
                 ("pivot_rejects", C.c_int64),
-                ("intervals", C.c_int64), ("sim_days", C.c_double)]
+                ("intervals", C.c_int64), ("sim_days", C.c_double),
+                ("h2_newton_iters", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -123,6 +124,8 @@ def lib():
             L.chad_flop_counts.argtypes = [C.c_void_p, C.c_int]
             L.chad_autotune.restype = C.c_int
             L.chad_autotune.argtypes = [C.c_void_p, C.c_double, C.POINTER(C.c_int32), C.c_void_p]
+            L.chad_kernel_variant.restype = C.c_int
+            L.chad_kernel_variant.argtypes = [C.c_int, C.c_int, C.c_int] + [C.POINTER(C.c_int32)] * 3
             L.chad_eval_model.restype = C.c_int
             L.chad_eval_model.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double,
                                           C.c_void_p, C.c_double, C.c_void_p, C.c_double,
@@ -179,7 +182,8 @@ def exported_symbols() -> list[str]:
             "chad_set_positions_by_id", "chad_load_frame", "chad_read_frame",
             "chad_get_interval", "chad_set_interval", "chad_debug_bounds",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
-            "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam"]
+            "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam",
+            "chad_kernel_variant"]
 
 MLP_IN, MLP_HID, MLP_OUT = 32, 64, 2
 MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT
@@ -232,7 +236,8 @@ def chad_mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, s
 
 
 FLOP_KEYS = ["rates_f", "rates_fj", "charge_E", "form_w", "factor", "solve", "jx", "stage",
-             "refine", "sm_setup", "sm_update", "sh_final", "scale_j"]
+             "refine", "sm_setup", "sm_update", "sh_final", "scale_j", "jx_twofloat",
+             "h2_coeffs", "h2_iter", "mx_fp32_extra", "mx_fp64_extra"]
 
 
 def flop_counts() -> dict:
@@ -241,6 +246,22 @@ def flop_counts() -> dict:
     out = np.zeros(len(FLOP_KEYS), dtype=np.int64)
     _check(L, None, L.chad_flop_counts(out.ctypes.data, len(FLOP_KEYS)))
     return dict(zip(FLOP_KEYS, (int(x) for x in out)))
+
+
+def attempt_flops_h2_mixed() -> dict:
+    """FP64 and FP32 operations of one step attempt of the mixed form with
+    S_h2 algebraic (kernel form 4), without the Newton iterations of Eq. 7
+    (FP64) and Eq. 8 (FP32), which are counted per iteration: FP32 rates with
+    J_d and u at the step's start and rates at the two stage points, the
+    sparse LU, two sparse solves for q and p2 and two per stage, the
+    Sherman-Morrison updates, three Eq. 8 coefficient sets, the two-float
+    J x of three refinement residuals and the two-float stage arithmetic;
+    FP64 for the evaluation points and the S_H guesses."""
+    f = flop_counts()
+    f32 = (f["rates_fj"] + 2 * f["rates_f"] + f["form_w"] + f["factor"] + 8 * f["solve"] +
+           f["sm_setup"] + 7 * f["sm_update"] + 3 * f["h2_coeffs"] + 3 * f["jx_twofloat"] +
+           f["mx_fp32_extra"])
+    return {"fp64": f["mx_fp64_extra"], "fp32": f32, "fp32_per_h2_iter": f["h2_iter"]}
 
 
 def attempt_flops(precision: int) -> dict:
@@ -268,13 +289,26 @@ def newton_flops() -> int:
     return flop_counts()["charge_E"] + 2
 
 
+NUM_VARIANTS = 7  # CHAD_NUM_VARIANTS
+
+
 def chad_autotune(ctx, dt_coupling_s):
     """Returns (chosen variant, ms per variant)."""
     L = lib()
     ch = C.c_int32(-1)
-    ms = np.zeros(3)
+    ms = np.zeros(NUM_VARIANTS)
     _check(L, ctx, L.chad_autotune(ctx, float(dt_coupling_s), C.byref(ch), ms.ctypes.data))
     return ch.value, ms
+
+
+def kernel_variant(precision, h2_algebraic, v) -> dict:
+    """Launch shape of integrator kernel variant v (chad_kernel_variant)."""
+    L = lib()
+    t, m, w = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(L, None, L.chad_kernel_variant(int(precision), int(bool(h2_algebraic)), int(v),
+                                          C.byref(t), C.byref(m), C.byref(w)))
+    return {"threads": t.value, "min_blocks": m.value, "w_shared": bool(w.value),
+            "registers_max": min(255, 65536 // (t.value * m.value))}
 
 
 def eval_model(params, T, y, y_in=None, D=0.0, V_liq=3400.0, V_gas=300.0, SH_guess=1e-7,

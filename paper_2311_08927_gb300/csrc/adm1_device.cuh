@@ -635,44 +635,46 @@ CHAD_HD void rates(const DC& c, const PQ& q, const R* y, const AcidBase& ab, Rat
 // dil holds the transport terms of every state (liquid: dilution; gas:
 // outflow) and N the ADM1 stoichiometry of the 19 processes and the three
 // gas transfers (r[19..21]).
-template <class R, class DC>
+// C: type of the stoichiometric coefficients in the products (R itself,
+// or float for a two-float accumulator R).
+template <class R, class DC, class C = R>
 CHAD_HD void stoich(const DC& c, const R* r, const R* dil, R* f) {
   const R dec = r[12] + r[13] + r[14] + r[15] + r[16] + r[17] + r[18];
-  f[iS_su] = dil[iS_su] + r[1] + R(c.c_su_li) * r[3] - r[4];
+  f[iS_su] = dil[iS_su] + r[1] + C(c.c_su_li) * r[3] - r[4];
   f[iS_aa] = dil[iS_aa] + r[2] - r[5];
-  f[iS_fa] = dil[iS_fa] + R(c.f_fa_li) * r[3] - r[6];
-  f[iS_va] = dil[iS_va] + R(c.aa_va) * r[5] - r[7];
-  f[iS_bu] = dil[iS_bu] + R(c.su_bu) * r[4] + R(c.aa_bu) * r[5] - r[8];
-  f[iS_pro] = dil[iS_pro] + R(c.su_pro) * r[4] + R(c.aa_pro) * r[5] + R(c.va_pro) * r[7] - r[9];
-  f[iS_ac] = dil[iS_ac] + R(c.su_ac) * r[4] + R(c.aa_ac) * r[5] + R(c.fa_ac) * r[6] +
-             R(c.va_ac) * r[7] + R(c.bu_ac) * r[8] + R(c.pro_ac) * r[9] - r[10];
-  f[iS_h2] = dil[iS_h2] + R(c.su_h2) * r[4] + R(c.aa_h2) * r[5] + R(c.fa_h2) * r[6] +
-             R(c.va_h2) * r[7] + R(c.bu_h2) * r[8] + R(c.pro_h2) * r[9] - r[11] - r[19];
-  f[iS_ch4] = dil[iS_ch4] + R(c.ac_ch4) * r[10] + R(c.h2_ch4) * r[11] - r[20];
-  R ic = dil[iS_IC] + R(c.cIC[12]) * dec - r[21];
+  f[iS_fa] = dil[iS_fa] + C(c.f_fa_li) * r[3] - r[6];
+  f[iS_va] = dil[iS_va] + C(c.aa_va) * r[5] - r[7];
+  f[iS_bu] = dil[iS_bu] + C(c.su_bu) * r[4] + C(c.aa_bu) * r[5] - r[8];
+  f[iS_pro] = dil[iS_pro] + C(c.su_pro) * r[4] + C(c.aa_pro) * r[5] + C(c.va_pro) * r[7] - r[9];
+  f[iS_ac] = dil[iS_ac] + C(c.su_ac) * r[4] + C(c.aa_ac) * r[5] + C(c.fa_ac) * r[6] +
+             C(c.va_ac) * r[7] + C(c.bu_ac) * r[8] + C(c.pro_ac) * r[9] - r[10];
+  f[iS_h2] = dil[iS_h2] + C(c.su_h2) * r[4] + C(c.aa_h2) * r[5] + C(c.fa_h2) * r[6] +
+             C(c.va_h2) * r[7] + C(c.bu_h2) * r[8] + C(c.pro_h2) * r[9] - r[11] - r[19];
+  f[iS_ch4] = dil[iS_ch4] + C(c.ac_ch4) * r[10] + C(c.h2_ch4) * r[11] - r[20];
+  R ic = dil[iS_IC] + C(c.cIC[12]) * dec - r[21];
 #pragma unroll
-  for (int j = 0; j < 12; ++j) ic += R(c.cIC[j]) * r[j];
+  for (int j = 0; j < 12; ++j) ic += C(c.cIC[j]) * r[j];
   f[iS_IC] = ic;
-  R in = dil[iS_IN] + R(c.nIN[0]) * r[0] + R(c.nIN[12]) * dec;
+  R in = dil[iS_IN] + C(c.nIN[0]) * r[0] + C(c.nIN[12]) * dec;
 #pragma unroll
-  for (int j = 4; j < 12; ++j) in += R(c.nIN[j]) * r[j];
+  for (int j = 4; j < 12; ++j) in += C(c.nIN[j]) * r[j];
   f[iS_IN] = in;
-  f[iS_I] = dil[iS_I] + R(c.f_sI) * r[0];
+  f[iS_I] = dil[iS_I] + C(c.f_sI) * r[0];
   f[iX_c] = dil[iX_c] - r[0] + dec;
-  f[iX_ch] = dil[iX_ch] + R(c.f_ch) * r[0] - r[1];
-  f[iX_pr] = dil[iX_pr] + R(c.f_pr) * r[0] - r[2];
-  f[iX_li] = dil[iX_li] + R(c.f_li) * r[0] - r[3];
-  f[iX_su] = dil[iX_su] + R(c.Y_su) * r[4] - r[12];
-  f[iX_aa] = dil[iX_aa] + R(c.Y_aa) * r[5] - r[13];
-  f[iX_fa] = dil[iX_fa] + R(c.Y_fa) * r[6] - r[14];
-  f[iX_c4] = dil[iX_c4] + R(c.Y_c4) * (r[7] + r[8]) - r[15];
-  f[iX_pro] = dil[iX_pro] + R(c.Y_pro) * r[9] - r[16];
-  f[iX_ac] = dil[iX_ac] + R(c.Y_ac) * r[10] - r[17];
-  f[iX_h2] = dil[iX_h2] + R(c.Y_h2) * r[11] - r[18];
-  f[iX_I] = dil[iX_I] + R(c.f_xI) * r[0];
+  f[iX_ch] = dil[iX_ch] + C(c.f_ch) * r[0] - r[1];
+  f[iX_pr] = dil[iX_pr] + C(c.f_pr) * r[0] - r[2];
+  f[iX_li] = dil[iX_li] + C(c.f_li) * r[0] - r[3];
+  f[iX_su] = dil[iX_su] + C(c.Y_su) * r[4] - r[12];
+  f[iX_aa] = dil[iX_aa] + C(c.Y_aa) * r[5] - r[13];
+  f[iX_fa] = dil[iX_fa] + C(c.Y_fa) * r[6] - r[14];
+  f[iX_c4] = dil[iX_c4] + C(c.Y_c4) * (r[7] + r[8]) - r[15];
+  f[iX_pro] = dil[iX_pro] + C(c.Y_pro) * r[9] - r[16];
+  f[iX_ac] = dil[iX_ac] + C(c.Y_ac) * r[10] - r[17];
+  f[iX_h2] = dil[iX_h2] + C(c.Y_h2) * r[11] - r[18];
+  f[iX_I] = dil[iX_I] + C(c.f_xI) * r[0];
   f[iS_cat] = dil[iS_cat];
   f[iS_an] = dil[iS_an];
-  const R vr = R(c.Vliq_over_Vgas);
+  const C vr = C(c.Vliq_over_Vgas);
   f[iG_h2] = dil[iG_h2] + vr * r[19];
   f[iG_ch4] = dil[iG_ch4] + vr * r[20];
   f[iG_co2] = dil[iG_co2] + vr * r[21];
@@ -719,45 +721,45 @@ CHAD_HD void balances(const DC& c, const R* y, R D, const Rates<R>& o, R* f) {
 // same stoichiometry as the rates; the transport terms are linearised
 // directly.  Arithmetic in precision RD (FP64 in the kernels) whatever the
 // precision RO of the partials.
-template <class RO, class RD, class DC>
-CHAD_HD void jvp(const DC& c, const RD* y, RD D, const Rates<RO>& o, const RD* x, RD s,
+template <class RO, class RD, class DC, class C = RD>
+CHAD_HD void jvp(const DC& c, const C* y, C D, const Rates<RO>& o, const RD* x, RD s,
                  RD* out) {
   RD dr[22];
-  dr[0] = RD(o.d1) * x[iX_c];
-  dr[1] = RD(o.d2) * x[iX_ch];
-  dr[2] = RD(o.d3) * x[iX_pr];
-  dr[3] = RD(o.d4) * x[iX_li];
-  dr[4] = RD(o.d5[0]) * x[iS_su] + RD(o.d5[1]) * x[iX_su] + RD(o.d5[2]) * x[iS_IN] +
-          RD(o.s5) * s;
-  dr[5] = RD(o.d6[0]) * x[iS_aa] + RD(o.d6[1]) * x[iX_aa] + RD(o.d6[2]) * x[iS_IN] +
-          RD(o.s6) * s;
-  dr[6] = RD(o.d7[0]) * x[iS_fa] + RD(o.d7[1]) * x[iX_fa] + RD(o.d7[2]) * x[iS_IN] +
-          RD(o.d7[3]) * x[iS_h2] + RD(o.s7) * s;
-  dr[7] = RD(o.d8[0]) * x[iS_va] + RD(o.d8[1]) * x[iS_bu] + RD(o.d8[2]) * x[iX_c4] +
-          RD(o.d8[3]) * x[iS_IN] + RD(o.d8[4]) * x[iS_h2] + RD(o.s8) * s;
-  dr[8] = RD(o.d9[0]) * x[iS_va] + RD(o.d9[1]) * x[iS_bu] + RD(o.d9[2]) * x[iX_c4] +
-          RD(o.d9[3]) * x[iS_IN] + RD(o.d9[4]) * x[iS_h2] + RD(o.s9) * s;
-  dr[9] = RD(o.d10[0]) * x[iS_pro] + RD(o.d10[1]) * x[iX_pro] +
-          RD(o.d10[2]) * x[iS_IN] + RD(o.d10[3]) * x[iS_h2] + RD(o.s10) * s;
-  dr[10] = RD(o.d11[0]) * x[iS_ac] + RD(o.d11[1]) * x[iX_ac] +
-           RD(o.d11[2]) * x[iS_IN] + RD(o.s11) * s;
-  dr[11] = RD(o.d12[0]) * x[iS_h2] + RD(o.d12[1]) * x[iX_h2] +
-           RD(o.d12[2]) * x[iS_IN] + RD(o.s12) * s;
+  dr[0] = C(o.d1) * x[iX_c];
+  dr[1] = C(o.d2) * x[iX_ch];
+  dr[2] = C(o.d3) * x[iX_pr];
+  dr[3] = C(o.d4) * x[iX_li];
+  dr[4] = C(o.d5[0]) * x[iS_su] + C(o.d5[1]) * x[iX_su] + C(o.d5[2]) * x[iS_IN] +
+          C(o.s5) * s;
+  dr[5] = C(o.d6[0]) * x[iS_aa] + C(o.d6[1]) * x[iX_aa] + C(o.d6[2]) * x[iS_IN] +
+          C(o.s6) * s;
+  dr[6] = C(o.d7[0]) * x[iS_fa] + C(o.d7[1]) * x[iX_fa] + C(o.d7[2]) * x[iS_IN] +
+          C(o.d7[3]) * x[iS_h2] + C(o.s7) * s;
+  dr[7] = C(o.d8[0]) * x[iS_va] + C(o.d8[1]) * x[iS_bu] + C(o.d8[2]) * x[iX_c4] +
+          C(o.d8[3]) * x[iS_IN] + C(o.d8[4]) * x[iS_h2] + C(o.s8) * s;
+  dr[8] = C(o.d9[0]) * x[iS_va] + C(o.d9[1]) * x[iS_bu] + C(o.d9[2]) * x[iX_c4] +
+          C(o.d9[3]) * x[iS_IN] + C(o.d9[4]) * x[iS_h2] + C(o.s9) * s;
+  dr[9] = C(o.d10[0]) * x[iS_pro] + C(o.d10[1]) * x[iX_pro] +
+          C(o.d10[2]) * x[iS_IN] + C(o.d10[3]) * x[iS_h2] + C(o.s10) * s;
+  dr[10] = C(o.d11[0]) * x[iS_ac] + C(o.d11[1]) * x[iX_ac] +
+           C(o.d11[2]) * x[iS_IN] + C(o.s11) * s;
+  dr[11] = C(o.d12[0]) * x[iS_h2] + C(o.d12[1]) * x[iX_h2] +
+           C(o.d12[2]) * x[iS_IN] + C(o.s12) * s;
 #pragma unroll
-  for (int k = 0; k < 7; ++k) dr[12 + k] = RD(o.ddec[k]) * x[iX_su + k];
-  dr[19] = RD(o.dT8[0]) * x[iS_h2] + RD(o.dT8[1]) * x[iG_h2];
-  dr[20] = RD(o.dT9[0]) * x[iS_ch4] + RD(o.dT9[1]) * x[iG_ch4];
-  dr[21] = RD(o.dT10[0]) * x[iS_IC] + RD(o.dT10[1]) * x[iG_co2] + RD(o.sT10) * s;
+  for (int k = 0; k < 7; ++k) dr[12 + k] = C(o.ddec[k]) * x[iX_su + k];
+  dr[19] = C(o.dT8[0]) * x[iS_h2] + C(o.dT8[1]) * x[iG_h2];
+  dr[20] = C(o.dT9[0]) * x[iS_ch4] + C(o.dT9[1]) * x[iG_ch4];
+  dr[21] = C(o.dT10[0]) * x[iS_IC] + C(o.dT10[1]) * x[iG_co2] + C(o.sT10) * s;
   RD dil[NS];
 #pragma unroll
   for (int i = 0; i < 26; ++i) dil[i] = -D * x[i];
-  const RD qv = RD(o.qv);
+  const C qv = C(o.qv);
   const RD dq =
-      RD(o.dqv) * (RD(o.P_h2) * x[iG_h2] + RD(o.P_ch4) * x[iG_ch4] + RD(o.P_co2) * x[iG_co2]);
+      C(o.dqv) * (C(o.P_h2) * x[iG_h2] + C(o.P_ch4) * x[iG_ch4] + C(o.P_co2) * x[iG_co2]);
   dil[iG_h2] = -x[iG_h2] * qv - y[iG_h2] * dq;
   dil[iG_ch4] = -x[iG_ch4] * qv - y[iG_ch4] * dq;
   dil[iG_co2] = -x[iG_co2] * qv - y[iG_co2] * dq;
-  stoich<RD>(c, dr, dil, out);
+  stoich<RD, DC, C>(c, dr, dil, out);
 }
 
 

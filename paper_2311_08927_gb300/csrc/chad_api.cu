@@ -362,7 +362,7 @@ chad_status chad_create(const chad_config* cfg, chad_ctx** out) {
   A(cudaMemset(c->d_mean, 0, sizeof(double) * 3 * c->n_dig));
   A(cudaMemset(c->d_interval, 0, sizeof(unsigned long long)));
   A(cudaMemset(c->d_queue, 0, sizeof(unsigned long long)));
-  DevCounters z{0, 0, 0, 0, 0, 0, 0x7fffffff, 0};
+  DevCounters z{0, 0, 0, 0, 0, 0, 0x7fffffff, 0, 0};
   A(cudaMemcpy(c->d_cnt, &z, sizeof(z), cudaMemcpyHostToDevice));
   if (e != cudaSuccess) {
     free_all(c);
@@ -1045,6 +1045,18 @@ chad_status chad_autotune(chad_ctx* c, double dt_coupling_s, int32_t* chosen, do
   return CHAD_OK;
 }
 
+chad_status chad_kernel_variant(int precision, int h2_algebraic, int v, int32_t* threads,
+                                int32_t* min_blocks, int32_t* w_shared) {
+  if (v < 0 || v >= kNumVariants) return CHAD_E_INVALID;
+  if (precision < CHAD_PREC_FP64 || precision > CHAD_PREC_MIXED_F32RATES) return CHAD_E_INVALID;
+  const int form = h2_algebraic ? (precision == CHAD_PREC_MIXED ? 4 : 3) : precision;
+  const KernelVariant k = kernel_variant(form, v);
+  if (threads) *threads = k.threads;
+  if (min_blocks) *min_blocks = k.min_blocks;
+  if (w_shared) *w_shared = k.w_shared;
+  return CHAD_OK;
+}
+
 chad_status chad_synchronize(chad_ctx* c) {
   if (!c) return CHAD_E_INVALID;
   CK(c, cudaStreamSynchronize(c->stream), "synchronize");
@@ -1094,9 +1106,10 @@ chad_status chad_read_states(chad_ctx* c, int digester, double* y, double* pos, 
     stats->failed_particles = failed;
     stats->mlp_redo = (int64_t)dc.mlp_redo;
     stats->pivot_rejects = (int64_t)dc.pivot_rejects;
+    stats->h2_newton_iters = (int64_t)dc.h2_iters;
     stats->intervals = c->intervals;
     stats->sim_days = c->sim_days;
-    DevCounters z{0, 0, 0, 0, 0, 0, 0x7fffffff, 0};
+    DevCounters z{0, 0, 0, 0, 0, 0, 0x7fffffff, 0, 0};
     CK(c, cudaMemcpy(c->d_cnt, &z, sizeof(z), cudaMemcpyHostToDevice), "reset counters");
     c->intervals = 0;
     c->sim_days = 0.0;

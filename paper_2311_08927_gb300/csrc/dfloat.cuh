@@ -85,19 +85,33 @@ CHAD_HD df df_of_double(double d) {
 }
 CHAD_HD double df_to_double(df a) { return double(a.hi) + double(a.lo); }
 
-// The same arithmetic as a scalar type, so that templated model routines
-// (the Jacobian-vector product and the stoichiometry) run in two-float
-// arithmetic unchanged.  Built from a float, the low part is zero.
+// A two-float accumulator as a scalar type, so that the templated model
+// routines (the Jacobian-vector product and the stoichiometry) run in it
+// unchanged: hi is the float sum of the terms, lo the float sum of the
+// rounding errors that TwoSum and TwoProd recover (the cascaded summation
+// "Sum2" of Ogita, Rump and Oishi, 2005).  lo is not renormalised into hi
+// after each operation; the value is hi + lo, accurate to O(2^-44) times
+// the sum of the magnitudes of the terms.  Products are only of a float
+// coefficient and an accumulator (three operations); a sum of two
+// accumulators is eight.
 struct DF {
-  df v;
+  float hi, lo;
   DF() = default;
-  CHAD_HD DF(float a) : v{a, 0.0f} {}
-  CHAD_HD explicit DF(df a) : v(a) {}
+  CHAD_HD DF(float a) : hi(a), lo(0.0f) {}
+  CHAD_HD DF(float h, float l) : hi(h), lo(l) {}
+  CHAD_HD df v() const { return df{hi, lo}; }
 };
-CHAD_HD DF operator+(DF a, DF b) { return DF(df_add(a.v, b.v)); }
-CHAD_HD DF operator-(DF a) { return DF(df_neg(a.v)); }
-CHAD_HD DF operator-(DF a, DF b) { return DF(df_add(a.v, df_neg(b.v))); }
-CHAD_HD DF operator*(DF a, DF b) { return DF(df_mul(a.v, b.v)); }
+CHAD_HD DF operator+(DF a, DF b) {
+  const df s = two_sum(a.hi, b.hi);
+  return DF(s.hi, s.lo + (a.lo + b.lo));
+}
+CHAD_HD DF operator-(DF a) { return DF(-a.hi, -a.lo); }
+CHAD_HD DF operator-(DF a, DF b) { return a + (-b); }
+CHAD_HD DF operator*(float c, DF a) {
+  const df p = two_prod(c, a.hi);
+  return DF(p.hi, fmaf(c, a.lo, p.lo));
+}
+CHAD_HD DF operator*(DF a, float c) { return c * a; }
 CHAD_HD DF& operator+=(DF& a, DF b) {
   a = a + b;
   return a;

@@ -148,9 +148,10 @@ def generate(pat: np.ndarray) -> str:
     w("constexpr int kDiag[NS] = {" + ", ".join(str(int(slot[s, s])) for s in order) + "};")
     w("")
     # ------------------------------------------------------------- W formation
-    w("// W_d = I - g J_d in place over the slots (fill slots hold zero in J_d)")
-    w("template <class R>")
-    w("CHAD_HD void form_w(R* w, R g) {")
+    w("// W_d = I - g J_d in place over the slots (fill slots hold zero in J_d).")
+    w("// W: the slot storage, a pointer or any accessor whose w[s] is a reference.")
+    w("template <class R, class W>")
+    w("CHAD_HD void form_w(W w, R g) {")
     w("#pragma unroll")
     w("  for (int s = 0; s < kNNZ; ++s) w[s] = -g * w[s];")
     for sidx in order:
@@ -159,8 +160,8 @@ def generate(pat: np.ndarray) -> str:
     w("")
     # ------------------------------------------------------------- factor
     w("// In-place LU; returns false if a pivot fails the threshold test.")
-    w("template <class R>")
-    w("CHAD_HD bool factor(R* w, R* dinv) {")
+    w("template <class R, class W>")
+    w("CHAD_HD bool factor(W w, R* dinv) {")
     w("  using P = PivTest<R>;")
     w("  bool ok = true;")
     for k in range(NS):
@@ -196,8 +197,8 @@ def generate(pat: np.ndarray) -> str:
     w("")
     # ------------------------------------------------------------- solve
     w("// Solve W x = b in place (b indexed by state).")
-    w("template <class R>")
-    w("CHAD_HD void solve(const R* w, const R* dinv, R* b) {")
+    w("template <class R, class W>")
+    w("CHAD_HD void solve(W w, const R* dinv, R* b) {")
     for k in range(NS):
         w(f"  R z{k} = b[{order[k]}];")
     sflops = 0

@@ -7,21 +7,20 @@
 namespace chad {
 
 #define CHAD_DECL(f, v) cudaError_t launch_integrate_f##f##_v##v(const StepArgs& a, cudaStream_t s);
-CHAD_DECL(0, 0) CHAD_DECL(0, 1) CHAD_DECL(0, 2)
-CHAD_DECL(1, 0) CHAD_DECL(1, 1) CHAD_DECL(1, 2)
-CHAD_DECL(2, 0) CHAD_DECL(2, 1) CHAD_DECL(2, 2)
-CHAD_DECL(3, 0) CHAD_DECL(3, 1) CHAD_DECL(3, 2)
-CHAD_DECL(4, 0) CHAD_DECL(4, 1) CHAD_DECL(4, 2)
+#define CHAD_FORM(f) CHAD_DECL(f, 0) CHAD_DECL(f, 1) CHAD_DECL(f, 2) CHAD_DECL(f, 3) \
+  CHAD_DECL(f, 4) CHAD_DECL(f, 5) CHAD_DECL(f, 6)
+CHAD_FORM(0) CHAD_FORM(1) CHAD_FORM(2) CHAD_FORM(3) CHAD_FORM(4)
+#undef CHAD_FORM
 #undef CHAD_DECL
 
 cudaError_t launch_integrate(const StepArgs& a, int precision, int variant, cudaStream_t s) {
   using Fn = cudaError_t (*)(const StepArgs&, cudaStream_t);
-  static const Fn table[5][kNumVariants] = {
-      {launch_integrate_f0_v0, launch_integrate_f0_v1, launch_integrate_f0_v2},
-      {launch_integrate_f1_v0, launch_integrate_f1_v1, launch_integrate_f1_v2},
-      {launch_integrate_f2_v0, launch_integrate_f2_v1, launch_integrate_f2_v2},
-      {launch_integrate_f3_v0, launch_integrate_f3_v1, launch_integrate_f3_v2},
-      {launch_integrate_f4_v0, launch_integrate_f4_v1, launch_integrate_f4_v2}};
+#define CHAD_ROW(f) {launch_integrate_f##f##_v0, launch_integrate_f##f##_v1, \
+  launch_integrate_f##f##_v2, launch_integrate_f##f##_v3, launch_integrate_f##f##_v4, \
+  launch_integrate_f##f##_v5, launch_integrate_f##f##_v6}
+  static const Fn table[5][kNumVariants] = {CHAD_ROW(0), CHAD_ROW(1), CHAD_ROW(2), CHAD_ROW(3),
+                                            CHAD_ROW(4)};
+#undef CHAD_ROW
   if (a.n <= 0) return cudaSuccess;
   if (variant < 0 || variant >= kNumVariants) variant = kDefaultVariant;
   if (precision < 0 || precision > 4) precision = 0;

@@ -1,9 +1,10 @@
-// Integrator kernel instance: precision form 0, at least 4 resident
-// 128-thread blocks per SM (sets the register budget).  See integrate_impl.cuh.
+// Integrator kernel instance: form 0, 128 threads per block, at least
+// 4 resident blocks per SM, W_d in per-thread arrays (variant 2 of
+// kernel_variant in kernels.h).  See integrate_impl.cuh.
 #include "integrate_impl.cuh"
 
 namespace chad {
 cudaError_t launch_integrate_f0_v2(const StepArgs& a, cudaStream_t s) {
-  return launch_variant<0, 4>(a, s);
+  return launch_variant<0, 128, 4, false>(a, s);
 }
 }  // namespace chad

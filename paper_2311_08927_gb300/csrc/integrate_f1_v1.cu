@@ -1,9 +1,10 @@
-// Integrator kernel instance: precision form 1, at least 3 resident
-// 128-thread blocks per SM (sets the register budget).  See integrate_impl.cuh.
+// Integrator kernel instance: form 1, 128 threads per block, at least
+// 3 resident blocks per SM, W_d in per-thread arrays (variant 1 of
+// kernel_variant in kernels.h).  See integrate_impl.cuh.
 #include "integrate_impl.cuh"
 
 namespace chad {
 cudaError_t launch_integrate_f1_v1(const StepArgs& a, cudaStream_t s) {
-  return launch_variant<1, 3>(a, s);
+  return launch_variant<1, 128, 3, false>(a, s);
 }
 }  // namespace chad

@@ -1,0 +1,10 @@
+// Integrator kernel instance: form 1, 256 threads per block, at least
+// 1 resident blocks per SM, W_d in per-thread arrays (variant 4 of
+// kernel_variant in kernels.h).  See integrate_impl.cuh.
+#include "integrate_impl.cuh"
+
+namespace chad {
+cudaError_t launch_integrate_f1_v4(const StepArgs& a, cudaStream_t s) {
+  return launch_variant<1, 256, 1, false>(a, s);
+}
+}  // namespace chad

@@ -1,0 +1,10 @@
+// Integrator kernel instance: form 2, 64 threads per block, at least
+// 4 resident blocks per SM, W_d in per-thread arrays (variant 3 of
+// kernel_variant in kernels.h).  See integrate_impl.cuh.
+#include "integrate_impl.cuh"
+
+namespace chad {
+cudaError_t launch_integrate_f2_v3(const StepArgs& a, cudaStream_t s) {
+  return launch_variant<2, 64, 4, false>(a, s);
+}
+}  // namespace chad

@@ -1,0 +1,10 @@
+// Integrator kernel instance: form 2, 32 threads per block, at least
+// 8 resident blocks per SM, W_d in per-thread arrays (variant 5 of
+// kernel_variant in kernels.h).  See integrate_impl.cuh.
+#include "integrate_impl.cuh"
+
+namespace chad {
+cudaError_t launch_integrate_f2_v5(const StepArgs& a, cudaStream_t s) {
+  return launch_variant<2, 32, 8, false>(a, s);
+}
+}  // namespace chad

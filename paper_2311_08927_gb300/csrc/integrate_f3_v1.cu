@@ -1,9 +1,10 @@
-// Integrator kernel instance: form 3 (FP64, S_h2 algebraic), at least 3 resident
-// 128-thread blocks per SM (sets the register budget).  See integrate_impl.cuh.
+// Integrator kernel instance: form 3, 128 threads per block, at least
+// 3 resident blocks per SM, W_d in per-thread arrays (variant 1 of
+// kernel_variant in kernels.h).  See integrate_impl.cuh.
 #include "integrate_impl.cuh"
 
 namespace chad {
 cudaError_t launch_integrate_f3_v1(const StepArgs& a, cudaStream_t s) {
-  return launch_variant<3, 3>(a, s);
+  return launch_variant<3, 128, 3, false>(a, s);
 }
 }  // namespace chad

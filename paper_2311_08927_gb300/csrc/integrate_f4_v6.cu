@@ -1,0 +1,10 @@
+// Integrator kernel instance: form 4 (mixed with S_h2 algebraic), 128 threads per block, at least
+// 2 resident blocks per SM, W_d in shared memory (variant 6 of
+// kernel_variant in kernels.h).  See integrate_mx.cuh.
+#include "integrate_mx.cuh"
+
+namespace chad {
+cudaError_t launch_integrate_f4_v6(const StepArgs& a, cudaStream_t s) {
+  return launch_variant_mx<128, 2, true>(a, s);
+}
+}  // namespace chad

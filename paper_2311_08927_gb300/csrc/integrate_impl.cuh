@@ -52,7 +52,7 @@ constexpr double kHdefault = 1e-6;                              // days
 constexpr double kPivTau = 0.1;  // threshold of the Sherman-Morrison denominator test
 
 struct Cnt {
-  int acc, rej, newton, fallback, failed, pivot, redo;
+  int acc, rej, newton, fallback, failed, pivot, redo, h2;
 };
 
 __device__ __forceinline__ int64_t queue_pop(unsigned long long* q) {
@@ -84,7 +84,7 @@ __device__ __forceinline__ void newton_h2(const DigConst& c, const PartConst& q,
   h2_coeffs<double>(c, q, y, D, ab, e);
   NewtonCounters nc{0, 0, 0};
   *SH2g = solve_h2(e, *SH2g, max_newton, nc);
-  cnt.newton += nc.iters;
+  cnt.h2 += nc.iters;
   cnt.fallback += nc.fallbacks;
   cnt.failed |= nc.failed;
 }
@@ -132,10 +132,10 @@ struct DCSel<float> {
   }
 };
 
-template <class R, class RS, bool SCALE, bool H2A = false>
+template <class R, class RS, bool SCALE, bool H2A = false, class W>
 __device__ __forceinline__ void eval_fj(const DigConst& c, const DigConstF* cf, const PartConst& q,
                                         const double* y, double D, double& SHg, int max_newton,
-                                        Cnt& cnt, double* f, R* w, R* u, Rates<R>& o,
+                                        Cnt& cnt, double* f, W w, R* u, Rates<R>& o,
                                         AcidBase& ab, R jscale, double* SH2g = nullptr) {
   const auto& cr = DCSel<R>::get(c, cf);
   newton(c, q, y, SHg, max_newton, cnt, ab);
@@ -193,8 +193,8 @@ __device__ __forceinline__ double sh_guess(double SH0, const double* v, const do
 // (rank-1 update).  The FP32<->FP64 conversions here use the hardware
 // instructions: there are ~120 per stage, and as integer sequences they
 // cost more issue slots than they free on the FP64 pipe.
-template <bool MIXED, class R>
-__device__ __forceinline__ void solve(const R* w, const R* dinv, const R* qv, R inv_delta,
+template <bool MIXED, class R, class W>
+__device__ __forceinline__ void solve(W w, const R* dinv, const R* qv, R inv_delta,
                                       const double* v, const R* vr, const DigConst& c,
                                       const double* y, double D, const Rates<R>& ko, double g,
                                       const double* b, double* x) {
@@ -259,22 +259,50 @@ __device__ __forceinline__ void stage_rhs(int st, const DigConst& c, const PartC
   }
 }
 
-template <int FORM, int MINB>
-__global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
+// Slot storage of W_d: a per-thread array (registers / local memory), or
+// thread t's column of a [kNNZ][BS] tile in dynamic shared memory (slot s of
+// consecutive threads in consecutive words: no bank conflicts).
+extern __shared__ __align__(16) unsigned char chad_dyn_smem[];
+template <class R, int BS>
+struct SmemSlots {
+  R* base;
+  __device__ __forceinline__ R& operator[](int s) const { return base[s * BS]; }
+};
+template <class R, int BS, bool WS>
+struct WStore;
+template <class R, int BS>
+struct WStore<R, BS, false> {
+  R a[sp::kNNZ];
+  __device__ __forceinline__ R* slots() { return a; }
+};
+template <class R, int BS>
+struct WStore<R, BS, true> {
+  __device__ __forceinline__ SmemSlots<R, BS> slots() {
+    return SmemSlots<R, BS>{reinterpret_cast<R*>(chad_dyn_smem) + threadIdx.x};
+  }
+};
+template <class R, int BS, bool WS>
+constexpr size_t wstore_smem_bytes() {
+  return WS ? sizeof(R) * sp::kNNZ * BS : 0;
+}
+
+template <int FORM, int BS, int MINB, bool WS>
+__global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
   constexpr bool MIXED = FORM == 1 || FORM == 2;
   constexpr bool H2A = FORM == 3;  // FP64 with S_h2 algebraic (Eq. 8)
   using R = typename std::conditional<MIXED, float, double>::type;
   using RS = typename std::conditional<FORM == 2, float, double>::type;
-  __shared__ unsigned long long s_acc, s_rej, s_newton, s_fb, s_piv, s_redo;
+  __shared__ unsigned long long s_acc, s_rej, s_newton, s_fb, s_piv, s_redo, s_h2;
   __shared__ int s_min, s_max;
   if (threadIdx.x == 0) {
-    s_acc = s_rej = s_newton = s_fb = s_piv = s_redo = 0ull;
+    s_acc = s_rej = s_newton = s_fb = s_piv = s_redo = s_h2 = 0ull;
     s_min = INT_MAX;
     s_max = 0;
   }
   __syncthreads();
 
-  R w[sp::kNNZ];
+  WStore<R, BS, WS> wst;
+  const auto w = wst.slots();
   R qv[NS];  // u = df/dS_H, then q = W_d^-1 (g u)
   R dinv[NS];
   Rates<R> ko;  // rates and partials at the step's start (mixed: kept for jvp)
@@ -316,7 +344,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     if (!__syncthreads_or(p >= 0)) break;
     if (p < 0) continue;
     if (fresh) {
-      cnt = Cnt{0, 0, 0, 0, 0, 0, 0};
+      cnt = Cnt{0, 0, 0, 0, 0, 0, 0, 0};
       c = &a.dc[a.dig[p]];
       if constexpr (MIXED) cf = &a.dcf[a.dig[p]];
       pc_load(a.pc, a.ld, p, q);
@@ -617,6 +645,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
       tot.fallback += cnt.fallback;
       tot.pivot += cnt.pivot;
       tot.redo += cnt.redo;
+      tot.h2 += cnt.h2;
       min_steps = min(min_steps, nacc);
       max_steps = max(max_steps, nacc);
       p = -1;
@@ -629,6 +658,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
   atomicAdd(&s_fb, (unsigned long long)tot.fallback);
   atomicAdd(&s_piv, (unsigned long long)tot.pivot);
   atomicAdd(&s_redo, (unsigned long long)tot.redo);
+  atomicAdd(&s_h2, (unsigned long long)tot.h2);
   atomicMin(&s_min, min_steps);
   atomicMax(&s_max, max_steps);
   __syncthreads();
@@ -639,6 +669,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
     atomicAdd(&a.counters->newton_fallbacks, s_fb);
     atomicAdd(&a.counters->pivot_rejects, s_piv);
     atomicAdd(&a.counters->mlp_redo, s_redo);
+    atomicAdd(&a.counters->h2_iters, s_h2);
     if (s_min != INT_MAX) atomicMin(&a.counters->min_steps, s_min);
     atomicMax(&a.counters->max_steps, s_max);
   }
@@ -648,23 +679,30 @@ __global__ void __launch_bounds__(128, MINB) integrate_kernel(StepArgs a) {
 
 // Launch one kernel variant: persistent grid (resident blocks per SM x SMs,
 // capped by the particle count), queue head reset first.
-template <int FORM, int MINB>
+template <int FORM, int BS, int MINB, bool WS>
 cudaError_t launch_variant(const StepArgs& a, cudaStream_t s) {
+  using R = typename std::conditional<FORM == 1 || FORM == 2, float, double>::type;
+  constexpr size_t smem = integ::wstore_smem_bytes<R, BS, WS>();
   static int per_sm = -1, sms = 0;
   if (per_sm < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integ::integrate_kernel<FORM, MINB>, 128, 0);
+    if (smem > 0) {
+      cudaError_t e = cudaFuncSetAttribute(integ::integrate_kernel<FORM, BS, MINB, WS>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integ::integrate_kernel<FORM, BS, MINB, WS>,
+                                                  BS, smem);
     if (per_sm < 1) per_sm = 1;
   }
-  const int block = 128;
   int64_t blocks = (int64_t)sms * per_sm;
-  const int64_t need = (a.n + block - 1) / block;
+  const int64_t need = (a.n + BS - 1) / BS;
   if (need < blocks) blocks = need;
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  integ::integrate_kernel<FORM, MINB><<<(unsigned)blocks, block, 0, s>>>(a);
+  integ::integrate_kernel<FORM, BS, MINB, WS><<<(unsigned)blocks, BS, smem, s>>>(a);
   return cudaGetLastError();
 }
 

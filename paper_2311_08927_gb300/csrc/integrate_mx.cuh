@@ -50,7 +50,7 @@ __device__ __forceinline__ float solve_h2_f32(const H2Bal<float>& e, float guess
   for (int it = 0; it < 12; ++it) {
     float dE;
     const float E = h2_eval<float>(e, S, dE);
-    cnt.newton++;
+    cnt.h2++;
     if (!(fabsf(E) <= fabsf(prevE)) || !(dE < 0.0f)) break;
     const float dS = E * __frcp_rn(dE);
     const float Sn = S - dS;
@@ -103,7 +103,8 @@ __device__ __forceinline__ void rates_f32(const DigConstF& cf, const PartConstF&
 }
 
 // x <- W^-1 x with the factored W_d and both Sherman-Morrison levels.
-__device__ __forceinline__ void wsolve(const float* w, const float* dinv, const float* qv,
+template <class W>
+__device__ __forceinline__ void wsolve(W w, const float* dinv, const float* qv,
                                        const float* vr, float inv_delta, const float* p2,
                                        const float* zh, float inv_delta2, float* x) {
   sp::solve<float>(w, dinv, x);
@@ -116,18 +117,19 @@ __device__ __forceinline__ void wsolve(const float* w, const float* dinv, const 
   for (int i = 0; i < NS; ++i) x[i] = fmaf(s2, p2[i], x[i]);
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(128, MINB) integrate_mx_kernel(StepArgs a) {
-  __shared__ unsigned long long s_acc, s_rej, s_newton, s_fb, s_piv, s_redo;
+template <int BS, int MINB, bool WS>
+__global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
+  __shared__ unsigned long long s_acc, s_rej, s_newton, s_fb, s_piv, s_redo, s_h2;
   __shared__ int s_min, s_max;
   if (threadIdx.x == 0) {
-    s_acc = s_rej = s_newton = s_fb = s_piv = s_redo = 0ull;
+    s_acc = s_rej = s_newton = s_fb = s_piv = s_redo = s_h2 = 0ull;
     s_min = INT_MAX;
     s_max = 0;
   }
   __syncthreads();
 
-  float w[sp::kNNZ];
+  WStore<float, BS, WS> wst;
+  const auto w = wst.slots();
   float qv[NS];    // u = df/dS_H, then q = W_d^-1 (g u)
   float dinv[NS];
   float p2[NS], zh[NS];  // second level: W_1^-1 (g w) and dS_h2/dy
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_mx_kernel(StepArgs a) {
     if (!__syncthreads_or(p >= 0)) break;
     if (p < 0) continue;
     if (fresh) {
-      cnt = Cnt{0, 0, 0, 0, 0, 0, 0};
+      cnt = Cnt{0, 0, 0, 0, 0, 0, 0, 0};
       c = &a.dc[a.dig[p]];
       cf = &a.dcf[a.dig[p]];
       pc_load(a.pc, a.ld, p, q);
@@ -345,29 +347,26 @@ __global__ void __launch_bounds__(128, MINB) integrate_mx_kernel(StepArgs a) {
         for (int i = 0; i < NS; ++i) x0[i] = b[i].hi;
         wsolve(w, dinv, qv, vr, inv_delta, p2, zh, inv_delta2, x0);
         {
-          DF xp[NS], jx[NS], yg[NS];
+          DF xp[NS], jx[NS];
 #pragma unroll
-          for (int i = 0; i < NS; ++i) {
-            xp[i] = DF(x0[i]);
-            yg[i] = DF(ys[i]);
-          }
+          for (int i = 0; i < NS; ++i) xp[i] = DF(x0[i]);
           DF zx(0.0f);
 #pragma unroll
           for (int j = 0; j < NS; ++j)
-            if (j != iS_h2) zx = zx + DF(zh[j]) * xp[j];
+            if (j != iS_h2) zx = zx + zh[j] * xp[j];
           xp[iS_h2] = zx;
           DF sv(0.0f);
           {
             const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
 #pragma unroll
-            for (int k = 0; k < 8; ++k) sv = sv + DF(vr[k]) * xp[hc[k]];
+            for (int k = 0; k < 8; ++k) sv = sv + vr[k] * xp[hc[k]];
           }
-          jvp<float, DF>(*cf, yg, DF(Df), ko, xp, sv, jx);
+          jvp<float, DF, DigConstF, float>(*cf, ys, Df, ko, xp, sv, jx);
           jx[iS_h2] = DF(0.0f);
           float r[NS];
 #pragma unroll
           for (int i = 0; i < NS; ++i) {
-            const df ri = df_add(df_add_f(b[i], -x0[i]), df_mul(gd, jx[i].v));
+            const df ri = df_add(df_add_f(b[i], -x0[i]), df_mul(gd, jx[i].v()));
             r[i] = ri.hi + ri.lo;
           }
           wsolve(w, dinv, qv, vr, inv_delta, p2, zh, inv_delta2, r);
@@ -455,6 +454,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_mx_kernel(StepArgs a) {
       tot.fallback += cnt.fallback;
       tot.pivot += cnt.pivot;
       tot.redo += cnt.redo;
+      tot.h2 += cnt.h2;
       min_steps = min(min_steps, nacc);
       max_steps = max(max_steps, nacc);
       p = -1;
@@ -467,6 +467,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_mx_kernel(StepArgs a) {
   atomicAdd(&s_fb, (unsigned long long)tot.fallback);
   atomicAdd(&s_piv, (unsigned long long)tot.pivot);
   atomicAdd(&s_redo, (unsigned long long)tot.redo);
+  atomicAdd(&s_h2, (unsigned long long)tot.h2);
   atomicMin(&s_min, min_steps);
   atomicMax(&s_max, max_steps);
   __syncthreads();
@@ -477,6 +478,7 @@ __global__ void __launch_bounds__(128, MINB) integrate_mx_kernel(StepArgs a) {
     atomicAdd(&a.counters->newton_fallbacks, s_fb);
     atomicAdd(&a.counters->pivot_rejects, s_piv);
     atomicAdd(&a.counters->mlp_redo, s_redo);
+    atomicAdd(&a.counters->h2_iters, s_h2);
     if (s_min != INT_MAX) atomicMin(&a.counters->min_steps, s_min);
     atomicMax(&a.counters->max_steps, s_max);
   }
@@ -484,23 +486,29 @@ __global__ void __launch_bounds__(128, MINB) integrate_mx_kernel(StepArgs a) {
 
 }  // namespace integ
 
-template <int MINB>
+template <int BS, int MINB, bool WS>
 cudaError_t launch_variant_mx(const StepArgs& a, cudaStream_t s) {
+  constexpr size_t smem = integ::wstore_smem_bytes<float, BS, WS>();
   static int per_sm = -1, sms = 0;
   if (per_sm < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integ::integrate_mx_kernel<MINB>, 128, 0);
+    if (smem > 0) {
+      cudaError_t e = cudaFuncSetAttribute(integ::integrate_mx_kernel<BS, MINB, WS>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integ::integrate_mx_kernel<BS, MINB, WS>,
+                                                  BS, smem);
     if (per_sm < 1) per_sm = 1;
   }
-  const int block = 128;
   int64_t blocks = (int64_t)sms * per_sm;
-  const int64_t need = (a.n + block - 1) / block;
+  const int64_t need = (a.n + BS - 1) / BS;
   if (need < blocks) blocks = need;
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  integ::integrate_mx_kernel<MINB><<<(unsigned)blocks, block, 0, s>>>(a);
+  integ::integrate_mx_kernel<BS, MINB, WS><<<(unsigned)blocks, BS, smem, s>>>(a);
   return cudaGetLastError();
 }
 

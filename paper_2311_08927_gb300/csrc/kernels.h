@@ -15,6 +15,7 @@ enum : int { ST_NEWTON = 1, ST_STEPS = 2, ST_HMIN = 4, ST_NEG = 8, ST_NAN = 16 }
 struct DevCounters {
   unsigned long long accepted, rejected, newton_iters, newton_fallbacks, pivot_rejects, mlp_redo;
   int min_steps, max_steps;
+  unsigned long long h2_iters;  // Eq. 8 Newton iterations (S_h2 algebraic)
 };
 
 struct StepArgs {
@@ -69,9 +70,27 @@ struct HeadspaceArgs {
   int64_t n;
 };
 
-// Integrator kernel variants (min resident blocks per SM = variant + 2)
-constexpr int kNumVariants = 3;
+// Integrator kernel variants, chosen per context and kernel form by the
+// autotuner: threads per block, minimum resident blocks per SM (which sets
+// the register budget, 65536 / (threads x blocks) up to 255) and where the
+// factored matrix W_d lives (0: per-thread arrays, i.e. registers spilling to
+// local memory; 1: the thread's column of a shared-memory tile, 128 threads
+// for the float forms, 64 for the FP64 forms, 2 blocks per SM).
+constexpr int kNumVariants = 7;
 constexpr int kDefaultVariant = 0;
+struct KernelVariant {
+  int threads, min_blocks, w_shared;
+};
+// form: 0-4 (FP64 forms 0 and 3 keep W_d in double)
+constexpr KernelVariant kernel_variant(int form, int v) {
+  return v == 0   ? KernelVariant{128, 2, 0}
+         : v == 1 ? KernelVariant{128, 3, 0}
+         : v == 2 ? KernelVariant{128, 4, 0}
+         : v == 3 ? KernelVariant{64, 4, 0}
+         : v == 4 ? KernelVariant{256, 1, 0}
+         : v == 5 ? KernelVariant{32, 8, 0}
+                  : KernelVariant{(form == 0 || form == 3) ? 64 : 128, 2, 1};
+}
 cudaError_t launch_integrate(const StepArgs& a, int precision, int variant, cudaStream_t s);
 cudaError_t launch_advect(const AdvectArgs& a, cudaStream_t s);
 // MLP guesses for every particle of a context (see mlp.cu)

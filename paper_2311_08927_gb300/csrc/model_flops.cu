@@ -44,6 +44,28 @@ HD inline Fc fmax(Fc a, Fc b) { return Fc(a.v > b.v ? a.v : b.v); }
 HD inline Fc pow(Fc a, Fc b) { CNT return Fc(::pow(a.v, b.v)); }
 HD inline bool isfinite(Fc a) { return ::isfinite(a.v); }
 
+// Two-float accumulator with the operation counts of the kernel's DF type
+// (dfloat.cuh), in FP32 flops (an FMA counts as two): a sum of two
+// accumulators is TwoSum (6) plus the sum of the low parts (2); a product of
+// a float coefficient and an accumulator is TwoProd (a product and an FMA,
+// 3) plus an FMA for the low part (2).
+struct DFc {
+  double v;
+  HD DFc() : v(0) {}
+  HD DFc(double x) : v(x) {}
+};
+#ifdef __CUDA_ARCH__
+#define CNT_N(k)
+#else
+#define CNT_N(k) g_ops += (k);
+#endif
+HD inline DFc operator+(DFc a, DFc b) { CNT_N(8) return DFc(a.v + b.v); }
+HD inline DFc operator-(DFc a, DFc b) { CNT_N(8) return DFc(a.v - b.v); }
+HD inline DFc operator-(DFc a) { return DFc(-a.v); }
+HD inline DFc operator*(Fc c, DFc a) { CNT_N(5) return DFc(c.v * a.v); }
+HD inline DFc operator*(DFc a, Fc c) { CNT_N(5) return DFc(c.v * a.v); }
+HD inline DFc& operator+=(DFc& a, DFc b) { a = a + b; return a; }
+
 }  // namespace
 }  // namespace chad
 
@@ -62,6 +84,12 @@ using namespace chad;
 // out[10] Sherman-Morrison update of one solve
 // out[11] move of the acid-base reciprocals to a converged Newton root
 // out[12] scaling of the rate partials by -g (FP64 form's W formation)
+// With n >= 18, the mixed form with S_h2 algebraic (kernel form 4) also:
+// out[13] J x from the FP32 rate partials in two-float arithmetic (FP32 flops)
+// out[14] coefficients of the Eq. 8 balance (h2_coeffs)
+// out[15] one Eq. 8 Newton iteration (h2_eval + update)
+// out[16] FP32 work of one attempt besides rates, LU, solves, J x and Eq. 8
+// out[17] FP64 work of one attempt besides the Eq. 7 Newton iterations
 extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   if (!out || n < 13) return CHAD_E_INVALID;
   DigConst c;
@@ -142,5 +170,46 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   out[7] = (int64_t)NS * 18;
   // s = v^T x (15), b - x + g jx (3/elt), x += dx (1/elt)
   out[8] = 15 + (int64_t)NS * 4;
+  if (n >= 18) {
+    {
+      DFc x[NS], jx[NS];
+      Fc ys[NS];
+      for (int i = 0; i < NS; ++i) { x[i] = DFc(1.0); ys[i] = Fc(1.0); }
+      g_ops = 0;
+      jvp<Fc, DFc, DigConst, Fc>(c, ys, Fc(0.1), o, x, DFc(1.0), jx);
+      out[13] = g_ops;
+    }
+    {
+      H2Bal<Fc> e;
+      g_ops = 0;
+      h2_coeffs<Fc>(c, q, y, Fc(0.1), ab, e);
+      out[14] = g_ops;
+      e.Kfa = e.Kc4 = e.Kpro = e.Kh2 = Fc(1.0);
+      Fc dE;
+      g_ops = 0;
+      h2_eval<Fc>(e, Fc(1e-6), dE);
+      out[15] = g_ops + 2;  // + the Newton update S - E/E'
+    }
+    // FP32 flops of one form-4 attempt outside the counted blocks, from the
+    // kernel source (two-float operations at their FP32 cost: TwoSum-based
+    // sum 11, product 10, sum with a float 10):
+    //   S_h2 surgery of J_d: zh (29 + 3 x 8), p2 (29), its reciprocal (1)   83
+    //   q scaling (29), second-level dot and denominator (58 + 3)           90
+    //   per stage (x3): two wsolve level-2 updates (2 x (58 + 1 + 58)),
+    //     x'_h2 = zh^T x (28 x 13), v^T x (8 x 13), residual b - x + g J x
+    //     (29 x 32), x = x0 + dx (29 x 6)                         234 + 468 + 928 + 174
+    //   stage right-hand sides: stage 1 (29 x 11), stage 2 (29 x 63),
+    //     k2 (29 x 11), stage-1 float point (29 x 2)                    29 x 87
+    //   error norm: k1 - 2 k2 + k3 (33), hi + lo (1), scale (5)         29 x 39
+    out[16] = 83 + 90 + 3 * (234 + 28 * 13 + 8 * 13 + (int64_t)NS * 32 + (int64_t)NS * 6) +
+              (int64_t)NS * 87 + (int64_t)NS * 39;
+    // FP64 flops of one form-4 attempt besides the Eq. 7 iterations (and the
+    // three root moves, counted with them): evaluation points y + (h/2) k1 in
+    // the 8 states of Eq. 7 and y + h k2 in all 29 (two FMAs each), the two
+    // tangent guesses of S_H (8 differences and 8 FMAs each, 24 counted),
+    // the tangent dS_H/dy (9 products and a reciprocal, 20 counted), g and
+    // h/2 (2)
+    out[17] = 8 * 4 + (int64_t)NS * 4 + 2 * 24 + 20 + 2;
+  }
   return CHAD_OK;
 }

@@ -57,9 +57,10 @@ struct Idx {
 // diagonal slots in elimination order
 constexpr int kDiag[NS] = {0, 2, 4, 5, 6, 8, 10, 12, 19, 24, 28, 31, 39, 51, 67, 73, 76, 82, 86, 90, 95, 106, 119, 137, 146, 157, 178, 196, 202};
 
-// W_d = I - g J_d in place over the slots (fill slots hold zero in J_d)
-template <class R>
-CHAD_HD void form_w(R* w, R g) {
+// W_d = I - g J_d in place over the slots (fill slots hold zero in J_d).
+// W: the slot storage, a pointer or any accessor whose w[s] is a reference.
+template <class R, class W>
+CHAD_HD void form_w(W w, R g) {
 #pragma unroll
   for (int s = 0; s < kNNZ; ++s) w[s] = -g * w[s];
   w[0] += R(1);
@@ -94,8 +95,8 @@ CHAD_HD void form_w(R* w, R g) {
 }
 
 // In-place LU; returns false if a pivot fails the threshold test.
-template <class R>
-CHAD_HD bool factor(R* w, R* dinv) {
+template <class R, class W>
+CHAD_HD bool factor(W w, R* dinv) {
   using P = PivTest<R>;
   bool ok = true;
   {  // pivot 0: state 11 (S_I), 0 rows x 1 cols
@@ -739,8 +740,8 @@ CHAD_HD bool factor(R* w, R* dinv) {
 }
 
 // Solve W x = b in place (b indexed by state).
-template <class R>
-CHAD_HD void solve(const R* w, const R* dinv, R* b) {
+template <class R, class W>
+CHAD_HD void solve(W w, const R* dinv, R* b) {
   R z0 = b[11];
   R z1 = b[23];
   R z2 = b[24];

@@ -37,7 +37,8 @@ class TrainedMLP:
 
 
 def sample_states(pop: I.Population, intervals: int, precision=CH.PREC_MIXED, skip: int = 1,
-                  max_samples: int | None = None, stream=None, initial: bool = True):
+                  max_samples: int | None = None, stream=None, initial: bool = True,
+                  h2_algebraic: bool = False):
     """Run the integrator on `pop` and collect (y, T, S_H, h) at every interval
     end after the first `skip` ones.  With `initial`, the loaded states are
     sampled too (a cold load is where the network is consulted): a first
@@ -46,7 +47,7 @@ def sample_states(pop: I.Population, intervals: int, precision=CH.PREC_MIXED, sk
     the first full interval.  Returns device tensors y [29][M], T [M],
     S_H [M], h [M]."""
     import torch
-    sim = CH.Simulator(pop, precision=precision, stream=stream)
+    sim = CH.Simulator(pop, precision=precision, stream=stream, h2_algebraic=h2_algebraic)
     sim.load()
     n = pop.n
     T = torch.from_numpy(np.ascontiguousarray(pop.T)).cuda()

@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_param_layout(L):
-    assert L.chad_abi_version() == 2
+    assert L.chad_abi_version() == 3
     assert CH.param_names() == I.PARAM_NAMES
     assert L.chad_param_name(-1) is None and L.chad_param_name(len(I.PARAM_NAMES)) is None
 

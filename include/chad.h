@@ -380,6 +380,50 @@ chad_status chad_mlp_grad(const uint16_t* X, const float* Y, int64_t n, const fl
                           float* grad, float* loss, void* scratch, size_t scratch_bytes,
                           void* cuda_stream);
 
+/* As chad_mlp_grad, without waiting: a tensor-core wait that timed out is
+   recorded on the device and reported by the next chad_mlp_wait.  A training
+   loop can then queue an epoch of batches (chad_mlp_gather, this,
+   chad_mlp_adam) and wait once. */
+chad_status chad_mlp_grad_async(const uint16_t* X, const float* Y, int64_t n,
+                                const float* params, float* grad, float* loss, void* scratch,
+                                size_t scratch_bytes, void* cuda_stream);
+
+/* Wait for the stream; CHAD_E_CUDA if a tensor-core wait of an MLP kernel
+   timed out since the last check (the record is then cleared). */
+chad_status chad_mlp_wait(void* cuda_stream);
+
+/* Bytes of scratch chad_mlp_feature_norm and chad_mlp_targets need. */
+size_t chad_mlp_prep_scratch_bytes(void);
+
+/* Standardisation of the MLP features over n >= 2 samples (device
+   pointers): y [29][ld], T [n] -> norm [2][32]: the mean and 1 / sample
+   standard deviation (floored at 1e-6) of log10 max(y_i, 1e-20) for the 29
+   states and of T/100; the padding features get mean 0, 1/std 1.  Sums in
+   FP64, reduced in a fixed order (deterministic).  Asynchronous. */
+chad_status chad_mlp_feature_norm(const double* y, int64_t ld, const double* T, int64_t n,
+                                  float* norm, void* scratch, size_t scratch_bytes,
+                                  void* cuda_stream);
+
+/* Training targets of n >= 2 samples (device pointers): out_norm [4] =
+   mean of log10 S_H, mean of log10 h, their sample standard deviations
+   (floored at 1e-6); Y [n][2] = the standardised targets.  Asynchronous. */
+chad_status chad_mlp_targets(const double* S_H, const double* h, int64_t n, float* Y,
+                             float* out_norm, void* scratch, size_t scratch_bytes,
+                             void* cuda_stream);
+
+/* One shuffled mini-batch (device pointers): rows k = 0 .. count-1 are
+   sample P_s(offset + P_e(start + k)) of X [M][32] BF16 (16-byte aligned)
+   and Y [M][2], written to Xb [count][32] and Yb [count][2].  P_s is a
+   keyed permutation of [0, M) (split_key): its positions [offset, offset +
+   n_part) form one split (training, validation, test); P_e a keyed
+   permutation of [0, n_part) (epoch_key), so each epoch visits the split in
+   a new order without a stored index array.  The permutations are
+   four-round Feistel networks walked to the range (bijections).
+   Requires offset + n_part <= M and start + count <= n_part.  Asynchronous. */
+chad_status chad_mlp_gather(const uint16_t* X, const float* Y, int64_t M, uint64_t split_key,
+                            int64_t offset, int64_t n_part, uint64_t epoch_key, int64_t start,
+                            int64_t count, uint16_t* Xb, float* Yb, void* cuda_stream);
+
 /* One Adam step (Kingma & Ba 2015, bias-corrected, step t >= 1) on the FP32
    master parameters: params, grad, m, v [NPARAM] device.  Asynchronous. */
 chad_status chad_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t t,
@@ -444,7 +488,8 @@ chad_status chad_probe_alu_peak(int fp64, double* tflops);
    the Eq. 8 balance coefficients, out[15] one Eq. 8 Newton iteration,
    out[16] the rest of one attempt's FP32 work (two-float stage arithmetic,
    residuals, second Sherman-Morrison level), out[17] the rest of its FP64
-   work (evaluation points, S_H guesses). */
+   work (evaluation points, S_H guesses); with n >= 19 out[18] the rates
+   with their partials alone. */
 chad_status chad_flop_counts(int64_t* out, int n);
 
 /* The integrator's device arithmetic helpers applied to x [n] (host

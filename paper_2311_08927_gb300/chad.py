@@ -114,6 +114,22 @@ def lib():
             L.chad_mlp_grad.restype = C.c_int
             L.chad_mlp_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+            L.chad_mlp_grad_async.restype = C.c_int
+            L.chad_mlp_grad_async.argtypes = L.chad_mlp_grad.argtypes
+            L.chad_mlp_wait.restype = C.c_int
+            L.chad_mlp_wait.argtypes = [C.c_void_p]
+            L.chad_mlp_prep_scratch_bytes.restype = C.c_size_t
+            L.chad_mlp_prep_scratch_bytes.argtypes = []
+            L.chad_mlp_feature_norm.restype = C.c_int
+            L.chad_mlp_feature_norm.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                                C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+            L.chad_mlp_targets.restype = C.c_int
+            L.chad_mlp_targets.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+            L.chad_mlp_gather.restype = C.c_int
+            L.chad_mlp_gather.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_int64,
+                                          C.c_int64, C.c_uint64, C.c_int64, C.c_int64, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]
             L.chad_mlp_adam.restype = C.c_int
             L.chad_mlp_adam.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                         C.c_float, C.c_float, C.c_float, C.c_float, C.c_void_p]
@@ -183,7 +199,9 @@ def exported_symbols() -> list[str]:
             "chad_get_interval", "chad_set_interval", "chad_debug_bounds",
             "chad_headspace_mean_noalloc", "chad_set_mlp", "chad_mlp_features",
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam",
-            "chad_kernel_variant"]
+            "chad_kernel_variant", "chad_mlp_grad_async", "chad_mlp_wait",
+            "chad_mlp_prep_scratch_bytes", "chad_mlp_feature_norm", "chad_mlp_targets",
+            "chad_mlp_gather"]
 
 MLP_IN, MLP_HID, MLP_OUT = 32, 64, 2
 MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT
@@ -225,6 +243,43 @@ def chad_mlp_grad(X, Y, params, grad, loss, scratch, stream=None):
                                     stream))
 
 
+def chad_mlp_grad_async(X, Y, params, grad, loss, scratch, stream=None):
+    L = lib()
+    _check(L, None, L.chad_mlp_grad_async(_dev(X), _dev(Y), X.shape[0], _dev(params), _dev(grad),
+                                          _dev(loss), _dev(scratch),
+                                          scratch.numel() * scratch.element_size(), stream))
+
+
+def chad_mlp_wait(stream=None):
+    L = lib()
+    _check(L, None, L.chad_mlp_wait(stream))
+
+
+def mlp_prep_scratch_bytes():
+    return lib().chad_mlp_prep_scratch_bytes()
+
+
+def chad_mlp_feature_norm(y, T, norm, scratch, stream=None):
+    L = lib()
+    _check(L, None, L.chad_mlp_feature_norm(_dev(y), y.shape[1], _dev(T), T.shape[0], _dev(norm),
+                                            _dev(scratch), scratch.numel() * scratch.element_size(),
+                                            stream))
+
+
+def chad_mlp_targets(S_H, h, Y, out_norm, scratch, stream=None):
+    L = lib()
+    _check(L, None, L.chad_mlp_targets(_dev(S_H), _dev(h), S_H.shape[0], _dev(Y), _dev(out_norm),
+                                       _dev(scratch), scratch.numel() * scratch.element_size(),
+                                       stream))
+
+
+def chad_mlp_gather(X, Y, split_key, offset, n_part, epoch_key, start, count, Xb, Yb, stream=None):
+    L = lib()
+    _check(L, None, L.chad_mlp_gather(_dev(X), _dev(Y), X.shape[0], int(split_key), int(offset),
+                                      int(n_part), int(epoch_key), int(start), int(count),
+                                      _dev(Xb), _dev(Yb), stream))
+
+
 def mlp_grad_scratch_bytes(n):
     return lib().chad_mlp_grad_scratch_bytes(int(n))
 
@@ -237,7 +292,7 @@ def chad_mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, s
 
 FLOP_KEYS = ["rates_f", "rates_fj", "charge_E", "form_w", "factor", "solve", "jx", "stage",
              "refine", "sm_setup", "sm_update", "sh_final", "scale_j", "jx_twofloat",
-             "h2_coeffs", "h2_iter", "mx_fp32_extra", "mx_fp64_extra"]
+             "h2_coeffs", "h2_iter", "mx_fp32_extra", "mx_fp64_extra", "rates_partials"]
 
 
 def flop_counts() -> dict:
@@ -254,13 +309,14 @@ def attempt_flops_h2_mixed() -> dict:
     (FP64) and Eq. 8 (FP32), which are counted per iteration: FP32 rates with
     J_d and u at the step's start and rates at the two stage points, the
     sparse LU, two sparse solves for q and p2 and two per stage, the
-    Sherman-Morrison updates, three Eq. 8 coefficient sets, the two-float
-    J x of three refinement residuals and the two-float stage arithmetic;
+    Sherman-Morrison updates, three Eq. 8 coefficient sets, the rate
+    partials recomputed for each of the three refinement residuals and
+    their two-float J x, and the two-float stage arithmetic;
     FP64 for the evaluation points and the S_H guesses."""
     f = flop_counts()
     f32 = (f["rates_fj"] + 2 * f["rates_f"] + f["form_w"] + f["factor"] + 8 * f["solve"] +
            f["sm_setup"] + 7 * f["sm_update"] + 3 * f["h2_coeffs"] + 3 * f["jx_twofloat"] +
-           f["mx_fp32_extra"])
+           3 * f["rates_partials"] + f["mx_fp32_extra"])
     return {"fp64": f["mx_fp64_extra"], "fp32": f32, "fp32_per_h2_iter": f["h2_iter"]}
 
 

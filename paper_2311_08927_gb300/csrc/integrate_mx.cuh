@@ -7,9 +7,9 @@
 //   * FP32: S_h2 from its mass balance (Eq. 8, the paper's DAE form), by
 //     Newton on the coefficients that the FP32 rates already hold;
 //   * two-float (about 48 bits, on the FP32 pipe): the stage right-hand
-//     sides, the stage vectors k1, k2, k3, the refinement residual
-//     r = b - W x of every solve (W x from the FP32 rate partials in
-//     two-float arithmetic) and the error combination k1 - 2 k2 + k3;
+//     sides, the refinement residual r = b - W x of every solve (W x from
+//     the FP32 rate partials in two-float arithmetic) and the error
+//     combination k1 - 2 k2 + k3 of the FP32 stage vectors (exact);
 //   * FP64: the charge-balance Newton for S_H (Eq. 7) at every rate
 //     evaluation and the state y, y + h/2 k1 and y + h k2.
 // One refinement step per solve: x0 = W^-1 b in FP32, x = x0 + W^-1 r.
@@ -133,11 +133,10 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
   float qv[NS];    // u = df/dS_H, then q = W_d^-1 (g u)
   float dinv[NS];
   float p2[NS], zh[NS];  // second level: W_1^-1 (g w) and dS_h2/dy
-  Rates<float> ko;       // rates and partials at the step's start
   double y[NS], y1[NS];  // state; evaluation point (after stage 2: the new state)
   float ys[NS], y1s[NS]; // float copies (rates, error scale)
-  float F0[NS], F1[NS];  // FP32 rates at y and at the stage-1 point
-  df k1[NS], k2[NS], xs[NS];
+  float F0[NS];           // FP32 rates at y; after stage 1 e32 F1 + 2 F0
+  float k1[NS], k2[NS], k3[NS];  // stage vectors (refined solutions, FP32)
   const double Tend = a.dt_days;
   const bool fixed = a.fixed_n > 0;
   Cnt tot{0, 0, 0, 0, 0, 0, 0};
@@ -220,10 +219,15 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
     // roots, rates, J_d and u at y (all FP32 but the Eq. 7 Newton)
     AcidBase ab0;
     roots(*c, *cf, q, qf, y, ys, Df, SHg, SH2g, a.max_newton, cnt, ab0);
-    rates<float, true>(*cf, qf, ys, ab0, ko);
-    balances<float>(*cf, ys, Df, ko, F0);
-    F0[iS_h2] = 0.0f;
-    jacobian<sp::Idx, float>(*cf, qf, ys, Df, ab0, ko, w, qv);
+    {
+      // the rate partials are recomputed for each refinement residual
+      // (from ys and ab0) rather than kept across the stages
+      Rates<float> ko;
+      rates<float, true>(*cf, qf, ys, ab0, ko);
+      balances<float>(*cf, ys, Df, ko, F0);
+      F0[iS_h2] = 0.0f;
+      jacobian<sp::Idx, float>(*cf, qf, ys, Df, ab0, ko, w, qv);
+    }
     const double SH0 = SHg;
     const float SH20 = SH2g;
     double vsh[8];
@@ -284,7 +288,12 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
       //   0: b = F0                                  -> k1 = x
       //   1: F1 = f(y + h/2 k1), b = F1 - k1         -> k2 = x + k1
       //   2: F2 = f(y + h k2),   b = F2 - e32 (k2 - F1) - 2 (k1 - F0)
-      //                                              -> k3 = x (in xs)
+      //                                              -> k3 = x
+      // The right-hand sides are formed in two-float from the FP32 rates and
+      // stage vectors; the refined solution x0 + W^-1 r is kept in FP32 (the
+      // stage rates it solves for are FP32).  After stage 1 the rates are
+      // needed only as C = e32 F1 + 2 F0 (kept in F0's place), so that
+      // b2 = F2 - e32 k2 - 2 k1 + C.
       const df e32 = df_of_double(kRB_e32);
 #pragma unroll 1
       for (int st = 0; st < 3; ++st) {
@@ -304,14 +313,14 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
               const int i = hc[k];
-              y1[i] = fma(hs, f64(k1[i].lo), fma(hs, f64(k1[i].hi), y[i]));
+              y1[i] = fma(hs, f64(k1[i]), y[i]);
             }
 #pragma unroll
-            for (int i = 0; i < NS; ++i) y1s[i] = fmaf(hsf, k1[i].hi, ys[i]);
+            for (int i = 0; i < NS; ++i) y1s[i] = fmaf(hsf, k1[i], ys[i]);
           } else {
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
-              y1[i] = fma(hh, f64(k2[i].lo), fma(hh, f64(k2[i].hi), y[i]));
+              y1[i] = fma(hh, f64(k2[i]), y[i]);
               y1s[i] = f32(y1[i]);
             }
           }
@@ -329,15 +338,15 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
           if (st == 1) {
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
-              F1[i] = Fs[i];
-              b[i] = df_sub(df_of(Fs[i]), k1[i]);
+              b[i] = two_sum(Fs[i], -k1[i]);
+              const df c1 = df_mul_f(e32, Fs[i]);
+              F0[i] = c1.hi + fmaf(2.0f, F0[i], c1.lo);  // C = e32 F1 + 2 F0
             }
           } else {
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
-              const df t1 = df_mul(e32, df_add_f(k2[i], -F1[i]));
-              const df t2 = df_add_f(k1[i], -F0[i]);
-              b[i] = df_sub(df_sub(df_of(Fs[i]), t1), df_add(t2, t2));
+              const df t1 = df_add_f(df_mul_f(e32, k2[i]), 2.0f * k1[i]);
+              b[i] = df_add_f(df_sub(df_of(Fs[i]), t1), F0[i]);
             }
           }
         }
@@ -346,6 +355,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
 #pragma unroll
         for (int i = 0; i < NS; ++i) x0[i] = b[i].hi;
         wsolve(w, dinv, qv, vr, inv_delta, p2, zh, inv_delta2, x0);
+        float xs[NS];
         {
           DF xp[NS], jx[NS];
 #pragma unroll
@@ -361,6 +371,8 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) sv = sv + vr[k] * xp[hc[k]];
           }
+          Rates<float> ko;
+          rates<float, true>(*cf, qf, ys, ab0, ko);
           jvp<float, DF, DigConstF, float>(*cf, ys, Df, ko, xp, sv, jx);
           jx[iS_h2] = DF(0.0f);
           float r[NS];
@@ -371,23 +383,27 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
           }
           wsolve(w, dinv, qv, vr, inv_delta, p2, zh, inv_delta2, r);
 #pragma unroll
-          for (int i = 0; i < NS; ++i) xs[i] = two_sum(x0[i], r[i]);
+          for (int i = 0; i < NS; ++i) xs[i] = x0[i] + r[i];
         }
         if (st == 0) {
 #pragma unroll
           for (int i = 0; i < NS; ++i) k1[i] = xs[i];
         } else if (st == 1) {
 #pragma unroll
-          for (int i = 0; i < NS; ++i) k2[i] = df_add(xs[i], k1[i]);
+          for (int i = 0; i < NS; ++i) k2[i] = xs[i] + k1[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < NS; ++i) k3[i] = xs[i];
         }
       }
       // scaled error norm max_i |h/6 (k1 - 2 k2 + k3)_i| / (atol_i + rtol
-      // max(|y_i|, |y1_i|)): the combination in two-float, the rest in FP32
+      // max(|y_i|, |y1_i|)): the combination of the FP32 stage vectors exact
+      // in two-float, the rest in FP32
       float nf = 0.0f;
       const float rtol = f32(a.rtol);
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
-        const df ed = df_add(df_sub(k1[i], df_add(k2[i], k2[i])), xs[i]);
+        const df ed = df_add_f(two_sum(k1[i], -2.0f * k2[i]), k3[i]);
         const float e = ed.hi + ed.lo;
         const float ym = fmaxf(fabsf(ys[i]), fabsf(y1s[i]));
         const float sc = fmaxf(fmaf(rtol, ym, f32(a.atol[i])), 1e-30f);

@@ -12,6 +12,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "chad.h"
@@ -683,6 +684,177 @@ __global__ void adam_kernel(float* P, const float* g, float* m, float* v, float 
   P[k] -= lr * (mk * c1) / (sqrtf(vk * c2) + eps);
 }
 
+// ---------------------------------------------------------------------------
+// Training data preparation on the device: feature and target statistics,
+// standardised targets and shuffled mini-batches.
+namespace prep {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 1024;
+constexpr int kNF = NS + 1;  // 29 log-scaled states and T/100
+
+// Feature f of sample p, as the features kernel forms it before standardising.
+__device__ __forceinline__ float raw_feature(const double* y, int64_t ld, const double* T,
+                                             int64_t p, int f) {
+  if (f < NS) return log10f(fmaxf((float)y[(int64_t)f * ld + p], kLogFloor));
+  return (float)T[p] * 0.01f;
+}
+
+// Block partials of sum and sum of squares (FP64) of every feature over a
+// grid-stride share of the samples: part[b][0][f], part[b][1][f].
+__global__ void __launch_bounds__(kThreads) feature_partials(const double* y, int64_t ld,
+                                                             const double* T, int64_t n,
+                                                             double* part) {
+  __shared__ double s1[kThreads], s2[kThreads];
+  for (int f = 0; f < kNF; ++f) {
+    double a = 0.0, b = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * kThreads) {
+      const double v = raw_feature(y, ld, T, p, f);
+      a += v;
+      b += v * v;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        s1[threadIdx.x] += s1[threadIdx.x + w];
+        s2[threadIdx.x] += s2[threadIdx.x + w];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      part[((int64_t)blockIdx.x * 2 + 0) * 32 + f] = s1[0];
+      part[((int64_t)blockIdx.x * 2 + 1) * 32 + f] = s2[0];
+    }
+    __syncthreads();
+  }
+}
+
+// Mean and 1/std (sample standard deviation, floored at 1e-6) of k series
+// from nb block partials in block order: norm[f] = mean, norm[stride + f] = 1/std.
+__global__ void moments_finish(const double* part, int nb, int k, int pstride, int64_t n,
+                               float* norm, int stride, int scale_std) {
+  const int f = threadIdx.x;
+  if (f >= k) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    a += part[((int64_t)i * 2 + 0) * pstride + f];
+    b += part[((int64_t)i * 2 + 1) * pstride + f];
+  }
+  const double mu = a / (double)n;
+  const double var = n > 1 ? fmax(b - a * mu, 0.0) / (double)(n - 1) : 0.0;
+  const double sd = fmax(sqrt(var), 1e-6);
+  norm[f] = (float)mu;
+  norm[stride + f] = scale_std ? (float)sd : (float)(1.0 / sd);
+}
+
+// Partials of the two targets log10 S_H and log10 h: part[b][0][k], part[b][1][k].
+__global__ void __launch_bounds__(kThreads) target_partials(const double* SH, const double* h,
+                                                            int64_t n, double* part) {
+  __shared__ double s[4][kThreads];
+  double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * kThreads) {
+    const double t0 = log10(SH[p]), t1 = log10(h[p]);
+    a0 += t0;
+    a1 += t1;
+    b0 += t0 * t0;
+    b1 += t1 * t1;
+  }
+  s[0][threadIdx.x] = a0;
+  s[1][threadIdx.x] = a1;
+  s[2][threadIdx.x] = b0;
+  s[3][threadIdx.x] = b1;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int j = 0; j < 4; ++j) s[j][threadIdx.x] += s[j][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[((int64_t)blockIdx.x * 2 + 0) * 2 + 0] = s[0][0];
+    part[((int64_t)blockIdx.x * 2 + 0) * 2 + 1] = s[1][0];
+    part[((int64_t)blockIdx.x * 2 + 1) * 2 + 0] = s[2][0];
+    part[((int64_t)blockIdx.x * 2 + 1) * 2 + 1] = s[3][0];
+  }
+}
+
+// Y[p] = (log10 S_H - mean, log10 h - mean) / std with out_norm = [means, stds].
+__global__ void target_write(const double* SH, const double* h, int64_t n, const float* on,
+                             float* Y) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  Y[2 * p + 0] = ((float)log10(SH[p]) - on[0]) / on[2];
+  Y[2 * p + 1] = ((float)log10(h[p]) - on[1]) / on[3];
+}
+
+// A keyed bijection of [0, n): a balanced four-round Feistel network on the
+// smallest even number of bits b with 2^b >= n, walked along its cycle
+// until the image falls inside [0, n) (at most 2^b - n + 1 steps; 2^b < 4n,
+// so a few in expectation).  Round function: Wellons' "lowbias32" integer
+// hash of the right half, the key and the round.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ uint64_t feistel(uint64_t x, int half, uint64_t key) {
+  const uint64_t mask = (1ull << half) - 1ull;
+  uint64_t L = x >> half, R = x & mask;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const uint32_t k = (uint32_t)(key >> (16 * r)) ^ (uint32_t)(key >> 32) * 0x9e3779b9u;
+    const uint64_t F = ((uint64_t)mix32((uint32_t)R ^ k ^ (uint32_t)r * 0x85ebca6bu) |
+                        ((uint64_t)mix32((uint32_t)(R >> 32) ^ k) << 32)) & mask;
+    const uint64_t t = L ^ F;
+    L = R;
+    R = t;
+  }
+  return (L << half) | R;
+}
+__device__ __forceinline__ int64_t permute(int64_t i, int64_t n, int half, uint64_t key) {
+  uint64_t y = (uint64_t)i;
+  do {
+    y = feistel(y, half, key);
+  } while (y >= (uint64_t)n);
+  return (int64_t)y;
+}
+
+// Mini-batch rows k = 0 .. count-1: sample P_split(off + P_epoch(start + k))
+// of X [M][32] BF16 and Y [M][2] -> Xb [count][32], Yb [count][2].  P_split
+// permutes [0, M) (its first n_tr positions are the training split, the next
+// ones validation and test), P_epoch permutes [0, n_part) of one split.
+__global__ void gather(const uint4* X, const float2* Y, int64_t M, int half_m, uint64_t key_m,
+                       int64_t off, int64_t n_part, int half_p, uint64_t key_p, int64_t start,
+                       int64_t count, uint4* Xb, float2* Yb) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int64_t j = permute(start + k, n_part, half_p, key_p);
+  const int64_t g = permute(off + j, M, half_m, key_m);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Xb[k * 4 + q] = X[g * 4 + q];
+  Yb[k] = Y[g];
+}
+
+__global__ void fill_ones(float* p, int n) {
+  if ((int)threadIdx.x < n) p[threadIdx.x] = 1.0f;
+}
+
+// half the even bit count of the Feistel domain of [0, n)
+inline int feistel_half(int64_t n) {
+  int b = 0;
+  while (b < 62 && (1ll << b) < n) ++b;
+  b += b & 1;
+  return b < 2 ? 1 : b / 2;
+}
+
+}  // namespace prep
+
 // One device int per GPU for the tensor-core kernels' wait timeouts.
 int* err_flag() {
   static int* flags[64] = {};
@@ -809,6 +981,95 @@ chad_status chad_mlp_grad(const uint16_t* X, const float* Y, int64_t n, const fl
       reinterpret_cast<const __nv_bfloat16*>(X), Y, n, 1.0f / (float)n, params, partial, lpart, err);
   mlp::reduce_kernel<<<(mlp::NPARAM + 255) / 256, 256, 0, s>>>(partial, (int)nb, grad, lpart, loss);
   return mlp::check_err(err, s);
+}
+
+chad_status chad_mlp_grad_async(const uint16_t* X, const float* Y, int64_t n, const float* params,
+                                float* grad, float* loss, void* scratch, size_t scratch_bytes,
+                                void* stream) {
+  if (n <= 0 || !X || !Y || !params || !grad || !scratch) return CHAD_E_INVALID;
+  if (scratch_bytes < chad_mlp_grad_scratch_bytes(n)) return CHAD_E_INVALID;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) return CHAD_E_INVALID;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(mlp::tc::gr::grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)mlp::tc::gr::smem_bytes()) != cudaSuccess)
+      return CHAD_E_CUDA;
+    attr = true;
+  }
+  int* err = mlp::err_flag();
+  if (!err) return CHAD_E_NOMEM;
+  int64_t nb = (n + mlp::tc::TILE - 1) / mlp::tc::TILE;
+  if (nb > mlp::sm_count()) nb = mlp::sm_count();
+  float* partial = static_cast<float*>(scratch);
+  float* lpart = partial + nb * mlp::NPARAM;
+  cudaStream_t s = (cudaStream_t)stream;
+  mlp::tc::gr::grad_kernel<<<(unsigned)nb, mlp::tc::gr::kThreads, mlp::tc::gr::smem_bytes(), s>>>(
+      reinterpret_cast<const __nv_bfloat16*>(X), Y, n, 1.0f / (float)n, params, partial, lpart, err);
+  mlp::reduce_kernel<<<(mlp::NPARAM + 255) / 256, 256, 0, s>>>(partial, (int)nb, grad, lpart, loss);
+  return cudaGetLastError() == cudaSuccess ? CHAD_OK : CHAD_E_CUDA;
+}
+
+chad_status chad_mlp_wait(void* stream) {
+  int* err = mlp::err_flag();
+  if (!err) return CHAD_E_NOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  const chad_status st = mlp::check_err(err, s);
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return CHAD_E_CUDA;
+  return st;
+}
+
+chad_status chad_mlp_feature_norm(const double* y, int64_t ld, const double* T, int64_t n,
+                                  float* norm, void* scratch, size_t scratch_bytes,
+                                  void* stream) {
+  if (n < 2 || !y || !T || !norm || !scratch || ld < n) return CHAD_E_INVALID;
+  if (scratch_bytes < chad_mlp_prep_scratch_bytes()) return CHAD_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)std::min<int64_t>(mlp::prep::kMaxBlocks, (n + mlp::prep::kThreads - 1) /
+                                                                   mlp::prep::kThreads);
+  double* part = static_cast<double*>(scratch);
+  mlp::prep::feature_partials<<<nb, mlp::prep::kThreads, 0, s>>>(y, ld, T, n, part);
+  // padding features: mean 0, 1/std 1
+  mlp::prep::moments_finish<<<1, 32, 0, s>>>(part, nb, mlp::prep::kNF, 32, n, norm, mlp::IN, 0);
+  if (cudaMemsetAsync(norm + mlp::prep::kNF, 0, sizeof(float) * (mlp::IN - mlp::prep::kNF), s) !=
+      cudaSuccess)
+    return CHAD_E_CUDA;
+  mlp::prep::fill_ones<<<1, 32, 0, s>>>(norm + mlp::IN + mlp::prep::kNF, mlp::IN - mlp::prep::kNF);
+  return cudaGetLastError() == cudaSuccess ? CHAD_OK : CHAD_E_CUDA;
+}
+
+chad_status chad_mlp_targets(const double* SH, const double* h, int64_t n, float* Y,
+                             float* out_norm, void* scratch, size_t scratch_bytes, void* stream) {
+  if (n < 2 || !SH || !h || !Y || !out_norm || !scratch) return CHAD_E_INVALID;
+  if (scratch_bytes < chad_mlp_prep_scratch_bytes()) return CHAD_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)std::min<int64_t>(mlp::prep::kMaxBlocks, (n + mlp::prep::kThreads - 1) /
+                                                                   mlp::prep::kThreads);
+  double* part = static_cast<double*>(scratch);
+  mlp::prep::target_partials<<<nb, mlp::prep::kThreads, 0, s>>>(SH, h, n, part);
+  mlp::prep::moments_finish<<<1, 32, 0, s>>>(part, nb, 2, 2, n, out_norm, 2, 1);
+  mlp::prep::target_write<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(SH, h, n, out_norm, Y);
+  return cudaGetLastError() == cudaSuccess ? CHAD_OK : CHAD_E_CUDA;
+}
+
+size_t chad_mlp_prep_scratch_bytes(void) {
+  return (size_t)mlp::prep::kMaxBlocks * 2 * 32 * sizeof(double);
+}
+
+chad_status chad_mlp_gather(const uint16_t* X, const float* Y, int64_t M, uint64_t split_key,
+                            int64_t offset, int64_t n_part, uint64_t epoch_key, int64_t start,
+                            int64_t count, uint16_t* Xb, float* Yb, void* stream) {
+  if (!X || !Y || !Xb || !Yb || M < 1 || n_part < 1 || count < 0) return CHAD_E_INVALID;
+  if (offset < 0 || offset + n_part > M || start < 0 || start + count > n_part)
+    return CHAD_E_INVALID;
+  if (((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Xb)) & 15) != 0 ||
+      ((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(Yb)) & 7) != 0)
+    return CHAD_E_INVALID;
+  if (count == 0) return CHAD_OK;
+  mlp::prep::gather<<<(unsigned)((count + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      reinterpret_cast<const uint4*>(X), reinterpret_cast<const float2*>(Y), M,
+      mlp::prep::feistel_half(M), split_key, offset, n_part, mlp::prep::feistel_half(n_part),
+      epoch_key, start, count, reinterpret_cast<uint4*>(Xb), reinterpret_cast<float2*>(Yb));
+  return cudaGetLastError() == cudaSuccess ? CHAD_OK : CHAD_E_CUDA;
 }
 
 chad_status chad_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t t,

@@ -90,6 +90,7 @@ using namespace chad;
 // out[15] one Eq. 8 Newton iteration (h2_eval + update)
 // out[16] FP32 work of one attempt besides rates, LU, solves, J x and Eq. 8
 // out[17] FP64 work of one attempt besides the Eq. 7 Newton iterations
+// With n >= 19: out[18] the rates with their partials alone (rates<., true>).
 extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   if (!out || n < 13) return CHAD_E_INVALID;
   DigConst c;
@@ -191,25 +192,31 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
       out[15] = g_ops + 2;  // + the Newton update S - E/E'
     }
     // FP32 flops of one form-4 attempt outside the counted blocks, from the
-    // kernel source (two-float operations at their FP32 cost: TwoSum-based
-    // sum 11, product 10, sum with a float 10):
+    // kernel source (two-float operations at their FP32 cost: TwoSum 6,
+    // TwoProd 3, a sum with a float 10, a sum 11, a product 10, a product
+    // with a float 8):
     //   S_h2 surgery of J_d: zh (29 + 3 x 8), p2 (29), its reciprocal (1)   83
     //   q scaling (29), second-level dot and denominator (58 + 3)           90
     //   per stage (x3): two wsolve level-2 updates (2 x (58 + 1 + 58)),
     //     x'_h2 = zh^T x (28 x 13), v^T x (8 x 13), residual b - x + g J x
-    //     (29 x 32), x = x0 + dx (29 x 6)                         234 + 468 + 928 + 174
-    //   stage right-hand sides: stage 1 (29 x 11), stage 2 (29 x 63),
-    //     k2 (29 x 11), stage-1 float point (29 x 2)                    29 x 87
-    //   error norm: k1 - 2 k2 + k3 (33), hi + lo (1), scale (5)         29 x 39
-    out[16] = 83 + 90 + 3 * (234 + 28 * 13 + 8 * 13 + (int64_t)NS * 32 + (int64_t)NS * 6) +
-              (int64_t)NS * 87 + (int64_t)NS * 39;
+    //     (29 x 32), x = x0 + dx (29)                          234 + 364 + 104 + 928 + 29
+    //   k2 = x + k1 (29); right-hand sides: stage 1 (29 x 17 with
+    //     C = e32 F1 + 2 F0), stage 2 (29 x 40), stage-1 float point (29 x 2)
+    //   error norm: k1 - 2 k2 + k3 exact (17), hi + lo (1), scale (4)   29 x 22
+    out[16] = 83 + 90 + 3 * (234 + 28 * 13 + 8 * 13 + (int64_t)NS * 32 + NS) + NS +
+              (int64_t)NS * (17 + 40 + 2) + (int64_t)NS * 22;
     // FP64 flops of one form-4 attempt besides the Eq. 7 iterations (and the
     // three root moves, counted with them): evaluation points y + (h/2) k1 in
-    // the 8 states of Eq. 7 and y + h k2 in all 29 (two FMAs each), the two
-    // tangent guesses of S_H (8 differences and 8 FMAs each, 24 counted),
-    // the tangent dS_H/dy (9 products and a reciprocal, 20 counted), g and
-    // h/2 (2)
-    out[17] = 8 * 4 + (int64_t)NS * 4 + 2 * 24 + 20 + 2;
+    // the 8 states of Eq. 7 and y + h k2 in all 29 (one FMA each), the two
+    // tangent guesses of S_H (24 each), the tangent dS_H/dy (20) and g, h/2
+    out[17] = 8 * 2 + (int64_t)NS * 2 + 2 * 24 + 20 + 2;
+  }
+  if (n >= 19) {
+    // out[18] rates with their partials alone (no balances, no Jacobian):
+    // the form-4 refinement residual recomputes them at each stage
+    g_ops = 0;
+    rates<Fc, true>(c, q, y, ab, o);
+    out[18] = g_ops;
   }
   return CHAD_OK;
 }

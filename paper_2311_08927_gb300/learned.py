@@ -14,7 +14,9 @@ without S_H and h -- e.g. a coupling that reloads particle states from a CFD
 frame), whose plain start is S_H = 1e-7 and h = 1e-6 d.
 
 Torch is used for device memory only; every numerical step runs in the
-library's kernels.
+library's kernels: feature and target statistics, standardisation, the
+shuffled batches (keyed permutations, no stored index arrays), the
+tensor-core forward/backward and Adam.
 """
 from __future__ import annotations
 
@@ -88,34 +90,33 @@ def sample_states(pop: I.Population, intervals: int, precision=CH.PREC_MIXED, sk
     return torch.cat(ys, 1), torch.cat(Ts), torch.cat(SHs), torch.cat(hs)
 
 
-def feature_norm(y, T):
-    """Mean and inverse std of the features (log10 max(y, 1e-20), T/100)."""
+def _prep_scratch():
     import torch
-    f = torch.log10(torch.clamp(y, min=1e-20)).float()
-    mu = torch.zeros(32, dtype=torch.float32, device="cuda")
-    inv = torch.ones(32, dtype=torch.float32, device="cuda")
-    mu[:NS] = f.mean(1)
-    inv[:NS] = 1.0 / torch.clamp(f.std(1), min=1e-6)
-    t = (T * 0.01).float()
-    mu[NS] = t.mean()
-    inv[NS] = 1.0 / torch.clamp(t.std(), min=1e-6)
-    return torch.cat([mu, inv])
+    return torch.empty(CH.mlp_prep_scratch_bytes() // 8 + 1, dtype=torch.float64, device="cuda")
+
+
+def feature_norm(y, T):
+    """Mean and inverse std of the features (log10 max(y, 1e-20), T/100),
+    computed by the library (chad_mlp_feature_norm)."""
+    import torch
+    norm = torch.empty(64, dtype=torch.float32, device="cuda")
+    CH.chad_mlp_feature_norm(y, T, norm, _prep_scratch())
+    return norm
 
 
 def build_dataset(y, T, SH, h, norm=None):
-    """Features X [M][32] (BF16 bits in int16) and standardised targets Y [M][2]."""
+    """Features X [M][32] (BF16 bits in int16) and standardised targets Y [M][2],
+    both formed by the library's kernels."""
     import torch
     if norm is None:
         norm = feature_norm(y, T)
     M = T.shape[0]
     X = torch.empty((M, 32), dtype=torch.int16, device="cuda")
     CH.chad_mlp_features(y, T, norm, X)
-    t = torch.stack([torch.log10(SH), torch.log10(h)], 1).float()
-    mu = t.mean(0)
-    sd = torch.clamp(t.std(0), min=1e-6)
-    Y = ((t - mu) / sd).contiguous()
-    out_norm = torch.cat([mu, sd]).cpu().numpy().astype(np.float32)
-    return X, Y, norm, out_norm
+    Y = torch.empty((M, 2), dtype=torch.float32, device="cuda")
+    on = torch.empty(4, dtype=torch.float32, device="cuda")
+    CH.chad_mlp_targets(SH, h, Y, on, _prep_scratch())
+    return X, Y, norm, on.cpu().numpy().astype(np.float32)
 
 
 def init_params(seed=0):
@@ -127,54 +128,66 @@ def init_params(seed=0):
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
 
 
+def _key(seed, k):
+    """64-bit permutation key number k of a training run (SplitMix64 of seed, k)."""
+    z = (seed * 0x9E3779B97F4A7C15 + (k + 1) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return z ^ (z >> 31)
+
+
 def train(X, Y, epochs=20, batch=32768, lr=3e-3, seed=0, split=(0.90, 0.05)):
     """Adam on the mean-squared error, train/validation/test split 90/5/5;
     the learning rate halves every 8 epochs.  Returns (params float32,
     history [(epoch, train loss, validation loss)], test loss); epoch -1 is
-    the validation loss before training."""
+    the validation loss before training.
+
+    Every step runs in the library: the split and the per-epoch order are
+    keyed permutations applied by chad_mlp_gather, the batch gradient is
+    chad_mlp_grad_async, the update chad_mlp_adam; each batch loss lands in
+    its own device slot and the host waits once per epoch (chad_mlp_wait)."""
     import torch
     M = X.shape[0]
-    g = torch.Generator(device="cuda")
-    g.manual_seed(seed)
-    perm = torch.randperm(M, device="cuda", generator=g)
     n_tr, n_va = int(split[0] * M), int(split[1] * M)
-    tr, va, te = perm[:n_tr], perm[n_tr:n_tr + n_va], perm[n_tr + n_va:]
+    n_te = M - n_tr - n_va
+    split_key = _key(seed, 0)
     P = torch.from_numpy(init_params(seed)).cuda()
     m = torch.zeros_like(P)
     v = torch.zeros_like(P)
     grad = torch.zeros_like(P)
-    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    Xb = torch.empty((batch, 32), dtype=torch.int16, device="cuda")
+    Yb = torch.empty((batch, 2), dtype=torch.float32, device="cuda")
     scratch = torch.empty(CH.mlp_grad_scratch_bytes(batch) // 4 + 1, dtype=torch.float32,
                           device="cuda")
+    bs = max(1, min(batch, n_tr))
+    nb = n_tr // bs
+    losses = torch.zeros(max(nb, (max(n_va, n_te) + batch - 1) // batch), dtype=torch.float32,
+                         device="cuda")
 
-    def eval_loss(idx):
-        Xe, Ye = X[idx].contiguous(), Y[idx].contiguous()
-        tot, cnt = 0.0, 0
-        for s in range(0, Xe.shape[0], batch):
-            xb, yb = Xe[s:s + batch], Ye[s:s + batch]
-            sc = torch.empty(CH.mlp_grad_scratch_bytes(xb.shape[0]) // 4 + 1, dtype=torch.float32,
-                             device="cuda")
-            CH.chad_mlp_grad(xb, yb, P, grad, loss, sc)
-            tot += float(loss.item()) * xb.shape[0]
-            cnt += xb.shape[0]
-        return tot / max(cnt, 1)
+    def eval_loss(off, n):
+        cnts = []
+        for k, s in enumerate(range(0, n, batch)):
+            c = min(batch, n - s)
+            CH.chad_mlp_gather(X, Y, split_key, off, n, 0, s, c, Xb, Yb)
+            CH.chad_mlp_grad_async(Xb[:c], Yb[:c], P, grad, losses[k:k + 1], scratch)
+            cnts.append(c)
+        CH.chad_mlp_wait()
+        lv = losses[:len(cnts)].cpu().numpy()
+        return float(np.dot(lv, cnts) / max(n, 1))
 
-    hist = [(-1, float("nan"), eval_loss(va))]  # before training
+    hist = [(-1, float("nan"), eval_loss(n_tr, n_va))]  # before training
     step = 0
     for ep in range(epochs):
-        order = tr[torch.randperm(n_tr, device="cuda", generator=g)]
-        run = 0.0
-        nb = 0
-        for s in range(0, n_tr - batch + 1, batch):
-            idx = order[s:s + batch]
-            xb, yb = X[idx].contiguous(), Y[idx].contiguous()
-            CH.chad_mlp_grad(xb, yb, P, grad, loss, scratch)
+        ek = _key(seed, ep + 1)
+        for b in range(nb):
+            CH.chad_mlp_gather(X, Y, split_key, 0, n_tr, ek, b * bs, bs, Xb, Yb)
+            CH.chad_mlp_grad_async(Xb[:bs], Yb[:bs], P, grad, losses[b:b + 1], scratch)
             step += 1
             CH.chad_mlp_adam(P, grad, m, v, step, lr * (0.5 ** (ep // 8)))
-            run += float(loss.item()) if (nb % 16 == 0) else 0.0
-            nb += 1
-        hist.append((ep, run / max(1, (nb + 15) // 16), eval_loss(va)))
-    return P.cpu().numpy(), hist, eval_loss(te)
+        CH.chad_mlp_wait()
+        run = float(losses[:nb].mean().item())
+        hist.append((ep, run, eval_loss(n_tr, n_va)))
+    return P.cpu().numpy(), hist, eval_loss(n_tr + n_va, n_te)
 
 
 def train_from_runs(pops, intervals=10, epochs=20, batch=32768, lr=3e-3, max_samples=None,

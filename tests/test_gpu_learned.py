@@ -217,3 +217,82 @@ def test_full_size_64_digesters_learned_mixed(trained):
         o = O.run(one, 60.0, 2, rtol=1e-6)
         assert np.array_equal(g["pos"][:, a:b], o["pos"]), d
         assert _relerr(g["y"][:, a:b], o["y"]).max() < 1e-4, d
+
+
+# ------------------------------------------------------------ training data preparation
+def test_feature_norm_and_targets_match_numpy():
+    """The library's statistics against numpy in FP64: feature means and
+    1/std (sample std) of log10 max(y, 1e-20) and T/100, target means and
+    stds of log10 S_H and log10 h, and the standardised targets."""
+    rng = np.random.default_rng(4)
+    n = 70001  # not a multiple of the block size
+    y = (I.x_ss()[:, None] * np.exp(0.3 * rng.standard_normal((I.NS, n))))
+    y[3, :50] = 0.0  # below the log floor
+    T = rng.uniform(303.15, 313.15, n)
+    SH = 10 ** rng.uniform(-8, -6, n)
+    h = 10 ** rng.uniform(-6, -3, n)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sc = torch.empty(CH.mlp_prep_scratch_bytes() // 8 + 1, dtype=torch.float64, device="cuda")
+    norm = torch.empty(64, dtype=torch.float32, device="cuda")
+    CH.chad_mlp_feature_norm(d(y), d(T), norm, sc)
+    f = np.vstack([np.log10(np.maximum(y.astype(np.float32), np.float32(1e-20))).astype(np.float64),
+                   (T.astype(np.float32) * np.float32(0.01)).astype(np.float64)])
+    nm = norm.cpu().numpy()
+    np.testing.assert_allclose(nm[:30], f.mean(1), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(nm[32:62], 1.0 / f.std(1, ddof=1), rtol=1e-5)
+    assert np.all(nm[30:32] == 0) and np.all(nm[62:64] == 1)
+    Y = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    on = torch.empty(4, dtype=torch.float32, device="cuda")
+    CH.chad_mlp_targets(d(SH), d(h), Y, on, sc)
+    t = np.vstack([np.log10(SH), np.log10(h)])
+    o = on.cpu().numpy()
+    np.testing.assert_allclose(o[:2], t.mean(1), rtol=1e-6)
+    np.testing.assert_allclose(o[2:], t.std(1, ddof=1), rtol=1e-5)
+    ref = ((t.T - o[:2]) / o[2:]).astype(np.float32)
+    np.testing.assert_allclose(Y.cpu().numpy(), ref, rtol=1e-5, atol=1e-5)
+
+
+def test_gather_visits_every_row_of_a_split_once():
+    """The keyed permutations are bijections: one pass over a split gathers
+    each of its rows exactly once; the three splits partition the data; a
+    different epoch key gives another order; the rows are copied intact."""
+    M = 10007
+    X = torch.arange(M * 32, dtype=torch.int32).remainder(30000).to(torch.int16).reshape(M, 32)
+    X[:, 0] = torch.arange(M, dtype=torch.int32).remainder(30000).to(torch.int16)
+    X = X.cuda().contiguous()
+    ids = np.arange(M, dtype=np.float32)
+    Y = torch.from_numpy(np.stack([ids, -ids], 1)).cuda()
+    seen = []
+    for off, n in ((0, 9000), (9000, 500), (9500, 507)):
+        Xb = torch.empty((n, 32), dtype=torch.int16, device="cuda")
+        Yb = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+        CH.chad_mlp_gather(X, Y, 12345, off, n, 777, 0, n, Xb, Yb)
+        r = Yb.cpu().numpy()
+        assert np.array_equal(r[:, 1], -r[:, 0])
+        rows = r[:, 0].astype(np.int64)
+        assert len(np.unique(rows)) == n
+        np.testing.assert_array_equal(Xb.cpu().numpy(), X.cpu().numpy()[rows])
+        seen.append(rows)
+    allr = np.concatenate(seen)
+    assert np.array_equal(np.sort(allr), np.arange(M))
+    Xb = torch.empty((9000, 32), dtype=torch.int16, device="cuda")
+    Yb = torch.empty((9000, 2), dtype=torch.float32, device="cuda")
+    CH.chad_mlp_gather(X, Y, 12345, 0, 9000, 778, 0, 9000, Xb, Yb)
+    other = Yb.cpu().numpy()[:, 0].astype(np.int64)
+    assert np.array_equal(np.sort(other), np.sort(seen[0])) and not np.array_equal(other, seen[0])
+
+
+def test_library_training_loop_reduces_the_loss():
+    """The in-library loop (gather, asynchronous gradient, Adam, one wait per
+    epoch) on a smooth synthetic target: the validation loss falls."""
+    from paper_2311_08927_gb300 import learned as Lm
+    rng = np.random.default_rng(9)
+    M = 60000
+    Xf = rng.standard_normal((M, 32)).astype(np.float32)
+    Xf[:, 30:] = 0
+    Yf = np.stack([np.tanh(Xf[:, 0] + 0.5 * Xf[:, 1]), Xf[:, 2] * Xf[:, 3] * 0.3], 1).astype(np.float32)
+    X = torch.from_numpy(_bf16_bits(Xf)).cuda()
+    Y = torch.from_numpy(Yf).cuda()
+    params, hist, test_loss = Lm.train(X, Y, epochs=6, batch=4096, lr=3e-3)
+    assert hist[-1][2] < 0.3 * hist[0][2], hist
+    assert abs(test_loss - hist[-1][2]) < 0.5 * hist[-1][2] + 1e-3

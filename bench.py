@@ -165,8 +165,8 @@ def alu_roofline(f64, f32, launch_ms, peak64, peak32):
 def kernel_sources_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("adm1_device.cuh", "integrate_impl.cuh", "rank1.cuh", "sparse_lu_gen.cuh", "model.h",
-              "kernels.h"):
+    for f in ("adm1_device.cuh", "integrate_impl.cuh", "integrate_mx.cuh", "dfloat.cuh", "rank1.cuh",
+              "sparse_lu_gen.cuh", "model.h", "kernels.h"):
         with open(os.path.join(ROOT, "paper_2311_08927_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -464,12 +464,14 @@ def run_ours(args, ws, rank, local, cfg=3):
     if rank != 0:
         return None
     fr = H["clocks"]
-    tpa, tsrc = measured_traffic_per_attempt(head) if cfg == 3 else (None, None)
+    tkey = head + ("_h2alg" if (h2m and head != "fp64_h2alg") else "")
+    tpa, tsrc = measured_traffic_per_attempt(tkey) if cfg == 3 else (None, None)
     traffic = None if tpa is None else tpa * H["attempts"] / args.steps
     default_n = {1: 1000, 2: 100_000, 3: N_PARTICLES, 4: 2_000_000, 5: None}[cfg]
     wl = meta["workload"] if (args.particles is None or N == default_n) else f"{meta['workload']}_n{N}"
+    metric = METRIC if cfg == 3 else f"particle-days simulated per second ({meta['desc']})"
     res = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": H["total_ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",

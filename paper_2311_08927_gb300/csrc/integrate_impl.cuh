@@ -286,6 +286,10 @@ constexpr size_t wstore_smem_bytes() {
   return WS ? sizeof(R) * sp::kNNZ * BS : 0;
 }
 
+// norm^(-1/3) of the step controller
+__device__ __forceinline__ float inv_cbrt(float x) { return rcbrtf(x); }
+__device__ __forceinline__ double inv_cbrt(double x) { return rcbrt(x); }
+
 template <int FORM, int BS, int MINB, bool WS>
 __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
   constexpr bool MIXED = FORM == 1 || FORM == 2;
@@ -446,7 +450,9 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
       piv_ok = piv_ok && isfinite(delta2) && delta2 != 0.0 &&
                fabs(delta2) >= kPivTau * fmax(1.0, fabs(s2));
     }
-    float norm = INFINITY;
+    // error norm and controller: FP64 in the FP64 forms, FP32 in the mixed ones
+    using NR = typename std::conditional<MIXED, float, double>::type;
+    NR norm = NR(INFINITY);
     if (!MIXED && !piv_ok) cnt.pivot++;
     double xs[NS];
     if constexpr (MIXED) {
@@ -571,20 +577,32 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
     }
     if (piv_ok || fixed) {
       // scaled error norm max_i |h/6 (k1 - 2 k2 + k3)_i| / (atol_i + rtol
-      // max(|y_i|, |y1_i|)): the combination, which cancels, in FP64;
-      // everything after it in FP32 (the accept test and the controller
-      // need a few digits only)
-      float nf = 0.0f;
-      const float rtol = cvt<float>(a.rtol);
+      // max(|y_i|, |y1_i|)).  FP64 forms: all of it in FP64, as the oracle.
+      // Mixed forms: the combination, which cancels, in FP64, everything
+      // after it in FP32 (the accept test needs a few digits only).
+      if constexpr (!MIXED) {
+        double nd = 0.0;
 #pragma unroll
-      for (int i = 0; i < NS; ++i) {
-        const float e = cvt<float>(fma(-2.0, k2[i], k1[i]) + xs[i]);
-        const float ym = fmaxf(fabsf(cvt<float>(y[i])), fabsf(cvt<float>(y1[i])));
-        const float sc = fmaxf(fmaf(rtol, ym, cvt<float>(a.atol[i])), 1e-30f);
-        const float r = fabsf(e) * __frcp_rn(sc);
-        if (!(r <= nf)) nf = r;  // NaN propagates
+        for (int i = 0; i < NS; ++i) {
+          const double e = fma(-2.0, k2[i], k1[i]) + xs[i];
+          const double sc = fma(a.rtol, fmax(fabs(y[i]), fabs(y1[i])), a.atol[i]);
+          const double r = fabs(e) * rcp<double>(sc);
+          if (!(r <= nd)) nd = r;  // NaN propagates
+        }
+        norm = nd * (hh * (1.0 / 6.0));
+      } else {
+        float nf = 0.0f;
+        const float rtol = cvt<float>(a.rtol);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          const float e = cvt<float>(fma(-2.0, k2[i], k1[i]) + xs[i]);
+          const float ym = fmaxf(fabsf(cvt<float>(y[i])), fabsf(cvt<float>(y1[i])));
+          const float sc = fmaxf(fmaf(rtol, ym, cvt<float>(a.atol[i])), 1e-30f);
+          const float r = fabsf(e) * __frcp_rn(sc);
+          if (!(r <= nf)) nf = r;  // NaN propagates
+        }
+        norm = nf * (cvt<float>(hh) * (1.0f / 6.0f));
       }
-      norm = nf * (cvt<float>(hh) * (1.0f / 6.0f));
     }
     if (fixed) {
 #pragma unroll
@@ -594,22 +612,22 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
       ++nacc;
       if (!isfinite(norm)) status |= ST_NAN;
       if (nacc >= a.fixed_n || (status & ST_NAN)) done = true;
-    } else if (norm <= 1.0f) {
+    } else if (norm <= NR(1)) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) y[i] = y1[i];
       if constexpr (H2A) y[iS_h2] = SH2g;  // Eq. 8 root at y1 (last evaluation)
       t = last ? Tend : t + hh;
       cnt.acc++;
       ++nacc;
-      float fac = (norm == 0.0f) ? 5.0f : fminf(5.0f, fmaxf(0.2f, 0.8f * powf(norm, -1.0f / 3.0f)));
-      if (rejected_prev) fac = fminf(fac, 1.0f);
+      NR fac = (norm == NR(0)) ? NR(5) : fmin(NR(5), fmax(NR(0.2), NR(0.8) * inv_cbrt(norm)));
+      if (rejected_prev) fac = fmin(fac, NR(1));
       h = hh * cvt<double>(fac);
       rejected_prev = false;
       if (last) done = true;
     } else {
       cnt.rej++;
-      const float fac =
-          !piv_ok ? 0.25f : (isfinite(norm) ? fmaxf(0.2f, 0.8f * powf(norm, -1.0f / 3.0f)) : 0.2f);
+      const NR fac = !piv_ok ? NR(0.25)
+                             : (isfinite(norm) ? fmax(NR(0.2), NR(0.8) * inv_cbrt(norm)) : NR(0.2));
       h = hh * cvt<double>(fac);
       rejected_prev = true;
       if (h < kHmin) {

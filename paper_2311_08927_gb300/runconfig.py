@@ -32,8 +32,8 @@ def read(p: str) -> dict:
         raise ValueError("workload must be 1 .. 5")
     if cfg.get("precision", "fp64") not in FORMS:
         raise ValueError(f"precision must be one of {sorted(FORMS)}")
-    if cfg.get("h2_algebraic") and cfg.get("precision", "fp64") != "fp64":
-        raise ValueError("h2_algebraic needs the fp64 form")
+    if cfg.get("h2_algebraic") and cfg.get("precision", "fp64") == "mixed_f32rates":
+        raise ValueError("h2_algebraic takes the fp64 or the mixed form")
     if not cfg.get("rtol", 1e-6) > 0 or not cfg.get("coupling_interval_s", 60.0) > 0:
         raise ValueError("rtol and coupling_interval_s must be > 0")
     if int(cfg.get("intervals", 1)) < 0:

@@ -101,9 +101,9 @@ def test_production_fp64_same_tolerance_tracks_oracle():
     o = oracle_run(pop, 60.0, 30, rtol=1e-6)
     e = relerr(g["y"], o["y"])
     assert np.median(e) < 1e-10 and e.max() < 1e-5
-    # the next step size comes from the controller, whose factor the GPU
-    # evaluates in FP32 (the oracle in FP64): agreement to FP32 precision
-    assert np.median(np.abs(g["h"] / o["h"] - 1)) < 1e-6
+    # the next step size comes from the controller, FP64 on both sides: the
+    # step sequences agree to the round-off of the (sparse vs dense) solves
+    assert np.median(np.abs(g["h"] / o["h"] - 1)) < 1e-9
 
 
 # ------------------------------------------------------------ Gate C: production forms

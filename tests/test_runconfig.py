@@ -17,6 +17,7 @@ def test_bundled_configs(name, n, intervals, prec, learned):
     pop, kw, dt, k = RC.load(RC.path(name), particles=500)
     assert pop.n == 500 and dt == 60.0 and k == intervals
     assert kw["precision"] == prec and kw["learned"] == learned and kw["rtol"] == 1e-6
+    assert kw["h2_algebraic"]  # the paper's Eq. 8 model, as the benchmark runs it
 
 
 def test_many_digester_config():
@@ -32,7 +33,7 @@ def test_diffusion_and_bad_configs(tmp_path):
     p.write_text(json.dumps(good))
     pop, kw, dt, k = RC.load(str(p))
     assert kw["diffusion"] == (1e-6, 0.006) and kw["h2_algebraic"] and k == 3 and pop.n == 2000
-    for bad in ({"workload": 9}, {"precision": "fp16"}, {"h2_algebraic": True, "precision": "mixed"},
+    for bad in ({"workload": 9}, {"precision": "fp16"}, {"h2_algebraic": True, "precision": "mixed_f32rates"},
                 {"typo": 1}, {"diffusion": {"D": 1e-6, "h": 0.0}}):
         q = tmp_path / "bad.json"
         q.write_text(json.dumps({**good, **bad}))

@@ -581,15 +581,19 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
       // Mixed forms: the combination, which cancels, in FP64, everything
       // after it in FP32 (the accept test needs a few digits only).
       if constexpr (!MIXED) {
-        double nd = 0.0;
+        // the largest ratio |e_i| / sc_i kept as the pair (en, sn), compared
+        // by cross products (sc_i > 0), so that one reciprocal suffices
+        double en = 0.0, sn = 1.0;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
-          const double e = fma(-2.0, k2[i], k1[i]) + xs[i];
+          const double e = fabs(fma(-2.0, k2[i], k1[i]) + xs[i]);
           const double sc = fma(a.rtol, fmax(fabs(y[i]), fabs(y1[i])), a.atol[i]);
-          const double r = fabs(e) * rcp<double>(sc);
-          if (!(r <= nd)) nd = r;  // NaN propagates
+          if (!(e * sn <= en * sc)) {  // NaN propagates as in the ratio form
+            en = e;
+            sn = sc;
+          }
         }
-        norm = nd * (hh * (1.0 / 6.0));
+        norm = en * rcp<double>(sn) * (hh * (1.0 / 6.0));
       } else {
         float nf = 0.0f;
         const float rtol = cvt<float>(a.rtol);

@@ -398,19 +398,21 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
       }
       // scaled error norm max_i |h/6 (k1 - 2 k2 + k3)_i| / (atol_i + rtol
       // max(|y_i|, |y1_i|)): the combination of the FP32 stage vectors exact
-      // in two-float, the rest in FP32
-      float nf = 0.0f;
-      const float rtol = f32(a.rtol);
+      // in two-float, the rest in FP32 (fixed steps need none)
+      if (!fixed) {
+        float nf = 0.0f;
+        const float rtol = f32(a.rtol);
 #pragma unroll
-      for (int i = 0; i < NS; ++i) {
-        const df ed = df_add_f(two_sum(k1[i], -2.0f * k2[i]), k3[i]);
-        const float e = ed.hi + ed.lo;
-        const float ym = fmaxf(fabsf(ys[i]), fabsf(y1s[i]));
-        const float sc = fmaxf(fmaf(rtol, ym, f32(a.atol[i])), 1e-30f);
-        const float r = fabsf(e) * __frcp_rn(sc);
-        if (!(r <= nf)) nf = r;  // NaN propagates
+        for (int i = 0; i < NS; ++i) {
+          const df ed = df_add_f(two_sum(k1[i], -2.0f * k2[i]), k3[i]);
+          const float e = ed.hi + ed.lo;
+          const float ym = fmaxf(fabsf(ys[i]), fabsf(y1s[i]));
+          const float sc = fmaxf(fmaf(rtol, ym, f32(a.atol[i])), 1e-30f);
+          const float r = fabsf(e) * __frcp_rn(sc);
+          if (!(r <= nf)) nf = r;  // NaN propagates
+        }
+        norm = nf * (f32(hh) * (1.0f / 6.0f));
       }
-      norm = nf * (f32(hh) * (1.0f / 6.0f));
     }
     const bool accept = fixed || norm <= 1.0f;
     if (accept) {
@@ -425,8 +427,9 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
       ++nacc;
     }
     if (fixed) {
-      if (!isfinite(norm)) status |= ST_NAN;
-      if (nacc >= a.fixed_n || (status & ST_NAN)) done = true;
+      // fixed steps need no error norm: a state that is not finite is
+      // flagged when the particle is stored
+      if (nacc >= a.fixed_n) done = true;
     } else if (accept) {
       t = last ? Tend : t + hh;
       float fac = (norm == 0.0f) ? 5.0f : fminf(5.0f, fmaxf(0.2f, 0.8f * powf(norm, -1.0f / 3.0f)));

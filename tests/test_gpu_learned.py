@@ -296,3 +296,43 @@ def test_library_training_loop_reduces_the_loss():
     params, hist, test_loss = Lm.train(X, Y, epochs=6, batch=4096, lr=3e-3)
     assert hist[-1][2] < 0.3 * hist[0][2], hist
     assert abs(test_loss - hist[-1][2]) < 0.5 * hist[-1][2] + 1e-3
+
+
+def test_learned_cold_restart_with_algebraic_h2():
+    """The mixed form with S_h2 algebraic (kernel form 4), network trained on
+    states of the same model: a restart without history takes fewer attempts
+    with the learned guesses, and both runs stay within 1e-4 of the tight
+    algebraic oracle."""
+    from paper_2311_08927_gb300 import learned as Lm
+    pop = I.config_population(3, n=20000, seed_offset=11)
+    y, T, SH, h = Lm.sample_states(I.config_population(3, n=30000, seed_offset=12), 5,
+                                   h2_algebraic=True)
+    X, Y, norm, onorm = Lm.build_dataset(y, T, SH, h)
+    params, hist, _ = Lm.train(X, Y, epochs=10, batch=2048, lr=2e-3)
+    model = Lm.TrainedMLP(params, norm.cpu().numpy(), onorm, hist)
+    sim = CH.Simulator(pop, precision=CH.PREC_MIXED, h2_algebraic=True)
+    sim.load()
+    sim.step(60.0, 5)
+    relaxed = sim.read()["y"]
+    sim.close()
+    runs = {}
+    for learned in (False, True):
+        s = CH.Simulator(pop, precision=CH.PREC_MIXED, h2_algebraic=True,
+                         learned=1 if learned else 0)
+        if learned:
+            CH.chad_set_mlp(s.ctx, model.params, model.feat_norm, model.out_norm)
+        s.load(y=relaxed)
+        s.step(60.0, 1)
+        runs[learned] = s.read()
+        s.close()
+    p, l = runs[False], runs[True]
+    assert np.all(p["status"] == 0) and np.all(l["status"] == 0)
+    att = lambda r: r["stats"]["accepted_steps"] + r["stats"]["rejected_steps"]
+    assert att(l) < att(p), (att(l), att(p))
+    assert l["stats"]["mlp_redo"] < 0.01 * pop.n
+    idx = np.arange(0, pop.n, 997)
+    sub = I.Population([I.Digester(n=len(idx))], relaxed[:, idx].copy(), pop.T[idx].copy(),
+                       np.zeros((3, len(idx))), False)
+    o = O.run(sub, 60.0, 1, rtol=1e-10, atol=I.atol_vector(1e-13), h2_algebraic=True)
+    for r in (p, l):
+        assert _relerr(r["y"][:, idx], o["y"]).max() < 1e-4

@@ -160,3 +160,36 @@ def test_full_size_1M_sampled():
                                   rng.choice(pop.n, 48, replace=False), [0, pop.n - 1]]))
     o = tight_oracle(subset(pop, idx), 60.0, 2)
     assert relerr(g["y"][:, idx], o["y"]).max() < TOL
+
+
+def test_empty_digester_single_particle_and_step_limit():
+    """Edge cases of the launch: a digester without particles next to one
+    with a single particle (one thread of one block), and a step limit that
+    sets the status bit instead of faulting."""
+    y1 = I.x_ss()[:, None].copy()
+    dg = [I.Digester(n=0), I.Digester(n=1)]
+    pop = I.Population(dg, y1, np.array([I.T_OP]), np.zeros((3, 1)), False)
+    g = mixed_h2(pop, 60.0, 3, fixed_substeps=2)
+    o = O.run(pop, 60.0, 3, fixed_n=2, h2_algebraic=True)
+    assert np.all(g["status"] == 0)
+    assert relerr(g["y"], o["y"]).max() < TOL
+    pop = I.config_population(1, n=64)
+    sim = CH.Simulator(pop, precision=CH.PREC_MIXED, h2_algebraic=True, max_steps=1)
+    sim.load()
+    sim.step(60.0, 1)
+    out = sim.read()
+    sim.close()
+    assert np.all(out["status"] & CH.P_STEPS)
+
+
+def test_counters_split_eq7_and_eq8_iterations():
+    """Eq. 7 (FP64) and Eq. 8 (FP32) Newton iterations are counted apart:
+    at least one of each per rate evaluation (three per step attempt)."""
+    pop = I.config_population(3, n=2000)
+    g = mixed_h2(pop, 60.0, 2, rtol=1e-6)
+    st = g["stats"]
+    attempts = st["accepted_steps"] + st["rejected_steps"]
+    full = 3 * (attempts - st["pivot_rejects"])  # an attempt stopped by a pivot test evaluates once
+    assert st["newton_iters"] >= full and st["h2_newton_iters"] >= full
+    d = gpu_run(pop, 60.0, 2, rtol=1e-6)  # S_h2 a state: no Eq. 8 iterations
+    assert d["stats"]["h2_newton_iters"] == 0

@@ -1083,6 +1083,12 @@ def main():
         res = run_ours(args, ws, rank, local, cfg)
     if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)
+    if ws > 1:
+        # every rank leaves together, after rank 0's untimed extras
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.barrier()
+            dist.destroy_process_group()
 
 
 if __name__ == "__main__":

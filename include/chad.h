@@ -404,9 +404,10 @@ chad_status chad_mlp_feature_norm(const double* y, int64_t ld, const double* T, 
                                   float* norm, void* scratch, size_t scratch_bytes,
                                   void* cuda_stream);
 
-/* Training targets of n >= 2 samples (device pointers): out_norm [4] =
-   mean of log10 S_H, mean of log10 h, their sample standard deviations
-   (floored at 1e-6); Y [n][2] = the standardised targets.  Asynchronous. */
+/* Training targets of n >= 2 samples (device pointers; S_H and h positive,
+   as the integrator stores them): out_norm [4] = mean of log10 S_H, mean of
+   log10 h, their sample standard deviations (floored at 1e-6); Y [n][2] =
+   the standardised targets.  Asynchronous. */
 chad_status chad_mlp_targets(const double* S_H, const double* h, int64_t n, float* Y,
                              float* out_norm, void* scratch, size_t scratch_bytes,
                              void* cuda_stream);

@@ -193,3 +193,17 @@ def test_counters_split_eq7_and_eq8_iterations():
     assert st["newton_iters"] >= full and st["h2_newton_iters"] >= full
     d = gpu_run(pop, 60.0, 2, rtol=1e-6)  # S_h2 a state: no Eq. 8 iterations
     assert d["stats"]["h2_newton_iters"] == 0
+
+
+def test_diffusion_between_particles_then_mixed_h2():
+    """Diffusion between particles (SPH operator, before the ADM1 step of each
+    interval) followed by form 4, whole lab-cylinder tank, adaptive: within
+    1e-4 of the tight algebraic oracle with the same diffusion."""
+    pop = I.config_population(2, n=1200)
+    dif = (1e-5, 0.024)  # D m^2/s, h m: about 1.3 particle spacings at 1,200 particles
+    g = mixed_h2(pop, 60.0, 3, rtol=1e-6, diffusion=dif)
+    o = O.run(pop, 60.0, 3, rtol=1e-10, atol=I.atol_vector(1e-13), h2_algebraic=True,
+              diffusion=dif)
+    assert np.all(g["status"] == 0)
+    assert np.array_equal(g["pos"], o["pos"])
+    assert relerr(g["y"], o["y"]).max() < TOL

@@ -338,3 +338,65 @@ def test_learned_cold_restart_with_algebraic_h2():
     o = O.run(sub, 60.0, 1, rtol=1e-10, atol=I.atol_vector(1e-13), h2_algebraic=True)
     for r in (p, l):
         assert _relerr(r["y"][:, idx], o["y"]).max() < 1e-4
+
+
+# ------------------------------------------------------------ full sizes, S_h2 algebraic
+@pytest.fixture(scope="module")
+def trained_h2():
+    """A small network trained on states of the S_h2-algebraic model."""
+    from paper_2311_08927_gb300 import learned as Lm
+    y, T, SH, h = Lm.sample_states(I.config_population(3, n=40000), 6, h2_algebraic=True)
+    X, Y, norm, onorm = Lm.build_dataset(y, T, SH, h)
+    params, hist, _ = Lm.train(X, Y, epochs=12, batch=2048, lr=2e-3)
+    return Lm.TrainedMLP(params, norm.cpu().numpy(), onorm, hist)
+
+
+def _learned_mixed_h2_run(pop, model, n_intervals):
+    sim = CH.Simulator(pop, precision=CH.PREC_MIXED, learned=1, h2_algebraic=True)
+    CH.chad_set_mlp(sim.ctx, model.params, model.feat_norm, model.out_norm)
+    sim.load()
+    sim.step(60.0, n_intervals)
+    out = sim.read()
+    sim.close()
+    return out
+
+
+def test_full_size_2M_learned_mixed_h2_sampled(trained_h2):
+    """2,000,000 particles, learned guesses from a cold load, kernel form 4
+    (the form the 2M benchmark line runs): every particle OK, under 5 % of
+    the guesses redone, and a seeded sample of 66 particles (slugs included)
+    recomputed by the oracle's algebraic mode within 1e-4."""
+    pop = I.config_population(4)
+    g = _learned_mixed_h2_run(pop, trained_h2, 2)
+    assert np.all(g["status"] == 0)
+    assert g["stats"]["mlp_redo"] < 0.05 * pop.n
+    rng = np.random.default_rng(14)
+    idx = np.sort(np.concatenate([rng.choice(pop.slugs, 16, replace=False),
+                                  rng.choice(pop.n, 48, replace=False), [0, pop.n - 1]]))
+    sp = I.Population([I.Digester(n=len(idx))], pop.y[:, idx].copy(), pop.T[idx].copy(),
+                      np.zeros((3, len(idx))), False)
+    o = O.run(sp, 60.0, 2, rtol=1e-6, h2_algebraic=True)
+    assert _relerr(g["y"][:, idx], o["y"]).max() < 1e-4
+
+
+def test_full_size_64_digesters_learned_mixed_h2(trained_h2):
+    """The 64-digester workload at full size in one learned form-4 run (the
+    form its benchmark line runs): every particle OK, the headspace states
+    equal within each digester, and the two smallest digesters recomputed
+    whole by the oracle's algebraic mode: positions bitwise, states within
+    1e-4."""
+    pop = I.config_population(5)
+    g = _learned_mixed_h2_run(pop, trained_h2, 2)
+    assert np.all(g["status"] == 0)
+    for d in range(64):
+        a, b = pop.offsets[d], pop.offsets[d + 1]
+        gas = g["y"][26:29, a:b]
+        assert np.all(gas == gas[:, :1]), d
+    cnt = np.diff(pop.offsets)
+    for d in np.argsort(cnt)[:2]:
+        a, b = pop.offsets[d], pop.offsets[d + 1]
+        one = I.Population([pop.digesters[d]], pop.y[:, a:b].copy(), pop.T[a:b].copy(),
+                           pop.pos[:, a:b].copy(), pop.shared_headspace)
+        o = O.run(one, 60.0, 2, rtol=1e-6, h2_algebraic=True)
+        assert np.array_equal(g["pos"][:, a:b], o["pos"]), d
+        assert _relerr(g["y"][:, a:b], o["y"]).max() < 1e-4, d

@@ -142,9 +142,9 @@ def test_diffusion_matches_oracle():
 
 def test_diffusion_production_tolerance_tracks_oracle():
     """Adaptive stepping at rtol 1e-6 on both sides after the same diffusion:
-    the GPU's FP32 step controller may differ from the oracle's FP64 one in
-    the last bits of a step size, so states agree to O(rtol) at worst and to
-    round-off for most particles (the bound of the production test above)."""
+    the step sizes agree to the round-off of the (sparse vs dense) solves, so
+    a rare accept/reject flip moves a particle by O(rtol) at worst; most agree
+    to round-off (the bound of the production test above)."""
     pop = I.config_population(2, n=1200)
     g = gpu_run(pop, 60.0, 3, diffusion=DIFFUSION)
     o = oracle_run(pop, 60.0, 3, diffusion=DIFFUSION)
@@ -690,7 +690,8 @@ def test_full_size_lab_cylinder_100k_whole_tank():
     noise, inlet slab, shared headspace), one 60-s interval in the FP64 form
     at rtol 1e-6, against the oracle on the whole tank at the same rtol:
     positions bitwise, states to round-off for most particles and within the
-    production bound for all (the GPU's step controller works in FP32)."""
+    production bound for all (a round-off flip of an accept/reject decision
+    moves a particle by O(rtol))."""
     pop = I.config_population(2)
     assert pop.n == 100_000
     g = gpu_run(pop, 60.0, 1, rtol=1e-6)

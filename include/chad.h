@@ -318,6 +318,12 @@ chad_status chad_step(chad_ctx* ctx, double dt_coupling_s, int n_intervals);
    memory.  Synchronous. */
 chad_status chad_autotune(chad_ctx* ctx, double dt_coupling_s, int32_t* chosen, double* ms);
 
+/* Use kernel variant v (0 <= v < CHAD_NUM_VARIANTS) for this context's
+   kernel form from the next chad_step on, in place of the default (0) or
+   the autotuner's choice: a fixed launch shape, e.g. for reproducible
+   timing.  Results do not depend on the variant. */
+chad_status chad_set_kernel_variant(chad_ctx* ctx, int variant);
+
 /* The launch shape of kernel variant v (0 <= v < CHAD_NUM_VARIANTS) for a
    context's configuration (precision and h2_algebraic as in chad_config):
    threads per block, minimum resident blocks per SM (the register budget

@@ -140,6 +140,8 @@ def lib():
             L.chad_flop_counts.argtypes = [C.c_void_p, C.c_int]
             L.chad_autotune.restype = C.c_int
             L.chad_autotune.argtypes = [C.c_void_p, C.c_double, C.POINTER(C.c_int32), C.c_void_p]
+            L.chad_set_kernel_variant.restype = C.c_int
+            L.chad_set_kernel_variant.argtypes = [C.c_void_p, C.c_int]
             L.chad_kernel_variant.restype = C.c_int
             L.chad_kernel_variant.argtypes = [C.c_int, C.c_int, C.c_int] + [C.POINTER(C.c_int32)] * 3
             L.chad_eval_model.restype = C.c_int
@@ -201,7 +203,7 @@ def exported_symbols() -> list[str]:
             "chad_mlp_forward", "chad_mlp_grad_scratch_bytes", "chad_mlp_grad", "chad_mlp_adam",
             "chad_kernel_variant", "chad_mlp_grad_async", "chad_mlp_wait",
             "chad_mlp_prep_scratch_bytes", "chad_mlp_feature_norm", "chad_mlp_targets",
-            "chad_mlp_gather"]
+            "chad_mlp_gather", "chad_set_kernel_variant"]
 
 MLP_IN, MLP_HID, MLP_OUT = 32, 64, 2
 MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT
@@ -355,6 +357,11 @@ def chad_autotune(ctx, dt_coupling_s):
     ms = np.zeros(NUM_VARIANTS)
     _check(L, ctx, L.chad_autotune(ctx, float(dt_coupling_s), C.byref(ch), ms.ctypes.data))
     return ch.value, ms
+
+
+def chad_set_kernel_variant(ctx, v) -> None:
+    L = lib()
+    _check(L, ctx, L.chad_set_kernel_variant(ctx, int(v)))
 
 
 def kernel_variant(precision, h2_algebraic, v) -> dict:

@@ -969,6 +969,15 @@ chad_status chad_step(chad_ctx* c, double dt_coupling_s, int n_intervals) {
   return CHAD_OK;
 }
 
+chad_status chad_set_kernel_variant(chad_ctx* c, int variant) {
+  if (!c) return CHAD_E_INVALID;
+  if (variant < 0 || variant >= kNumVariants)
+    return fail(c, CHAD_E_INVALID, "variant must be in [0, CHAD_NUM_VARIANTS)");
+  c->variant[kernel_form(c)] = variant;
+  drop_graph(c);
+  return CHAD_OK;
+}
+
 chad_status chad_autotune(chad_ctx* c, double dt_coupling_s, int32_t* chosen, double* ms) {
   if (!c) return CHAD_E_INVALID;
   if (!(dt_coupling_s > 0.0) || !std::isfinite(dt_coupling_s))

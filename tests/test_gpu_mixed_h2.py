@@ -207,3 +207,46 @@ def test_diffusion_between_particles_then_mixed_h2():
     assert np.all(g["status"] == 0)
     assert np.array_equal(g["pos"], o["pos"])
     assert relerr(g["y"], o["y"]).max() < TOL
+
+
+def test_full_size_lab_cylinder_100k_whole_tank():
+    """The lab-cylinder workload at full size (100,000 particles, swirl +
+    noise, inlet slab, shared headspace), one 60-s interval in form 4 at
+    rtol 1e-6, against the oracle's algebraic mode on the whole tank at the
+    same rtol: positions bitwise, states within 1e-4."""
+    pop = I.config_population(2)
+    assert pop.n == 100_000
+    g = mixed_h2(pop, 60.0, 1, rtol=1e-6)
+    o = O.run(pop, 60.0, 1, rtol=1e-6, h2_algebraic=True)
+    assert np.all(g["status"] == 0) and np.all(o["status"] == 0)
+    assert np.array_equal(g["pos"], o["pos"])
+    assert relerr(g["y"], o["y"]).max() < TOL
+
+
+@pytest.mark.parametrize("precision,h2", [(CH.PREC_FP64, False), (CH.PREC_FP64, True),
+                                          (CH.PREC_MIXED, False), (CH.PREC_MIXED, True)])
+def test_every_kernel_variant_gives_the_same_states(precision, h2):
+    """Every launch shape the autotuner chooses from (threads per block,
+    register budget, the factored matrix in registers or in shared memory),
+    forced with chad_set_kernel_variant, integrates the same states: the
+    arithmetic does not depend on the shape.  A ragged population (not a
+    multiple of any block size) with slugs and a temperature spread."""
+    pop = I.config_population(3, n=1500)
+    outs = []
+    for v in range(CH.NUM_VARIANTS):
+        sim = CH.Simulator(pop, precision=precision, h2_algebraic=h2, rtol=1e-6)
+        CH.chad_set_kernel_variant(sim.ctx, v)
+        sim.load()
+        sim.step(60.0, 2)
+        outs.append(sim.read())
+        sim.close()
+    for v, o in enumerate(outs):
+        assert np.all(o["status"] == 0), v
+        assert relerr(o["y"], outs[0]["y"]).max() <= 1e-12, v
+        assert o["stats"]["accepted_steps"] == outs[0]["stats"]["accepted_steps"], v
+    with pytest.raises(CH.ChadError):
+        sim = CH.Simulator(pop, precision=precision, h2_algebraic=h2)
+        try:
+            CH.chad_set_kernel_variant(sim.ctx, CH.NUM_VARIANTS)
+        finally:
+            sim.close()

@@ -55,7 +55,7 @@ def test_single_process_needs_no_process_group():
 
 
 def test_reference_arm_under_torchrun_two_ranks():
-    """bench.py --impl reference launched as the multi-GPU driver launches it
+    """bench.py --impl reference launched as a multi-GPU benchmark run is
     (torch.distributed.run, two ranks, 127.0.0.1): rank 0 alone times the
     oracle and prints one JSON line; rank 1 exits 0 without work."""
     import json

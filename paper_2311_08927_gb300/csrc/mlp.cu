@@ -874,6 +874,41 @@ int sm_count() {
   return sms > 0 ? sms : 1;
 }
 
+// a gradient partial per tile at most, each with its loss
+size_t grad_scratch_bytes(int64_t n) {
+  const int64_t nb = (n + tc::TILE - 1) / tc::TILE;
+  return (size_t)nb * (NPARAM + 1) * sizeof(float);
+}
+
+// The fused forward + backward and the fixed-order reduction of its
+// partials, queued on s; a tensor-core wait that times out sets the device
+// error flag (not read here).
+chad_status grad_launch(const uint16_t* X, const float* Y, int64_t n, const float* params,
+                        float* grad, float* loss, void* scratch, size_t scratch_bytes,
+                        cudaStream_t s) {
+  if (n <= 0 || !X || !Y || !params || !grad || !scratch) return CHAD_E_INVALID;
+  if (scratch_bytes < grad_scratch_bytes(n)) return CHAD_E_INVALID;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) return CHAD_E_INVALID;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(tc::gr::grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc::gr::smem_bytes()) != cudaSuccess)
+      return CHAD_E_CUDA;
+    attr = true;
+  }
+  int* err = err_flag();
+  if (!err) return CHAD_E_NOMEM;
+  // one CTA per SM at most, and one per tile
+  int64_t nb = (n + tc::TILE - 1) / tc::TILE;
+  if (nb > sm_count()) nb = sm_count();
+  float* partial = static_cast<float*>(scratch);
+  float* lpart = partial + nb * NPARAM;
+  tc::gr::grad_kernel<<<(unsigned)nb, tc::gr::kThreads, tc::gr::smem_bytes(), s>>>(
+      reinterpret_cast<const __nv_bfloat16*>(X), Y, n, 1.0f / (float)n, params, partial, lpart, err);
+  reduce_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(partial, (int)nb, grad, lpart, loss);
+  return cudaGetLastError() == cudaSuccess ? CHAD_OK : CHAD_E_CUDA;
+}
+
 // Launch status, then the kernel's timeout flag (waits for the stream).
 chad_status check_err(int* err, cudaStream_t s) {
   int h = 0;
@@ -950,63 +985,25 @@ chad_status chad_mlp_forward(const uint16_t* X, int64_t n, const float* params, 
   return mlp::check_err(err, s);
 }
 
-size_t chad_mlp_grad_scratch_bytes(int64_t n) {
-  const int64_t nb = (n + mlp::tc::TILE - 1) / mlp::tc::TILE;  // a partial per tile at most
-  return (size_t)nb * (mlp::NPARAM + 1) * sizeof(float);
-}
+size_t chad_mlp_grad_scratch_bytes(int64_t n) { return mlp::grad_scratch_bytes(n); }
 
 chad_status chad_mlp_grad(const uint16_t* X, const float* Y, int64_t n, const float* params,
                           float* grad, float* loss, void* scratch, size_t scratch_bytes,
                           void* stream) {
-  if (n <= 0 || !X || !Y || !params || !grad || !scratch) return CHAD_E_INVALID;
-  if (scratch_bytes < chad_mlp_grad_scratch_bytes(n)) return CHAD_E_INVALID;
-  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) return CHAD_E_INVALID;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(mlp::tc::gr::grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)mlp::tc::gr::smem_bytes()) != cudaSuccess)
-      return CHAD_E_CUDA;
-    attr = true;
-  }
   int* err = mlp::err_flag();
   if (!err) return CHAD_E_NOMEM;
-  // one CTA per SM at most, and one per tile
-  int64_t nb = (n + mlp::tc::TILE - 1) / mlp::tc::TILE;
-  if (nb > mlp::sm_count()) nb = mlp::sm_count();
-  float* partial = static_cast<float*>(scratch);
-  float* lpart = partial + nb * mlp::NPARAM;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return CHAD_E_CUDA;
-  mlp::tc::gr::grad_kernel<<<(unsigned)nb, mlp::tc::gr::kThreads, mlp::tc::gr::smem_bytes(), s>>>(
-      reinterpret_cast<const __nv_bfloat16*>(X), Y, n, 1.0f / (float)n, params, partial, lpart, err);
-  mlp::reduce_kernel<<<(mlp::NPARAM + 255) / 256, 256, 0, s>>>(partial, (int)nb, grad, lpart, loss);
+  const chad_status st = mlp::grad_launch(X, Y, n, params, grad, loss, scratch, scratch_bytes, s);
+  if (st != CHAD_OK) return st;
   return mlp::check_err(err, s);
 }
 
 chad_status chad_mlp_grad_async(const uint16_t* X, const float* Y, int64_t n, const float* params,
                                 float* grad, float* loss, void* scratch, size_t scratch_bytes,
                                 void* stream) {
-  if (n <= 0 || !X || !Y || !params || !grad || !scratch) return CHAD_E_INVALID;
-  if (scratch_bytes < chad_mlp_grad_scratch_bytes(n)) return CHAD_E_INVALID;
-  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) return CHAD_E_INVALID;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(mlp::tc::gr::grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)mlp::tc::gr::smem_bytes()) != cudaSuccess)
-      return CHAD_E_CUDA;
-    attr = true;
-  }
-  int* err = mlp::err_flag();
-  if (!err) return CHAD_E_NOMEM;
-  int64_t nb = (n + mlp::tc::TILE - 1) / mlp::tc::TILE;
-  if (nb > mlp::sm_count()) nb = mlp::sm_count();
-  float* partial = static_cast<float*>(scratch);
-  float* lpart = partial + nb * mlp::NPARAM;
-  cudaStream_t s = (cudaStream_t)stream;
-  mlp::tc::gr::grad_kernel<<<(unsigned)nb, mlp::tc::gr::kThreads, mlp::tc::gr::smem_bytes(), s>>>(
-      reinterpret_cast<const __nv_bfloat16*>(X), Y, n, 1.0f / (float)n, params, partial, lpart, err);
-  mlp::reduce_kernel<<<(mlp::NPARAM + 255) / 256, 256, 0, s>>>(partial, (int)nb, grad, lpart, loss);
-  return cudaGetLastError() == cudaSuccess ? CHAD_OK : CHAD_E_CUDA;
+  return mlp::grad_launch(X, Y, n, params, grad, loss, scratch, scratch_bytes,
+                          (cudaStream_t)stream);
 }
 
 chad_status chad_mlp_wait(void* stream) {

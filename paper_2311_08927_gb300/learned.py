@@ -185,7 +185,7 @@ def train(X, Y, epochs=20, batch=32768, lr=3e-3, seed=0, split=(0.90, 0.05)):
             step += 1
             CH.chad_mlp_adam(P, grad, m, v, step, lr * (0.5 ** (ep // 8)))
         CH.chad_mlp_wait()
-        run = float(losses[:nb].mean().item())
+        run = float(losses[:nb].cpu().numpy().astype(np.float64).mean())  # a copy, no kernel
         hist.append((ep, run, eval_loss(n_tr, n_va)))
     return P.cpu().numpy(), hist, eval_loss(n_tr + n_va, n_te)
 

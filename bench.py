@@ -145,9 +145,11 @@ def work_per_launch(CH, precision, stats, steps, h2=False):
         af = CH.attempt_flops_h2_mixed()
         f32 = attempts * af["fp32"] + stats["h2_newton_iters"] * af["fp32_per_h2_iter"]
     else:
-        af = CH.attempt_flops(precision)
+        af = CH.attempt_flops(precision, h2)
         f32 = attempts * af["fp32"]
     f64 = attempts * (af["fp64"] + 3 * fin) + stats["newton_iters"] * nf
+    if "fp64_per_h2_iter" in af:
+        f64 += stats["h2_newton_iters"] * af["fp64_per_h2_iter"]
     return f64 / steps, f32 / steps, af
 
 
@@ -166,7 +168,7 @@ def kernel_sources_hash():
     import hashlib
     h = hashlib.sha256()
     for f in ("adm1_device.cuh", "integrate_impl.cuh", "integrate_mx.cuh", "dfloat.cuh", "rank1.cuh",
-              "sparse_lu_gen.cuh", "model.h", "kernels.h"):
+              "sparse_lu_gen.cuh", "sparse_lu_h2a_gen.cuh", "model.h", "kernels.h"):
         with open(os.path.join(ROOT, "paper_2311_08927_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

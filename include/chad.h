@@ -496,7 +496,9 @@ chad_status chad_probe_alu_peak(int fp64, double* tflops);
    out[16] the rest of one attempt's FP32 work (two-float stage arithmetic,
    residuals, second Sherman-Morrison level), out[17] the rest of its FP64
    work (evaluation points, S_H guesses); with n >= 19 out[18] the rates
-   with their partials alone. */
+   with their partials alone; with n >= 22 out[19] W formation, out[20]
+   LU and out[21] one solve of the LU without S_h2's row and column, which
+   the forms with S_h2 algebraic factor. */
 chad_status chad_flop_counts(int64_t* out, int n);
 
 /* The integrator's device arithmetic helpers applied to x [n] (host

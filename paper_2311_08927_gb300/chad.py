@@ -294,7 +294,8 @@ def chad_mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, s
 
 FLOP_KEYS = ["rates_f", "rates_fj", "charge_E", "form_w", "factor", "solve", "jx", "stage",
              "refine", "sm_setup", "sm_update", "sh_final", "scale_j", "jx_twofloat",
-             "h2_coeffs", "h2_iter", "mx_fp32_extra", "mx_fp64_extra", "rates_partials"]
+             "h2_coeffs", "h2_iter", "mx_fp32_extra", "mx_fp64_extra", "rates_partials",
+             "form_w_h2a", "factor_h2a", "solve_h2a"]
 
 
 def flop_counts() -> dict:
@@ -314,22 +315,38 @@ def attempt_flops_h2_mixed() -> dict:
     Sherman-Morrison updates, three Eq. 8 coefficient sets, the rate
     partials recomputed for each of the three refinement residuals and
     their two-float J x, and the two-float stage arithmetic;
-    FP64 for the evaluation points and the S_H guesses."""
+    FP64 for the evaluation points and the S_H guesses.  The LU is the one
+    without S_h2's row and column (spa)."""
     f = flop_counts()
-    f32 = (f["rates_fj"] + 2 * f["rates_f"] + f["form_w"] + f["factor"] + 8 * f["solve"] +
+    f32 = (f["rates_fj"] + 2 * f["rates_f"] + f["form_w_h2a"] + f["factor_h2a"] +
+           8 * f["solve_h2a"] +
            f["sm_setup"] + 7 * f["sm_update"] + 3 * f["h2_coeffs"] + 3 * f["jx_twofloat"] +
            3 * f["rates_partials"] + f["mx_fp32_extra"])
     return {"fp64": f["mx_fp64_extra"], "fp32": f32, "fp32_per_h2_iter": f["h2_iter"]}
 
 
-def attempt_flops(precision: int) -> dict:
+def attempt_flops(precision: int, h2_algebraic: bool = False) -> dict:
     """FP64 and FP32 operations of one W-method step attempt, without the
     Eq. 7 Newton iterations (counted separately per iteration).  The linear
     algebra is the Sherman-Morrison form: one LU of I - g J_d, one solve for
     q = (I - g J_d)^-1 g u, and per stage one solve plus the rank-1 update;
     the mixed form adds one FP64 residual (J x from the rate partials) and a
-    second FP32 solve per stage."""
+    second FP32 solve per stage.  With h2_algebraic (FP64 form only; the
+    mixed form's count is attempt_flops_h2_mixed): the LU without S_h2 (spa),
+    a fifth solve for the second Sherman-Morrison vector p2 and its update
+    of each stage, the Eq. 8 coefficients at the three evaluation points and
+    the S_h2 tangent guesses (its Newton iterations counted per iteration,
+    h2_iter)."""
     f = flop_counts()
+    if precision == PREC_FP64 and h2_algebraic:
+        # W_d as in the FP64 form over the 28 states of spa; p2: solve, first
+        # level, zh^T p2 and 1 - s (59); zh from the S_h2 row (29 + 24 + 1);
+        # per stage the second level (2 x 29 + 1 + 2 x 29); two tangent
+        # guesses of the Eq. 8 root (2 x 29 each)
+        f64 = (f["rates_fj"] + 2 * f["rates_f"] + f["scale_j"] + (NS - 1) + f["factor_h2a"] +
+               5 * f["solve_h2a"] + f["sm_setup"] + 4 * f["sm_update"] + f["stage"] +
+               3 * f["h2_coeffs"] + 59 + 54 + 3 * 117 + 2 * 58)
+        return {"fp64": f64, "fp32": 0, "fp64_per_h2_iter": f["h2_iter"]}
     if precision == PREC_FP64:
         # W_d: the rate partials scaled by -g before the scatter, plus the diagonal ones
         f64 = (f["rates_fj"] + 2 * f["rates_f"] + f["scale_j"] + NS + f["factor"] +

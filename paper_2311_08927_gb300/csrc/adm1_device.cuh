@@ -321,29 +321,87 @@ __host__ __device__ inline bool newton_only(const DigConst& c, const PartConst& 
 
 // Newton from `guess`; an iterate leaving (0, inf) or a growing |E| switches
 // to bisection on [1e-14, 1] (geometric midpoint, at most 200 halvings).
+// The same iterates as newton_only followed by the bisection, written as one
+// loop around a single evaluation of Eq. 7: each evaluation inlines seven
+// reciprocals, and one copy of it instead of seven keeps the integrator's
+// code within reach of the instruction cache.
 __host__ __device__ inline void solve_SH(const DigConst& c, const PartConst& q, const double* y,
                                          double guess, int max_iters, AcidBase& ab,
                                          NewtonCounters& nc) {
-  if (newton_only(c, q, y, guess, max_iters, INFINITY, ab, nc.iters)) return;
-  nc.fallbacks++;
-  double lo = kSH_lo, hi = kSH_hi;
-  const double elo = charge_E(c, q, y, lo, ab);
-  const double ehi = charge_E(c, q, y, hi, ab);
-  if (!(elo < 0.0 && ehi > 0.0)) {
-    nc.failed = 1;
-    ab.SH = (guess > 0.0 && isfinite(guess)) ? guess : 1e-7;
-    charge_E(c, q, y, ab.SH, ab);
-    return;
-  }
-  for (int it = 0; it < 200; ++it) {
+  enum { kNewton, kLo, kHi, kBisect, kFinal };
+  const double start = (guess > 0.0 && isfinite(guess)) ? guess : 1e-7;
+  int phase = max_iters > 0 ? kNewton : kLo;
+  if (phase == kLo) nc.fallbacks++;
+  double S = phase == kNewton ? start : kSH_lo;  // point of the next evaluation
+  double prevE = INFINITY, lo = kSH_lo, hi = kSH_hi, elo = 0.0;
+  int it = 0;
+  for (;;) {
+    const double E = charge_E(c, q, y, S, ab);
+    if (phase == kFinal) {
+      ab.SH = S;
+      return;
+    }
+    if (phase == kNewton) {
+      nc.iters++;
+      bool fail = !isfinite(E) || fabs(E) > fabs(prevE);
+      if (!fail) {
+        const double dS = E * rcp<double>(ab.dEdS);
+        const double Sn = S - dS;
+        fail = !(Sn > 0.0) || !isfinite(Sn);
+        if (!fail && (fabs(dS) <= 1e-8 * Sn || fabs(E) <= 1e-15)) {
+          // converged: move the reciprocals 1/S and 1/(K_a + S) to the root
+          // to first order (|r dS| <= 1e-8: relative error at the FP64
+          // rounding level) and dE/dS with them
+          ab.SH = Sn;
+          root_shift(c, q, y, ab, S, -dS);
+          return;
+        }
+        if (!fail) {
+          prevE = E;
+          S = Sn;
+          fail = ++it >= max_iters;
+        }
+      }
+      if (fail) {
+        nc.fallbacks++;
+        phase = kLo;
+        S = lo;
+      }
+      continue;
+    }
+    if (phase == kLo) {
+      elo = E;
+      phase = kHi;
+      S = hi;
+      continue;
+    }
+    if (phase == kHi) {
+      if (!(elo < 0.0 && E > 0.0)) {  // no sign change: keep the guess
+        nc.failed = 1;
+        phase = kFinal;
+        S = start;
+        continue;
+      }
+      phase = kBisect;
+      it = 0;
+    } else {  // kBisect: E at the midpoint S
+      ++it;
+      if (E == 0.0) {
+        lo = hi = S;
+      } else if (E < 0.0) {
+        lo = S;
+      } else {
+        hi = S;
+      }
+    }
     const double mid = sqrt(lo * hi);
-    if (!(mid > lo && mid < hi)) break;
-    const double e = charge_E(c, q, y, mid, ab);
-    if (e == 0.0) { lo = hi = mid; break; }
-    if (e < 0.0) lo = mid; else hi = mid;
+    if (lo == hi || it >= 200 || !(mid > lo && mid < hi)) {
+      phase = kFinal;
+      S = sqrt(lo * hi);
+    } else {
+      S = mid;
+    }
   }
-  ab.SH = sqrt(lo * hi);
-  charge_E(c, q, y, ab.SH, ab);
 }
 
 // dS_H/dy_k = -(dE/dy_k) / (dE/dS_H) (implicit function theorem on Eq. 7)

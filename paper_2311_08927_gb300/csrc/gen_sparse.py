@@ -21,6 +21,17 @@ slot indices:
                      identity where the order is safe
   solve(w, dinv, b)  forward / back substitution in the static order
 
+A second header, sparse_lu_h2a_gen.cuh (namespace spa), serves the forms
+with S_h2 algebraic (Eq. 8): there S_h2 is not a state of W_d (its row and
+column go to the second Sherman-Morrison level), so its LU runs over the
+other 28 states only and needs fewer slots and less fill.  Its slot()
+returns, besides the LU slots, positions past them for the S_h2 row
+(kNNZ + c) and the S_h2 column (kNNZ + NS + r), so that the Jacobian scatter
+can deliver those two vectors apart from the factored matrix.
+
+Each header also defines `struct Lu` with the same static members in both
+namespaces, so that the kernels take the LU as a template parameter.
+
 Run from the repository root:  python paper_2311_08927_gb300/csrc/gen_sparse.py
 """
 from __future__ import annotations
@@ -38,6 +49,8 @@ from paper_2311_08927_gb300 import inputs as I  # noqa: E402
 
 NS = I.NS
 OUT = os.path.join(HERE, "sparse_lu_gen.cuh")
+OUT_H2A = os.path.join(HERE, "sparse_lu_h2a_gen.cuh")
+I_H2 = I.STATE_NAMES.index("S_h2")
 
 
 def jacobian_pattern(n_samples: int = 400, seed: int = 12345) -> np.ndarray:
@@ -63,9 +76,10 @@ def jacobian_pattern(n_samples: int = 400, seed: int = 12345) -> np.ndarray:
     return pat
 
 
-def markowitz(pat: np.ndarray) -> list[int]:
+def markowitz(pat: np.ndarray, states=None) -> list[int]:
+    """Elimination order over `states` (all states by default)."""
     A = pat.copy()
-    rem = list(range(NS))
+    rem = list(range(NS)) if states is None else list(states)
     order = []
     while rem:
         best = None
@@ -87,46 +101,77 @@ def markowitz(pat: np.ndarray) -> list[int]:
 
 
 def symbolic_fill(pat: np.ndarray, order: list[int]) -> np.ndarray:
+    n = len(order)
     P = pat[np.ix_(order, order)].copy()  # permuted positions
-    for k in range(NS):
-        rows = [i for i in range(k + 1, NS) if P[i, k]]
-        cols = [j for j in range(k + 1, NS) if P[k, j]]
+    for k in range(n):
+        rows = [i for i in range(k + 1, n) if P[i, k]]
+        cols = [j for j in range(k + 1, n) if P[k, j]]
         for i in rows:
             for j in cols:
                 P[i, j] = True
     return P
 
 
-def generate(pat: np.ndarray) -> str:
-    order = markowitz(pat)
+def generate(pat: np.ndarray, h2a: bool = False) -> str:
+    """The full LU (namespace sp) or, with h2a, the LU without S_h2's row and
+    column (namespace spa) for the forms with S_h2 algebraic."""
+    ns = "spa" if h2a else "sp"
+    if h2a:
+        pat = pat.copy()
+        pat[I_H2, :] = False
+        pat[:, I_H2] = False
+        states = [s for s in range(NS) if s != I_H2]
+    else:
+        states = list(range(NS))
+    n_piv = len(states)
+    order = markowitz(pat, states)
     F = symbolic_fill(pat, order)  # in permuted positions
-    pos = {s: k for k, s in enumerate(order)}
     slot = -np.ones((NS, NS), dtype=int)
     n = 0
-    for k in range(NS):              # row-major over permuted positions
-        for j in range(NS):
+    for k in range(n_piv):           # row-major over permuted positions
+        for j in range(n_piv):
             if F[k, j]:
                 slot[order[k], order[j]] = n
                 n += 1
     nnz = n
+    if h2a:  # the S_h2 row and column, past the LU slots
+        for c in range(NS):
+            slot[I_H2, c] = nnz + c
+        for r in range(NS):
+            if r != I_H2:
+                slot[r, I_H2] = nnz + NS + r
+    n_store = nnz + (2 * NS if h2a else 0)
     nnz_j = int(pat.sum())
     flops = 0
     L = []
     w = L.append
     w("// GENERATED by gen_sparse.py from the library's own Jacobian pattern -- do not edit.")
-    w("// Static-order (Markowitz) sparse LU of W_d = I - g J_d for the 29 ADM1 states")
-    w("// (J_d: the Jacobian with S_H held fixed).")
+    if h2a:
+        w("// Static-order (Markowitz) sparse LU of W_d = I - g J_d without the S_h2 row and")
+        w("// column (S_h2 algebraic, Eq. 8: those go to a second Sherman-Morrison level),")
+        w(f"// over the other {n_piv} ADM1 states (J_d: the Jacobian with S_H held fixed).")
+    else:
+        w("// Static-order (Markowitz) sparse LU of W_d = I - g J_d for the 29 ADM1 states")
+        w("// (J_d: the Jacobian with S_H held fixed).")
     w(f"// pattern nnz(J_d) = {nnz_j}, slots with fill = {nnz}")
     w("#pragma once")
     w('#include "adm1_device.cuh"')
     w("")
     w("namespace chad {")
-    w("namespace sp {")
+    w(f"namespace {ns} {{")
     w("")
     w(f"constexpr int kNNZ = {nnz};")
     w(f"constexpr int kNNZ_J = {nnz_j};")
+    if h2a:
+        w(f"constexpr int kPiv = {n_piv};  // pivots (every state but S_h2)")
+        w("// slots of the Jacobian scatter: the LU's, then the S_h2 row (kNNZ + c)")
+        w("// and the S_h2 column (kNNZ + NS + r)")
+        w(f"constexpr int kStore = {n_store};")
+    else:
+        w(f"constexpr int kPiv = {n_piv};")
+        w(f"constexpr int kStore = {n_store};")
     w("// elimination position -> state index")
-    w("constexpr int kOrder[NS] = {" + ", ".join(str(v) for v in order) + "};")
+    w("constexpr int kOrder[kPiv] = {" + ", ".join(str(v) for v in order) + "};")
     w("")
     w("CHAD_HD constexpr int slot(int r, int c) {")
     w("  // row-major table over states, -1 = structurally zero")
@@ -141,11 +186,11 @@ def generate(pat: np.ndarray) -> str:
     w("")
     w("struct Idx {")
     w("  static CHAD_HD constexpr int at(int r, int c) { return slot(r, c); }")
-    w("  static constexpr int size = kNNZ;")
+    w("  static constexpr int size = kStore;")
     w("};")
     w("")
     w("// diagonal slots in elimination order")
-    w("constexpr int kDiag[NS] = {" + ", ".join(str(int(slot[s, s])) for s in order) + "};")
+    w("constexpr int kDiag[kPiv] = {" + ", ".join(str(int(slot[s, s])) for s in order) + "};")
     w("")
     # ------------------------------------------------------------- W formation
     w("// W_d = I - g J_d in place over the slots (fill slots hold zero in J_d).")
@@ -164,11 +209,11 @@ def generate(pat: np.ndarray) -> str:
     w("CHAD_HD bool factor(W w, R* dinv) {")
     w("  using P = PivTest<R>;")
     w("  bool ok = true;")
-    for k in range(NS):
+    for k in range(n_piv):
         pv = order[k]
         d = slot[pv, pv]
-        sub = [i for i in range(k + 1, NS) if F[i, k]]
-        ucols = [j for j in range(k + 1, NS) if F[k, j]]
+        sub = [i for i in range(k + 1, n_piv) if F[i, k]]
+        ucols = [j for j in range(k + 1, n_piv) if F[k, j]]
         w(f"  {{  // pivot {k}: state {pv} ({I.STATE_NAMES[pv]}), {len(sub)} rows x {len(ucols)} cols")
         w(f"    const R pv = w[{d}];")
         if sub:
@@ -196,32 +241,49 @@ def generate(pat: np.ndarray) -> str:
     w("}")
     w("")
     # ------------------------------------------------------------- solve
-    w("// Solve W x = b in place (b indexed by state).")
+    if h2a:
+        w("// Solve W x = b in place (b indexed by state; b[S_h2] is left as it is:")
+        w("// W_d's S_h2 row is the identity's).")
+    else:
+        w("// Solve W x = b in place (b indexed by state).")
     w("template <class R, class W>")
     w("CHAD_HD void solve(W w, const R* dinv, R* b) {")
-    for k in range(NS):
+    for k in range(n_piv):
         w(f"  R z{k} = b[{order[k]}];")
     sflops = 0
-    for k in range(NS):  # forward, unit lower
+    for k in range(n_piv):  # forward, unit lower
         terms = [(j, slot[order[k], order[j]]) for j in range(k) if F[k, j]]
-        for j, s in terms:
-            w(f"  z{k} -= w[{s}] * z{j};")
+        for j, s_ in terms:
+            w(f"  z{k} -= w[{s_}] * z{j};")
             sflops += 2
-    for k in reversed(range(NS)):  # back
-        terms = [(j, slot[order[k], order[j]]) for j in range(k + 1, NS) if F[k, j]]
-        for j, s in terms:
-            w(f"  z{k} -= w[{s}] * z{j};")
+    for k in reversed(range(n_piv)):  # back
+        terms = [(j, slot[order[k], order[j]]) for j in range(k + 1, n_piv) if F[k, j]]
+        for j, s_ in terms:
+            w(f"  z{k} -= w[{s_}] * z{j};")
             sflops += 2
         w(f"  z{k} *= dinv[{k}];")
         sflops += 1
-    for k in range(NS):
+    for k in range(n_piv):
         w(f"  b[{order[k]}] = z{k};")
     w("}")
     w("")
     w(f"constexpr int kFactorFlops = {flops};")
     w(f"constexpr int kSolveFlops = {sflops};")
     w("")
-    w("}  // namespace sp")
+    w("// The LU as a type, so that the kernels can take it as a template parameter.")
+    w("struct Lu {")
+    w("  using Index = Idx;")
+    w("  static constexpr int nnz = kNNZ;")
+    w("  static constexpr int store = kStore;")
+    w("  template <class R, class W>")
+    w("  static CHAD_HD void form(W w, R g) { form_w<R>(w, g); }")
+    w("  template <class R, class W>")
+    w("  static CHAD_HD bool lu(W w, R* dinv) { return factor<R>(w, dinv); }")
+    w("  template <class R, class W>")
+    w("  static CHAD_HD void sub(W w, const R* dinv, R* b) { solve<R>(w, dinv, b); }")
+    w("};")
+    w("")
+    w(f"}}  // namespace {ns}")
     w("}  // namespace chad")
     return "\n".join(L) + "\n", dict(nnz=nnz, nnz_j=nnz_j, factor=flops, solve=sflops,
                                       order=[I.STATE_NAMES[s] for s in order])
@@ -229,10 +291,11 @@ def generate(pat: np.ndarray) -> str:
 
 def main():
     pat = jacobian_pattern()
-    src, info = generate(pat)
-    with open(OUT, "w") as fh:
-        fh.write(src)
-    print(f"wrote {OUT}: {info}")
+    for out, h2a in ((OUT, False), (OUT_H2A, True)):
+        src, info = generate(pat, h2a)
+        with open(out, "w") as fh:
+            fh.write(src)
+        print(f"wrote {out}: {info}")
 
 
 if __name__ == "__main__":

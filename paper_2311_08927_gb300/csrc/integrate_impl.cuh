@@ -41,6 +41,7 @@
 #include "kernels.h"
 #include "rank1.cuh"
 #include "sparse_lu_gen.cuh"
+#include "sparse_lu_h2a_gen.cuh"
 
 namespace chad {
 namespace integ {
@@ -116,6 +117,8 @@ __device__ __forceinline__ void eval_f(const DigConst& c, const PartConst& q, co
 // f(y) in precision RS, J_d (sparse slots) and u = df/dS_H in precision R,
 // one Newton solve.  SCALE (FP64 form only, where R is RS): J_d and u come
 // out multiplied by jscale (the rate partials are scaled after f is formed).
+// IX: the slot map of the Jacobian scatter (sp::Idx; with S_h2 algebraic
+// spa::Idx, with w an H2Split that takes S_h2's row and column apart).
 // The digester constants in the precision of the Jacobian evaluation.
 template <class R>
 struct DCSel;
@@ -132,7 +135,7 @@ struct DCSel<float> {
   }
 };
 
-template <class R, class RS, bool SCALE, bool H2A = false, class W>
+template <class R, class RS, bool SCALE, bool H2A = false, class IX = sp::Idx, class W>
 __device__ __forceinline__ void eval_fj(const DigConst& c, const DigConstF* cf, const PartConst& q,
                                         const double* y, double D, double& SHg, int max_newton,
                                         Cnt& cnt, double* f, W w, R* u, Rates<R>& o,
@@ -155,9 +158,9 @@ __device__ __forceinline__ void eval_fj(const DigConst& c, const DigConstF* cf, 
     }
     if constexpr (SCALE) {
       scale_partials<R>(o, jscale);
-      jacobian<sp::Idx, R>(cr, q, yr, R(D) * jscale, ab, o, w, u);
+      jacobian<IX, R>(cr, q, yr, R(D) * jscale, ab, o, w, u);
     } else {
-      jacobian<sp::Idx, R>(cr, q, yr, R(D), ab, o, w, u);
+      jacobian<IX, R>(cr, q, yr, R(D), ab, o, w, u);
     }
   }
   if (!std::is_same<R, RS>::value) {
@@ -193,7 +196,7 @@ __device__ __forceinline__ double sh_guess(double SH0, const double* v, const do
 // (rank-1 update).  The FP32<->FP64 conversions here use the hardware
 // instructions: there are ~120 per stage, and as integer sequences they
 // cost more issue slots than they free on the FP64 pipe.
-template <bool MIXED, class R, class W>
+template <bool MIXED, class R, class LU, class W>
 __device__ __forceinline__ void solve(W w, const R* dinv, const R* qv, R inv_delta,
                                       const double* v, const R* vr, const DigConst& c,
                                       const double* y, double D, const Rates<R>& ko, double g,
@@ -201,7 +204,7 @@ __device__ __forceinline__ void solve(W w, const R* dinv, const R* qv, R inv_del
   R t[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) t[i] = R(b[i]);
-  sp::solve<R>(w, dinv, t);
+  LU::template sub<R>(w, dinv, t);
   rank1::update<R>(qv, vr, inv_delta, t);
 #pragma unroll
   for (int i = 0; i < NS; ++i) x[i] = double(t[i]);
@@ -210,7 +213,7 @@ __device__ __forceinline__ void solve(W w, const R* dinv, const R* qv, R inv_del
     jvp<R, double>(c, y, D, ko, x, rank1::vdot<double>(v, x), jx);
 #pragma unroll
     for (int i = 0; i < NS; ++i) t[i] = R(b[i] - x[i] + g * jx[i]);
-    sp::solve<R>(w, dinv, t);
+    LU::template sub<R>(w, dinv, t);
     rank1::update<R>(qv, vr, inv_delta, t);
 #pragma unroll
     for (int i = 0; i < NS; ++i) x[i] += double(t[i]);
@@ -268,23 +271,38 @@ struct SmemSlots {
   R* base;
   __device__ __forceinline__ R& operator[](int s) const { return base[s * BS]; }
 };
-template <class R, int BS, bool WS>
+// N: the LU's slots (sp::kNNZ, or spa::kNNZ for the forms with S_h2 algebraic).
+template <class R, int BS, bool WS, int N = sp::kNNZ>
 struct WStore;
-template <class R, int BS>
-struct WStore<R, BS, false> {
-  R a[sp::kNNZ];
+template <class R, int BS, int N>
+struct WStore<R, BS, false, N> {
+  R a[N];
   __device__ __forceinline__ R* slots() { return a; }
 };
-template <class R, int BS>
-struct WStore<R, BS, true> {
+template <class R, int BS, int N>
+struct WStore<R, BS, true, N> {
   __device__ __forceinline__ SmemSlots<R, BS> slots() {
     return SmemSlots<R, BS>{reinterpret_cast<R*>(chad_dyn_smem) + threadIdx.x};
   }
 };
-template <class R, int BS, bool WS>
+template <class R, int BS, bool WS, int N = sp::kNNZ>
 constexpr size_t wstore_smem_bytes() {
-  return WS ? sizeof(R) * sp::kNNZ * BS : 0;
+  return WS ? sizeof(R) * N * BS : 0;
 }
+
+// Storage of the Jacobian scatter for the LU without S_h2 (spa): the LU's
+// slots in w, the S_h2 row (slot spa::kNNZ + c) in row[c] and the S_h2
+// column (slot spa::kNNZ + NS + r) in col[r].  The slots are compile-time
+// constants in the unrolled scatter, so the selection costs nothing.
+template <class R, class W>
+struct H2Split {
+  W w;
+  R* row;
+  R* col;
+  __device__ __forceinline__ R& operator[](int s) const {
+    return s < spa::kNNZ ? w[s] : (s < spa::kNNZ + NS ? row[s - spa::kNNZ] : col[s - spa::kNNZ - NS]);
+  }
+};
 
 // norm^(-1/3) of the step controller
 __device__ __forceinline__ float inv_cbrt(float x) { return rcbrtf(x); }
@@ -305,7 +323,9 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
   }
   __syncthreads();
 
-  WStore<R, BS, WS> wst;
+  // S_h2 algebraic: the LU without S_h2's row and column (spa)
+  using LU = typename std::conditional<H2A, spa::Lu, sp::Lu>::type;
+  WStore<R, BS, WS, LU::nnz> wst;
   const auto w = wst.slots();
   R qv[NS];  // u = df/dS_H, then q = W_d^-1 (g u)
   R dinv[NS];
@@ -393,8 +413,9 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
     // FP64: J_d and u come out scaled by -g, so W_d = I + (-g J_d) and
     // q = W_d^-1 (g u) = -W_d^-1 (-g u)
     if constexpr (H2A)
-      eval_fj<R, RS, true, true>(*c, cf, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0,
-                                 R(-g), &SH2g);
+      eval_fj<R, RS, true, true, spa::Idx>(*c, cf, q, y, D, SHg, a.max_newton, cnt, F0,
+                                           H2Split<R, decltype(w)>{w, zh, p2}, qv, ko, ab0,
+                                           R(-g), &SH2g);
     else
       eval_fj<R, RS, !MIXED>(*c, cf, q, y, D, SHg, a.max_newton, cnt, F0, w, qv, ko, ab0,
                              R(-g));
@@ -406,41 +427,33 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
     for (int k = 0; k < 8; ++k) vr[k] = R(vsh[k]);
     const double SH20 = SH2g;
     if constexpr (H2A) {
-      // The S_h2 row of -g J_d gives dS_h2/dy = -(J_h2,j + u_h2 v_j) / J_h2,h2
-      // (the scale cancels); its column times -1 is g w.  Both leave W_d,
-      // whose S_h2 row becomes the identity's, and u loses its S_h2 entry.
-      const double rjj = rcp<double>(w[sp::slot(iS_h2, iS_h2)]);
+      // The S_h2 row of -g J_d (delivered into zh by the scatter) gives
+      // dS_h2/dy = -(J_h2,j + u_h2 v_j) / J_h2,h2 (the scale cancels); its
+      // column (into p2) times -1 is g w.  Neither is part of W_d (the LU
+      // spa runs over the other states, S_h2's row of W_d is the
+      // identity's), and u loses its S_h2 entry.  Entries outside the
+      // Jacobian's pattern (sp::slot < 0) are zero.
+      const double rjj = rcp<double>(zh[iS_h2]);
 #pragma unroll
-      for (int j = 0; j < NS; ++j) {
-        const int sl = sp::slot(iS_h2, j);
-        zh[j] = (sl >= 0 && j != iS_h2) ? -w[sl] * rjj : 0.0;
-      }
+      for (int j = 0; j < NS; ++j)
+        zh[j] = (sp::slot(iS_h2, j) >= 0 && j != iS_h2) ? -zh[j] * rjj : 0.0;
       const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
 #pragma unroll
       for (int k = 0; k < 8; ++k) zh[hc[k]] -= qv[iS_h2] * vsh[k] * rjj;
 #pragma unroll
-      for (int i = 0; i < NS; ++i) {
-        const int sl = sp::slot(i, iS_h2);
-        p2[i] = (sl >= 0 && i != iS_h2) ? -w[sl] : 0.0;
-        if (sl >= 0) w[sl] = 0.0;
-      }
-#pragma unroll
-      for (int j = 0; j < NS; ++j) {
-        const int sl = sp::slot(iS_h2, j);
-        if (sl >= 0) w[sl] = 0.0;
-      }
+      for (int i = 0; i < NS; ++i) p2[i] = (sp::slot(i, iS_h2) >= 0 && i != iS_h2) ? -p2[i] : 0.0;
       qv[iS_h2] = R(0);
     }
-    sp::form_w<R>(w, MIXED ? R(g) : R(-1));
-    const bool lu_ok = sp::factor<R>(w, dinv);
+    LU::template form<R>(w, MIXED ? R(g) : R(-1));
+    const bool lu_ok = LU::template lu<R>(w, dinv);
     R inv_delta = R(0);
     // FP64: q and the Sherman-Morrison denominator here; mixed: in its loop
-    const bool sm_ok = MIXED || rank1::setup<R>(w, dinv, R(-1), vr, R(kPivTau), qv, &inv_delta);
+    const bool sm_ok = MIXED || rank1::setup<R, LU>(w, dinv, R(-1), vr, R(kPivTau), qv, &inv_delta);
     bool piv_ok = lu_ok && sm_ok;
     if constexpr (H2A) {
       // p2 = W_1^-1 (g w) with W_1 = W_d - g u v^T (first Sherman-Morrison
       // level), then the second level's denominator 1 - zh^T p2
-      sp::solve<double>(w, dinv, p2);
+      LU::template sub<double>(w, dinv, p2);
       rank1::update<double>(qv, vr, inv_delta, p2);
       double s2 = 0.0;
 #pragma unroll
@@ -479,7 +492,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
           const int npass = st >= 0 ? 2 : 1;
 #pragma unroll 1
           for (int pass = 0; pass < npass; ++pass) {
-            sp::solve<R>(w, dinv, t);
+            LU::template sub<R>(w, dinv, t);
             if (st < 0) break;
             rank1::update<R>(qv, vr, inv_delta, t);
             if (pass == 0) {
@@ -557,7 +570,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
               tmp[i] = tmp[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
           }
         }
-        solve<MIXED, R>(w, dinv, qv, inv_delta, vsh, vr, *c, y, D, ko, g, tmp, xs);
+        solve<MIXED, R, LU>(w, dinv, qv, inv_delta, vsh, vr, *c, y, D, ko, g, tmp, xs);
         if constexpr (H2A) {
           double s2 = 0.0;
 #pragma unroll
@@ -704,7 +717,8 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
 template <int FORM, int BS, int MINB, bool WS>
 cudaError_t launch_variant(const StepArgs& a, cudaStream_t s) {
   using R = typename std::conditional<FORM == 1 || FORM == 2, float, double>::type;
-  constexpr size_t smem = integ::wstore_smem_bytes<R, BS, WS>();
+  using LU = typename std::conditional<FORM == 3, spa::Lu, sp::Lu>::type;
+  constexpr size_t smem = integ::wstore_smem_bytes<R, BS, WS, LU::nnz>();
   static int per_sm = -1, sms = 0;
   if (per_sm < 0) {
     int dev = 0;

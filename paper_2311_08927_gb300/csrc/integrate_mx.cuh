@@ -26,7 +26,10 @@
 // (S_h2: w the S_h2 column of J_d, zh = dS_h2/dy including the path
 // through S_H).  The residual's J_eff x is the product J_d x' + u (v^T x)
 // of the rate partials with x' = x except x'_h2 = zh^T x, and a zero S_h2
-// row.
+// row.  W_d is factored by the generated LU over the 28 other states
+// (sparse_lu_h2a_gen.cuh: 167 slots and 419 flops against 203 and 664 with
+// S_h2 in it); the Jacobian scatter delivers S_h2's row into zh and its
+// column into p2 directly (H2Split), so they never occupy LU slots.
 #pragma once
 #include "dfloat.cuh"
 #include "integrate_impl.cuh"
@@ -107,7 +110,7 @@ template <class W>
 __device__ __forceinline__ void wsolve(W w, const float* dinv, const float* qv,
                                        const float* vr, float inv_delta, const float* p2,
                                        const float* zh, float inv_delta2, float* x) {
-  sp::solve<float>(w, dinv, x);
+  spa::solve<float>(w, dinv, x);
   rank1::update<float>(qv, vr, inv_delta, x);
   float s2 = 0.0f;
 #pragma unroll
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
   }
   __syncthreads();
 
-  WStore<float, BS, WS> wst;
+  WStore<float, BS, WS, spa::kNNZ> wst;
   const auto w = wst.slots();
   float qv[NS];    // u = df/dS_H, then q = W_d^-1 (g u)
   float dinv[NS];
@@ -226,7 +229,8 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
       rates<float, true>(*cf, qf, ys, ab0, ko);
       balances<float>(*cf, ys, Df, ko, F0);
       F0[iS_h2] = 0.0f;
-      jacobian<sp::Idx, float>(*cf, qf, ys, Df, ab0, ko, w, qv);
+      jacobian<spa::Idx, float>(*cf, qf, ys, Df, ab0, ko,
+                                H2Split<float, decltype(w)>{w, zh, p2}, qv);
     }
     const double SH0 = SHg;
     const float SH20 = SH2g;
@@ -238,39 +242,29 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
     // S_h2 leaves W_d: dS_h2/dy = -(J_h2,j + u_h2 v_j) / J_h2,h2 from its
     // row, g times its column becomes the second Sherman-Morrison vector
     {
-      const float rjj = __frcp_rn(w[sp::slot(iS_h2, iS_h2)]);
+      const float rjj = __frcp_rn(zh[iS_h2]);
 #pragma unroll
-      for (int j = 0; j < NS; ++j) {
-        const int sl = sp::slot(iS_h2, j);
-        zh[j] = (sl >= 0 && j != iS_h2) ? -w[sl] * rjj : 0.0f;
-      }
+      for (int j = 0; j < NS; ++j)
+        zh[j] = (sp::slot(iS_h2, j) >= 0 && j != iS_h2) ? -zh[j] * rjj : 0.0f;
       const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
 #pragma unroll
       for (int k = 0; k < 8; ++k) zh[hc[k]] -= qv[iS_h2] * vr[k] * rjj;
 #pragma unroll
-      for (int i = 0; i < NS; ++i) {
-        const int sl = sp::slot(i, iS_h2);
-        p2[i] = (sl >= 0 && i != iS_h2) ? gf * w[sl] : 0.0f;
-        if (sl >= 0) w[sl] = 0.0f;
-      }
-#pragma unroll
-      for (int j = 0; j < NS; ++j) {
-        const int sl = sp::slot(iS_h2, j);
-        if (sl >= 0) w[sl] = 0.0f;
-      }
+      for (int i = 0; i < NS; ++i)
+        p2[i] = (sp::slot(i, iS_h2) >= 0 && i != iS_h2) ? gf * p2[i] : 0.0f;
       qv[iS_h2] = 0.0f;
     }
-    sp::form_w<float>(w, gf);
-    const bool lu_ok = sp::factor<float>(w, dinv);
+    spa::form_w<float>(w, gf);
+    const bool lu_ok = spa::factor<float>(w, dinv);
     float inv_delta = 0.0f, inv_delta2 = 0.0f;
     bool piv_ok = lu_ok;
     if (lu_ok || fixed) {
       // q = W_d^-1 (g u), then p2 = W_1^-1 (g w) with W_1 = W_d - g u v^T
 #pragma unroll
       for (int i = 0; i < NS; ++i) qv[i] *= gf;
-      sp::solve<float>(w, dinv, qv);
+      spa::solve<float>(w, dinv, qv);
       piv_ok = rank1::denominator<float>(qv, vr, float(kPivTau), &inv_delta) && piv_ok;
-      sp::solve<float>(w, dinv, p2);
+      spa::solve<float>(w, dinv, p2);
       rank1::update<float>(qv, vr, inv_delta, p2);
       float s2 = 0.0f;
 #pragma unroll
@@ -507,7 +501,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
 
 template <int BS, int MINB, bool WS>
 cudaError_t launch_variant_mx(const StepArgs& a, cudaStream_t s) {
-  constexpr size_t smem = integ::wstore_smem_bytes<float, BS, WS>();
+  constexpr size_t smem = integ::wstore_smem_bytes<float, BS, WS, spa::kNNZ>();
   static int per_sm = -1, sms = 0;
   if (per_sm < 0) {
     int dev = 0;

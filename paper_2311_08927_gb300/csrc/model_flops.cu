@@ -11,6 +11,7 @@
 #include "model.h"
 #include "rank1.cuh"
 #include "sparse_lu_gen.cuh"
+#include "sparse_lu_h2a_gen.cuh"
 
 namespace chad {
 namespace {
@@ -217,6 +218,24 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
     g_ops = 0;
     rates<Fc, true>(c, q, y, ab, o);
     out[18] = g_ops;
+  }
+  if (n >= 22) {
+    // out[19..21] W formation, LU and one solve of the LU without S_h2's
+    // row and column (spa), which the forms with S_h2 algebraic factor
+    static Fc wa[spa::kNNZ];
+    for (int s = 0; s < spa::kNNZ; ++s) wa[s] = Fc(0.0);
+    g_ops = 0;
+    spa::form_w<Fc>(wa, Fc(1e-4));
+    out[19] = g_ops;
+    Fc dinva[NS];
+    g_ops = 0;
+    spa::factor<Fc>(wa, dinva);
+    out[20] = g_ops;
+    Fc ba[NS];
+    for (int i = 0; i < NS; ++i) ba[i] = Fc(1.0);
+    g_ops = 0;
+    spa::solve<Fc>(wa, dinva, ba);
+    out[21] = g_ops;
   }
   return CHAD_OK;
 }

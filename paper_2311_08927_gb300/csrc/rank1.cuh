@@ -40,14 +40,15 @@ CHAD_HD bool denominator(const R* q, const R* v, R tau, R* inv_delta) {
   return isfinite(delta) && fabs(delta) >= tau * fmax(R(1), fabs(s)) && delta != R(0);
 }
 
-// u (in q) -> q = W_d^-1 (g u) with the factored W_d (slot storage w);
+// u (in q) -> q = W_d^-1 (g u) with the factored W_d (slot storage w, LU
+// one of the generated sparse LUs: sp::Lu, or spa::Lu without S_h2);
 // *inv_delta = 1/delta.  Returns false when delta fails the threshold test or
 // is not finite.
-template <class R, class W>
+template <class R, class LU = sp::Lu, class W>
 CHAD_HD bool setup(W w, const R* dinv, R g, const R* v, R tau, R* q, R* inv_delta) {
 #pragma unroll
   for (int i = 0; i < NS; ++i) q[i] *= g;
-  sp::solve<R>(w, dinv, q);
+  LU::template sub<R>(w, dinv, q);
   const R s = vdot<R>(v, q);
   const R delta = R(1) - s;
   *inv_delta = rcp<R>(delta);

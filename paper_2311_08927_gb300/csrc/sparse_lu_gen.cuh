@@ -10,8 +10,10 @@ namespace sp {
 
 constexpr int kNNZ = 203;
 constexpr int kNNZ_J = 174;
+constexpr int kPiv = 29;
+constexpr int kStore = 203;
 // elimination position -> state index
-constexpr int kOrder[NS] = {11, 23, 24, 25, 13, 14, 15, 8, 26, 28, 21, 22, 27, 9, 16, 0, 18, 2, 20, 17, 1, 6, 5, 12, 3, 4, 7, 10, 19};
+constexpr int kOrder[kPiv] = {11, 23, 24, 25, 13, 14, 15, 8, 26, 28, 21, 22, 27, 9, 16, 0, 18, 2, 20, 17, 1, 6, 5, 12, 3, 4, 7, 10, 19};
 
 CHAD_HD constexpr int slot(int r, int c) {
   // row-major table over states, -1 = structurally zero
@@ -51,11 +53,11 @@ CHAD_HD constexpr int slot(int r, int c) {
 
 struct Idx {
   static CHAD_HD constexpr int at(int r, int c) { return slot(r, c); }
-  static constexpr int size = kNNZ;
+  static constexpr int size = kStore;
 };
 
 // diagonal slots in elimination order
-constexpr int kDiag[NS] = {0, 2, 4, 5, 6, 8, 10, 12, 19, 24, 28, 31, 39, 51, 67, 73, 76, 82, 86, 90, 95, 106, 119, 137, 146, 157, 178, 196, 202};
+constexpr int kDiag[kPiv] = {0, 2, 4, 5, 6, 8, 10, 12, 19, 24, 28, 31, 39, 51, 67, 73, 76, 82, 86, 90, 95, 106, 119, 137, 146, 157, 178, 196, 202};
 
 // W_d = I - g J_d in place over the slots (fill slots hold zero in J_d).
 // W: the slot storage, a pointer or any accessor whose w[s] is a reference.
@@ -1007,6 +1009,19 @@ CHAD_HD void solve(W w, const R* dinv, R* b) {
 
 constexpr int kFactorFlops = 640;
 constexpr int kSolveFlops = 377;
+
+// The LU as a type, so that the kernels can take it as a template parameter.
+struct Lu {
+  using Index = Idx;
+  static constexpr int nnz = kNNZ;
+  static constexpr int store = kStore;
+  template <class R, class W>
+  static CHAD_HD void form(W w, R g) { form_w<R>(w, g); }
+  template <class R, class W>
+  static CHAD_HD bool lu(W w, R* dinv) { return factor<R>(w, dinv); }
+  template <class R, class W>
+  static CHAD_HD void sub(W w, const R* dinv, R* b) { solve<R>(w, dinv, b); }
+};
 
 }  // namespace sp
 }  // namespace chad

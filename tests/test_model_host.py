@@ -46,11 +46,47 @@ def test_host_model_rates_and_analytic_jacobian_match_oracle():
 
 
 def test_generated_sparse_lu_is_current():
+    """Both generated LUs (all states; without S_h2 for the forms with S_h2
+    algebraic) match what the generator makes of the model's pattern now."""
     sys.path.insert(0, os.path.join(ROOT, "paper_2311_08927_gb300", "csrc"))
     import gen_sparse as G
-    src, info = G.generate(G.jacobian_pattern())
-    with open(G.OUT) as fh:
-        assert fh.read() == src, "sparse_lu_gen.cuh is stale: rerun gen_sparse.py"
+    pat = G.jacobian_pattern()
+    for out, h2a in ((G.OUT, False), (G.OUT_H2A, True)):
+        src, info = G.generate(pat, h2a)
+        with open(out) as fh:
+            assert fh.read() == src, f"{os.path.basename(out)} is stale: rerun gen_sparse.py"
+
+
+def test_reduced_lu_leaves_out_s_h2_only():
+    """The LU of the forms with S_h2 algebraic: 28 pivots (every state but
+    S_h2), every structural nonzero of J_d outside S_h2's row and column has
+    an LU slot, and S_h2's row and column map to the positions past the LU
+    slots that the Jacobian scatter hands to the second Sherman-Morrison
+    level."""
+    sys.path.insert(0, os.path.join(ROOT, "paper_2311_08927_gb300", "csrc"))
+    import gen_sparse as G
+    pat = G.jacobian_pattern()
+    src, info = G.generate(pat, True)
+    NS = I.NS
+    h2 = I.STATE_NAMES.index("S_h2")
+    assert len(info["order"]) == NS - 1 and "S_h2" not in info["order"]
+    import re
+    nnz = int(re.search(r"constexpr int kNNZ = (\d+);", src).group(1))
+    table = re.search(r"const int t\[NS \* NS\] = \{(.*?)\};", src, re.S).group(1)
+    slot = np.array([int(x) for x in table.replace("\n", " ").split(",")]).reshape(NS, NS)
+    for r in range(NS):
+        for c in range(NS):
+            if r == h2:
+                assert slot[r, c] == nnz + c
+            elif c == h2:
+                assert slot[r, c] == nnz + NS + r
+            elif pat[r, c]:
+                assert 0 <= slot[r, c] < nnz
+    lu = slot[np.ix_([i for i in range(NS) if i != h2], [i for i in range(NS) if i != h2])]
+    assert sorted(lu[lu >= 0].tolist()) == list(range(nnz))
+    # fewer slots and flops than the LU over all 29 states
+    _, full = G.generate(pat, False)
+    assert info["nnz"] < full["nnz"] and info["factor"] < full["factor"]
 
 
 def test_direct_jacobian_nonzeros_have_sparse_slots():

@@ -13,13 +13,14 @@ fill gives the storage slots.  The emitted code is straight-line with static
 slot indices:
 
   slot(r, c)         storage slot of W_rc (-1 when structurally zero)
-  factor(w, dinv)    in-place LU in the static order; returns false when a
+  factor(w)          in-place LU in the static order, the reciprocal of each
+                     pivot stored in its diagonal slot; returns false when a
                      pivot fails the threshold test |u_kk| >= 0.1 max_i |l_ik u_kk|
                      (equivalently |w_kk| >= 0.1 max_i |w_ik| before scaling,
                      PivTest in adm1_device.cuh) or is zero or not finite; the
                      caller then shrinks the step, which drives W towards the
                      identity where the order is safe
-  solve(w, dinv, b)  forward / back substitution in the static order
+  solve(w, b)        forward / back substitution in the static order
 
 A second header, sparse_lu_h2a_gen.cuh (namespace spa), serves the forms
 with S_h2 algebraic (Eq. 8): there S_h2 is not a state of W_d (its row and
@@ -204,9 +205,11 @@ def generate(pat: np.ndarray, h2a: bool = False) -> str:
     w("}")
     w("")
     # ------------------------------------------------------------- factor
-    w("// In-place LU; returns false if a pivot fails the threshold test.")
+    w("// In-place LU; the diagonal slots receive the reciprocals of the pivots")
+    w("// (the only use the solve makes of them).  Returns false if a pivot fails")
+    w("// the threshold test.")
     w("template <class R, class W>")
-    w("CHAD_HD bool factor(W w, R* dinv) {")
+    w("CHAD_HD bool factor(W w) {")
     w("  using P = PivTest<R>;")
     w("  bool ok = true;")
     for k in range(n_piv):
@@ -226,7 +229,7 @@ def generate(pat: np.ndarray, h2a: bool = False) -> str:
         else:
             w("    ok = ok && P::good(P::key(pv));")
         w("    const R inv = rcp<R>(pv);")
-        w(f"    dinv[{k}] = inv;")
+        w(f"    w[{d}] = inv;")
         flops += 1
         for i in sub:
             sik = slot[order[i], pv]
@@ -247,7 +250,7 @@ def generate(pat: np.ndarray, h2a: bool = False) -> str:
     else:
         w("// Solve W x = b in place (b indexed by state).")
     w("template <class R, class W>")
-    w("CHAD_HD void solve(W w, const R* dinv, R* b) {")
+    w("CHAD_HD void solve(W w, R* b) {")
     for k in range(n_piv):
         w(f"  R z{k} = b[{order[k]}];")
     sflops = 0
@@ -261,7 +264,7 @@ def generate(pat: np.ndarray, h2a: bool = False) -> str:
         for j, s_ in terms:
             w(f"  z{k} -= w[{s_}] * z{j};")
             sflops += 2
-        w(f"  z{k} *= dinv[{k}];")
+        w(f"  z{k} *= w[{int(slot[order[k], order[k]])}];")
         sflops += 1
     for k in range(n_piv):
         w(f"  b[{order[k]}] = z{k};")
@@ -278,9 +281,9 @@ def generate(pat: np.ndarray, h2a: bool = False) -> str:
     w("  template <class R, class W>")
     w("  static CHAD_HD void form(W w, R g) { form_w<R>(w, g); }")
     w("  template <class R, class W>")
-    w("  static CHAD_HD bool lu(W w, R* dinv) { return factor<R>(w, dinv); }")
+    w("  static CHAD_HD bool lu(W w) { return factor<R>(w); }")
     w("  template <class R, class W>")
-    w("  static CHAD_HD void sub(W w, const R* dinv, R* b) { solve<R>(w, dinv, b); }")
+    w("  static CHAD_HD void sub(W w, R* b) { solve<R>(w, b); }")
     w("};")
     w("")
     w(f"}}  // namespace {ns}")

@@ -197,14 +197,14 @@ __device__ __forceinline__ double sh_guess(double SH0, const double* v, const do
 // instructions: there are ~120 per stage, and as integer sequences they
 // cost more issue slots than they free on the FP64 pipe.
 template <bool MIXED, class R, class LU, class W>
-__device__ __forceinline__ void solve(W w, const R* dinv, const R* qv, R inv_delta,
+__device__ __forceinline__ void solve(W w, const R* qv, R inv_delta,
                                       const double* v, const R* vr, const DigConst& c,
                                       const double* y, double D, const Rates<R>& ko, double g,
                                       const double* b, double* x) {
   R t[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) t[i] = R(b[i]);
-  LU::template sub<R>(w, dinv, t);
+  LU::template sub<R>(w, t);
   rank1::update<R>(qv, vr, inv_delta, t);
 #pragma unroll
   for (int i = 0; i < NS; ++i) x[i] = double(t[i]);
@@ -213,7 +213,7 @@ __device__ __forceinline__ void solve(W w, const R* dinv, const R* qv, R inv_del
     jvp<R, double>(c, y, D, ko, x, rank1::vdot<double>(v, x), jx);
 #pragma unroll
     for (int i = 0; i < NS; ++i) t[i] = R(b[i] - x[i] + g * jx[i]);
-    LU::template sub<R>(w, dinv, t);
+    LU::template sub<R>(w, t);
     rank1::update<R>(qv, vr, inv_delta, t);
 #pragma unroll
     for (int i = 0; i < NS; ++i) x[i] += double(t[i]);
@@ -328,7 +328,6 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
   WStore<R, BS, WS, LU::nnz> wst;
   const auto w = wst.slots();
   R qv[NS];  // u = df/dS_H, then q = W_d^-1 (g u)
-  R dinv[NS];
   Rates<R> ko;  // rates and partials at the step's start (mixed: kept for jvp)
   // algebraic S_h2: second rank-1 pair of W (p2 = W_1^-1 g w with w the S_h2
   // column of J_d, zh = dS_h2/dy) and the running Eq. 8 root
@@ -445,15 +444,15 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
       qv[iS_h2] = R(0);
     }
     LU::template form<R>(w, MIXED ? R(g) : R(-1));
-    const bool lu_ok = LU::template lu<R>(w, dinv);
+    const bool lu_ok = LU::template lu<R>(w);
     R inv_delta = R(0);
     // FP64: q and the Sherman-Morrison denominator here; mixed: in its loop
-    const bool sm_ok = MIXED || rank1::setup<R, LU>(w, dinv, R(-1), vr, R(kPivTau), qv, &inv_delta);
+    const bool sm_ok = MIXED || rank1::setup<R, LU>(w, R(-1), vr, R(kPivTau), qv, &inv_delta);
     bool piv_ok = lu_ok && sm_ok;
     if constexpr (H2A) {
       // p2 = W_1^-1 (g w) with W_1 = W_d - g u v^T (first Sherman-Morrison
       // level), then the second level's denominator 1 - zh^T p2
-      LU::template sub<double>(w, dinv, p2);
+      LU::template sub<double>(w, p2);
       rank1::update<double>(qv, vr, inv_delta, p2);
       double s2 = 0.0;
 #pragma unroll
@@ -492,7 +491,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
           const int npass = st >= 0 ? 2 : 1;
 #pragma unroll 1
           for (int pass = 0; pass < npass; ++pass) {
-            LU::template sub<R>(w, dinv, t);
+            LU::template sub<R>(w, t);
             if (st < 0) break;
             rank1::update<R>(qv, vr, inv_delta, t);
             if (pass == 0) {
@@ -570,7 +569,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_kernel(StepArgs a) {
               tmp[i] = tmp[i] - kRB_e32 * (k2[i] - F1[i]) - 2.0 * (k1[i] - F0[i]);
           }
         }
-        solve<MIXED, R, LU>(w, dinv, qv, inv_delta, vsh, vr, *c, y, D, ko, g, tmp, xs);
+        solve<MIXED, R, LU>(w, qv, inv_delta, vsh, vr, *c, y, D, ko, g, tmp, xs);
         if constexpr (H2A) {
           double s2 = 0.0;
 #pragma unroll

@@ -37,6 +37,12 @@
 namespace chad {
 namespace integ {
 
+// the eight states that enter Eq. 7
+__host__ __device__ constexpr bool in_eq7(int i) {
+  return i == iS_va || i == iS_bu || i == iS_pro || i == iS_ac || i == iS_IC || i == iS_IN ||
+         i == iS_cat || i == iS_an;
+}
+
 // binary64 -> float and float -> binary64 of the kernel (hardware conversions)
 __device__ __forceinline__ float f32(double d) { return float(d); }
 __device__ __forceinline__ double f64(float f) { return double(f); }
@@ -107,10 +113,10 @@ __device__ __forceinline__ void rates_f32(const DigConstF& cf, const PartConstF&
 
 // x <- W^-1 x with the factored W_d and both Sherman-Morrison levels.
 template <class W>
-__device__ __forceinline__ void wsolve(W w, const float* dinv, const float* qv,
+__device__ __forceinline__ void wsolve(W w, const float* qv,
                                        const float* vr, float inv_delta, const float* p2,
                                        const float* zh, float inv_delta2, float* x) {
-  spa::solve<float>(w, dinv, x);
+  spa::solve<float>(w, x);
   rank1::update<float>(qv, vr, inv_delta, x);
   float s2 = 0.0f;
 #pragma unroll
@@ -134,9 +140,8 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
   WStore<float, BS, WS, spa::kNNZ> wst;
   const auto w = wst.slots();
   float qv[NS];    // u = df/dS_H, then q = W_d^-1 (g u)
-  float dinv[NS];
   float p2[NS], zh[NS];  // second level: W_1^-1 (g w) and dS_h2/dy
-  double y[NS], y1[NS];  // state; evaluation point (after stage 2: the new state)
+  double y[NS], y1[NS];  // state; evaluation point (only the eight states of Eq. 7)
   float ys[NS], y1s[NS]; // float copies (rates, error scale)
   float F0[NS];           // FP32 rates at y; after stage 1 e32 F1 + 2 F0
   float k1[NS], k2[NS], k3[NS];  // stage vectors (refined solutions, FP32)
@@ -255,16 +260,16 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
       qv[iS_h2] = 0.0f;
     }
     spa::form_w<float>(w, gf);
-    const bool lu_ok = spa::factor<float>(w, dinv);
+    const bool lu_ok = spa::factor<float>(w);
     float inv_delta = 0.0f, inv_delta2 = 0.0f;
     bool piv_ok = lu_ok;
     if (lu_ok || fixed) {
       // q = W_d^-1 (g u), then p2 = W_1^-1 (g w) with W_1 = W_d - g u v^T
 #pragma unroll
       for (int i = 0; i < NS; ++i) qv[i] *= gf;
-      spa::solve<float>(w, dinv, qv);
+      spa::solve<float>(w, qv);
       piv_ok = rank1::denominator<float>(qv, vr, float(kPivTau), &inv_delta) && piv_ok;
-      spa::solve<float>(w, dinv, p2);
+      spa::solve<float>(w, p2);
       rank1::update<float>(qv, vr, inv_delta, p2);
       float s2 = 0.0f;
 #pragma unroll
@@ -296,10 +301,11 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
 #pragma unroll
           for (int i = 0; i < NS; ++i) b[i] = df_of(F0[i]);
         } else {
-          // evaluation point y + (h/2) k1 or y + h k2.  Stage 1 needs FP64
-          // only in the eight states of Eq. 7 (its Newton); its FP32 rates
+          // evaluation point y + (h/2) k1 or y + h k2.  Both need FP64 only
+          // in the eight states of Eq. 7 (its Newton); stage 1's FP32 rates
           // take y + (h/2) k1 in float.  Stage 2's point is the new state:
-          // all of it in FP64, and its float copy rounded from that.
+          // its float copy is rounded from the FP64 sum, which is formed
+          // again on acceptance rather than held through the stage.
           if (st == 1) {
             const double hs = 0.5 * hh;
             const float hsf = f32(hs);
@@ -314,11 +320,21 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
           } else {
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
-              y1[i] = fma(hh, f64(k2[i]), y[i]);
-              y1s[i] = f32(y1[i]);
+              const double yn = fma(hh, f64(k2[i]), y[i]);
+              if (in_eq7(i)) y1[i] = yn;
+              y1s[i] = f32(yn);
             }
           }
-          SHg = sh_guess(SH0, vsh, y, y1);
+          {
+            // tangent guess of the Eq. 7 root from the FP32 tangent and the
+            // step's increment (h/2 k1 or h k2): only Newton's start moves
+            const int hc[8] = {iS_va, iS_bu, iS_pro, iS_ac, iS_IC, iS_IN, iS_cat, iS_an};
+            float ds = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ds = fmaf(vr[k], st == 1 ? k1[hc[k]] : k2[hc[k]], ds);
+            const double g = fma(st == 1 ? 0.5 * hh : hh, f64(ds), SH0);
+            SHg = (g > 0.5 * SH0 && g < 2.0 * SH0) ? g : SH0;
+          }
           {
             float g2 = SH20;
 #pragma unroll
@@ -348,7 +364,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
         float x0[NS];
 #pragma unroll
         for (int i = 0; i < NS; ++i) x0[i] = b[i].hi;
-        wsolve(w, dinv, qv, vr, inv_delta, p2, zh, inv_delta2, x0);
+        wsolve(w, qv, vr, inv_delta, p2, zh, inv_delta2, x0);
         float xs[NS];
         {
           DF xp[NS], jx[NS];
@@ -375,7 +391,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
             const df ri = df_add(df_add_f(b[i], -x0[i]), df_mul(gd, jx[i].v()));
             r[i] = ri.hi + ri.lo;
           }
-          wsolve(w, dinv, qv, vr, inv_delta, p2, zh, inv_delta2, r);
+          wsolve(w, qv, vr, inv_delta, p2, zh, inv_delta2, r);
 #pragma unroll
           for (int i = 0; i < NS; ++i) xs[i] = x0[i] + r[i];
         }
@@ -412,7 +428,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
     if (accept) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
-        y[i] = y1[i];
+        y[i] = fma(hh, f64(k2[i]), y[i]);  // y + h k2, as at stage 2
         ys[i] = y1s[i];
       }
       y[iS_h2] = f64(SH2g);  // Eq. 8 root at the new state (last evaluation)

@@ -136,14 +136,13 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   g_ops = 0;
   sp::form_w<Fc>(w, Fc(1e-4));
   out[3] = g_ops;
-  Fc dinv[NS];
   g_ops = 0;
-  sp::factor<Fc>(w, dinv);
+  sp::factor<Fc>(w);
   out[4] = g_ops;
   Fc b[NS];
   for (int i = 0; i < NS; ++i) b[i] = Fc(1.0);
   g_ops = 0;
-  sp::solve<Fc>(w, dinv, b);
+  sp::solve<Fc>(w, b);
   out[5] = g_ops;
   {
     Fc x[NS], jx[NS];
@@ -156,7 +155,7 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
   Fc inv_delta;
   for (int i = 0; i < NS; ++i) u[i] = Fc(1.0);
   g_ops = 0;
-  rank1::setup<Fc>(w, dinv, Fc(1e-4), v, Fc(0.1), u, &inv_delta);
+  rank1::setup<Fc>(w, Fc(1e-4), v, Fc(0.1), u, &inv_delta);
   out[9] = g_ops - out[5];
   g_ops = 0;
   rank1::update<Fc>(u, v, inv_delta, b);
@@ -227,14 +226,13 @@ extern "C" chad_status chad_flop_counts(int64_t* out, int n) {
     g_ops = 0;
     spa::form_w<Fc>(wa, Fc(1e-4));
     out[19] = g_ops;
-    Fc dinva[NS];
     g_ops = 0;
-    spa::factor<Fc>(wa, dinva);
+    spa::factor<Fc>(wa);
     out[20] = g_ops;
     Fc ba[NS];
     for (int i = 0; i < NS; ++i) ba[i] = Fc(1.0);
     g_ops = 0;
-    spa::solve<Fc>(wa, dinva, ba);
+    spa::solve<Fc>(wa, ba);
     out[21] = g_ops;
   }
   return CHAD_OK;

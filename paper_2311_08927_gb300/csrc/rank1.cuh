@@ -45,10 +45,10 @@ CHAD_HD bool denominator(const R* q, const R* v, R tau, R* inv_delta) {
 // *inv_delta = 1/delta.  Returns false when delta fails the threshold test or
 // is not finite.
 template <class R, class LU = sp::Lu, class W>
-CHAD_HD bool setup(W w, const R* dinv, R g, const R* v, R tau, R* q, R* inv_delta) {
+CHAD_HD bool setup(W w, R g, const R* v, R tau, R* q, R* inv_delta) {
 #pragma unroll
   for (int i = 0; i < NS; ++i) q[i] *= g;
-  LU::template sub<R>(w, dinv, q);
+  LU::template sub<R>(w, q);
   const R s = vdot<R>(v, q);
   const R delta = R(1) - s;
   *inv_delta = rcp<R>(delta);

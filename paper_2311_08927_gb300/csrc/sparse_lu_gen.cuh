@@ -96,41 +96,43 @@ CHAD_HD void form_w(W w, R g) {
   w[202] += R(1);
 }
 
-// In-place LU; returns false if a pivot fails the threshold test.
+// In-place LU; the diagonal slots receive the reciprocals of the pivots
+// (the only use the solve makes of them).  Returns false if a pivot fails
+// the threshold test.
 template <class R, class W>
-CHAD_HD bool factor(W w, R* dinv) {
+CHAD_HD bool factor(W w) {
   using P = PivTest<R>;
   bool ok = true;
   {  // pivot 0: state 11 (S_I), 0 rows x 1 cols
     const R pv = w[0];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[0] = inv;
+    w[0] = inv;
   }
   {  // pivot 1: state 23 (X_I), 0 rows x 1 cols
     const R pv = w[2];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[1] = inv;
+    w[2] = inv;
   }
   {  // pivot 2: state 24 (S_cat), 0 rows x 0 cols
     const R pv = w[4];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[2] = inv;
+    w[4] = inv;
   }
   {  // pivot 3: state 25 (S_an), 0 rows x 0 cols
     const R pv = w[5];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[3] = inv;
+    w[5] = inv;
   }
   {  // pivot 4: state 13 (X_ch), 2 rows x 1 cols
     const R pv = w[6];
     const typename P::K cm = P::kmax(P::key(w[44]), P::key(w[70]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[4] = inv;
+    w[6] = inv;
     { const R l = w[44] * inv; w[44] = l;
       w[61] -= l * w[7];
     }
@@ -143,7 +145,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::key(w[45]), P::key(w[93]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[5] = inv;
+    w[8] = inv;
     { const R l = w[45] * inv; w[45] = l;
       w[61] -= l * w[9];
     }
@@ -156,7 +158,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::key(w[46]), P::key(w[71])), P::key(w[80]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[6] = inv;
+    w[10] = inv;
     { const R l = w[46] * inv; w[46] = l;
       w[61] -= l * w[11];
     }
@@ -172,7 +174,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::key(w[34]);
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[7] = inv;
+    w[12] = inv;
     { const R l = w[34] * inv; w[34] = l;
       w[37] -= l * w[13];
       w[38] -= l * w[14];
@@ -187,7 +189,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::key(w[23]), P::key(w[35])), P::key(w[161]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[8] = inv;
+    w[19] = inv;
     { const R l = w[23] * inv; w[23] = l;
       w[24] -= l * w[20];
       w[25] -= l * w[21];
@@ -209,7 +211,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::key(w[36]), P::key(w[47])), P::key(w[162]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[9] = inv;
+    w[24] = inv;
     { const R l = w[36] * inv; w[36] = l;
       w[39] -= l * w[25];
       w[40] -= l * w[26];
@@ -231,7 +233,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[37]), P::key(w[48])), P::key(w[98])), P::key(w[126])), P::key(w[181]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[10] = inv;
+    w[28] = inv;
     { const R l = w[37] * inv; w[37] = l;
       w[41] -= l * w[29];
       w[43] -= l * w[30];
@@ -258,7 +260,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[38]), P::key(w[49])), P::key(w[127])), P::key(w[163])), P::key(w[182]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[11] = inv;
+    w[31] = inv;
     { const R l = w[38] * inv; w[38] = l;
       w[42] -= l * w[32];
       w[43] -= l * w[33];
@@ -285,7 +287,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::key(w[50]), P::key(w[164]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[12] = inv;
+    w[39] = inv;
     { const R l = w[50] * inv; w[50] = l;
       w[51] -= l * w[40];
       w[59] -= l * w[41];
@@ -304,7 +306,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::key(w[165]);
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[13] = inv;
+    w[51] = inv;
     { const R l = w[165] * inv; w[165] = l;
       w[166] -= l * w[52];
       w[167] -= l * w[53];
@@ -328,7 +330,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[72]), P::key(w[99])), P::key(w[114])), P::key(w[128])), P::key(w[151])), P::key(w[166])), P::key(w[183]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[14] = inv;
+    w[67] = inv;
     { const R l = w[72] * inv; w[72] = l;
       w[73] -= l * w[68];
       w[75] -= l * w[69];
@@ -363,7 +365,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[100]), P::key(w[115])), P::key(w[129])), P::key(w[152])), P::key(w[167])), P::key(w[184]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[15] = inv;
+    w[73] = inv;
     { const R l = w[100] * inv; w[100] = l;
       w[108] -= l * w[74];
       w[112] -= l * w[75];
@@ -394,7 +396,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[81]), P::key(w[101])), P::key(w[130])), P::key(w[168])), P::key(w[185]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[16] = inv;
+    w[76] = inv;
     { const R l = w[81] * inv; w[81] = l;
       w[82] -= l * w[77];
       w[84] -= l * w[78];
@@ -426,7 +428,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::key(w[102]), P::key(w[131])), P::key(w[169])), P::key(w[186]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[17] = inv;
+    w[82] = inv;
     { const R l = w[102] * inv; w[102] = l;
       w[108] -= l * w[83];
       w[111] -= l * w[84];
@@ -453,7 +455,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[103]), P::key(w[116])), P::key(w[132])), P::key(w[170])), P::key(w[187]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[18] = inv;
+    w[86] = inv;
     { const R l = w[103] * inv; w[103] = l;
       w[107] -= l * w[87];
       w[111] -= l * w[88];
@@ -485,7 +487,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[94]), P::key(w[104])), P::key(w[117])), P::key(w[133])), P::key(w[143])), P::key(w[153])), P::key(w[171])), P::key(w[188]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[19] = inv;
+    w[90] = inv;
     { const R l = w[94] * inv; w[94] = l;
       w[95] -= l * w[91];
       w[97] -= l * w[92];
@@ -524,7 +526,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[105]), P::key(w[118])), P::key(w[134])), P::key(w[144])), P::key(w[154])), P::key(w[172])), P::key(w[189]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[20] = inv;
+    w[95] = inv;
     { const R l = w[105] * inv; w[105] = l;
       w[108] -= l * w[96];
       w[112] -= l * w[97];
@@ -559,7 +561,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::key(w[135]), P::key(w[173])), P::key(w[190]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[21] = inv;
+    w[106] = inv;
     { const R l = w[135] * inv; w[135] = l;
       w[136] -= l * w[107];
       w[137] -= l * w[108];
@@ -593,7 +595,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::key(w[136]), P::key(w[174])), P::key(w[191]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[22] = inv;
+    w[119] = inv;
     { const R l = w[136] * inv; w[136] = l;
       w[137] -= l * w[120];
       w[138] -= l * w[121];
@@ -624,7 +626,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::key(w[145]), P::key(w[155])), P::key(w[175])), P::key(w[192]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[23] = inv;
+    w[137] = inv;
     { const R l = w[145] * inv; w[145] = l;
       w[146] -= l * w[138];
       w[147] -= l * w[139];
@@ -659,7 +661,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::key(w[156]), P::key(w[176])), P::key(w[193])), P::key(w[198]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[24] = inv;
+    w[146] = inv;
     { const R l = w[156] * inv; w[156] = l;
       w[157] -= l * w[147];
       w[158] -= l * w[148];
@@ -690,7 +692,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::key(w[177]), P::key(w[194])), P::key(w[199]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[25] = inv;
+    w[157] = inv;
     { const R l = w[177] * inv; w[177] = l;
       w[178] -= l * w[158];
       w[179] -= l * w[159];
@@ -712,7 +714,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::key(w[195]), P::key(w[200]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[26] = inv;
+    w[178] = inv;
     { const R l = w[195] * inv; w[195] = l;
       w[196] -= l * w[179];
       w[197] -= l * w[180];
@@ -727,7 +729,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::key(w[201]);
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[27] = inv;
+    w[196] = inv;
     { const R l = w[201] * inv; w[201] = l;
       w[202] -= l * w[197];
     }
@@ -736,14 +738,14 @@ CHAD_HD bool factor(W w, R* dinv) {
     const R pv = w[202];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[28] = inv;
+    w[202] = inv;
   }
   return ok;
 }
 
 // Solve W x = b in place (b indexed by state).
 template <class R, class W>
-CHAD_HD void solve(W w, const R* dinv, R* b) {
+CHAD_HD void solve(W w, R* b) {
   R z0 = b[11];
   R z1 = b[23];
   R z2 = b[24];
@@ -862,34 +864,34 @@ CHAD_HD void solve(W w, const R* dinv, R* b) {
   z28 -= w[199] * z25;
   z28 -= w[200] * z26;
   z28 -= w[201] * z27;
-  z28 *= dinv[28];
+  z28 *= w[202];
   z27 -= w[197] * z28;
-  z27 *= dinv[27];
+  z27 *= w[196];
   z26 -= w[179] * z27;
   z26 -= w[180] * z28;
-  z26 *= dinv[26];
+  z26 *= w[178];
   z25 -= w[158] * z26;
   z25 -= w[159] * z27;
   z25 -= w[160] * z28;
-  z25 *= dinv[25];
+  z25 *= w[157];
   z24 -= w[147] * z25;
   z24 -= w[148] * z26;
   z24 -= w[149] * z27;
   z24 -= w[150] * z28;
-  z24 *= dinv[24];
+  z24 *= w[146];
   z23 -= w[138] * z24;
   z23 -= w[139] * z25;
   z23 -= w[140] * z26;
   z23 -= w[141] * z27;
   z23 -= w[142] * z28;
-  z23 *= dinv[23];
+  z23 *= w[137];
   z22 -= w[120] * z23;
   z22 -= w[121] * z24;
   z22 -= w[122] * z25;
   z22 -= w[123] * z26;
   z22 -= w[124] * z27;
   z22 -= w[125] * z28;
-  z22 *= dinv[22];
+  z22 *= w[119];
   z21 -= w[107] * z22;
   z21 -= w[108] * z23;
   z21 -= w[109] * z24;
@@ -897,31 +899,31 @@ CHAD_HD void solve(W w, const R* dinv, R* b) {
   z21 -= w[111] * z26;
   z21 -= w[112] * z27;
   z21 -= w[113] * z28;
-  z21 *= dinv[21];
+  z21 *= w[106];
   z20 -= w[96] * z23;
   z20 -= w[97] * z27;
-  z20 *= dinv[20];
+  z20 *= w[95];
   z19 -= w[91] * z20;
   z19 -= w[92] * z27;
-  z19 *= dinv[19];
+  z19 *= w[90];
   z18 -= w[87] * z22;
   z18 -= w[88] * z26;
   z18 -= w[89] * z27;
-  z18 *= dinv[18];
+  z18 *= w[86];
   z17 -= w[83] * z23;
   z17 -= w[84] * z26;
   z17 -= w[85] * z27;
-  z17 *= dinv[17];
+  z17 *= w[82];
   z16 -= w[77] * z17;
   z16 -= w[78] * z26;
   z16 -= w[79] * z27;
-  z16 *= dinv[16];
+  z16 *= w[76];
   z15 -= w[74] * z23;
   z15 -= w[75] * z27;
-  z15 *= dinv[15];
+  z15 *= w[73];
   z14 -= w[68] * z15;
   z14 -= w[69] * z27;
-  z14 *= dinv[14];
+  z14 *= w[67];
   z13 -= w[52] * z14;
   z13 -= w[53] * z15;
   z13 -= w[54] * z16;
@@ -937,45 +939,45 @@ CHAD_HD void solve(W w, const R* dinv, R* b) {
   z13 -= w[64] * z26;
   z13 -= w[65] * z27;
   z13 -= w[66] * z28;
-  z13 *= dinv[13];
+  z13 *= w[51];
   z12 -= w[40] * z13;
   z12 -= w[41] * z21;
   z12 -= w[42] * z26;
   z12 -= w[43] * z27;
-  z12 *= dinv[12];
+  z12 *= w[39];
   z11 -= w[32] * z26;
   z11 -= w[33] * z27;
-  z11 *= dinv[11];
+  z11 *= w[31];
   z10 -= w[29] * z21;
   z10 -= w[30] * z27;
-  z10 *= dinv[10];
+  z10 *= w[28];
   z9 -= w[25] * z12;
   z9 -= w[26] * z13;
   z9 -= w[27] * z26;
-  z9 *= dinv[9];
+  z9 *= w[24];
   z8 -= w[20] * z9;
   z8 -= w[21] * z12;
   z8 -= w[22] * z26;
-  z8 *= dinv[8];
+  z8 *= w[19];
   z7 -= w[13] * z10;
   z7 -= w[14] * z11;
   z7 -= w[15] * z12;
   z7 -= w[16] * z21;
   z7 -= w[17] * z26;
   z7 -= w[18] * z27;
-  z7 *= dinv[7];
+  z7 *= w[12];
   z6 -= w[11] * z23;
-  z6 *= dinv[6];
+  z6 *= w[10];
   z5 -= w[9] * z23;
-  z5 *= dinv[5];
+  z5 *= w[8];
   z4 -= w[7] * z23;
-  z4 *= dinv[4];
-  z3 *= dinv[3];
-  z2 *= dinv[2];
+  z4 *= w[6];
+  z3 *= w[5];
+  z2 *= w[4];
   z1 -= w[3] * z23;
-  z1 *= dinv[1];
+  z1 *= w[2];
   z0 -= w[1] * z23;
-  z0 *= dinv[0];
+  z0 *= w[0];
   b[11] = z0;
   b[23] = z1;
   b[24] = z2;
@@ -1018,9 +1020,9 @@ struct Lu {
   template <class R, class W>
   static CHAD_HD void form(W w, R g) { form_w<R>(w, g); }
   template <class R, class W>
-  static CHAD_HD bool lu(W w, R* dinv) { return factor<R>(w, dinv); }
+  static CHAD_HD bool lu(W w) { return factor<R>(w); }
   template <class R, class W>
-  static CHAD_HD void sub(W w, const R* dinv, R* b) { solve<R>(w, dinv, b); }
+  static CHAD_HD void sub(W w, R* b) { solve<R>(w, b); }
 };
 
 }  // namespace sp

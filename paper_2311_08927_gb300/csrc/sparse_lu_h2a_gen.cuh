@@ -98,41 +98,43 @@ CHAD_HD void form_w(W w, R g) {
   w[166] += R(1);
 }
 
-// In-place LU; returns false if a pivot fails the threshold test.
+// In-place LU; the diagonal slots receive the reciprocals of the pivots
+// (the only use the solve makes of them).  Returns false if a pivot fails
+// the threshold test.
 template <class R, class W>
-CHAD_HD bool factor(W w, R* dinv) {
+CHAD_HD bool factor(W w) {
   using P = PivTest<R>;
   bool ok = true;
   {  // pivot 0: state 11 (S_I), 0 rows x 1 cols
     const R pv = w[0];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[0] = inv;
+    w[0] = inv;
   }
   {  // pivot 1: state 23 (X_I), 0 rows x 1 cols
     const R pv = w[2];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[1] = inv;
+    w[2] = inv;
   }
   {  // pivot 2: state 24 (S_cat), 0 rows x 0 cols
     const R pv = w[4];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[2] = inv;
+    w[4] = inv;
   }
   {  // pivot 3: state 25 (S_an), 0 rows x 0 cols
     const R pv = w[5];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[3] = inv;
+    w[5] = inv;
   }
   {  // pivot 4: state 13 (X_ch), 2 rows x 1 cols
     const R pv = w[6];
     const typename P::K cm = P::kmax(P::key(w[37]), P::key(w[75]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[4] = inv;
+    w[6] = inv;
     { const R l = w[37] * inv; w[37] = l;
       w[53] -= l * w[7];
     }
@@ -145,7 +147,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::key(w[38]), P::key(w[84]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[5] = inv;
+    w[8] = inv;
     { const R l = w[38] * inv; w[38] = l;
       w[53] -= l * w[9];
     }
@@ -158,7 +160,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::key(w[39]), P::key(w[64])), P::key(w[76]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[6] = inv;
+    w[10] = inv;
     { const R l = w[39] * inv; w[39] = l;
       w[53] -= l * w[11];
     }
@@ -174,7 +176,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::key(w[14]), P::key(w[40])), P::key(w[115])), P::key(w[147]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[7] = inv;
+    w[12] = inv;
     { const R l = w[14] * inv; w[14] = l;
       w[19] -= l * w[13];
     }
@@ -193,7 +195,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::key(w[23]);
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[8] = inv;
+    w[15] = inv;
     { const R l = w[23] * inv; w[23] = l;
       w[25] -= l * w[16];
       w[27] -= l * w[17];
@@ -206,7 +208,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::key(w[24]), P::key(w[30]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[9] = inv;
+    w[20] = inv;
     { const R l = w[24] * inv; w[24] = l;
       w[25] -= l * w[21];
       w[26] -= l * w[22];
@@ -221,7 +223,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::key(w[31]);
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[10] = inv;
+    w[25] = inv;
     { const R l = w[31] * inv; w[31] = l;
       w[32] -= l * w[26];
       w[34] -= l * w[27];
@@ -234,7 +236,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::key(w[41]);
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[11] = inv;
+    w[32] = inv;
     { const R l = w[41] * inv; w[41] = l;
       w[42] -= l * w[33];
       w[43] -= l * w[34];
@@ -246,14 +248,14 @@ CHAD_HD bool factor(W w, R* dinv) {
     const R pv = w[42];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[12] = inv;
+    w[42] = inv;
   }
   {  // pivot 13: state 21 (X_ac), 3 rows x 2 cols
     const R pv = w[58];
     const typename P::K cm = P::kmax(P::kmax(P::key(w[89]), P::key(w[116])), P::key(w[148]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[13] = inv;
+    w[58] = inv;
     { const R l = w[89] * inv; w[89] = l;
       w[97] -= l * w[59];
       w[102] -= l * w[60];
@@ -272,7 +274,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::key(w[65]), P::key(w[90])), P::key(w[117])), P::key(w[149]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[14] = inv;
+    w[61] = inv;
     { const R l = w[65] * inv; w[65] = l;
       w[66] -= l * w[62];
       w[68] -= l * w[63];
@@ -295,7 +297,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::key(w[91]), P::key(w[118])), P::key(w[150]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[15] = inv;
+    w[66] = inv;
     { const R l = w[91] * inv; w[91] = l;
       w[99] -= l * w[67];
       w[102] -= l * w[68];
@@ -314,7 +316,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::key(w[92]), P::key(w[104])), P::key(w[119])), P::key(w[151]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[16] = inv;
+    w[69] = inv;
     { const R l = w[92] * inv; w[92] = l;
       w[98] -= l * w[70];
       w[102] -= l * w[71];
@@ -337,7 +339,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[77]), P::key(w[93])), P::key(w[105])), P::key(w[120])), P::key(w[138])), P::key(w[152]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[17] = inv;
+    w[72] = inv;
     { const R l = w[77] * inv; w[77] = l;
       w[78] -= l * w[73];
       w[80] -= l * w[74];
@@ -368,7 +370,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[94]), P::key(w[106])), P::key(w[121])), P::key(w[139])), P::key(w[153]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[18] = inv;
+    w[78] = inv;
     { const R l = w[94] * inv; w[94] = l;
       w[99] -= l * w[79];
       w[102] -= l * w[80];
@@ -395,7 +397,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[85]), P::key(w[95])), P::key(w[107])), P::key(w[122])), P::key(w[131])), P::key(w[140])), P::key(w[154]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[19] = inv;
+    w[81] = inv;
     { const R l = w[85] * inv; w[85] = l;
       w[86] -= l * w[82];
       w[88] -= l * w[83];
@@ -430,7 +432,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::kmax(P::kmax(P::kmax(P::key(w[96]), P::key(w[108])), P::key(w[123])), P::key(w[132])), P::key(w[141])), P::key(w[155]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[20] = inv;
+    w[86] = inv;
     { const R l = w[96] * inv; w[96] = l;
       w[99] -= l * w[87];
       w[102] -= l * w[88];
@@ -461,7 +463,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::key(w[124]), P::key(w[156]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[21] = inv;
+    w[97] = inv;
     { const R l = w[124] * inv; w[124] = l;
       w[125] -= l * w[98];
       w[126] -= l * w[99];
@@ -484,7 +486,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::key(w[125]), P::key(w[157]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[22] = inv;
+    w[109] = inv;
     { const R l = w[125] * inv; w[125] = l;
       w[126] -= l * w[110];
       w[127] -= l * w[111];
@@ -505,7 +507,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::key(w[133]), P::key(w[142])), P::key(w[158]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[23] = inv;
+    w[126] = inv;
     { const R l = w[133] * inv; w[133] = l;
       w[134] -= l * w[127];
       w[135] -= l * w[128];
@@ -530,7 +532,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::kmax(P::key(w[143]), P::key(w[159])), P::key(w[163]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[24] = inv;
+    w[134] = inv;
     { const R l = w[143] * inv; w[143] = l;
       w[144] -= l * w[135];
       w[145] -= l * w[136];
@@ -552,7 +554,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::kmax(P::key(w[160]), P::key(w[164]));
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[25] = inv;
+    w[144] = inv;
     { const R l = w[160] * inv; w[160] = l;
       w[161] -= l * w[145];
       w[162] -= l * w[146];
@@ -567,7 +569,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const typename P::K cm = P::key(w[165]);
     ok = ok && P::good(P::key(pv), cm);
     const R inv = rcp<R>(pv);
-    dinv[26] = inv;
+    w[161] = inv;
     { const R l = w[165] * inv; w[165] = l;
       w[166] -= l * w[162];
     }
@@ -576,7 +578,7 @@ CHAD_HD bool factor(W w, R* dinv) {
     const R pv = w[166];
     ok = ok && P::good(P::key(pv));
     const R inv = rcp<R>(pv);
-    dinv[27] = inv;
+    w[166] = inv;
   }
   return ok;
 }
@@ -584,7 +586,7 @@ CHAD_HD bool factor(W w, R* dinv) {
 // Solve W x = b in place (b indexed by state; b[S_h2] is left as it is:
 // W_d's S_h2 row is the identity's).
 template <class R, class W>
-CHAD_HD void solve(W w, const R* dinv, R* b) {
+CHAD_HD void solve(W w, R* b) {
   R z0 = b[11];
   R z1 = b[23];
   R z2 = b[24];
@@ -680,58 +682,58 @@ CHAD_HD void solve(W w, const R* dinv, R* b) {
   z27 -= w[163] * z24;
   z27 -= w[164] * z25;
   z27 -= w[165] * z26;
-  z27 *= dinv[27];
+  z27 *= w[166];
   z26 -= w[162] * z27;
-  z26 *= dinv[26];
+  z26 *= w[161];
   z25 -= w[145] * z26;
   z25 -= w[146] * z27;
-  z25 *= dinv[25];
+  z25 *= w[144];
   z24 -= w[135] * z25;
   z24 -= w[136] * z26;
   z24 -= w[137] * z27;
-  z24 *= dinv[24];
+  z24 *= w[134];
   z23 -= w[127] * z24;
   z23 -= w[128] * z25;
   z23 -= w[129] * z26;
   z23 -= w[130] * z27;
-  z23 *= dinv[23];
+  z23 *= w[126];
   z22 -= w[110] * z23;
   z22 -= w[111] * z24;
   z22 -= w[112] * z25;
   z22 -= w[113] * z26;
   z22 -= w[114] * z27;
-  z22 *= dinv[22];
+  z22 *= w[109];
   z21 -= w[98] * z22;
   z21 -= w[99] * z23;
   z21 -= w[100] * z24;
   z21 -= w[101] * z25;
   z21 -= w[102] * z26;
   z21 -= w[103] * z27;
-  z21 *= dinv[21];
+  z21 *= w[97];
   z20 -= w[87] * z23;
   z20 -= w[88] * z26;
-  z20 *= dinv[20];
+  z20 *= w[86];
   z19 -= w[82] * z20;
   z19 -= w[83] * z26;
-  z19 *= dinv[19];
+  z19 *= w[81];
   z18 -= w[79] * z23;
   z18 -= w[80] * z26;
-  z18 *= dinv[18];
+  z18 *= w[78];
   z17 -= w[73] * z18;
   z17 -= w[74] * z26;
-  z17 *= dinv[17];
+  z17 *= w[72];
   z16 -= w[70] * z22;
   z16 -= w[71] * z26;
-  z16 *= dinv[16];
+  z16 *= w[69];
   z15 -= w[67] * z23;
   z15 -= w[68] * z26;
-  z15 *= dinv[15];
+  z15 *= w[66];
   z14 -= w[62] * z15;
   z14 -= w[63] * z26;
-  z14 *= dinv[14];
+  z14 *= w[61];
   z13 -= w[59] * z21;
   z13 -= w[60] * z26;
-  z13 *= dinv[13];
+  z13 *= w[58];
   z12 -= w[43] * z13;
   z12 -= w[44] * z14;
   z12 -= w[45] * z15;
@@ -747,39 +749,39 @@ CHAD_HD void solve(W w, const R* dinv, R* b) {
   z12 -= w[55] * z25;
   z12 -= w[56] * z26;
   z12 -= w[57] * z27;
-  z12 *= dinv[12];
+  z12 *= w[42];
   z11 -= w[33] * z12;
   z11 -= w[34] * z13;
   z11 -= w[35] * z21;
   z11 -= w[36] * z26;
-  z11 *= dinv[11];
+  z11 *= w[32];
   z10 -= w[26] * z11;
   z10 -= w[27] * z13;
   z10 -= w[28] * z21;
   z10 -= w[29] * z26;
-  z10 *= dinv[10];
+  z10 *= w[25];
   z9 -= w[21] * z10;
   z9 -= w[22] * z11;
-  z9 *= dinv[9];
+  z9 *= w[20];
   z8 -= w[16] * z10;
   z8 -= w[17] * z13;
   z8 -= w[18] * z21;
   z8 -= w[19] * z26;
-  z8 *= dinv[8];
+  z8 *= w[15];
   z7 -= w[13] * z26;
-  z7 *= dinv[7];
+  z7 *= w[12];
   z6 -= w[11] * z23;
-  z6 *= dinv[6];
+  z6 *= w[10];
   z5 -= w[9] * z23;
-  z5 *= dinv[5];
+  z5 *= w[8];
   z4 -= w[7] * z23;
-  z4 *= dinv[4];
-  z3 *= dinv[3];
-  z2 *= dinv[2];
+  z4 *= w[6];
+  z3 *= w[5];
+  z2 *= w[4];
   z1 -= w[3] * z23;
-  z1 *= dinv[1];
+  z1 *= w[2];
   z0 -= w[1] * z23;
-  z0 *= dinv[0];
+  z0 *= w[0];
   b[11] = z0;
   b[23] = z1;
   b[24] = z2;
@@ -821,9 +823,9 @@ struct Lu {
   template <class R, class W>
   static CHAD_HD void form(W w, R g) { form_w<R>(w, g); }
   template <class R, class W>
-  static CHAD_HD bool lu(W w, R* dinv) { return factor<R>(w, dinv); }
+  static CHAD_HD bool lu(W w) { return factor<R>(w); }
   template <class R, class W>
-  static CHAD_HD void sub(W w, const R* dinv, R* b) { solve<R>(w, dinv, b); }
+  static CHAD_HD void sub(W w, R* b) { solve<R>(w, b); }
 };
 
 }  // namespace spa

@@ -56,6 +56,17 @@ struct Cnt {
   int acc, rej, newton, fallback, failed, pivot, redo, h2;
 };
 
+// The digester constants are read where they are used: an opaque copy of
+// their pointer before each evaluation keeps the compiler from hoisting the
+// loaded constants out of the stage loop and holding them through the LU
+// and the solves (they are the same for every lane of a digester, and the
+// loads come back from L1).
+template <class T>
+__device__ __forceinline__ const T* reread(const T* p) {
+  asm volatile("" : "+l"(p));
+  return p;
+}
+
 __device__ __forceinline__ int64_t queue_pop(unsigned long long* q) {
   const unsigned m = __activemask();
   const int lane = threadIdx.x & 31;

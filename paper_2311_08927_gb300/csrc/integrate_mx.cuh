@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
     }
     // roots, rates, J_d and u at y (all FP32 but the Eq. 7 Newton)
     AcidBase ab0;
-    roots(*c, *cf, q, qf, y, ys, Df, SHg, SH2g, a.max_newton, cnt, ab0);
+    roots(*reread(c), *reread(cf), q, qf, y, ys, Df, SHg, SH2g, a.max_newton, cnt, ab0);
     {
       // the rate partials are recomputed for each refinement residual
       // (from ys and ab0) rather than kept across the stages
@@ -342,9 +342,9 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
             SH2g = (g2 > 0.5f * SH20 && g2 < 2.0f * SH20) ? g2 : SH20;
           }
           AcidBase ab;
-          roots(*c, *cf, q, qf, y1, y1s, Df, SHg, SH2g, a.max_newton, cnt, ab);
+          roots(*reread(c), *reread(cf), q, qf, y1, y1s, Df, SHg, SH2g, a.max_newton, cnt, ab);
           float Fs[NS];
-          rates_f32(*cf, qf, y1s, Df, ab, Fs);
+          rates_f32(*reread(cf), qf, y1s, Df, ab, Fs);
           if (st == 1) {
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
@@ -382,8 +382,9 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
             for (int k = 0; k < 8; ++k) sv = sv + vr[k] * xp[hc[k]];
           }
           Rates<float> ko;
-          rates<float, true>(*cf, qf, ys, ab0, ko);
-          jvp<float, DF, DigConstF, float>(*cf, ys, Df, ko, xp, sv, jx);
+          const DigConstF& cfr = *reread(cf);
+          rates<float, true>(cfr, qf, ys, ab0, ko);
+          jvp<float, DF, DigConstF, float>(cfr, ys, Df, ko, xp, sv, jx);
           jx[iS_h2] = DF(0.0f);
           float r[NS];
 #pragma unroll

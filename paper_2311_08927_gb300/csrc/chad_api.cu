@@ -845,6 +845,7 @@ static cudaError_t enqueue_interval(chad_ctx* c, double dt_days, int variant, cu
   a.order = nullptr;
   a.SH_learned = learned_now ? c->d_SH_learned : nullptr;
   a.h_learned = learned_now ? c->d_h_learned : nullptr;
+  a.n_dig = c->n_dig;
   cudaError_t e;
   if (learned_now) {
     const float* P = c->d_mlp;

@@ -37,6 +37,13 @@
 namespace chad {
 namespace integ {
 
+// an opaque copy of an index (a digester's): loads through it are not
+// hoisted out of the loop they are in
+__device__ __forceinline__ int reread_i(int i) {
+  asm volatile("" : "+r"(i));
+  return i;
+}
+
 // the eight states that enter Eq. 7
 __host__ __device__ constexpr bool in_eq7(int i) {
   return i == iS_va || i == iS_bu || i == iS_pro || i == iS_ac || i == iS_IC || i == iS_IN ||
@@ -126,7 +133,11 @@ __device__ __forceinline__ void wsolve(W w, const float* qv,
   for (int i = 0; i < NS; ++i) x[i] = fmaf(s2, p2[i], x[i]);
 }
 
-template <int BS, int MINB, bool WS>
+// IDX: contexts with more than one digester, whose warps hold particles of
+// several digesters (the queue refills lanes one by one); there the
+// per-thread-array shapes re-read the digester constants through an opaque
+// copy of the digester index.
+template <int BS, int MINB, bool WS, bool IDX>
 __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
   __shared__ unsigned long long s_acc, s_rej, s_newton, s_fb, s_piv, s_redo, s_h2;
   __shared__ int s_min, s_max;
@@ -153,6 +164,22 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
   int64_t p = -1;
   const DigConst* c = nullptr;
   const DigConstF* cf = nullptr;
+  int dg = 0;  // digester of the particle
+  // The digester constants, read again before each evaluation (see reread)
+  // through an opaque copy of their pointer, or with IDX (several
+  // digesters) and W_d in per-thread arrays of the digester index: the two
+  // compile to different code, and measured on 64 digesters (one interval
+  // pair of the 128-thread shape) the index copy took 1,141 ms against
+  // 2,517 ms, while on one digester the pointer copy with W_d in shared
+  // memory was the fastest shape.
+  auto dcn = [&]() -> const DigConst& {
+    if constexpr (IDX && !WS) return a.dc[reread_i(dg)];
+    else return *reread(c);
+  };
+  auto dcfn = [&]() -> const DigConstF& {
+    if constexpr (IDX && !WS) return a.dcf[reread_i(dg)];
+    else return *reread(cf);
+  };
   PartConst q;
   PartConstF qf;
   double SHg = 0.0, h = 0.0, t = 0.0;
@@ -178,8 +205,9 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
     if (p < 0) continue;
     if (fresh) {
       cnt = Cnt{0, 0, 0, 0, 0, 0, 0, 0};
-      c = &a.dc[a.dig[p]];
-      cf = &a.dcf[a.dig[p]];
+      dg = a.dig[p];
+      c = &a.dc[dg];
+      cf = &a.dcf[dg];
       pc_load(a.pc, a.ld, p, q);
       narrow_pc(q, qf);
 #pragma unroll
@@ -226,7 +254,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
     }
     // roots, rates, J_d and u at y (all FP32 but the Eq. 7 Newton)
     AcidBase ab0;
-    roots(*reread(c), *reread(cf), q, qf, y, ys, Df, SHg, SH2g, a.max_newton, cnt, ab0);
+    roots(dcn(), dcfn(), q, qf, y, ys, Df, SHg, SH2g, a.max_newton, cnt, ab0);
     {
       // the rate partials are recomputed for each refinement residual
       // (from ys and ab0) rather than kept across the stages
@@ -342,9 +370,9 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
             SH2g = (g2 > 0.5f * SH20 && g2 < 2.0f * SH20) ? g2 : SH20;
           }
           AcidBase ab;
-          roots(*reread(c), *reread(cf), q, qf, y1, y1s, Df, SHg, SH2g, a.max_newton, cnt, ab);
+          roots(dcn(), dcfn(), q, qf, y1, y1s, Df, SHg, SH2g, a.max_newton, cnt, ab);
           float Fs[NS];
-          rates_f32(*reread(cf), qf, y1s, Df, ab, Fs);
+          rates_f32(dcfn(), qf, y1s, Df, ab, Fs);
           if (st == 1) {
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
@@ -382,7 +410,7 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
             for (int k = 0; k < 8; ++k) sv = sv + vr[k] * xp[hc[k]];
           }
           Rates<float> ko;
-          const DigConstF& cfr = *reread(cf);
+          const DigConstF& cfr = dcfn();
           rates<float, true>(cfr, qf, ys, ab0, ko);
           jvp<float, DF, DigConstF, float>(cfr, ys, Df, ko, xp, sv, jx);
           jx[iS_h2] = DF(0.0f);
@@ -516,8 +544,8 @@ __global__ void __launch_bounds__(BS, MINB) integrate_mx_kernel(StepArgs a) {
 
 }  // namespace integ
 
-template <int BS, int MINB, bool WS>
-cudaError_t launch_variant_mx(const StepArgs& a, cudaStream_t s) {
+template <int BS, int MINB, bool WS, bool IDX>
+cudaError_t launch_variant_mx_k(const StepArgs& a, cudaStream_t s) {
   constexpr size_t smem = integ::wstore_smem_bytes<float, BS, WS, spa::kNNZ>();
   static int per_sm = -1, sms = 0;
   if (per_sm < 0) {
@@ -525,12 +553,12 @@ cudaError_t launch_variant_mx(const StepArgs& a, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (smem > 0) {
-      cudaError_t e = cudaFuncSetAttribute(integ::integrate_mx_kernel<BS, MINB, WS>,
+      cudaError_t e = cudaFuncSetAttribute(integ::integrate_mx_kernel<BS, MINB, WS, IDX>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integ::integrate_mx_kernel<BS, MINB, WS>,
-                                                  BS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, integ::integrate_mx_kernel<BS, MINB, WS, IDX>, BS, smem);
     if (per_sm < 1) per_sm = 1;
   }
   int64_t blocks = (int64_t)sms * per_sm;
@@ -538,8 +566,14 @@ cudaError_t launch_variant_mx(const StepArgs& a, cudaStream_t s) {
   if (need < blocks) blocks = need;
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  integ::integrate_mx_kernel<BS, MINB, WS><<<(unsigned)blocks, BS, smem, s>>>(a);
+  integ::integrate_mx_kernel<BS, MINB, WS, IDX><<<(unsigned)blocks, BS, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int BS, int MINB, bool WS>
+cudaError_t launch_variant_mx(const StepArgs& a, cudaStream_t s) {
+  return a.n_dig > 1 ? launch_variant_mx_k<BS, MINB, WS, true>(a, s)
+                     : launch_variant_mx_k<BS, MINB, WS, false>(a, s);
 }
 
 }  // namespace chad

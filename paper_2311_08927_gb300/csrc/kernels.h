@@ -42,6 +42,7 @@ struct StepArgs {
   const int* order;           // [n] queue position -> particle (null: identity)
   const double* SH_learned;   // learned guesses for particles without history (or null)
   const double* h_learned;
+  int n_dig;                  // digesters of the context
 };
 
 struct AdvectArgs {

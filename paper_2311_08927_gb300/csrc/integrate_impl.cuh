@@ -742,6 +742,18 @@ cudaError_t launch_variant(const StepArgs& a, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integ::integrate_kernel<FORM, BS, MINB, WS>,
                                                   BS, smem);
     if (per_sm < 1) per_sm = 1;
+    // the smallest shared carve-out that holds the resident blocks' tiles
+    // (none without a tile): the rest of the unified array is L1 for the
+    // spilled per-thread state, whatever kernels ran before (a large-tile
+    // kernel otherwise leaves the shared share large)
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const long long need = smem > 0 ? (long long)per_sm * ((long long)smem + 2048) : 0;
+    const int pct = smem_sm > 0 ? (int)((need * 100 + smem_sm - 1) / smem_sm) : 100;
+    cudaError_t e = cudaFuncSetAttribute(integ::integrate_kernel<FORM, BS, MINB, WS>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         pct < 100 ? pct : 100);
+    if (e != cudaSuccess) return e;
   }
   int64_t blocks = (int64_t)sms * per_sm;
   const int64_t need = (a.n + BS - 1) / BS;

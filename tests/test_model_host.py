@@ -160,3 +160,40 @@ def test_matrix_free_jacobian_vector_product():
         ref = Jo @ x
         sc = np.abs(Jo) @ np.abs(x) + 1e-300
         assert np.max(np.abs(Jx - ref) / sc) < 1e-12
+
+
+def test_flop_counts_of_the_reduced_lu_follow_the_generator():
+    """The operation counter, run over the library's own templated LU code,
+    agrees with the generator's static counts for both LUs, and the
+    per-attempt counts of the forms with S_h2 algebraic use the 28-state LU
+    (the FP64 form's count is the FP64 form 0's minus the LU savings plus its
+    Eq. 8 work, counted per coefficient set and per extra solve)."""
+    sys.path.insert(0, os.path.join(ROOT, "paper_2311_08927_gb300", "csrc"))
+    import gen_sparse as G
+    pat = G.jacobian_pattern()
+    src_full, full = G.generate(pat, False)
+    src_red, red = G.generate(pat, True)
+    f = CH.flop_counts()
+    assert f["solve"] == full["solve"] and f["solve_h2a"] == red["solve"]
+    # the counter also counts the threshold test's 0.1 x max of every pivot
+    # with a sub-column, which the generator's static count leaves out
+    tests = "ok = ok && P::good(P::key(pv), cm);"
+    assert f["factor"] - full["factor"] == src_full.count(tests)
+    assert f["factor_h2a"] - red["factor"] == src_red.count(tests)
+    assert f["form_w_h2a"] < f["form_w"]
+    mx = CH.attempt_flops_h2_mixed()
+    # 8 solves, one LU and one W formation of the 28-state LU in form 4
+    lu_saving = (f["form_w"] - f["form_w_h2a"]) + (f["factor"] - f["factor_h2a"]) + \
+        8 * (f["solve"] - f["solve_h2a"])
+    full_lu = (f["rates_fj"] + 2 * f["rates_f"] + f["form_w"] + f["factor"] + 8 * f["solve"] +
+               f["sm_setup"] + 7 * f["sm_update"] + 3 * f["h2_coeffs"] + 3 * f["jx_twofloat"] +
+               3 * f["rates_partials"] + f["mx_fp32_extra"])
+    assert mx["fp32"] == full_lu - lu_saving
+    f3 = CH.attempt_flops(CH.PREC_FP64, True)
+    f0 = CH.attempt_flops(CH.PREC_FP64, False)
+    assert f3["fp64_per_h2_iter"] == f["h2_iter"]
+    extra = f3["fp64"] - f0["fp64"]
+    expect = (-(f["factor"] - f["factor_h2a"]) - 1            # LU; one diagonal one fewer
+              + 5 * f["solve_h2a"] - 4 * f["solve"]          # the p2 solve, smaller solves
+              + f["sm_update"] + 3 * f["h2_coeffs"] + 59 + 54 + 3 * 117 + 2 * 58)
+    assert extra == expect

@@ -197,3 +197,97 @@ def test_flop_counts_of_the_reduced_lu_follow_the_generator():
               + 5 * f["solve_h2a"] - 4 * f["solve"]          # the p2 solve, smaller solves
               + f["sm_update"] + 3 * f["h2_coeffs"] + 59 + 54 + 3 * 117 + 2 * 58)
     assert extra == expect
+
+
+def _run_generated_lu(src, nnz, slot, W_vals, g, b):
+    """Execute the generated form_w / factor / solve of one LU header on the
+    host, statement by statement (the emitted code is straight-line with
+    literal slot indices), in float64."""
+    import re
+    w = np.array(W_vals, dtype=np.float64)
+    # form_w: w = -g w, then the diagonal ones
+    body = src[src.index("CHAD_HD void form_w("):src.index("// In-place LU")]
+    w *= -g
+    for m in re.finditer(r"w\[(\d+)\] \+= R\(1\);", body):
+        w[int(m.group(1))] += 1.0
+    body = src[src.index("CHAD_HD bool factor("):src.index("return ok;")]
+    inv = l = None
+    for line in body.splitlines():
+        line = line.strip()
+        m = re.match(r"const R pv = w\[(\d+)\];", line)
+        if m:
+            pv = w[int(m.group(1))]
+            inv = 1.0 / pv
+            continue
+        m = re.match(r"w\[(\d+)\] = inv;", line)
+        if m:
+            w[int(m.group(1))] = inv
+            continue
+        m = re.match(r"\{ const R l = w\[(\d+)\] \* inv; w\[(\d+)\] = l;", line)
+        if m:
+            l = w[int(m.group(1))] * inv
+            w[int(m.group(2))] = l
+            continue
+        m = re.match(r"w\[(\d+)\] -= l \* w\[(\d+)\];", line)
+        if m:
+            w[int(m.group(1))] -= l * w[int(m.group(2))]
+    body = src[src.index("CHAD_HD void solve("):src.index("constexpr int kFactorFlops")]
+    b = np.array(b, dtype=np.float64)
+    z = {}
+    for line in body.splitlines():
+        line = line.strip()
+        m = re.match(r"R z(\d+) = b\[(\d+)\];", line)
+        if m:
+            z[int(m.group(1))] = b[int(m.group(2))]
+            continue
+        m = re.match(r"z(\d+) -= w\[(\d+)\] \* z(\d+);", line)
+        if m:
+            z[int(m.group(1))] -= w[int(m.group(2))] * z[int(m.group(3))]
+            continue
+        m = re.match(r"z(\d+) \*= w\[(\d+)\];", line)
+        if m:
+            z[int(m.group(1))] *= w[int(m.group(2))]
+            continue
+        m = re.match(r"b\[(\d+)\] = z(\d+);", line)
+        if m:
+            b[int(m.group(1))] = z[int(m.group(2))]
+    return b
+
+
+@pytest.mark.parametrize("h2a", [False, True])
+def test_generated_lu_solves_like_a_dense_solver(h2a):
+    """The generated static-order LU (all 29 states, or the 28 without S_h2),
+    executed statement by statement on the host, solves (I - g J_d) x = b
+    as numpy's dense solver does, for random J_d on the library's own
+    pattern; without S_h2, W_d's S_h2 row is the identity's (b[S_h2] passes
+    through) and S_h2's row and column of J_d take no part."""
+    import re
+    sys.path.insert(0, os.path.join(ROOT, "paper_2311_08927_gb300", "csrc"))
+    import gen_sparse as G
+    NS = I.NS
+    h2 = I.STATE_NAMES.index("S_h2")
+    pat = G.jacobian_pattern()
+    src, info = G.generate(pat, h2a)
+    nnz = int(re.search(r"constexpr int kNNZ = (\d+);", src).group(1))
+    table = re.search(r"const int t\[NS \* NS\] = \{(.*?)\};", src, re.S).group(1)
+    slot = np.array([int(x) for x in table.replace("\n", " ").split(",")]).reshape(NS, NS)
+    rng = np.random.default_rng(7)
+    for trial in range(5):
+        J = np.where(pat, rng.standard_normal((NS, NS)), 0.0)
+        J[np.diag_indices(NS)] = -np.abs(J[np.diag_indices(NS)]) - 1.0
+        if h2a:
+            J[h2, :] = 0.0
+            J[:, h2] = 0.0
+        g = [0.05, 0.3, 1.0, 3.0, 10.0][trial]
+        vals = np.zeros(nnz)
+        for r in range(NS):
+            for c in range(NS):
+                s = slot[r, c]
+                if 0 <= s < nnz:
+                    vals[s] = J[r, c]
+        b = rng.standard_normal(NS)
+        x = _run_generated_lu(src, nnz, slot, vals, g, b)
+        ref = np.linalg.solve(np.eye(NS) - g * J, b)
+        assert np.max(np.abs(x - ref)) <= 1e-10 * max(1.0, np.max(np.abs(ref))), (h2a, g)
+        if h2a:
+            assert x[h2] == b[h2]
